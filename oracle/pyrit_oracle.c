@@ -1,0 +1,505 @@
+/*
+ * PYRIT CPU oracle -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow and deliberately literal CPU implementation of what the coding path computes:
+ * systematic MDS erasure encoding and decoding over GF(2^w) = F2[x]/(p(x)), p the all-one
+ * polynomial (AOP) of degree w, with log/antilog tables and a Cauchy generator matrix.
+ * It also holds a small reference for the ring R_{2,n} = F2[x]/(x^n+1) that the tests use to
+ * check the paper's algebraic claims.
+ *
+ * It shares no code, header, table or constant with the CUDA library. Only the tests, the
+ * package's smoke check and the benchmark's CPU-baseline leg may load it. The product path
+ * never calls it.
+ *
+ * Paper: J. Detchart, J. Lacan, "Improving the coding speed of erasure codes with polynomial
+ * ring transforms", arXiv:1709.00178. Citations below name its sections and equations.
+ *
+ * Conventions (all readings of the paper are listed in the design notes):
+ *  - A field or ring element is an integer whose bit i is the coefficient of x^i (Sec. 2.1).
+ *  - A block is w packets of P bytes, packet q at byte offset q*P. Bit b of byte t of packet q
+ *    is coefficient q of symbol (t, b): every (t, b) is an independent symbol lane.
+ *  - Generator G is (k+m) x k, row-major, systematic (top k x k = identity).
+ */
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORACLE_MAX_W 16
+#define ORACLE_MAX_K 64
+
+/* ------------------------------------------------------------------------------------------ */
+/* Polynomials over F2 (Sec. 2.1)                                                              */
+/* ------------------------------------------------------------------------------------------ */
+
+/* Degree of a nonzero polynomial; -1 for the zero polynomial. */
+static int poly_deg(uint64_t a) {
+  int d = -1;
+  while (a) {
+    d++;
+    a >>= 1;
+  }
+  return d;
+}
+
+/* Remainder of a(x) divided by p(x) over F2, by schoolbook long division. */
+uint64_t oracle_poly_mod(uint64_t a, uint64_t p) {
+  int dp = poly_deg(p);
+  if (dp < 0) return 0;
+  for (int d = 63; d >= dp; d--)
+    if ((a >> d) & 1) a ^= p << (d - dp);
+  return a;
+}
+
+/* Carry-less (F2[x]) product of two polynomials of degree < 32. */
+uint64_t oracle_poly_mul(uint64_t a, uint64_t b) {
+  uint64_t r = 0;
+  for (int i = 0; i < 32; i++)
+    if ((b >> i) & 1) r ^= a << i;
+  return r;
+}
+
+/* The all-one polynomial of degree w: 1 + x + ... + x^w (Sec. 2.3). */
+uint64_t oracle_aop(int w) { return (((uint64_t)1) << (w + 1)) - 1; }
+
+/* Irreducibility of the AOP of degree w, by trial division by every polynomial of degree
+ * 1..w/2 (the definition of irreducible, not the paper's number-theoretic criterion, so
+ * that the tests can check that criterion against it). Returns 1 if irreducible. */
+int oracle_aop_irreducible(int w) {
+  if (w < 1 || w > 30) return 0;
+  uint64_t p = oracle_aop(w);
+  for (int d = 1; d <= w / 2; d++)
+    for (uint64_t f = (uint64_t)1 << d; f < ((uint64_t)1 << (d + 1)); f++)
+      if (oracle_poly_mod(p, f) == 0) return 0;
+  return 1;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* The field GF(2^w) = F2[x]/(AOP) (Sec. 2.1, Sec. 2.3)                                        */
+/* ------------------------------------------------------------------------------------------ */
+
+/* Field product by the definition: carry-less product, then remainder mod the AOP. */
+uint32_t oracle_gf_mul_slow(int w, uint32_t a, uint32_t b) {
+  return (uint32_t)oracle_poly_mod(oracle_poly_mul(a, b), oracle_aop(w));
+}
+
+/* Multiplicative order of a nonzero element (0 if its powers reach 0 or never return to 1,
+ * which only happens when the modulus is reducible). */
+uint32_t oracle_gf_order(int w, uint32_t g) {
+  uint32_t q = (1u << w);
+  uint32_t v = g;
+  for (uint32_t e = 1; e <= q; e++) {
+    if (v == 1) return e;
+    if (v == 0) return 0;
+    v = oracle_gf_mul_slow(w, v, g);
+  }
+  return 0;
+}
+
+typedef struct {
+  int w;
+  uint32_t q1;    /* 2^w - 1, the order of the multiplicative group */
+  uint32_t g;     /* the primitive element used for the tables */
+  uint32_t* log;  /* log[a] for a != 0 */
+  uint32_t* alog; /* alog[e] = g^e, e in [0, 2^w - 1) */
+} gf_t;
+
+/* The primitive element: the smallest integer >= 2 whose order is 2^w - 1. Under an AOP the
+ * element x (= 2) has order w+1 (x^{w+1} = 1), so it is not primitive unless w+1 = 2^w - 1;
+ * the paper does not name a generator, hence the search. Returns 0 if none exists. */
+uint32_t oracle_gf_primitive(int w) {
+  if (w < 2 || w > ORACLE_MAX_W || !oracle_aop_irreducible(w)) return 0;
+  uint32_t q1 = (1u << w) - 1;
+  for (uint32_t g = 2; g <= q1; g++)
+    if (oracle_gf_order(w, g) == q1) return g;
+  return 0;
+}
+
+static int gf_init(gf_t* f, int w) {
+  f->w = w;
+  f->q1 = (1u << w) - 1;
+  f->g = oracle_gf_primitive(w);
+  f->log = NULL;
+  f->alog = NULL;
+  if (!f->g) return -1;
+  f->log = (uint32_t*)calloc((size_t)1 << w, sizeof(uint32_t));
+  f->alog = (uint32_t*)calloc((size_t)1 << w, sizeof(uint32_t));
+  if (!f->log || !f->alog) return -1;
+  uint32_t v = 1;
+  for (uint32_t e = 0; e < f->q1; e++) {
+    f->alog[e] = v;
+    f->log[v] = e;
+    v = oracle_gf_mul_slow(w, v, f->g);
+  }
+  return 0;
+}
+
+static void gf_free(gf_t* f) {
+  free(f->log);
+  free(f->alog);
+}
+
+static inline uint32_t gf_mul(const gf_t* f, uint32_t a, uint32_t b) {
+  if (!a || !b) return 0;
+  return f->alog[(f->log[a] + f->log[b]) % f->q1];
+}
+
+static inline uint32_t gf_inv(const gf_t* f, uint32_t a) {
+  return f->alog[(f->q1 - f->log[a]) % f->q1];
+}
+
+/* Exported table access so that the tests can pin the tables against the definition. */
+int oracle_gf_tables(int w, uint32_t* log_out, uint32_t* alog_out, uint32_t* g_out) {
+  gf_t f;
+  if (gf_init(&f, w)) {
+    gf_free(&f);
+    return -1;
+  }
+  memcpy(log_out, f.log, sizeof(uint32_t) << w);
+  memcpy(alog_out, f.alog, sizeof(uint32_t) << w);
+  *g_out = f.g;
+  gf_free(&f);
+  return 0;
+}
+
+/* Table-based product and inverse, exported for the tests (0 has no inverse: returns 0). */
+uint32_t oracle_gf_mul(int w, uint32_t a, uint32_t b) {
+  gf_t f;
+  if (gf_init(&f, w)) {
+    gf_free(&f);
+    return 0;
+  }
+  uint32_t r = gf_mul(&f, a, b);
+  gf_free(&f);
+  return r;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Generator and matrix inverse (Sec. 3: "generalized Cauchy matrices")                        */
+/* ------------------------------------------------------------------------------------------ */
+
+/* Systematic generator G = [I_k ; C], C[i][j] = 1 / (x_i + y_j) with x_i = k + i and y_j = j.
+ * The paper names generalized Cauchy matrices without their parameters; this is the plain
+ * Cauchy matrix on those points. It needs k + m <= 2^w so that all points are distinct.
+ * Returns 0, or -1 for an unsupported field, -2 for k + m > 2^w. */
+int oracle_cauchy(int w, int k, int m, uint32_t* G) {
+  if (k < 1 || m < 0 || k > ORACLE_MAX_K) return -2;
+  if ((uint64_t)k + (uint64_t)m > ((uint64_t)1 << w)) return -2;
+  gf_t f;
+  if (gf_init(&f, w)) {
+    gf_free(&f);
+    return -1;
+  }
+  for (int r = 0; r < k; r++)
+    for (int c = 0; c < k; c++) G[r * k + c] = (r == c);
+  for (int i = 0; i < m; i++)
+    for (int j = 0; j < k; j++) G[(k + i) * k + j] = gf_inv(&f, (uint32_t)(k + i) ^ (uint32_t)j);
+  gf_free(&f);
+  return 0;
+}
+
+/* Gauss-Jordan inverse of a k x k matrix over GF(2^w). The pivot of column c is the first row
+ * at or below row c with a nonzero entry in column c. Returns 0, or -1 if singular. */
+static int gf_invert(const gf_t* f, int k, const uint32_t* A, uint32_t* Inv) {
+  uint32_t* M = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)k * (size_t)(2 * k));
+  if (!M) return -1;
+  for (int r = 0; r < k; r++)
+    for (int c = 0; c < 2 * k; c++) M[r * 2 * k + c] = (c < k) ? A[r * k + c] : (uint32_t)(c - k == r);
+  for (int c = 0; c < k; c++) {
+    int piv = -1;
+    for (int r = c; r < k; r++)
+      if (M[r * 2 * k + c]) {
+        piv = r;
+        break;
+      }
+    if (piv < 0) {
+      free(M);
+      return -1;
+    }
+    if (piv != c)
+      for (int x = 0; x < 2 * k; x++) {
+        uint32_t t = M[c * 2 * k + x];
+        M[c * 2 * k + x] = M[piv * 2 * k + x];
+        M[piv * 2 * k + x] = t;
+      }
+    uint32_t s = gf_inv(f, M[c * 2 * k + c]);
+    for (int x = 0; x < 2 * k; x++) M[c * 2 * k + x] = gf_mul(f, M[c * 2 * k + x], s);
+    for (int r = 0; r < k; r++) {
+      if (r == c || !M[r * 2 * k + c]) continue;
+      uint32_t e = M[r * 2 * k + c];
+      for (int x = 0; x < 2 * k; x++) M[r * 2 * k + x] ^= gf_mul(f, e, M[c * 2 * k + x]);
+    }
+  }
+  for (int r = 0; r < k; r++)
+    for (int c = 0; c < k; c++) Inv[r * k + c] = M[r * 2 * k + k + c];
+  free(M);
+  return 0;
+}
+
+int oracle_gf_invert(int w, int k, const uint32_t* A, uint32_t* Inv) {
+  gf_t f;
+  if (gf_init(&f, w)) {
+    gf_free(&f);
+    return -2;
+  }
+  int rc = gf_invert(&f, k, A, Inv);
+  gf_free(&f);
+  return rc;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Encode and decode on bit-sliced blocks (Sec. 3, Sec. 4)                                     */
+/* ------------------------------------------------------------------------------------------ */
+
+/* Symbol (t, b) of a block: coefficient q is bit b of byte t of packet q. */
+static inline uint32_t gather_symbol(const uint8_t* blk, int w, size_t P, size_t t, int b) {
+  uint32_t s = 0;
+  for (int q = 0; q < w; q++) s |= (uint32_t)((blk[(size_t)q * P + t] >> b) & 1) << q;
+  return s;
+}
+
+static inline void scatter_symbol(uint8_t* blk, int w, size_t P, size_t t, int b, uint32_t s) {
+  for (int q = 0; q < w; q++) {
+    uint8_t* byte = &blk[(size_t)q * P + t];
+    *byte = (uint8_t)((*byte & ~(1u << b)) | (((s >> q) & 1) << b));
+  }
+}
+
+typedef struct {
+  const gf_t* f;
+  int k, m;
+  const uint32_t* G;
+  const uint8_t* data;
+  uint8_t* parity;
+  size_t P, t0, t1;
+} enc_job_t;
+
+/* parity_i = sum_j G[k+i][j] * d_j for every symbol lane in byte range [t0, t1). */
+static void* enc_run(void* arg) {
+  enc_job_t* J = (enc_job_t*)arg;
+  int w = J->f->w;
+  size_t blk = (size_t)w * J->P;
+  uint32_t d[ORACLE_MAX_K];
+  for (size_t t = J->t0; t < J->t1; t++)
+    for (int b = 0; b < 8; b++) {
+      for (int j = 0; j < J->k; j++) d[j] = gather_symbol(J->data + (size_t)j * blk, w, J->P, t, b);
+      for (int i = 0; i < J->m; i++) {
+        uint32_t acc = 0;
+        for (int j = 0; j < J->k; j++) acc ^= gf_mul(J->f, J->G[(J->k + i) * J->k + j], d[j]);
+        scatter_symbol(J->parity + (size_t)i * blk, w, J->P, t, b, acc);
+      }
+    }
+  return NULL;
+}
+
+/* Splits the byte range over threads: every thread codes a different part of every symbol,
+ * the decomposition of Sec. 4.2. */
+static void run_threads(void* (*fn)(void*), void* jobs, size_t job_size, int nthreads) {
+  pthread_t th[256];
+  if (nthreads > 256) nthreads = 256;
+  for (int i = 1; i < nthreads; i++) pthread_create(&th[i], NULL, fn, (char*)jobs + i * job_size);
+  fn(jobs);
+  for (int i = 1; i < nthreads; i++) pthread_join(th[i], NULL);
+}
+
+/* Encodes one stripe. data: k blocks of w*P bytes, contiguous; parity: m blocks, written.
+ * Returns 0, -1 for an unsupported field, -3 for bad sizes. */
+int oracle_encode(int w, int k, int m, const uint32_t* G, const uint8_t* data, uint8_t* parity,
+                  size_t P, int nthreads) {
+  if (k < 1 || k > ORACLE_MAX_K || m < 0 || P == 0) return -3;
+  if (nthreads < 1) nthreads = 1;
+  if ((size_t)nthreads > P) nthreads = (int)P;
+  gf_t f;
+  if (gf_init(&f, w)) {
+    gf_free(&f);
+    return -1;
+  }
+  enc_job_t jobs[256];
+  if (nthreads > 256) nthreads = 256;
+  for (int i = 0; i < nthreads; i++) {
+    jobs[i] = (enc_job_t){&f, k, m, G, data, parity, P, P * (size_t)i / (size_t)nthreads,
+                          P * (size_t)(i + 1) / (size_t)nthreads};
+  }
+  run_threads(enc_run, jobs, sizeof(enc_job_t), nthreads);
+  gf_free(&f);
+  return 0;
+}
+
+typedef struct {
+  const gf_t* f;
+  int k, m;
+  const uint32_t* G;
+  const uint32_t* Inv;  /* k x k inverse of the survivors' rows */
+  const int* surv;      /* the k survivor indices */
+  uint64_t erased;
+  uint8_t* blocks;
+  size_t P, t0, t1;
+} dec_job_t;
+
+/* Recovers the data symbols d = Inv * (survivor symbols), writes the erased data blocks,
+ * then re-encodes every erased parity block from the full data vector. */
+static void* dec_run(void* arg) {
+  dec_job_t* J = (dec_job_t*)arg;
+  int w = J->f->w, k = J->k, m = J->m;
+  size_t blk = (size_t)w * J->P;
+  uint32_t y[ORACLE_MAX_K], d[ORACLE_MAX_K];
+  for (size_t t = J->t0; t < J->t1; t++)
+    for (int b = 0; b < 8; b++) {
+      for (int s = 0; s < k; s++) y[s] = gather_symbol(J->blocks + (size_t)J->surv[s] * blk, w, J->P, t, b);
+      for (int j = 0; j < k; j++) {
+        uint32_t acc = 0;
+        for (int s = 0; s < k; s++) acc ^= gf_mul(J->f, J->Inv[j * k + s], y[s]);
+        d[j] = acc;
+      }
+      for (int e = 0; e < k + m; e++) {
+        if (!((J->erased >> e) & 1)) continue;
+        uint32_t val;
+        if (e < k) {
+          val = d[e];
+        } else {
+          val = 0;
+          for (int j = 0; j < k; j++) val ^= gf_mul(J->f, J->G[e * k + j], d[j]);
+        }
+        scatter_symbol(J->blocks + (size_t)e * blk, w, J->P, t, b, val);
+      }
+    }
+  return NULL;
+}
+
+/* Decodes one stripe in place. blocks: k+m blocks of w*P bytes, contiguous (data then parity);
+ * bit e of `erased` marks block e lost; every erased block is rebuilt. The survivors are the
+ * first k non-erased blocks in index order (the paper does not say which to use; the result
+ * is the same for any choice because the code is MDS).
+ * Returns 0, -1 unsupported field, -3 bad sizes, -4 more than m erasures, -5 singular. */
+int oracle_decode(int w, int k, int m, const uint32_t* G, uint8_t* blocks, uint64_t erased,
+                  size_t P, int nthreads) {
+  if (k < 1 || k > ORACLE_MAX_K || m < 0 || k + m > 64 || P == 0) return -3;
+  int ne = 0;
+  for (int e = 0; e < k + m; e++) ne += (int)((erased >> e) & 1);
+  if ((erased >> (k + m)) != 0 && k + m < 64) return -3;
+  if (ne > m) return -4;
+  if (ne == 0) return 0;
+  gf_t f;
+  if (gf_init(&f, w)) {
+    gf_free(&f);
+    return -1;
+  }
+  int surv[ORACLE_MAX_K];
+  int ns = 0;
+  for (int e = 0; e < k + m && ns < k; e++)
+    if (!((erased >> e) & 1)) surv[ns++] = e;
+  uint32_t* Gs = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)k * (size_t)k);
+  uint32_t* Inv = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)k * (size_t)k);
+  for (int s = 0; s < k; s++)
+    for (int c = 0; c < k; c++) Gs[s * k + c] = G[surv[s] * k + c];
+  int rc = gf_invert(&f, k, Gs, Inv);
+  if (rc == 0) {
+    if (nthreads < 1) nthreads = 1;
+    if ((size_t)nthreads > P) nthreads = (int)P;
+    if (nthreads > 256) nthreads = 256;
+    dec_job_t jobs[256];
+    for (int i = 0; i < nthreads; i++)
+      jobs[i] = (dec_job_t){&f, k, m, G, Inv, surv, erased, blocks, P,
+                            P * (size_t)i / (size_t)nthreads, P * (size_t)(i + 1) / (size_t)nthreads};
+    run_threads(dec_run, jobs, sizeof(dec_job_t), nthreads);
+  } else {
+    rc = -5;
+  }
+  free(Gs);
+  free(Inv);
+  gf_free(&f);
+  return rc;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Ring reference R_{2,n} = F2[x]/(x^n + 1) (Sec. 2.1, Props. 1-2, Sec. 2.3)                    */
+/* ------------------------------------------------------------------------------------------ */
+
+/* Product in R_{2,n}: cyclic convolution of the coefficient vectors (x^n = 1). */
+uint32_t oracle_ring_mul(int n, uint32_t a, uint32_t b) {
+  uint32_t r = 0;
+  for (int i = 0; i < n; i++)
+    if ((a >> i) & 1)
+      for (int j = 0; j < n; j++)
+        if ((b >> j) & 1) r ^= 1u << ((i + j) % n);
+  return r;
+}
+
+/* Every idempotent e (e*e = e) of R_{2,n}, by brute force over all 2^n elements.
+ * Returns how many were written to out (capacity cap). */
+int oracle_ring_idempotents(int n, uint32_t* out, int cap) {
+  int c = 0;
+  for (uint32_t e = 0; e < (1u << n); e++)
+    if (oracle_ring_mul(n, e, e) == e) {
+      if (c < cap) out[c] = e;
+      c++;
+    }
+  return c;
+}
+
+/* All ring elements r with r mod p = u (the set from which the sparse transform picks), by
+ * brute force over all 2^n elements. Returns the count (written up to cap). */
+int oracle_ring_representatives(int w, int n, uint32_t u, uint32_t* out, int cap) {
+  uint64_t p = oracle_aop(w);
+  int c = 0;
+  for (uint32_t r = 0; r < (1u << n); r++)
+    if (oracle_poly_mod(r, p) == u) {
+      if (c < cap) out[c] = r;
+      c++;
+    }
+  return c;
+}
+
+static int popcount32(uint32_t v) {
+  int c = 0;
+  while (v) {
+    c += (int)(v & 1);
+    v >>= 1;
+  }
+  return c;
+}
+
+/* Sparse transform phi_S (Sec. 2.2): the representative of u with the fewest ones; ties go to
+ * the smallest integer (ties cannot occur for an AOP with n odd). */
+uint32_t oracle_sparse_rep(int w, int n, uint32_t u) {
+  uint64_t p = oracle_aop(w);
+  uint32_t best = 0;
+  int bw = 99;
+  for (uint32_t r = 0; r < (1u << n); r++)
+    if (oracle_poly_mod(r, p) == u) {
+      int wt = popcount32(r);
+      if (wt < bw) {
+        bw = wt;
+        best = r;
+      }
+    }
+  return best;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Element-wise batch forms of the above, so that exhaustive tests do not pay one foreign call */
+/* per pair. Each is the same definition applied to cnt pairs.                                 */
+/* ------------------------------------------------------------------------------------------ */
+
+int oracle_gf_mul_vec(int w, const uint32_t* a, const uint32_t* b, uint32_t* out, size_t cnt) {
+  gf_t f;
+  if (gf_init(&f, w)) {
+    gf_free(&f);
+    return -1;
+  }
+  for (size_t i = 0; i < cnt; i++) out[i] = gf_mul(&f, a[i], b[i]);
+  gf_free(&f);
+  return 0;
+}
+
+void oracle_gf_mul_slow_vec(int w, const uint32_t* a, const uint32_t* b, uint32_t* out, size_t cnt) {
+  for (size_t i = 0; i < cnt; i++) out[i] = oracle_gf_mul_slow(w, a[i], b[i]);
+}
+
+void oracle_ring_mul_vec(int n, const uint32_t* a, const uint32_t* b, uint32_t* out, size_t cnt) {
+  for (size_t i = 0; i < cnt; i++) out[i] = oracle_ring_mul(n, a[i], b[i]);
+}
+
+void oracle_poly_mod_vec(uint64_t p, const uint32_t* a, uint32_t* out, size_t cnt) {
+  for (size_t i = 0; i < cnt; i++) out[i] = (uint32_t)oracle_poly_mod(a[i], p);
+}
