@@ -1,0 +1,166 @@
+/*
+ * pyrit.h -- C ABI of the GB300 PYRIT erasure codec.
+ *
+ * PYRIT (polynomial ring transform; Detchart & Lacan, arXiv:1709.00178) computes systematic MDS
+ * erasure codes over the field GF(2^w) = F2[x]/(p(x)), p the all-one polynomial (AOP) of degree w,
+ * by doing every multiplication in the ring R_{2,n} = F2[x]/(x^n + 1), n = w + 1:
+ *   - each generator (or decoding-matrix) coefficient u is replaced by its sparsest ring
+ *     representative phi_S(u) (Sec. 2.2, "the sparse transform");
+ *   - each source block is embedded in the ring by padding it with a zero packet (phi_E,
+ *     Sec. 2.3.2), so multiplying it by x^s is a cyclic rotation of its packets and multiplying
+ *     by phi_S(u) is an XOR of one rotation per set bit of phi_S(u) (Sec. 3);
+ *   - the ring result is mapped back to the field by the remainder mod p, which for an AOP is
+ *     "XOR the top packet into every other packet" (phi_E^{-1}, Sec. 2.3.2).
+ *
+ * Data layout. A block is w packets of P bytes, contiguous, packet q at byte offset q*P. Bit b of
+ * byte t of packet q is coefficient q (of x^q) of the field symbol in lane (t, b); every lane is
+ * an independent codeword. A stripe is k data blocks and m parity blocks; block index e runs
+ * over data (0..k-1) then parity (k..k+m-1).
+ *
+ * Ownership. The caller owns every data buffer (device memory, e.g. a torch tensor's data_ptr());
+ * the library owns plans, batches, servers and the device memory they hold.
+ *
+ * Asynchrony. Coding calls enqueue work on the caller's stream and return; they never
+ * synchronise except where stated. Buffers must stay valid until that work completes.
+ *
+ * Errors. Every int-returning call returns PYRIT_OK (0) or a negative PYRIT_E_* code and never
+ * launches work when it fails validation. No C++ exception crosses this boundary.
+ * pyrit_strerror() names a code.
+ *
+ * Alignment. The staged (TMA) kernel is used when P is a multiple of 16 and every block pointer
+ * is 16-byte aligned; any other P or alignment is accepted and coded by a plain-load kernel.
+ */
+#ifndef PYRIT_H
+#define PYRIT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Exported symbols (the library is built with hidden visibility by default). */
+#if defined(__GNUC__)
+#define PYRIT_API __attribute__((visibility("default")))
+#else
+#define PYRIT_API
+#endif
+
+/* Same type as cudaStream_t; NULL is the legacy default stream. */
+typedef struct CUstream_st* pyrit_stream_t;
+
+/* ---- status codes ------------------------------------------------------------------------ */
+#define PYRIT_OK 0
+#define PYRIT_E_INVALID_ARG -1        /* null pointer, P = 0, k/m out of range, bad mask bits  */
+#define PYRIT_E_UNSUPPORTED_FIELD -2  /* n != w+1, or the AOP of degree w is reducible         */
+#define PYRIT_E_TOO_LONG -3           /* k + m > 2^w: the default Cauchy code needs distinct points */
+#define PYRIT_E_NOT_MDS -4            /* generator not systematic, entry >= 2^w, or a singular
+                                         k x k submatrix was found                              */
+#define PYRIT_E_TOO_MANY_ERASURES -5  /* more than m blocks erased                              */
+#define PYRIT_E_CUDA -6               /* a CUDA runtime call failed                             */
+#define PYRIT_E_OOM -7                /* host or device allocation failed                       */
+#define PYRIT_E_BUDGET -8             /* server: request larger than the admission budget      */
+#define PYRIT_E_TIMEOUT -9            /* a bounded device or host wait gave up                  */
+#define PYRIT_E_BUSY -10              /* server: request queue full, retry later               */
+
+/* Limits of this build. */
+#define PYRIT_MAX_K 32 /* data blocks per stripe                   */
+#define PYRIT_MAX_M 8  /* parity blocks per stripe                 */
+
+/* Operations. */
+#define PYRIT_OP_ENCODE 0
+#define PYRIT_OP_DECODE 1
+
+/* Name of a status code (static string). */
+PYRIT_API const char* pyrit_strerror(int status);
+
+/* ---- plan (host only; no GPU needed) ------------------------------------------------------ */
+
+typedef struct pyrit_plan_s* pyrit_plan_t;
+
+/* Creates a coding plan for a systematic (k+m, k) code over GF(2^w), n = w+1.
+ *   w, n : field degree and ring size. n must be w + 1 (AOP rings only) and the AOP of degree w
+ *          irreducible (w+1 prime with 2 a primitive root mod w+1, Sec. 2.3); the kernels are
+ *          built for w in {2, 4, 10, 12} (n in {3, 5, 11, 13}).
+ *   k, m : 1 <= k <= PYRIT_MAX_K, 0 <= m <= PYRIT_MAX_M.
+ *   G    : NULL for the default generator [I_k ; C], C[i][j] = 1/(x_i + y_j) with x_i = k+i,
+ *          y_j = j (a Cauchy matrix, Sec. 3 "generalized Cauchy matrices"; requires
+ *          k + m <= 2^w), or a host array of (k+m)*k uint32 entries, row-major, whose top k rows
+ *          must be the identity. A user G is checked for the MDS property (every k x k row
+ *          subset invertible, Sec. 2.2) when there are at most 20000 subsets; otherwise a
+ *          singular subset is reported by pyrit_decode as PYRIT_E_NOT_MDS.
+ * Computes phi_S of every parity coefficient (Sec. 2.2). Host memory only: no device call.
+ * On success *out owns the plan; release it with pyrit_plan_destroy. */
+PYRIT_API int pyrit_plan_create(int w, int n, int k, int m, const uint32_t* G, pyrit_plan_t* out);
+PYRIT_API void pyrit_plan_destroy(pyrit_plan_t plan);
+
+/* Plan parameters (any pointer may be NULL). */
+PYRIT_API int pyrit_plan_info(pyrit_plan_t plan, int* w, int* n, int* k, int* m);
+
+/* Copies the (k+m) x k generator, row-major, into G_out. */
+PYRIT_API int pyrit_plan_generator(pyrit_plan_t plan, uint32_t* G_out);
+
+/* Copies the m x k ring masks of the parity rows, row-major: masks_out[i*k + j] = phi_S(G[k+i][j])
+ * as an n-bit mask (bit s = coefficient of x^s). */
+PYRIT_API int pyrit_plan_encode_masks(pyrit_plan_t plan, uint16_t* masks_out);
+
+/* The decoding matrix for an erasure pattern (bit e of `erasures` = block e lost), as ring masks:
+ * the survivors are the first k non-erased blocks in index order; every erased block is rebuilt:
+ * an erased data block e from row e of Inv = (G restricted to the survivors' rows)^{-1}, an erased
+ * parity block from G[e] * Inv (Sec. 4.3: the decoding matrix depends on the loss pattern).
+ * Outputs (host arrays): survivors_out[k]; erased_out[ne] (ascending); masks_out[ne*k] with
+ * masks_out[r*k + s] = phi_S(D[r][s]); *ne_out = number of erased blocks (may be 0).
+ * Computed once per (plan, pattern) and cached in the plan. */
+PYRIT_API int pyrit_plan_decode_masks(pyrit_plan_t plan, uint64_t erasures, int* survivors_out,
+                            int* erased_out, uint16_t* masks_out, int* ne_out);
+
+/* phi_S of one field element u < 2^w: the lighter of its two ring representatives u and
+ * u + p(x) (Sec. 2.2; for an AOP and odd n the weights differ, so there is no tie).
+ * Returns the n-bit mask, or 0xFFFFFFFF for a bad argument. */
+PYRIT_API uint32_t pyrit_sparse_transform(int w, int n, uint32_t u);
+
+/* Field product in GF(2^w) under the AOP, computed by the planner (host). */
+PYRIT_API uint32_t pyrit_gf_mul(int w, uint32_t a, uint32_t b);
+
+/* ---- single-stripe coding (device; asynchronous on `stream`) ------------------------------ */
+
+/* Encodes one stripe: parity[i] = sum_j G[k+i][j] * data[j] in every symbol lane.
+ *   data   : host array of k device pointers, each to a block of w*P bytes (read).
+ *   parity : host array of m device pointers, each to a block of w*P bytes (written).
+ *   P      : packet bytes, >= 1.
+ * The fused ring kernel stages the sources through shared memory with bulk-async copies,
+ * embeds them (phi_E), accumulates XORs of packet rotations for every set bit of phi_S(G[k+i][j])
+ * and reduces mod p (phi_E^{-1}) before storing. No device memory is allocated. */
+PYRIT_API int pyrit_encode(pyrit_plan_t plan, const void* const* data, void* const* parity, size_t P,
+                 pyrit_stream_t stream);
+
+/* Decodes one stripe in place: every block whose bit is set in `erasures` is rebuilt.
+ *   blocks    : host array of k+m device pointers (data then parity); erased blocks are written,
+ *               the others read.
+ *   erasures  : bit e set = block e lost; popcount <= m, else PYRIT_E_TOO_MANY_ERASURES.
+ * The decoding matrix comes from the plan's cache (a miss computes it on the host, Sec. 4.3).
+ * Erasures == 0 is a no-op. */
+PYRIT_API int pyrit_decode(pyrit_plan_t plan, void* const* blocks, uint64_t erasures, size_t P,
+                 pyrit_stream_t stream);
+
+/* ---- device status ----------------------------------------------------------------------- */
+
+/* Reads and clears the device-side error word of the current device (synchronises the device).
+ * Kernels set it when a bounded wait gives up (PYRIT_E_TIMEOUT) instead of spinning forever.
+ * *code_out receives 0 or a PYRIT_E_* code; *where_out (may be NULL) a kernel-specific site id. */
+PYRIT_API int pyrit_device_status(int* code_out, int* where_out);
+
+/* ---- synthetic inputs (device) ------------------------------------------------------------ */
+
+/* Fills dst[0, nbytes) with bytes [offset, offset + nbytes) of the counter-mode SplitMix64 stream
+ * `seed` (word i = mix(seed + (i+1) * 0x9E3779B97F4A7C15), little-endian bytes; Steele et al.,
+ * OOPSLA 2014). Input generator for tests and benchmarks; no coding arithmetic. */
+PYRIT_API int pyrit_synth_fill(void* dst, size_t nbytes, uint64_t seed, uint64_t offset,
+                     pyrit_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PYRIT_H */

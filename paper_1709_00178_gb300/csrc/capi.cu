@@ -1,0 +1,65 @@
+// C ABI entry points of the single-stripe coding path and of the device status word.
+#include <cuda_runtime.h>
+
+#include "pyrit_internal.h"
+
+using namespace pyrit;
+
+namespace {
+
+// Codes one job: the staged kernel when P and every pointer allow 16-byte bulk copies, else the
+// plain-load kernel. The job travels in the kernel's parameters: nothing is allocated.
+int run_job(int n, const JobDesc& job, cudaStream_t stream) {
+  if (job.nout == 0) return PYRIT_OK;
+  if (job_is_staged(job)) {
+    const TileShape sh = default_shape(n, job.nout, job.P);
+    const uint32_t tpj = (uint32_t)((job.P + sh.tw - 1) / sh.tw);
+    return launch_staged(n, sh, &job, nullptr, nullptr, tpj, tpj, 0, stream);
+  }
+  return launch_plain(n, job, stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+int pyrit_encode(pyrit_plan_t plan, const void* const* data, void* const* parity, size_t P, pyrit_stream_t stream) {
+  if (!plan || !data || (plan->m > 0 && !parity) || P == 0 || P > (1ull << 40)) return PYRIT_E_INVALID_ARG;
+  for (int j = 0; j < plan->k; ++j)
+    if (!data[j]) return PYRIT_E_INVALID_ARG;
+  for (int i = 0; i < plan->m; ++i)
+    if (!parity[i]) return PYRIT_E_INVALID_ARG;
+  if (plan->m == 0) return PYRIT_OK;
+  JobDesc job;
+  make_encode_job(plan, data, parity, P, &job);
+  return run_job(plan->n, job, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int pyrit_decode(pyrit_plan_t plan, void* const* blocks, uint64_t erasures, size_t P, pyrit_stream_t stream) {
+  if (!plan || !blocks || P == 0 || P > (1ull << 40)) return PYRIT_E_INVALID_ARG;
+  const int nb = plan->k + plan->m;
+  for (int b = 0; b < nb; ++b)
+    if (!blocks[b]) return PYRIT_E_INVALID_ARG;
+  DecodeEntry e;
+  const int rc = plan_decode_entry(plan, erasures, &e);
+  if (rc != PYRIT_OK) return rc;
+  if (e.ne == 0) return PYRIT_OK;
+  JobDesc job;
+  make_decode_job(plan, e, blocks, P, &job);
+  return run_job(plan->n, job, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int pyrit_device_status(int* code_out, int* where_out) {
+  if (!code_out) return PYRIT_E_INVALID_ARG;
+  int* w = device_error_word();
+  if (!w) return PYRIT_E_CUDA;
+  int h[2] = {0, 0};
+  if (cudaDeviceSynchronize() != cudaSuccess) return PYRIT_E_CUDA;
+  if (cudaMemcpy(h, w, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return PYRIT_E_CUDA;
+  if (cudaMemset(w, 0, sizeof(h)) != cudaSuccess) return PYRIT_E_CUDA;
+  *code_out = h[0];
+  if (where_out) *where_out = h[1];
+  return PYRIT_OK;
+}
+
+}  // extern "C"

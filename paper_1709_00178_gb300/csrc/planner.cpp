@@ -1,0 +1,306 @@
+// Host planner: field checks, the sparse transform phi_S, generator validation and the decoding
+// matrices (paper Secs. 2.2, 2.3, 3 and 4.3). Host memory only; no CUDA call.
+#include <algorithm>
+#include <cstring>
+#include <new>
+
+#include "pyrit_internal.h"
+
+namespace pyrit {
+
+// Sec. 2.3: the AOP of degree w is irreducible iff w+1 is prime and 2 generates the
+// multiplicative group of F_{w+1} (read from the text's "w generates F*_{w+1}", which its own
+// GF(16) example contradicts literally). The kernels are instantiated for n in {3, 5, 11, 13}.
+bool aop_field_supported(int w, int n) {
+  if (w < 2 || w > 15 || n != w + 1) return false;
+  const int p = w + 1;
+  for (int d = 2; d * d <= p; ++d)
+    if (p % d == 0) return false;
+  int order = 1;
+  for (int v = 2 % p; v != 1; v = (v * 2) % p) ++order;
+  if (order != w) return false;
+  return n == 3 || n == 5 || n == 11 || n == 13;
+}
+
+// Product in GF(2^w) = F2[x]/(1 + x + ... + x^w): shift-and-add, reducing each time the shifted
+// multiplicand reaches degree w with x^w = 1 + x + ... + x^{w-1}.
+uint32_t gf_mul(int w, uint32_t a, uint32_t b) {
+  const uint32_t low = (1u << w) - 1;
+  uint32_t r = 0;
+  for (int i = 0; i < w; ++i) {
+    if ((b >> i) & 1u) r ^= a;
+    a <<= 1;
+    if ((a >> w) & 1u) a = (a & low) ^ low;
+  }
+  return r;
+}
+
+// a^{-1} = a^{2^w - 2} (Fermat), by square-and-multiply. gf_inv(0) = 0.
+uint32_t gf_inv(int w, uint32_t a) {
+  uint32_t e = (1u << w) - 2, r = 1, s = a;
+  while (e) {
+    if (e & 1u) r = gf_mul(w, r, s);
+    s = gf_mul(w, s, s);
+    e >>= 1;
+  }
+  return a ? r : 0;
+}
+
+// phi_S (Sec. 2.2) for an AOP: the ring elements reducing to u mod p are u and u + p(x), where
+// p(x) is the all-ones polynomial of n = w+1 coefficients, i.e. the complement of u in n bits.
+// Their weights are t and n - t; n odd means the lighter one is unique.
+uint32_t sparse_rep(int w, int n, uint32_t u) {
+  const uint32_t all = (1u << n) - 1;
+  const uint32_t lo = u & ((1u << w) - 1), hi = lo ^ all;
+  return __builtin_popcount(lo) <= __builtin_popcount(hi) ? lo : hi;
+}
+
+// Inverse over GF(2^w) by elimination with row swaps (k <= 32). Returns false if singular.
+static bool invert(int w, int k, const uint32_t* A, uint32_t* out) {
+  uint32_t a[kMaxIn][kMaxIn], b[kMaxIn][kMaxIn];
+  for (int r = 0; r < k; ++r)
+    for (int c = 0; c < k; ++c) {
+      a[r][c] = A[r * k + c];
+      b[r][c] = (r == c);
+    }
+  for (int c = 0; c < k; ++c) {
+    int piv = c;
+    while (piv < k && a[piv][c] == 0) ++piv;
+    if (piv == k) return false;
+    if (piv != c)
+      for (int x = 0; x < k; ++x) {
+        std::swap(a[c][x], a[piv][x]);
+        std::swap(b[c][x], b[piv][x]);
+      }
+    const uint32_t s = gf_inv(w, a[c][c]);
+    for (int x = 0; x < k; ++x) {
+      a[c][x] = gf_mul(w, a[c][x], s);
+      b[c][x] = gf_mul(w, b[c][x], s);
+    }
+    for (int r = 0; r < k; ++r) {
+      if (r == c || a[r][c] == 0) continue;
+      const uint32_t f = a[r][c];
+      for (int x = 0; x < k; ++x) {
+        a[r][x] ^= gf_mul(w, f, a[c][x]);
+        b[r][x] ^= gf_mul(w, f, b[c][x]);
+      }
+    }
+  }
+  for (int r = 0; r < k; ++r)
+    for (int c = 0; c < k; ++c) out[r * k + c] = b[r][c];
+  return true;
+}
+
+// Every k x k row subset of G invertible (the MDS property, Sec. 2.2), by enumeration.
+static bool all_subsets_invertible(int w, int k, int m, const uint32_t* G) {
+  int idx[kMaxIn + kMaxOut];
+  for (int i = 0; i < k; ++i) idx[i] = i;
+  uint32_t sub[kMaxIn * kMaxIn], inv[kMaxIn * kMaxIn];
+  const int nrow = k + m;
+  while (true) {
+    for (int r = 0; r < k; ++r)
+      for (int c = 0; c < k; ++c) sub[r * k + c] = G[idx[r] * k + c];
+    if (!invert(w, k, sub, inv)) return false;
+    int i = k - 1;
+    while (i >= 0 && idx[i] == nrow - k + i) --i;
+    if (i < 0) return true;
+    ++idx[i];
+    for (int j = i + 1; j < k; ++j) idx[j] = idx[j - 1] + 1;
+  }
+}
+
+static double binom(int a, int b) {
+  double r = 1;
+  for (int i = 1; i <= b; ++i) r = r * (a - b + i) / i;
+  return r;
+}
+
+int plan_decode_entry(pyrit_plan_s* p, uint64_t erasures, DecodeEntry* out) {
+  const int k = p->k, m = p->m, w = p->w, n = p->n;
+  if (k + m < 64 && (erasures >> (k + m)) != 0) return PYRIT_E_INVALID_ARG;
+  if (__builtin_popcountll(erasures) > m) return PYRIT_E_TOO_MANY_ERASURES;
+  {
+    std::lock_guard<std::mutex> lk(p->mu);
+    auto it = p->dcache.find(erasures);
+    if (it != p->dcache.end()) {
+      *out = it->second;
+      return out->status;
+    }
+  }
+  DecodeEntry e;
+  int ns = 0;
+  for (int b = 0; b < k + m; ++b) {
+    if ((erasures >> b) & 1u)
+      e.erased[e.ne++] = b;
+    else if (ns < k)
+      e.surv[ns++] = b;
+  }
+  std::memset(e.mask, 0, sizeof(e.mask));
+  if (e.ne > 0) {
+    uint32_t Gs[kMaxIn * kMaxIn], Inv[kMaxIn * kMaxIn];
+    for (int s = 0; s < k; ++s)
+      for (int c = 0; c < k; ++c) Gs[s * k + c] = p->G[e.surv[s] * k + c];
+    if (!invert(w, k, Gs, Inv)) {
+      e.status = PYRIT_E_NOT_MDS;
+    } else {
+      for (int r = 0; r < e.ne; ++r) {
+        const int b = e.erased[r];
+        for (int s = 0; s < k; ++s) {
+          uint32_t v;
+          if (b < k) {
+            v = Inv[b * k + s];
+          } else {  // an erased parity block: G[b] times Inv
+            v = 0;
+            for (int j = 0; j < k; ++j) v ^= gf_mul(w, p->G[b * k + j], Inv[j * k + s]);
+          }
+          e.mask[r][s] = (uint16_t)sparse_rep(w, n, v);
+        }
+      }
+    }
+  }
+  {
+    std::lock_guard<std::mutex> lk(p->mu);
+    p->dcache.emplace(erasures, e);
+  }
+  *out = e;
+  return e.status;
+}
+
+void make_encode_job(const pyrit_plan_s* p, const void* const* data, void* const* parity, size_t P,
+                     JobDesc* job) {
+  std::memset(job, 0, sizeof(*job));
+  job->nin = p->k;
+  job->nout = p->m;
+  job->P = P;
+  for (int j = 0; j < p->k; ++j) job->in[j] = static_cast<const uint8_t*>(data[j]);
+  for (int i = 0; i < p->m; ++i) job->out[i] = static_cast<uint8_t*>(parity[i]);
+  for (int i = 0; i < p->m; ++i)
+    for (int j = 0; j < p->k; ++j) job->mask[j][i] = p->enc_mask[i * p->k + j];
+}
+
+void make_decode_job(const pyrit_plan_s* p, const DecodeEntry& e, void* const* blocks, size_t P,
+                     JobDesc* job) {
+  std::memset(job, 0, sizeof(*job));
+  job->nin = p->k;
+  job->nout = e.ne;
+  job->P = P;
+  for (int s = 0; s < p->k; ++s) job->in[s] = static_cast<const uint8_t*>(blocks[e.surv[s]]);
+  for (int r = 0; r < e.ne; ++r) job->out[r] = static_cast<uint8_t*>(blocks[e.erased[r]]);
+  for (int r = 0; r < e.ne; ++r)
+    for (int s = 0; s < p->k; ++s) job->mask[s][r] = e.mask[r][s];
+}
+
+}  // namespace pyrit
+
+using namespace pyrit;
+
+extern "C" {
+
+const char* pyrit_strerror(int s) {
+  switch (s) {
+    case PYRIT_OK: return "ok";
+    case PYRIT_E_INVALID_ARG: return "invalid argument";
+    case PYRIT_E_UNSUPPORTED_FIELD: return "unsupported field (n must be w+1 with an irreducible AOP)";
+    case PYRIT_E_TOO_LONG: return "code too long for the field (k+m > 2^w)";
+    case PYRIT_E_NOT_MDS: return "generator is not systematic MDS";
+    case PYRIT_E_TOO_MANY_ERASURES: return "more erasures than parity blocks";
+    case PYRIT_E_CUDA: return "CUDA error";
+    case PYRIT_E_OOM: return "out of memory";
+    case PYRIT_E_BUDGET: return "request exceeds the admission budget";
+    case PYRIT_E_TIMEOUT: return "bounded wait timed out";
+    case PYRIT_E_BUSY: return "queue full";
+    default: return "unknown status";
+  }
+}
+
+int pyrit_plan_create(int w, int n, int k, int m, const uint32_t* G, pyrit_plan_t* out) {
+  if (!out) return PYRIT_E_INVALID_ARG;
+  *out = nullptr;
+  if (k < 1 || k > kMaxIn || m < 0 || m > kMaxOut) return PYRIT_E_INVALID_ARG;
+  if (!aop_field_supported(w, n)) return PYRIT_E_UNSUPPORTED_FIELD;
+  if (!G && (uint64_t)k + (uint64_t)m > (1ull << w)) return PYRIT_E_TOO_LONG;
+  pyrit_plan_s* p = new (std::nothrow) pyrit_plan_s;
+  if (!p) return PYRIT_E_OOM;
+  p->w = w;
+  p->n = n;
+  p->k = k;
+  p->m = m;
+  p->G.assign((size_t)(k + m) * k, 0);
+  if (G) {
+    for (int r = 0; r < k + m; ++r)
+      for (int c = 0; c < k; ++c) {
+        const uint32_t v = G[r * k + c];
+        if (v >= (1u << w) || (r < k && v != (uint32_t)(r == c))) {
+          delete p;
+          return PYRIT_E_NOT_MDS;
+        }
+        p->G[r * k + c] = v;
+      }
+    if (binom(k + m, k) <= 20000.0 && !all_subsets_invertible(w, k, m, p->G.data())) {
+      delete p;
+      return PYRIT_E_NOT_MDS;
+    }
+  } else {
+    // Cauchy: C[i][j] = 1 / (x_i + y_j), x_i = k + i, y_j = j (all points distinct).
+    for (int r = 0; r < k; ++r) p->G[r * k + r] = 1;
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < k; ++j) p->G[(k + i) * k + j] = gf_inv(w, (uint32_t)(k + i) ^ (uint32_t)j);
+  }
+  p->enc_mask.resize((size_t)m * k);
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < k; ++j) p->enc_mask[i * k + j] = (uint16_t)sparse_rep(w, n, p->G[(k + i) * k + j]);
+  *out = p;
+  return PYRIT_OK;
+}
+
+void pyrit_plan_destroy(pyrit_plan_t p) { delete p; }
+
+int pyrit_plan_info(pyrit_plan_t p, int* w, int* n, int* k, int* m) {
+  if (!p) return PYRIT_E_INVALID_ARG;
+  if (w) *w = p->w;
+  if (n) *n = p->n;
+  if (k) *k = p->k;
+  if (m) *m = p->m;
+  return PYRIT_OK;
+}
+
+int pyrit_plan_generator(pyrit_plan_t p, uint32_t* G_out) {
+  if (!p || !G_out) return PYRIT_E_INVALID_ARG;
+  std::memcpy(G_out, p->G.data(), p->G.size() * sizeof(uint32_t));
+  return PYRIT_OK;
+}
+
+int pyrit_plan_encode_masks(pyrit_plan_t p, uint16_t* masks_out) {
+  if (!p || !masks_out) return PYRIT_E_INVALID_ARG;
+  std::memcpy(masks_out, p->enc_mask.data(), p->enc_mask.size() * sizeof(uint16_t));
+  return PYRIT_OK;
+}
+
+int pyrit_plan_decode_masks(pyrit_plan_t p, uint64_t erasures, int* survivors_out, int* erased_out,
+                            uint16_t* masks_out, int* ne_out) {
+  if (!p) return PYRIT_E_INVALID_ARG;
+  DecodeEntry e;
+  const int rc = plan_decode_entry(p, erasures, &e);
+  if (rc != PYRIT_OK) return rc;
+  if (ne_out) *ne_out = e.ne;
+  if (survivors_out)
+    for (int s = 0; s < p->k; ++s) survivors_out[s] = e.surv[s];
+  if (erased_out)
+    for (int r = 0; r < e.ne; ++r) erased_out[r] = e.erased[r];
+  if (masks_out)
+    for (int r = 0; r < e.ne; ++r)
+      for (int s = 0; s < p->k; ++s) masks_out[r * p->k + s] = e.mask[r][s];
+  return PYRIT_OK;
+}
+
+uint32_t pyrit_sparse_transform(int w, int n, uint32_t u) {
+  if (!aop_field_supported(w, n) || u >= (1u << w)) return 0xFFFFFFFFu;
+  return sparse_rep(w, n, u);
+}
+
+uint32_t pyrit_gf_mul(int w, uint32_t a, uint32_t b) {
+  if (w < 2 || w > 15) return 0;
+  return gf_mul(w, a & ((1u << w) - 1), b & ((1u << w) - 1));
+}
+
+}  // extern "C"

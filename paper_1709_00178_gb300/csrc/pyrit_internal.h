@@ -1,0 +1,106 @@
+// Internal declarations shared by the library's translation units (not part of the C ABI).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <mutex>
+#include <unordered_map>
+#include <vector>
+
+#include <cuda_runtime_api.h>
+
+#include "../../include/pyrit.h"
+
+namespace pyrit {
+
+constexpr int kMaxIn = PYRIT_MAX_K;   // sources of one coding job (data blocks or survivors)
+constexpr int kMaxOut = PYRIT_MAX_M;  // destinations of one coding job (parity or erased blocks)
+
+// One coding job: out[i] = sum_j u_ij * in[j] over GF(2^w) in every symbol lane, where the
+// coefficient u_ij is given by its ring representative mask[j][i] (bit s = coefficient of x^s).
+// Encoding a stripe is the job (data -> parity, the generator's parity rows); decoding is the job
+// (survivors -> erased blocks, the decoding matrix). Lives in kernel parameters or device memory.
+struct alignas(16) JobDesc {
+  const uint8_t* in[kMaxIn];
+  uint8_t* out[kMaxOut];
+  uint16_t mask[kMaxIn][kMaxOut];  // source-major so one 16-byte load gives every output's mask
+  uint64_t P;                      // packet bytes
+  int32_t nin, nout;
+};
+
+// Launch arguments of the staged ring kernel. Tiles are (job, column range [col0, col0 + tw)).
+// With tiles == nullptr every job has the same P and tiles_per_job = ceil(P / tw) tiles, tile t
+// covering job t / tiles_per_job.
+struct CodeArgs {
+  const JobDesc* jobs;  // device array; nullptr: the single job `job0`
+  const uint2* tiles;   // optional explicit tile list {job, col0}
+  uint32_t ntiles;
+  uint32_t tiles_per_job;
+  uint32_t tw;          // tile width in bytes (multiple of 16)
+  uint32_t groups;      // consumer warps are split into this many output groups
+  uint32_t stages;      // shared-memory pipeline depth
+  int* err;             // device error word (code, site) or nullptr
+  JobDesc job0;
+};
+
+// Tile-shape choice of one launch.
+struct TileShape {
+  int words;   // 32-bit words per consumer thread per packet
+  int warps;   // consumer warps per CTA
+  int stages;  // pipeline depth
+  int groups;  // output groups
+  int tw;      // tile width (bytes)
+  int ctas_per_sm;
+};
+
+// ---- planner (host) -------------------------------------------------------------------------
+bool aop_field_supported(int w, int n);
+uint32_t gf_mul(int w, uint32_t a, uint32_t b);
+uint32_t gf_inv(int w, uint32_t a);
+uint32_t sparse_rep(int w, int n, uint32_t u);
+
+struct DecodeEntry {
+  int status = PYRIT_OK;
+  int ne = 0;
+  int surv[kMaxIn];
+  int erased[kMaxOut];
+  uint16_t mask[kMaxOut][kMaxIn];  // row r = erased block erased[r], column s = survivor surv[s]
+};
+
+}  // namespace pyrit
+
+struct pyrit_plan_s {
+  int w, n, k, m;
+  std::vector<uint32_t> G;         // (k+m) x k
+  std::vector<uint16_t> enc_mask;  // m x k
+  std::mutex mu;
+  std::unordered_map<uint64_t, pyrit::DecodeEntry> dcache;
+};
+
+namespace pyrit {
+// Looks up or computes the decoding matrix of `erasures` (thread-safe). Returns a status.
+int plan_decode_entry(pyrit_plan_s* p, uint64_t erasures, DecodeEntry* out);
+// Fills a job for encoding one stripe.
+void make_encode_job(const pyrit_plan_s* p, const void* const* data, void* const* parity, size_t P,
+                     JobDesc* job);
+// Fills a job for decoding one stripe with a decode entry.
+void make_decode_job(const pyrit_plan_s* p, const DecodeEntry& e, void* const* blocks, size_t P,
+                     JobDesc* job);
+
+// ---- kernels (device launchers) --------------------------------------------------------------
+// True when every pointer of the job is 16-byte aligned and P is a multiple of 16.
+bool job_is_staged(const JobDesc& j);
+// Default tile shape for ring size n and the largest job output count.
+TileShape default_shape(int n, int max_nout, size_t P);
+// Launches the staged ring kernel. `jobs_dev` may be null for a single job passed by value.
+int launch_staged(int n, const TileShape& shape, const JobDesc* job0, const JobDesc* jobs_dev,
+                  const uint2* tiles_dev, uint32_t ntiles, uint32_t tiles_per_job, int grid_ctas,
+                  cudaStream_t stream);
+// Launches the plain-load kernel (any P and alignment) for one job.
+int launch_plain(int n, const JobDesc& job, cudaStream_t stream);
+// Device error word of the current device (allocated on first use), or nullptr on failure.
+int* device_error_word();
+// Multiprocessor count of the current device.
+int sm_count();
+
+}  // namespace pyrit

@@ -1,0 +1,187 @@
+"""ctypes binding of the C ABI in ``include/pyrit.h`` (argument marshalling only).
+
+Every function keeps its C name. Pointer arguments accept ints (device addresses, e.g. a torch
+tensor's ``data_ptr()``), lists of ints (host arrays of device pointers) or numpy arrays (host
+arrays). A negative status raises :class:`PyritError`. Streams are ``cudaStream_t`` values as ints
+(``torch.cuda.current_stream().cuda_stream``) or None for the default stream.
+
+Importing this module loads ``libpyrit.so`` and fails loudly if it has not been built
+(``python -c "import __graft_entry__ as g; g.build()"``); there is no fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpyrit.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libpyrit.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+PYRIT_OK = 0
+PYRIT_E_INVALID_ARG = -1
+PYRIT_E_UNSUPPORTED_FIELD = -2
+PYRIT_E_TOO_LONG = -3
+PYRIT_E_NOT_MDS = -4
+PYRIT_E_TOO_MANY_ERASURES = -5
+PYRIT_E_CUDA = -6
+PYRIT_E_OOM = -7
+PYRIT_E_BUDGET = -8
+PYRIT_E_TIMEOUT = -9
+PYRIT_E_BUSY = -10
+PYRIT_MAX_K = 32
+PYRIT_MAX_M = 8
+PYRIT_OP_ENCODE = 0
+PYRIT_OP_DECODE = 1
+
+_i, _u32, _u64, _sz, _vp = ctypes.c_int, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_size_t, ctypes.c_void_p
+
+_SIGS = {
+    "pyrit_strerror": (ctypes.c_char_p, [_i]),
+    "pyrit_plan_create": (_i, [_i, _i, _i, _i, _vp, ctypes.POINTER(_vp)]),
+    "pyrit_plan_destroy": (None, [_vp]),
+    "pyrit_plan_info": (_i, [_vp, _vp, _vp, _vp, _vp]),
+    "pyrit_plan_generator": (_i, [_vp, _vp]),
+    "pyrit_plan_encode_masks": (_i, [_vp, _vp]),
+    "pyrit_plan_decode_masks": (_i, [_vp, _u64, _vp, _vp, _vp, _vp]),
+    "pyrit_sparse_transform": (_u32, [_i, _i, _u32]),
+    "pyrit_gf_mul": (_u32, [_i, _u32, _u32]),
+    "pyrit_encode": (_i, [_vp, _vp, _vp, _sz, _vp]),
+    "pyrit_decode": (_i, [_vp, _vp, _u64, _sz, _vp]),
+    "pyrit_device_status": (_i, [_vp, _vp]),
+    "pyrit_synth_fill": (_i, [_vp, _sz, _u64, _u64, _vp]),
+}
+
+
+def _bind(sigs):
+    for name, (res, args) in sigs.items():
+        f = getattr(_lib, name)
+        f.restype = res
+        f.argtypes = args
+
+
+_bind(_SIGS)
+
+#: Every symbol the header declares (the CPU test checks the library exports each of them).
+EXPORTS = tuple(_SIGS)
+
+
+class PyritError(RuntimeError):
+    def __init__(self, status, where=""):
+        self.status = status
+        super().__init__("%s%s (status %d)" % (where + ": " if where else "",
+                                              _lib.pyrit_strerror(status).decode(), status))
+
+
+def _check(rc, where):
+    if rc < 0:
+        raise PyritError(rc, where)
+    return rc
+
+
+def _ptr_array(ptrs):
+    """Host array of device pointers from a list of ints / tensors."""
+    vals = [p.data_ptr() if hasattr(p, "data_ptr") else int(p) for p in ptrs]
+    return (ctypes.c_void_p * max(1, len(vals)))(*vals)
+
+
+def _np_ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if hasattr(s, "cuda_stream"):
+        return ctypes.c_void_p(s.cuda_stream)
+    return ctypes.c_void_p(int(s))
+
+
+def _dev(p):
+    return ctypes.c_void_p(p.data_ptr() if hasattr(p, "data_ptr") else int(p))
+
+
+# ---- C-named functions ------------------------------------------------------------------------
+
+def pyrit_strerror(status):
+    return _lib.pyrit_strerror(status).decode()
+
+
+def pyrit_plan_create(w, n, k, m, G=None):
+    """Returns an opaque plan handle (int). G: None or a (k+m) x k array of field elements."""
+    h = ctypes.c_void_p()
+    g = None
+    if G is not None:
+        g = np.ascontiguousarray(np.asarray(G, dtype=np.uint32))
+        if g.shape != (k + m, k):
+            raise ValueError("G must be (k+m) x k")
+    _check(_lib.pyrit_plan_create(w, n, k, m, _np_ptr(g) if g is not None else None, ctypes.byref(h)),
+           "pyrit_plan_create")
+    return h.value
+
+
+def pyrit_plan_destroy(plan):
+    _lib.pyrit_plan_destroy(plan)
+
+
+def pyrit_plan_info(plan):
+    v = [ctypes.c_int() for _ in range(4)]
+    _check(_lib.pyrit_plan_info(plan, *[ctypes.byref(x) for x in v]), "pyrit_plan_info")
+    return tuple(x.value for x in v)
+
+
+def pyrit_plan_generator(plan):
+    w, n, k, m = pyrit_plan_info(plan)
+    G = np.zeros((k + m, k), np.uint32)
+    _check(_lib.pyrit_plan_generator(plan, _np_ptr(G)), "pyrit_plan_generator")
+    return G
+
+
+def pyrit_plan_encode_masks(plan):
+    w, n, k, m = pyrit_plan_info(plan)
+    M = np.zeros((m, k), np.uint16)
+    _check(_lib.pyrit_plan_encode_masks(plan, _np_ptr(M)), "pyrit_plan_encode_masks")
+    return M
+
+
+def pyrit_plan_decode_masks(plan, erasures):
+    """Returns (survivors[k], erased[ne], masks[ne, k])."""
+    w, n, k, m = pyrit_plan_info(plan)
+    surv = np.zeros(k, np.int32)
+    er = np.zeros(max(1, m), np.int32)
+    M = np.zeros((max(1, m), k), np.uint16)
+    ne = ctypes.c_int()
+    _check(_lib.pyrit_plan_decode_masks(plan, erasures, _np_ptr(surv), _np_ptr(er), _np_ptr(M), ctypes.byref(ne)),
+           "pyrit_plan_decode_masks")
+    return surv, er[:ne.value].copy(), M[:ne.value].copy()
+
+
+def pyrit_sparse_transform(w, n, u):
+    return int(_lib.pyrit_sparse_transform(w, n, u))
+
+
+def pyrit_gf_mul(w, a, b):
+    return int(_lib.pyrit_gf_mul(w, a, b))
+
+
+def pyrit_encode(plan, data, parity, P, stream=None):
+    """data: k device pointers (ints or tensors); parity: m device pointers."""
+    return _check(_lib.pyrit_encode(plan, _ptr_array(data), _ptr_array(parity), P, _stream(stream)), "pyrit_encode")
+
+
+def pyrit_decode(plan, blocks, erasures, P, stream=None):
+    """blocks: k+m device pointers; erased ones are rebuilt in place."""
+    return _check(_lib.pyrit_decode(plan, _ptr_array(blocks), erasures, P, _stream(stream)), "pyrit_decode")
+
+
+def pyrit_device_status():
+    code, where = ctypes.c_int(), ctypes.c_int()
+    _check(_lib.pyrit_device_status(ctypes.byref(code), ctypes.byref(where)), "pyrit_device_status")
+    return code.value, where.value
+
+
+def pyrit_synth_fill(dst, nbytes, seed, offset=0, stream=None):
+    return _check(_lib.pyrit_synth_fill(_dev(dst), nbytes, seed, offset, _stream(stream)), "pyrit_synth_fill")

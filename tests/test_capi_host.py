@@ -1,0 +1,190 @@
+"""Host-side checks of the C ABI (no GPU): the library exports every declared symbol, and the
+planner's field arithmetic, sparse transform (Sec. 2.2), default generator and decoding matrices
+(Sec. 4.3) agree with the independent CPU oracle; invalid calls return their documented codes
+before any device work."""
+import ctypes
+import glob
+import itertools
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1709_00178_gb300 import pyrit
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+RINGS = [(2, 3), (4, 5), (10, 11), (12, 13)]
+
+
+def test_library_exports_every_declared_symbol():
+    declared = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        declared |= set(re.findall(r"PYRIT_API\s+[\w\s\*]+?\b(pyrit_\w+)\s*\(", open(h).read()))
+    assert declared, "no declarations found"
+    lib = ctypes.CDLL(pyrit.LIB_PATH)
+    for name in sorted(declared):
+        assert hasattr(lib, name), name
+    assert declared == set(pyrit.EXPORTS)
+
+
+def _brute_sparse(w, n):
+    """phi_S for every u by brute force over all 2^n ring elements (oracle reduction)."""
+    p = oracle.aop(w)
+    reds = oracle.poly_mod_vec(p, np.arange(1 << n, dtype=np.uint32))
+    best = {}
+    for r, u in enumerate(reds.tolist()):
+        key = (bin(r).count("1"), r)
+        if u not in best or key < best[u][0]:
+            best[u] = (key, r)
+    return np.array([best[u][1] for u in range(1 << w)], np.uint32)
+
+
+@pytest.mark.parametrize("w,n", RINGS)
+def test_sparse_transform_matches_brute_force(w, n):
+    ref = _brute_sparse(w, n)
+    got = np.array([pyrit.pyrit_sparse_transform(w, n, u) for u in range(1 << w)], np.uint32)
+    assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("w", [2, 4, 10, 12])
+def test_planner_field_product(w):
+    q = 1 << w
+    rng = np.random.default_rng(w)
+    if w <= 10:
+        a = np.repeat(np.arange(q), q)
+        b = np.tile(np.arange(q), q)
+        if w == 10:
+            sel = rng.choice(a.size, 200000, replace=False)
+            a, b = a[sel], b[sel]
+    else:
+        a = rng.integers(0, q, 200000)
+        b = rng.integers(0, q, 200000)
+    ref = oracle.gf_mul_slow_vec(w, a, b)
+    got = np.array([pyrit.pyrit_gf_mul(w, int(x), int(y)) for x, y in zip(a, b)], np.uint32)
+    assert np.array_equal(got, ref)
+
+
+def test_field_support_matches_oracle_irreducibility():
+    for w in range(2, 16):
+        supported = True
+        try:
+            h = pyrit.pyrit_plan_create(w, w + 1, 1, 1)
+            pyrit.pyrit_plan_destroy(h)
+        except pyrit.PyritError as e:
+            assert e.status == pyrit.PYRIT_E_UNSUPPORTED_FIELD
+            supported = False
+        assert supported == (oracle.aop_irreducible(w) and w + 1 in (3, 5, 11, 13)), w
+
+
+@pytest.mark.parametrize("w,k,m", [(2, 2, 2), (4, 4, 2), (10, 10, 4), (12, 16, 4), (4, 12, 4), (12, 32, 8)])
+def test_default_generator_and_encode_masks(w, k, m):
+    plan = pyrit.pyrit_plan_create(w, w + 1, k, m)
+    try:
+        assert pyrit.pyrit_plan_info(plan) == (w, w + 1, k, m)
+        G = pyrit.pyrit_plan_generator(plan)
+        assert np.array_equal(G, oracle.cauchy(w, k, m))
+        sp = _brute_sparse(w, w + 1)
+        assert np.array_equal(pyrit.pyrit_plan_encode_masks(plan), sp[G[k:]].astype(np.uint16))
+    finally:
+        pyrit.pyrit_plan_destroy(plan)
+
+
+def _oracle_decode_matrix(w, k, m, G, erasures):
+    surv = [e for e in range(k + m) if not (erasures >> e) & 1][:k]
+    erased = [e for e in range(k + m) if (erasures >> e) & 1]
+    Inv = oracle.gf_invert(w, G[surv])
+    rows = []
+    for e in erased:
+        if e < k:
+            rows.append(Inv[e])
+        else:
+            r = np.zeros(k, np.uint32)
+            for s in range(k):
+                acc = 0
+                for j in range(k):
+                    acc ^= oracle.gf_mul_slow(w, int(G[e, j]), int(Inv[j, s]))
+                r[s] = acc
+            rows.append(r)
+    return np.array(surv), np.array(erased), np.array(rows, np.uint32).reshape(len(erased), k)
+
+
+@pytest.mark.parametrize("w,k,m,exhaustive", [(4, 4, 2, True), (10, 10, 4, False), (12, 16, 4, False)])
+def test_decode_masks_match_oracle(w, k, m, exhaustive):
+    plan = pyrit.pyrit_plan_create(w, w + 1, k, m)
+    sp = _brute_sparse(w, w + 1)
+    try:
+        G = pyrit.pyrit_plan_generator(plan)
+        if exhaustive:
+            pats = [sum(1 << x for x in c) for e in range(0, m + 1) for c in itertools.combinations(range(k + m), e)]
+        else:
+            rng = np.random.default_rng(k)
+            pats = [0] + [sum(1 << int(x) for x in rng.choice(k + m, int(rng.integers(1, m + 1)), replace=False))
+                          for _ in range(25)]
+        for pat in pats:
+            surv, er, M = pyrit.pyrit_plan_decode_masks(plan, pat)
+            s2, e2, D = _oracle_decode_matrix(w, k, m, G, pat)
+            assert list(surv) == list(s2) and list(er) == list(e2)
+            assert np.array_equal(M, sp[D].astype(np.uint16)), hex(pat)
+    finally:
+        pyrit.pyrit_plan_destroy(plan)
+
+
+def test_error_codes():
+    E = pyrit
+    cases = [
+        (lambda: E.pyrit_plan_create(6, 7, 3, 2), E.PYRIT_E_UNSUPPORTED_FIELD),   # AOP reducible
+        (lambda: E.pyrit_plan_create(4, 6, 3, 2), E.PYRIT_E_UNSUPPORTED_FIELD),   # n != w+1
+        (lambda: E.pyrit_plan_create(4, 5, 12, 5), E.PYRIT_E_TOO_LONG),           # k+m > 16
+        (lambda: E.pyrit_plan_create(4, 5, 0, 2), E.PYRIT_E_INVALID_ARG),
+        (lambda: E.pyrit_plan_create(4, 5, 33, 2), E.PYRIT_E_INVALID_ARG),
+        (lambda: E.pyrit_plan_create(4, 5, 4, 9), E.PYRIT_E_INVALID_ARG),
+    ]
+    for f, code in cases:
+        with pytest.raises(E.PyritError) as ei:
+            f()
+        assert ei.value.status == code
+
+
+def test_user_generator_validation():
+    w, k, m = 4, 3, 2
+    G = oracle.cauchy(w, k, m)
+    h = pyrit.pyrit_plan_create(w, w + 1, k, m, G)
+    pyrit.pyrit_plan_destroy(h)
+    bad = G.copy()
+    bad[0, 1] = 1  # not systematic
+    with pytest.raises(pyrit.PyritError) as ei:
+        pyrit.pyrit_plan_create(w, w + 1, k, m, bad)
+    assert ei.value.status == pyrit.PYRIT_E_NOT_MDS
+    sing = G.copy()
+    sing[k + 1] = sing[k]  # two equal parity rows: a singular 3x3 subset
+    with pytest.raises(pyrit.PyritError) as ei:
+        pyrit.pyrit_plan_create(w, w + 1, k, m, sing)
+    assert ei.value.status == pyrit.PYRIT_E_NOT_MDS
+    big = G.copy()
+    big[k, 0] = 16
+    with pytest.raises(pyrit.PyritError) as ei:
+        pyrit.pyrit_plan_create(w, w + 1, k, m, big)
+    assert ei.value.status == pyrit.PYRIT_E_NOT_MDS
+
+
+def test_invalid_coding_calls_fail_before_device_work():
+    plan = pyrit.pyrit_plan_create(4, 5, 4, 2)
+    try:
+        fake = [16 * (i + 1) for i in range(6)]
+        with pytest.raises(pyrit.PyritError) as ei:
+            pyrit.pyrit_decode(plan, fake, 0b111, 64)  # 3 erasures > m = 2
+        assert ei.value.status == pyrit.PYRIT_E_TOO_MANY_ERASURES
+        with pytest.raises(pyrit.PyritError) as ei:
+            pyrit.pyrit_decode(plan, fake, 1 << 6, 64)  # bit outside the stripe
+        assert ei.value.status == pyrit.PYRIT_E_INVALID_ARG
+        with pytest.raises(pyrit.PyritError) as ei:
+            pyrit.pyrit_encode(plan, fake[:4], fake[4:], 0)  # P = 0
+        assert ei.value.status == pyrit.PYRIT_E_INVALID_ARG
+        with pytest.raises(pyrit.PyritError) as ei:
+            pyrit.pyrit_encode(plan, fake[:3] + [0], fake[4:], 64)  # null block
+        assert ei.value.status == pyrit.PYRIT_E_INVALID_ARG
+        assert pyrit.pyrit_decode(plan, fake, 0, 64) == 0  # nothing erased: no work
+    finally:
+        pyrit.pyrit_plan_destroy(plan)
