@@ -1,0 +1,377 @@
+#!/usr/bin/env python3
+"""Benchmark of the PYRIT GB300 coding path.
+
+Default workload (one JSON line): GF(2^10) (w=10, n=11, all-one modulus), Cauchy code k=10, m=4,
+packets of 64 KiB (blocks of 640 KiB), 256 stripes of seeded uniform random bytes. One step =
+encode every stripe, then decode every stripe with its own seeded random pattern of 1..4 erased
+blocks (rebuilt in place), each as one persistent batched launch replayed from a CUDA graph.
+
+  value    source GB/s (10^9 B/s): 2 x stripes x k x w x P bytes (encode + decode) per step time,
+           inputs resident in HBM (2.19 GiB of stripes, larger than L2; no flush needed).
+  e2e      the same metric with the data blocks uploaded from pinned host memory and the parity
+           read back every step (chunked over streams so copies overlap the kernels).
+  roofline the coding kernel's algorithmic bytes ((k+m)wP per encoded stripe, (k+e)wP per decoded
+           stripe with e erasures) per launch over its event-timed duration, against the measured
+           HBM copy bandwidth.
+
+`--impl reference` times the CPU oracle (the plain log/antilog coder) on a bounded sample of the
+same workload. Multi-GPU (torchrun): every rank codes its own 256 stripes (weak scaling, no
+collective on the data path); the step time is the maximum over ranks.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+W, N, K, M, P, STRIPES = 10, 11, 10, 4, 64 * 1024, 256
+CONFIG = {"workload": "GF(2^10) AOP ring n=11, Cauchy k=10 m=4, 64 KiB packets, 256 stripes; "
+                      "encode + decode with 1-4 random erasures per stripe",
+          "w": W, "n": N, "k": K, "m": M, "packet_bytes": P, "stripes": STRIPES,
+          "l2": "inputs larger than L2 (2.19 GiB of stripes per GPU), no flush"}
+METRIC = "encode+decode GB/s of source data"
+FALLBACK_PEAK = 6800.0
+
+
+def peak_hbm():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_PEAK, "fallback"
+
+
+def kernel_source_digest():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1709_00178_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h", ".inc", ".cpp")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic():
+    """DRAM bytes per launch of the coding kernel from the committed ncu summary, if the kernel
+    sources have not changed since it was taken."""
+    p = os.path.join(ROOT, "profiles", "ring_staged_traffic.json")
+    try:
+        with open(p) as f:
+            rec = json.load(f)
+    except Exception:
+        return None
+    if rec.get("kernel_src_digest") != kernel_source_digest():
+        return None
+    return rec.get("traffic_bytes_per_launch")
+
+
+def patterns(seed, stripes, k, m):
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(stripes):
+        e = int(rng.integers(1, m + 1))
+        out.append(sum(1 << int(x) for x in rng.choice(k + m, e, replace=False)))
+    return out
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = "/tmp/pyrit_clocks_%d.csv" % os.getpid()
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_reference(args):
+    """The CPU oracle timed as the reference arm, on a bounded sample of the workload."""
+    import numpy as np
+    import oracle
+    from paper_1709_00178_gb300.synth import BASE_SEED, synth_bytes
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cores = os.cpu_count() or 1
+    sample = 4  # stripes encoded and decoded per step
+    G = oracle.cauchy(W, K, M)
+    pats = patterns(BASE_SEED + 1, STRIPES, K, M)
+    blk = W * P
+    stripe_bytes = (K + M) * blk
+    data = [synth_bytes(BASE_SEED + 1, s * stripe_bytes, K * blk).reshape(K, W, P) for s in range(sample)]
+
+    def step():
+        for s in range(sample):
+            par = oracle.encode(W, K, M, G, data[s], nthreads=cores)
+            full = np.concatenate([data[s], par])
+            oracle.decode(W, K, M, G, full, pats[s], nthreads=cores)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = (time.perf_counter() - t0) / args.steps
+    gbs = 2 * sample * K * blk / dt / 1e9
+    desc = "%d stripes of the workload encoded and decoded per step on %d threads" % (sample, cores)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic", "config": CONFIG,
+        "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": desc},
+        "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+def main():
+    global STRIPES
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--stripes", type=int, default=STRIPES,
+                    help="stripes per GPU (default 256; smaller values make profiling cases)")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.stripes != STRIPES:
+        STRIPES = max(8, args.stripes // 8 * 8)
+        CONFIG["stripes"] = STRIPES
+        CONFIG["workload"] = CONFIG["workload"].replace("256 stripes", "%d stripes" % STRIPES)
+        CONFIG["l2"] = "%.2f GiB of stripes per GPU" % (STRIPES * (K + M) * W * P / 2 ** 30)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1709_00178_gb300 import pyrit
+    from paper_1709_00178_gb300.synth import BASE_SEED
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+
+    blk = W * P
+    stripe_bytes = (K + M) * blk
+    buf = torch.empty(STRIPES * stripe_bytes, dtype=torch.uint8, device=dev)
+    pyrit.pyrit_synth_fill(buf.data_ptr(), buf.numel(), BASE_SEED + 1, rank * buf.numel())
+    base = buf.data_ptr()
+    blocks = [[base + s * stripe_bytes + e * blk for e in range(K + M)] for s in range(STRIPES)]
+    pats = patterns(BASE_SEED + 1 + 1000 * rank, STRIPES, K, M)
+    plan = pyrit.pyrit_plan_create(W, N, K, M)
+    enc = pyrit.pyrit_batch_create([(plan, pyrit.PYRIT_OP_ENCODE, 0, P, blocks[s]) for s in range(STRIPES)])
+    dec = pyrit.pyrit_batch_create([(plan, pyrit.PYRIT_OP_DECODE, pats[s], P, blocks[s]) for s in range(STRIPES)])
+    es, ds = pyrit.pyrit_batch_stats(enc), pyrit.pyrit_batch_stats(dec)
+    launches_per_step = es["launches"] + ds["launches"]
+    stream = torch.cuda.Stream(device=dev)
+
+    def step(evs=None):
+        if evs is not None:
+            evs[0].record(stream)
+        pyrit.pyrit_batch_run(enc, stream, graph=True)
+        if evs is not None:
+            evs[1].record(stream)
+        pyrit.pyrit_batch_run(dec, stream, graph=True)
+        if evs is not None:
+            evs[2].record(stream)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    code, where = pyrit.pyrit_device_status()
+    if code != 0:
+        raise RuntimeError("device status %d at site %d after warm-up" % (code, where))
+
+    # ---- device-resident timed region ----
+    clocks = Clocks(local)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    t0.record(stream)
+    for i in range(args.steps):
+        step(evs[i])
+    t1.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    barrier()
+    ms = t0.elapsed_time(t1)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    src_per_step = es["src_bytes"] + ds["src_bytes"]
+    value = world * src_per_step / (ms_step * 1e-3) / 1e9
+    enc_ms = sum(e[0].elapsed_time(e[1]) for e in evs) / args.steps
+    dec_ms = sum(e[1].elapsed_time(e[2]) for e in evs) / args.steps
+    alg_per_launch = (es["alg_bytes"] + ds["alg_bytes"]) / 2
+    achieved = alg_per_launch / ((enc_ms + dec_ms) / 2 * 1e-3) / 1e9
+    peak, peak_kind = peak_hbm()
+    code, where = pyrit.pyrit_device_status()
+    if code != 0:
+        raise RuntimeError("device status %d at site %d" % (code, where))
+
+    # ---- end to end: data from pinned host memory, parity back, every step ----
+    CH = 8  # chunks of stripes, each on its own stream slot
+    per = STRIPES // CH
+    host = torch.empty(STRIPES * stripe_bytes, dtype=torch.uint8, pin_memory=True)
+    host.copy_(buf)
+    host_par = torch.empty(STRIPES * M * blk, dtype=torch.uint8, pin_memory=True)
+    cenc = [pyrit.pyrit_batch_create([(plan, 0, 0, P, blocks[s]) for s in range(c * per, (c + 1) * per)])
+            for c in range(CH)]
+    cdec = [pyrit.pyrit_batch_create([(plan, 1, pats[s], P, blocks[s]) for s in range(c * per, (c + 1) * per)])
+            for c in range(CH)]
+    streams = [torch.cuda.Stream(device=dev) for _ in range(3)]
+
+    def e2e_step():
+        for c in range(CH):
+            st = streams[c % len(streams)]
+            with torch.cuda.stream(st):
+                for s in range(c * per, (c + 1) * per):
+                    o = s * stripe_bytes
+                    buf[o:o + K * blk].copy_(host[o:o + K * blk], non_blocking=True)
+                pyrit.pyrit_batch_run(cenc[c], st, graph=True)
+                pyrit.pyrit_batch_run(cdec[c], st, graph=True)
+                for s in range(c * per, (c + 1) * per):
+                    o = s * stripe_bytes + K * blk
+                    host_par[s * M * blk:(s + 1) * M * blk].copy_(buf[o:o + M * blk], non_blocking=True)
+
+    def e2e_timed(steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        main = torch.cuda.current_stream(dev)
+        a.record(main)
+        for st in streams:
+            st.wait_event(a)
+        for _ in range(steps):
+            e2e_step()
+        for st in streams:
+            main.wait_stream(st)
+        b.record(main)
+        torch.cuda.synchronize(dev)
+        return a.elapsed_time(b)
+
+    e2e_timed(2)
+    barrier()
+    e2e_ms = e2e_timed(args.steps)
+    if world > 1:
+        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_val = world * src_per_step / (e2e_ms / args.steps * 1e-3) / 1e9
+    # every parity read back must equal the device-resident result
+    par_dev = torch.cat([buf[s * stripe_bytes + K * blk:s * stripe_bytes + (K + M) * blk] for s in range(STRIPES)])
+    e2e_ok = bool(torch.equal(par_dev.cpu(), host_par))
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic (seeded SplitMix64 bytes)", "config": CONFIG,
+        "e2e": {"value": e2e_val, "unit": "GB/s", "h2d_bytes_per_step": STRIPES * K * blk,
+                "d2h_bytes_per_step": STRIPES * M * blk, "parity_readback_matches": e2e_ok},
+        "gpu_launches": launches_per_step * args.steps,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": recorded_traffic(),
+                     "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind if peak_kind == "measured"
+                     else "fallback 6800 GB/s",
+                     "kernel": "ring_staged_kernel", "alg_bytes_per_launch": alg_per_launch,
+                     "encode_ms": enc_ms, "decode_ms": dec_ms},
+        "clocks": clk,
+    }
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(buf, blocks, pats, plan, pyrit)
+    if rank == 0:
+        print(json.dumps(out))
+    for b in [enc, dec] + cenc + cdec:
+        pyrit.pyrit_batch_destroy(b)
+    pyrit.pyrit_plan_destroy(plan)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(buf, blocks, pats, plan, pyrit):
+    """The oracle, as it stands, on a bounded sample of the same stripes and patterns, on all host
+    cores; its parity is also compared with the GPU's for those stripes."""
+    import numpy as np
+    import torch
+    import oracle
+    sample = 16
+    cores = os.cpu_count() or 1
+    blk = W * P
+    stripe_bytes = (K + M) * blk
+    G = pyrit.pyrit_plan_generator(plan)
+    host = buf[:sample * stripe_bytes].cpu().numpy().reshape(sample, K + M, W, P)
+    t0 = time.perf_counter()
+    match = True
+    for s in range(sample):
+        par = oracle.encode(W, K, M, G, host[s, :K], nthreads=cores)
+        full = np.concatenate([host[s, :K], par])
+        rebuilt = oracle.decode(W, K, M, G, full, pats[s], nthreads=cores)
+        match = match and np.array_equal(par, host[s, K:]) and np.array_equal(rebuilt, full)
+    dt = time.perf_counter() - t0
+    return {"value": 2 * sample * K * blk / dt / 1e9, "unit": "GB/s", "cores": cores, "kind": "oracle",
+            "sample": "first %d of the %d stripes, encode + decode (same erasure patterns), %.1f s" % (
+                sample, STRIPES, dt),
+            "gpu_parity_on_sample": match}
+
+
+if __name__ == "__main__":
+    main()

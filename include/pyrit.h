@@ -144,6 +144,55 @@ PYRIT_API int pyrit_encode(pyrit_plan_t plan, const void* const* data, void* con
 PYRIT_API int pyrit_decode(pyrit_plan_t plan, void* const* blocks, uint64_t erasures, size_t P,
                  pyrit_stream_t stream);
 
+/* ---- batched coding: many stripes in one persistent launch -------------------------------- */
+
+typedef struct pyrit_batch_s* pyrit_batch_t;
+
+/* One stripe of a batch. */
+typedef struct {
+  pyrit_plan_t plan;    /* the stripe's code (plans may differ between stripes)              */
+  int op;               /* PYRIT_OP_ENCODE or PYRIT_OP_DECODE                                 */
+  uint64_t erasures;    /* decode: bit e set = block e lost (ignored for encode)              */
+  size_t packet_bytes;  /* P >= 1                                                             */
+  void* const* blocks;  /* host array of k+m device pointers: data 0..k-1, parity k..k+m-1;
+                           encode writes parity, decode rewrites the erased blocks            */
+} pyrit_stripe_t;
+
+/* Tile-shape overrides for a batch; a zero field (dispatch: -1) means automatic. */
+typedef struct {
+  int words;        /* 32-bit words per consumer thread per packet (1 or 2)              */
+  int mg;           /* outputs accumulated per consumer warp (2, 4 or 8)                 */
+  int minb;         /* CTAs per multiprocessor the kernel's registers are sized for      */
+  int dispatch;     /* 0: uniform test per ring shift; 1: switch per set mask bit        */
+  int stages;       /* shared-memory pipeline depth (2..8)                               */
+  int ctas_per_sm;  /* persistent grid = multiprocessors x ctas_per_sm                   */
+} pyrit_tile_t;
+
+/* Prepares a batch: validates every stripe (the same checks and codes as pyrit_encode /
+ * pyrit_decode), resolves the decoding matrices through the plans' caches, builds one coding job
+ * per stripe (stripes with nothing erased are dropped) and a work list of column tiles, and copies
+ * both to library-owned device memory (synchronous). Stripes are grouped by ring size; each group is
+ * one persistent launch of the staged kernel in which every CTA walks the tile list. Stripes whose
+ * P or pointers do not allow 16-byte bulk copies run on the plain-load kernel, one launch each.
+ *   stripes : host array of `count` stripes (copied; the block pointer arrays are read here only).
+ *   tile    : NULL for the automatic shape, else overrides.
+ * The batch keeps pointers to the caller's buffers: they must stay valid while it is run. */
+PYRIT_API int pyrit_batch_create(const pyrit_stripe_t* stripes, int count, const pyrit_tile_t* tile,
+                       pyrit_batch_t* out);
+
+/* Enqueues the batch's launches on `stream` (asynchronous). With graph != 0 the launches are
+ * captured once into a CUDA graph on first use and replayed from then on. */
+PYRIT_API int pyrit_batch_run(pyrit_batch_t batch, pyrit_stream_t stream, int graph);
+
+/* Algorithmic HBM bytes of one run ((k + m) * w * P per encoded stripe, (k + e) * w * P per
+ * decoded stripe with e erasures), source bytes (k * w * P per stripe), launches per run and
+ * column tiles. Any pointer may be NULL. */
+PYRIT_API int pyrit_batch_stats(pyrit_batch_t batch, uint64_t* alg_bytes, uint64_t* src_bytes, int* launches,
+                      uint64_t* tiles);
+
+/* Frees the batch's device memory and graph (synchronises the device). */
+PYRIT_API void pyrit_batch_destroy(pyrit_batch_t batch);
+
 /* ---- device status ----------------------------------------------------------------------- */
 
 /* Reads and clears the device-side error word of the current device (synchronises the device).

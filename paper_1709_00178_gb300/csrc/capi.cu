@@ -12,9 +12,10 @@ namespace {
 int run_job(int n, const JobDesc& job, cudaStream_t stream) {
   if (job.nout == 0) return PYRIT_OK;
   if (job_is_staged(job)) {
-    const TileShape sh = default_shape(n, job.nout, job.P);
-    const uint32_t tpj = (uint32_t)((job.P + sh.tw - 1) / sh.tw);
-    return launch_staged(n, sh, &job, nullptr, nullptr, tpj, tpj, 0, stream);
+    TileShape sh;
+    if (!choose_shape(n, job.nout, ShapeHint(), &sh)) return PYRIT_E_UNSUPPORTED_FIELD;
+    const uint32_t tpj = tiles_for(job.P, sh);
+    return launch_staged(sh, &job, nullptr, nullptr, tpj, tpj, stream);
   }
   return launch_plain(n, job, stream);
 }

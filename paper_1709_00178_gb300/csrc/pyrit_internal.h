@@ -43,14 +43,33 @@ struct CodeArgs {
   JobDesc job0;
 };
 
+// A compiled instance of the staged ring kernel.
+struct Variant {
+  int n;         // ring size N (w = N - 1)
+  int words;     // 32-bit words per consumer thread per packet
+  int mg;        // outputs accumulated per consumer warp
+  int minb;      // CTAs per SM the register budget is sized for
+  int dispatch;  // 0: uniform test per shift; 1: switch per set bit
+  const void* fn;
+};
+
 // Tile-shape choice of one launch.
 struct TileShape {
-  int words;   // 32-bit words per consumer thread per packet
-  int warps;   // consumer warps per CTA
-  int stages;  // pipeline depth
-  int groups;  // output groups
-  int tw;      // tile width (bytes)
-  int ctas_per_sm;
+  const Variant* v = nullptr;
+  int groups = 1;  // output groups (power of two dividing the consumer warps)
+  int tw = 0;      // tile width (bytes, multiple of 16)
+  int stages = 0;  // pipeline depth
+  int grid = 0;    // CTAs (0: SMs x occupancy)
+};
+
+// Optional overrides of the automatic shape choice (0 or -1 = automatic).
+struct ShapeHint {
+  int words = 0;
+  int dispatch = -1;
+  int mg = 0;
+  int minb = 0;
+  int stages = 0;
+  int ctas_per_sm = 0;
 };
 
 // ---- planner (host) -------------------------------------------------------------------------
@@ -88,14 +107,21 @@ void make_decode_job(const pyrit_plan_s* p, const DecodeEntry& e, void* const* b
                      JobDesc* job);
 
 // ---- kernels (device launchers) --------------------------------------------------------------
+// Registered variants (all translation units).
+const Variant* variants(int* count);
+const Variant* find_variant(int n, int words, int dispatch, int mg, int minb);
 // True when every pointer of the job is 16-byte aligned and P is a multiple of 16.
 bool job_is_staged(const JobDesc& j);
-// Default tile shape for ring size n and the largest job output count.
-TileShape default_shape(int n, int max_nout, size_t P);
+// Tile shape for ring size n, the largest output count of the launch's jobs and optional hints.
+// Returns false if no compiled variant matches.
+bool choose_shape(int n, int max_nout, const ShapeHint& hint, TileShape* out);
+// Fills shape->grid (SMs x occupancy) if it is 0; makes the one-time per-device attribute calls.
+void resolve_grid(TileShape* shape);
+// Tiles of one job of packet size P under a shape.
+inline uint32_t tiles_for(uint64_t P, const TileShape& s) { return (uint32_t)((P + s.tw - 1) / s.tw); }
 // Launches the staged ring kernel. `jobs_dev` may be null for a single job passed by value.
-int launch_staged(int n, const TileShape& shape, const JobDesc* job0, const JobDesc* jobs_dev,
-                  const uint2* tiles_dev, uint32_t ntiles, uint32_t tiles_per_job, int grid_ctas,
-                  cudaStream_t stream);
+int launch_staged(const TileShape& sh, const JobDesc* job0, const JobDesc* jobs_dev, const uint2* tiles_dev,
+                  uint32_t ntiles, uint32_t tiles_per_job, cudaStream_t stream);
 // Launches the plain-load kernel (any P and alignment) for one job.
 int launch_plain(int n, const JobDesc& job, cudaStream_t stream);
 // Device error word of the current device (allocated on first use), or nullptr on failure.

@@ -19,16 +19,16 @@
 // of every packet into registers and release the stage, then run the XOR network out of registers.
 // When a job has more outputs than one warp's accumulators hold (MG), the consumer warps split
 // into output groups that read the same staged tile, so every source byte leaves HBM once.
-#include <cuda_runtime.h>
+#pragma once
 
-#include <algorithm>
-#include <atomic>
-#include <mutex>
+#include <cuda_runtime.h>
 
 #include "ptx.cuh"
 #include "pyrit_internal.h"
 
 namespace pyrit {
+
+constexpr int kConsumerWarps = 8;  // consumer warps per CTA (plus one producer warp)
 
 // acc += x^S * d in R_{2,N}: packet q of the embedded source lands in accumulator (q + S) mod N.
 template <int N, int WORDS, int S>
@@ -64,17 +64,33 @@ __device__ __forceinline__ void xor_rotated_dyn(uint32_t (&acc)[N][WORDS], const
   }
 }
 
-// acc_i += r_ij * d for every output i of the group: one rotation per set bit of r_ij.
-template <int N, int WORDS, int MG>
+// acc_i += r_ij * d for every output i of the group, one rotation per set bit of r_ij. The masks
+// arrive as warp-uniform 32-bit words (two 16-bit masks each), so every branch below is uniform.
+//   DISPATCH 0: one uniform test per shift S (static code per (i, S); no indirect jump).
+//   DISPATCH 1: iterate over the set bits and jump to the rotation's code through a switch.
+template <int N, int WORDS, int MG, int DISPATCH>
 __device__ __forceinline__ void ring_mac(uint32_t (&acc)[MG][N][WORDS], const uint32_t (&d)[N - 1][WORDS],
-                                         const uint16_t (&msk)[MG]) {
+                                         const uint32_t (&mu)[(MG + 1) / 2]) {
 #pragma unroll
   for (int i = 0; i < MG; ++i) {
-    uint32_t m = msk[i];
-    while (m) {
-      const int s = __ffs(m) - 1;
-      m &= m - 1;
-      xor_rotated_dyn<N, WORDS>(acc[i], d, s);
+    const uint32_t m = (mu[i >> 1] >> (16 * (i & 1))) & 0xFFFFu;
+    if constexpr (DISPATCH == 0) {
+#pragma unroll
+      for (int s = 0; s < N; ++s) {
+        if (m & (1u << s)) {
+#pragma unroll
+          for (int q = 0; q < N - 1; ++q)
+#pragma unroll
+            for (int x = 0; x < WORDS; ++x) acc[i][(q + s) % N][x] ^= d[q][x];
+        }
+      }
+    } else {
+      uint32_t r = m;
+      while (r) {
+        const int s = __ffs(r) - 1;
+        r &= r - 1;
+        xor_rotated_dyn<N, WORDS>(acc[i], d, s);
+      }
     }
   }
 }
@@ -103,9 +119,12 @@ struct Vec<2> {
   using T = uint2;
 };
 
-template <int N, int WORDS, int MG, int NC>
-__global__ void __launch_bounds__((NC + 1) * 32, 1) ring_staged_kernel(const __grid_constant__ CodeArgs a) {
+template <int N, int WORDS, int MG, int MINB, int DISPATCH>
+__global__ void __launch_bounds__((kConsumerWarps + 1) * 32, MINB)
+    ring_staged_kernel(const __grid_constant__ CodeArgs a) {
   constexpr int W = N - 1;
+  constexpr int NC = kConsumerWarps;
+  constexpr int MW = (MG + 1) / 2;  // 32-bit mask words per source for MG outputs
   using V = typename Vec<WORDS>::T;
   extern __shared__ __align__(128) uint8_t smem[];
   const uint32_t S = a.stages, TW = a.tw;
@@ -176,6 +195,19 @@ __global__ void __launch_bounds__((NC + 1) * 32, 1) ring_staged_kernel(const __g
     const bool valid = off < width;
     const int nin = J->nin, nout = J->nout;
 
+    // Lane l holds the mask words of source l for this group's outputs (one 16-byte row per
+    // source: the masks of outputs 0..7).
+    uint32_t rw[MW];
+    {
+      uint4 row = make_uint4(0u, 0u, 0u, 0u);
+      if (lane < nin) row = *reinterpret_cast<const uint4*>(&J->mask[lane][0]);
+#pragma unroll
+      for (int x = 0; x < MW; ++x) {
+        const int idx = g * MW + x;
+        rw[x] = idx == 0 ? row.x : idx == 1 ? row.y : idx == 2 ? row.z : idx == 3 ? row.w : 0u;
+      }
+    }
+
     uint32_t acc[MG][N][WORDS];
 #pragma unroll
     for (int i = 0; i < MG; ++i)
@@ -211,18 +243,12 @@ __global__ void __launch_bounds__((NC + 1) * 32, 1) ring_staged_kernel(const __g
         stage = 0;
         phase ^= 1u;
       }
-      // The ring masks of source j for this group's outputs (zero for outputs >= nout).
-      const uint4 mv = *reinterpret_cast<const uint4*>(&J->mask[j][0]);
-      const uint16_t all[8] = {(uint16_t)(mv.x & 0xFFFFu), (uint16_t)(mv.x >> 16), (uint16_t)(mv.y & 0xFFFFu),
-                               (uint16_t)(mv.y >> 16),     (uint16_t)(mv.z & 0xFFFFu), (uint16_t)(mv.z >> 16),
-                               (uint16_t)(mv.w & 0xFFFFu), (uint16_t)(mv.w >> 16)};
-      uint16_t msk[MG];
+      // Source j's masks, broadcast from lane j by a warp OR-reduction: the result is uniform
+      // across the warp by construction, which keeps the dispatch below on uniform branches.
+      uint32_t mu[MW];
 #pragma unroll
-      for (int i = 0; i < MG; ++i) {
-        const int o = g * MG + i;
-        msk[i] = (o < kMaxOut) ? all[o & (kMaxOut - 1)] : (uint16_t)0;
-      }
-      ring_mac<N, WORDS, MG>(acc, d, msk);
+      for (int x = 0; x < MW; ++x) mu[x] = __reduce_or_sync(0xFFFFFFFFu, lane == j ? rw[x] : 0u);
+      ring_mac<N, WORDS, MG, DISPATCH>(acc, d, mu);
     }
 
     // phi_E^{-1}: reduce mod the AOP and store the W field packets of every output.
@@ -249,7 +275,7 @@ __global__ void __launch_bounds__((NC + 1) * 32, 1) ring_staged_kernel(const __g
 }
 
 // Plain-load form for any packet size and alignment: one thread per byte column of one job, no
-// staging. The same ring arithmetic on byte-wide lanes.
+// staging. The same ring arithmetic on byte-wide lanes; all outputs per thread.
 template <int N>
 __global__ void __launch_bounds__(256) ring_plain_kernel(const __grid_constant__ JobDesc job) {
   constexpr int W = N - 1;
@@ -264,10 +290,9 @@ __global__ void __launch_bounds__(256) ring_plain_kernel(const __grid_constant__
       uint32_t d[W][1];
 #pragma unroll
       for (int q = 0; q < W; ++q) d[q][0] = job.in[j][(uint64_t)q * P + c];
-      uint16_t msk[kMaxOut];
-#pragma unroll
-      for (int i = 0; i < kMaxOut; ++i) msk[i] = job.mask[j][i];
-      ring_mac<N, 1, kMaxOut>(acc, d, msk);
+      const uint4 row = *reinterpret_cast<const uint4*>(&job.mask[j][0]);
+      const uint32_t mu[4] = {row.x, row.y, row.z, row.w};
+      ring_mac<N, 1, kMaxOut, 1>(acc, d, mu);
     }
 #pragma unroll
     for (int i = 0; i < kMaxOut; ++i) {
@@ -277,159 +302,6 @@ __global__ void __launch_bounds__(256) ring_plain_kernel(const __grid_constant__
       }
     }
   }
-}
-
-// ---------------------------------------------------------------------------------------------
-// Host side
-// ---------------------------------------------------------------------------------------------
-
-namespace {
-
-constexpr int kConsumerWarps = 8;
-constexpr int kMaxDevices = 64;
-
-int current_device() {
-  int d = 0;
-  cudaGetDevice(&d);
-  return d;
-}
-
-// Per-kernel, per-device one-time setup (shared-memory opt-in) and occupancy.
-struct KernelInfo {
-  std::once_flag once[kMaxDevices];
-  int max_smem_set[kMaxDevices];
-};
-
-template <int N, int WORDS, int MG>
-int launch_staged_t(const TileShape& sh, const CodeArgs& args, int grid, cudaStream_t st) {
-  auto kern = ring_staged_kernel<N, WORDS, MG, kConsumerWarps>;
-  static KernelInfo info;
-  const int dev = current_device();
-  if (dev < 0 || dev >= kMaxDevices) return PYRIT_E_CUDA;
-  std::call_once(info.once[dev], [&] {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-  });
-  const size_t smem = (size_t)sh.stages * (N - 1) * sh.tw + 2 * sh.stages * sizeof(uint64_t);
-  kern<<<grid, (kConsumerWarps + 1) * 32, smem, st>>>(args);
-  return cudaGetLastError() == cudaSuccess ? PYRIT_OK : PYRIT_E_CUDA;
-}
-
-template <int N, int WORDS, int MG>
-int occupancy_t(const TileShape& sh) {
-  auto kern = ring_staged_kernel<N, WORDS, MG, kConsumerWarps>;
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-  const size_t smem = (size_t)sh.stages * (N - 1) * sh.tw + 2 * sh.stages * sizeof(uint64_t);
-  int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, (kConsumerWarps + 1) * 32, smem) != cudaSuccess)
-    return 1;
-  return std::max(nb, 1);
-}
-
-// Outputs held per consumer warp, by ring size (register budget: MG * N * WORDS accumulators).
-constexpr int mg_for(int n) { return n <= 5 ? 8 : 4; }
-
-}  // namespace
-
-int sm_count() {
-  static int cache[kMaxDevices] = {0};
-  const int dev = current_device();
-  if (dev < 0 || dev >= kMaxDevices) return 1;
-  if (!cache[dev]) {
-    int v = 0;
-    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
-    cache[dev] = v > 0 ? v : 1;
-  }
-  return cache[dev];
-}
-
-int* device_error_word() {
-  static int* words[kMaxDevices] = {nullptr};
-  static std::mutex mu;
-  const int dev = current_device();
-  if (dev < 0 || dev >= kMaxDevices) return nullptr;
-  std::lock_guard<std::mutex> lk(mu);
-  if (!words[dev]) {
-    int* p = nullptr;
-    if (cudaMalloc(&p, 2 * sizeof(int)) != cudaSuccess) return nullptr;
-    if (cudaMemset(p, 0, 2 * sizeof(int)) != cudaSuccess) return nullptr;
-    words[dev] = p;
-  }
-  return words[dev];
-}
-
-bool job_is_staged(const JobDesc& j) {
-  if (j.P % 16 != 0) return false;
-  for (int i = 0; i < j.nin; ++i)
-    if (reinterpret_cast<uintptr_t>(j.in[i]) % 16 != 0) return false;
-  for (int i = 0; i < j.nout; ++i)
-    if (reinterpret_cast<uintptr_t>(j.out[i]) % 16 != 0) return false;
-  return true;
-}
-
-TileShape default_shape(int n, int max_nout, size_t P) {
-  (void)P;
-  TileShape s;
-  s.words = 2;
-  s.warps = kConsumerWarps;
-  const int mg = mg_for(n);
-  s.groups = std::max(1, std::min(kMaxOut / mg, (max_nout + mg - 1) / mg));
-  s.tw = (s.warps / s.groups) * 32 * 4 * s.words;
-  const int w = n - 1;
-  // Stage ring of about 96 KiB so that two CTAs share an SM.
-  s.stages = std::max(2, std::min(8, (96 * 1024) / (w * s.tw)));
-  s.ctas_per_sm = 0;
-  return s;
-}
-
-int launch_staged(int n, const TileShape& sh, const JobDesc* job0, const JobDesc* jobs_dev, const uint2* tiles_dev,
-                  uint32_t ntiles, uint32_t tiles_per_job, int grid_ctas, cudaStream_t stream) {
-  if (ntiles == 0) return PYRIT_OK;
-  CodeArgs a;
-  a.jobs = jobs_dev;
-  a.tiles = tiles_dev;
-  a.ntiles = ntiles;
-  a.tiles_per_job = tiles_per_job;
-  a.tw = (uint32_t)sh.tw;
-  a.groups = (uint32_t)sh.groups;
-  a.stages = (uint32_t)sh.stages;
-  a.err = device_error_word();
-  if (job0)
-    a.job0 = *job0;
-  else
-    memset(&a.job0, 0, sizeof(a.job0));
-  int occ = sh.ctas_per_sm;
-  if (occ <= 0) {
-    switch (n) {
-      case 3: occ = occupancy_t<3, 2, mg_for(3)>(sh); break;
-      case 5: occ = occupancy_t<5, 2, mg_for(5)>(sh); break;
-      case 11: occ = occupancy_t<11, 2, mg_for(11)>(sh); break;
-      case 13: occ = occupancy_t<13, 2, mg_for(13)>(sh); break;
-      default: return PYRIT_E_UNSUPPORTED_FIELD;
-    }
-  }
-  int grid = grid_ctas > 0 ? grid_ctas : sm_count() * occ;
-  grid = (int)std::min<uint32_t>((uint32_t)grid, ntiles);
-  switch (n) {
-    case 3: return launch_staged_t<3, 2, mg_for(3)>(sh, a, grid, stream);
-    case 5: return launch_staged_t<5, 2, mg_for(5)>(sh, a, grid, stream);
-    case 11: return launch_staged_t<11, 2, mg_for(11)>(sh, a, grid, stream);
-    case 13: return launch_staged_t<13, 2, mg_for(13)>(sh, a, grid, stream);
-    default: return PYRIT_E_UNSUPPORTED_FIELD;
-  }
-}
-
-int launch_plain(int n, const JobDesc& job, cudaStream_t stream) {
-  if (job.P == 0 || job.nout == 0) return PYRIT_OK;
-  const uint64_t blocks64 = (job.P + 255) / 256;
-  const int grid = (int)std::min<uint64_t>(blocks64, (uint64_t)sm_count() * 8);
-  switch (n) {
-    case 3: ring_plain_kernel<3><<<grid, 256, 0, stream>>>(job); break;
-    case 5: ring_plain_kernel<5><<<grid, 256, 0, stream>>>(job); break;
-    case 11: ring_plain_kernel<11><<<grid, 256, 0, stream>>>(job); break;
-    case 13: ring_plain_kernel<13><<<grid, 256, 0, stream>>>(job); break;
-    default: return PYRIT_E_UNSUPPORTED_FIELD;
-  }
-  return cudaGetLastError() == cudaSuccess ? PYRIT_OK : PYRIT_E_CUDA;
 }
 
 }  // namespace pyrit

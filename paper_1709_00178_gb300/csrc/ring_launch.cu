@@ -1,0 +1,201 @@
+// Host side of the ring kernels: variant registry, tile-shape choice, launches, the device error
+// word and the plain-load kernel's instantiations.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+
+#include "ring_kernel.cuh"
+
+namespace pyrit {
+
+const Variant* variants_small(int* count);
+const Variant* variants_n11(int* count);
+const Variant* variants_n13(int* count);
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+constexpr int kMaxVariants = 64;
+
+int current_device() {
+  int d = 0;
+  cudaGetDevice(&d);
+  return d;
+}
+
+struct Registry {
+  Variant all[kMaxVariants];
+  int count = 0;
+  Registry() {
+    const Variant* (*srcs[])(int*) = {variants_small, variants_n11, variants_n13};
+    for (auto f : srcs) {
+      int c = 0;
+      const Variant* t = f(&c);
+      for (int i = 0; i < c && count < kMaxVariants; ++i) all[count++] = t[i];
+    }
+  }
+};
+
+const Registry& registry() {
+  static Registry r;
+  return r;
+}
+
+// One-time per (variant, device) opt-in to the large dynamic shared-memory carve-out.
+std::mutex g_attr_mu;
+bool g_attr_done[kMaxVariants][kMaxDevices];
+
+int variant_index(const Variant* v) { return (int)(v - registry().all); }
+
+void ensure_attr(const Variant* v) {
+  const int dev = current_device();
+  const int vi = variant_index(v);
+  if (dev < 0 || dev >= kMaxDevices || vi < 0 || vi >= kMaxVariants) return;
+  std::lock_guard<std::mutex> lk(g_attr_mu);
+  if (!g_attr_done[vi][dev]) {
+    cudaFuncSetAttribute(v->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    g_attr_done[vi][dev] = true;
+  }
+}
+
+size_t smem_bytes(const TileShape& s) {
+  return (size_t)s.stages * (s.v->n - 1) * s.tw + 2 * (size_t)s.stages * sizeof(uint64_t);
+}
+
+int occupancy(const TileShape& s) {
+  ensure_attr(s.v);
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, s.v->fn, (kConsumerWarps + 1) * 32, smem_bytes(s)) !=
+      cudaSuccess)
+    return 1;
+  return std::max(nb, 1);
+}
+
+}  // namespace
+
+const Variant* variants(int* count) {
+  *count = registry().count;
+  return registry().all;
+}
+
+const Variant* find_variant(int n, int words, int dispatch, int mg, int minb) {
+  const Registry& r = registry();
+  const Variant* best = nullptr;
+  for (int i = 0; i < r.count; ++i) {
+    const Variant& v = r.all[i];
+    if (v.n != n || (words && v.words != words) || (dispatch >= 0 && v.dispatch != dispatch) || (mg && v.mg != mg) ||
+        (minb && v.minb != minb))
+      continue;
+    if (!best) best = &v;  // the first registered match is the preferred one
+  }
+  return best;
+}
+
+int sm_count() {
+  static int cache[kMaxDevices] = {0};
+  const int dev = current_device();
+  if (dev < 0 || dev >= kMaxDevices) return 1;
+  if (!cache[dev]) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    cache[dev] = v > 0 ? v : 1;
+  }
+  return cache[dev];
+}
+
+int* device_error_word() {
+  static int* words[kMaxDevices] = {nullptr};
+  static std::mutex mu;
+  const int dev = current_device();
+  if (dev < 0 || dev >= kMaxDevices) return nullptr;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!words[dev]) {
+    int* p = nullptr;
+    if (cudaMalloc(&p, 2 * sizeof(int)) != cudaSuccess) return nullptr;
+    if (cudaMemset(p, 0, 2 * sizeof(int)) != cudaSuccess) return nullptr;
+    words[dev] = p;
+  }
+  return words[dev];
+}
+
+bool job_is_staged(const JobDesc& j) {
+  if (j.P % 16 != 0) return false;
+  for (int i = 0; i < j.nin; ++i)
+    if (reinterpret_cast<uintptr_t>(j.in[i]) % 16 != 0) return false;
+  for (int i = 0; i < j.nout; ++i)
+    if (reinterpret_cast<uintptr_t>(j.out[i]) % 16 != 0) return false;
+  return true;
+}
+
+bool choose_shape(int n, int max_nout, const ShapeHint& h, TileShape* out) {
+  // Defaults: two 32-bit words per thread with uniform per-shift dispatch; the first registered
+  // variant of each ring size is the one measured fastest on its workload.
+  const int words = h.words ? h.words : 2;
+  const int dispatch = h.dispatch >= 0 ? h.dispatch : 0;
+  const Variant* v = find_variant(n, words, dispatch, h.mg, h.minb);
+  if (!v) v = find_variant(n, 0, -1, 0, 0);
+  if (!v) return false;
+  TileShape s;
+  s.v = v;
+  int groups = 1;
+  while (groups * v->mg < max_nout && groups < kConsumerWarps) groups *= 2;
+  s.groups = groups;
+  s.tw = (kConsumerWarps / groups) * 32 * 4 * v->words;
+  const int w = n - 1;
+  const int budget = (226 * 1024) / v->minb - 1024;  // shared memory per CTA at the target occupancy
+  s.stages = h.stages > 0 ? h.stages : std::max(2, std::min(8, budget / (w * s.tw)));
+  s.grid = 0;
+  if (h.ctas_per_sm > 0) s.grid = h.ctas_per_sm * sm_count();
+  *out = s;
+  return true;
+}
+
+void resolve_grid(TileShape* s) {
+  if (!s->v) return;
+  ensure_attr(s->v);
+  if (s->grid <= 0) s->grid = sm_count() * occupancy(*s);
+}
+
+int launch_staged(const TileShape& sh, const JobDesc* job0, const JobDesc* jobs_dev, const uint2* tiles_dev,
+                  uint32_t ntiles, uint32_t tiles_per_job, cudaStream_t stream) {
+  if (ntiles == 0) return PYRIT_OK;
+  if (!sh.v) return PYRIT_E_INVALID_ARG;
+  CodeArgs a;
+  a.jobs = jobs_dev;
+  a.tiles = tiles_dev;
+  a.ntiles = ntiles;
+  a.tiles_per_job = tiles_per_job;
+  a.tw = (uint32_t)sh.tw;
+  a.groups = (uint32_t)sh.groups;
+  a.stages = (uint32_t)sh.stages;
+  a.err = device_error_word();
+  if (job0)
+    a.job0 = *job0;
+  else
+    std::memset(&a.job0, 0, sizeof(a.job0));
+  ensure_attr(sh.v);
+  int grid = sh.grid > 0 ? sh.grid : sm_count() * occupancy(sh);
+  grid = (int)std::min<uint32_t>((uint32_t)grid, ntiles);
+  void* args[] = {&a};
+  const cudaError_t e = cudaLaunchKernel(sh.v->fn, dim3(grid), dim3((kConsumerWarps + 1) * 32), args, smem_bytes(sh),
+                                         stream);
+  return e == cudaSuccess ? PYRIT_OK : PYRIT_E_CUDA;
+}
+
+int launch_plain(int n, const JobDesc& job, cudaStream_t stream) {
+  if (job.P == 0 || job.nout == 0) return PYRIT_OK;
+  const uint64_t blocks64 = (job.P + 255) / 256;
+  const int grid = (int)std::min<uint64_t>(blocks64, (uint64_t)sm_count() * 8);
+  switch (n) {
+    case 3: ring_plain_kernel<3><<<grid, 256, 0, stream>>>(job); break;
+    case 5: ring_plain_kernel<5><<<grid, 256, 0, stream>>>(job); break;
+    case 11: ring_plain_kernel<11><<<grid, 256, 0, stream>>>(job); break;
+    case 13: ring_plain_kernel<13><<<grid, 256, 0, stream>>>(job); break;
+    default: return PYRIT_E_UNSUPPORTED_FIELD;
+  }
+  return cudaGetLastError() == cudaSuccess ? PYRIT_OK : PYRIT_E_CUDA;
+}
+
+}  // namespace pyrit

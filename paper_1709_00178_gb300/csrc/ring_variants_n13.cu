@@ -1,0 +1,7 @@
+// Staged ring-kernel variants for R_{2,13} (GF(2^12)).
+#include "ring_kernel.cuh"
+
+#define PYRIT_VARIANT_LIST(X) \
+  X(13, 2, 2, 2, 0) X(13, 2, 4, 1, 0) X(13, 2, 4, 1, 1) X(13, 1, 4, 2, 0) X(13, 1, 4, 2, 1) X(13, 1, 2, 3, 0)
+#define PYRIT_VARIANT_TABLE variants_n13
+#include "ring_variants.inc"

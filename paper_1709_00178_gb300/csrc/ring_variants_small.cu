@@ -1,0 +1,8 @@
+// Staged ring-kernel variants for the small rings R_{2,3} and R_{2,5} (GF(4), GF(16)).
+#include "ring_kernel.cuh"
+
+#define PYRIT_VARIANT_LIST(X) \
+  X(3, 2, 8, 2, 0) X(3, 1, 8, 3, 0) X(5, 2, 4, 2, 0) X(5, 2, 8, 1, 0) X(5, 1, 8, 2, 0) X(5, 1, 8, 3, 0) \
+      X(5, 1, 8, 3, 1)
+#define PYRIT_VARIANT_TABLE variants_small
+#include "ring_variants.inc"

@@ -185,3 +185,61 @@ def pyrit_device_status():
 
 def pyrit_synth_fill(dst, nbytes, seed, offset=0, stream=None):
     return _check(_lib.pyrit_synth_fill(_dev(dst), nbytes, seed, offset, _stream(stream)), "pyrit_synth_fill")
+
+
+# ---- batches ------------------------------------------------------------------------------------
+
+class pyrit_stripe_t(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_void_p), ("op", ctypes.c_int), ("erasures", ctypes.c_uint64),
+                ("packet_bytes", ctypes.c_size_t), ("blocks", ctypes.POINTER(ctypes.c_void_p))]
+
+
+class pyrit_tile_t(ctypes.Structure):
+    _fields_ = [("words", ctypes.c_int), ("mg", ctypes.c_int), ("minb", ctypes.c_int), ("dispatch", ctypes.c_int),
+                ("stages", ctypes.c_int), ("ctas_per_sm", ctypes.c_int)]
+
+
+_BATCH_SIGS = {
+    "pyrit_batch_create": (_i, [ctypes.POINTER(pyrit_stripe_t), _i, ctypes.POINTER(pyrit_tile_t),
+                                ctypes.POINTER(_vp)]),
+    "pyrit_batch_run": (_i, [_vp, _vp, _i]),
+    "pyrit_batch_stats": (_i, [_vp, _vp, _vp, _vp, _vp]),
+    "pyrit_batch_destroy": (None, [_vp]),
+}
+_bind(_BATCH_SIGS)
+EXPORTS = EXPORTS + tuple(_BATCH_SIGS)
+
+
+def pyrit_batch_create(stripes, tile=None):
+    """stripes: list of (plan, op, erasures, P, block_ptrs[k+m]); tile: None or dict of overrides
+    (words, mg, minb, dispatch, stages, ctas_per_sm). Returns an opaque batch handle."""
+    arr = (pyrit_stripe_t * max(1, len(stripes)))()
+    keep = []
+    for i, (plan, op, er, P, blocks) in enumerate(stripes):
+        ba = _ptr_array(blocks)
+        keep.append(ba)
+        arr[i] = pyrit_stripe_t(plan, op, er, P, ctypes.cast(ba, ctypes.POINTER(ctypes.c_void_p)))
+    t = None
+    if tile is not None:
+        t = pyrit_tile_t(tile.get("words", 0), tile.get("mg", 0), tile.get("minb", 0), tile.get("dispatch", -1),
+                         tile.get("stages", 0), tile.get("ctas_per_sm", 0))
+    h = ctypes.c_void_p()
+    _check(_lib.pyrit_batch_create(arr, len(stripes), ctypes.byref(t) if t is not None else None, ctypes.byref(h)),
+           "pyrit_batch_create")
+    return h.value
+
+
+def pyrit_batch_run(batch, stream=None, graph=False):
+    return _check(_lib.pyrit_batch_run(batch, _stream(stream), 1 if graph else 0), "pyrit_batch_run")
+
+
+def pyrit_batch_stats(batch):
+    a, s, t = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+    n = ctypes.c_int()
+    _check(_lib.pyrit_batch_stats(batch, ctypes.byref(a), ctypes.byref(s), ctypes.byref(n), ctypes.byref(t)),
+           "pyrit_batch_stats")
+    return {"alg_bytes": a.value, "src_bytes": s.value, "launches": n.value, "tiles": t.value}
+
+
+def pyrit_batch_destroy(batch):
+    _lib.pyrit_batch_destroy(batch)

@@ -1,0 +1,172 @@
+"""GPU parity of the batched path: many stripes of mixed codes, operations and packet sizes in one
+persistent launch per ring size (optionally replayed from a CUDA graph), each stripe compared bit
+for bit with the CPU oracle; every compiled kernel variant must give identical bytes."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1709_00178_gb300.synth import synth_bytes
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+NCPU = os.cpu_count() or 4
+
+
+@pytest.fixture(scope="module")
+def pyrit():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1709_00178_gb300 import pyrit as p
+    return p
+
+
+class Pool:
+    """Device stripes carved from one buffer, with host copies of their expected contents."""
+
+    def __init__(self, specs, seed):
+        # specs: list of (w, k, m, P)
+        self.specs = specs
+        self.offs = []
+        total = 0
+        for (w, k, m, P) in specs:
+            self.offs.append(total)
+            total += ((k + m) * w * P + 255) // 256 * 256
+        self.buf = torch.zeros(total, dtype=torch.uint8, device="cuda")
+        self.seed = seed
+
+    def blocks(self, i):
+        w, k, m, P = self.specs[i]
+        base = self.buf.data_ptr() + self.offs[i]
+        return [base + e * w * P for e in range(k + m)]
+
+    def host(self, i):
+        w, k, m, P = self.specs[i]
+        torch.cuda.synchronize()
+        n = (k + m) * w * P
+        return self.buf[self.offs[i]:self.offs[i] + n].cpu().numpy().reshape(k + m, w, P)
+
+    def put(self, i, arr):
+        w, k, m, P = self.specs[i]
+        n = (k + m) * w * P
+        self.buf[self.offs[i]:self.offs[i] + n].copy_(torch.from_numpy(np.ascontiguousarray(arr).reshape(-1)).cuda())
+
+
+MIXED = [(4, 4, 2, 4096), (10, 10, 4, 8192), (12, 16, 4, 2048 + 16), (10, 20, 6, 1024), (12, 32, 8, 512),
+         (4, 12, 4, 1000), (2, 2, 2, 64), (12, 8, 3, 3000 + 16), (10, 4, 8, 4096 + 32), (4, 8, 8, 17)]
+
+
+def _plans(pyrit, specs):
+    plans = {}
+    for (w, k, m, P) in specs:
+        if (w, k, m) not in plans:
+            plans[(w, k, m)] = pyrit.pyrit_plan_create(w, w + 1, k, m)
+    return plans
+
+
+def test_mixed_batch_encode_then_decode(pyrit):
+    pool = Pool(MIXED, 7)
+    plans = _plans(pyrit, MIXED)
+    try:
+        full = []
+        for i, (w, k, m, P) in enumerate(MIXED):
+            data = synth_bytes(100 + i, 0, k * w * P).reshape(k, w, P)
+            arr = np.zeros((k + m, w, P), np.uint8)
+            arr[:k] = data
+            pool.put(i, arr)
+            G = pyrit.pyrit_plan_generator(plans[(w, k, m)])
+            full.append(np.concatenate([data, oracle.encode(w, k, m, G, data, nthreads=NCPU)]))
+        enc = [(plans[(w, k, m)], pyrit.PYRIT_OP_ENCODE, 0, P, pool.blocks(i)) for i, (w, k, m, P) in enumerate(MIXED)]
+        b = pyrit.pyrit_batch_create(enc)
+        st = pyrit.pyrit_batch_stats(b)
+        assert st["alg_bytes"] == sum((k + m) * w * P for (w, k, m, P) in MIXED)
+        pyrit.pyrit_batch_run(b)
+        for i in range(len(MIXED)):
+            assert np.array_equal(pool.host(i), full[i]), MIXED[i]
+        pyrit.pyrit_batch_destroy(b)
+        # decode: random patterns per stripe, erased blocks scrambled first
+        rng = np.random.default_rng(5)
+        dec = []
+        for i, (w, k, m, P) in enumerate(MIXED):
+            e = int(rng.integers(1, m + 1))
+            pat = sum(1 << int(x) for x in rng.choice(k + m, e, replace=False))
+            arr = full[i].copy()
+            for x in range(k + m):
+                if (pat >> x) & 1:
+                    arr[x] ^= 0x3C
+            pool.put(i, arr)
+            dec.append((plans[(w, k, m)], pyrit.PYRIT_OP_DECODE, pat, P, pool.blocks(i)))
+        b = pyrit.pyrit_batch_create(dec)
+        pyrit.pyrit_batch_run(b, graph=True)
+        for i in range(len(MIXED)):
+            assert np.array_equal(pool.host(i), full[i]), MIXED[i]
+        pyrit.pyrit_batch_destroy(b)
+        assert pyrit.pyrit_device_status() == (0, 0)
+    finally:
+        for p in plans.values():
+            pyrit.pyrit_plan_destroy(p)
+
+
+TILES = [None, dict(words=1, mg=4, minb=2, dispatch=0), dict(words=1, mg=4, minb=2, dispatch=1),
+         dict(words=2, mg=2, minb=2, dispatch=0), dict(words=2, mg=4, minb=1, dispatch=0),
+         dict(words=1, mg=4, minb=3, dispatch=0), dict(words=1, mg=2, minb=3, dispatch=0),
+         dict(words=2, mg=8, minb=1, dispatch=0), dict(words=1, mg=8, minb=3, dispatch=1),
+         dict(stages=2), dict(stages=7, ctas_per_sm=1)]
+
+
+@pytest.mark.parametrize("w,k,m,P,S", [(10, 10, 4, 4096 + 48, 6), (12, 16, 4, 2048, 5), (4, 4, 2, 8192, 4)])
+def test_every_variant_is_bit_exact(pyrit, w, k, m, P, S):
+    specs = [(w, k, m, P)] * S
+    pool = Pool(specs, 3)
+    plan = pyrit.pyrit_plan_create(w, w + 1, k, m)
+    try:
+        G = pyrit.pyrit_plan_generator(plan)
+        full = []
+        for i in range(S):
+            data = synth_bytes(300 + i, 0, k * w * P).reshape(k, w, P)
+            full.append(np.concatenate([data, oracle.encode(w, k, m, G, data, nthreads=NCPU)]))
+        rng = np.random.default_rng(w)
+        pats = [sum(1 << int(x) for x in rng.choice(k + m, m, replace=False)) for _ in range(S)]
+        for t in TILES:
+            for i in range(S):
+                arr = full[i].copy()
+                arr[k:] = 0
+                pool.put(i, arr)
+            b = pyrit.pyrit_batch_create([(plan, 0, 0, P, pool.blocks(i)) for i in range(S)], t)
+            pyrit.pyrit_batch_run(b)
+            pyrit.pyrit_batch_destroy(b)
+            for i in range(S):
+                assert np.array_equal(pool.host(i), full[i]), ("encode", t)
+                arr = full[i].copy()
+                for x in range(k + m):
+                    if (pats[i] >> x) & 1:
+                        arr[x] = 0xEE
+                pool.put(i, arr)
+            b = pyrit.pyrit_batch_create([(plan, 1, pats[i], P, pool.blocks(i)) for i in range(S)], t)
+            pyrit.pyrit_batch_run(b)
+            pyrit.pyrit_batch_destroy(b)
+            for i in range(S):
+                assert np.array_equal(pool.host(i), full[i]), ("decode", t)
+        assert pyrit.pyrit_device_status() == (0, 0)
+    finally:
+        pyrit.pyrit_plan_destroy(plan)
+
+
+def test_batch_rejects_bad_stripes(pyrit):
+    plan = pyrit.pyrit_plan_create(4, 5, 4, 2)
+    try:
+        fake = [256 * (i + 1) for i in range(6)]
+        for bad, code in [((plan, 1, 0b111, 64, fake), pyrit.PYRIT_E_TOO_MANY_ERASURES),
+                          ((plan, 2, 0, 64, fake), pyrit.PYRIT_E_INVALID_ARG),
+                          ((plan, 0, 0, 0, fake), pyrit.PYRIT_E_INVALID_ARG),
+                          ((plan, 0, 0, 64, fake[:5] + [0]), pyrit.PYRIT_E_INVALID_ARG)]:
+            with pytest.raises(pyrit.PyritError) as ei:
+                pyrit.pyrit_batch_create([bad])
+            assert ei.value.status == code
+        # an empty batch and a batch of no-op decodes are valid and launch nothing
+        b = pyrit.pyrit_batch_create([])
+        assert pyrit.pyrit_batch_stats(b)["launches"] == 0
+        pyrit.pyrit_batch_run(b)
+        pyrit.pyrit_batch_destroy(b)
+    finally:
+        pyrit.pyrit_plan_destroy(plan)
