@@ -63,6 +63,8 @@ typedef struct CUstream_st* pyrit_stream_t;
 #define PYRIT_E_BUDGET -8             /* server: request larger than the admission budget      */
 #define PYRIT_E_TIMEOUT -9            /* a bounded device or host wait gave up                  */
 #define PYRIT_E_BUSY -10              /* server: request queue full, retry later               */
+#define PYRIT_E_SCRATCH_LIMIT -11     /* more stripes or tiles than pyrit_code_stripes_noalloc's
+                                         fixed scratch holds                                     */
 
 /* Limits of this build. */
 #define PYRIT_MAX_K 32 /* data blocks per stripe                   */
@@ -192,6 +194,35 @@ PYRIT_API int pyrit_batch_stats(pyrit_batch_t batch, uint64_t* alg_bytes, uint64
 
 /* Frees the batch's device memory and graph (synchronises the device). */
 PYRIT_API void pyrit_batch_destroy(pyrit_batch_t batch);
+
+/* ---- coding without device allocation --------------------------------------------------- */
+
+#define PYRIT_NOALLOC_MAX_STRIPES 256  /* stripes per call                                       */
+#define PYRIT_NOALLOC_MAX_TILES 16384  /* column tiles per call (about P / 1 KiB per stripe)     */
+
+/* Codes up to PYRIT_NOALLOC_MAX_STRIPES stripes (each encode or decode, as in pyrit_batch_create)
+ * without allocating any device memory. The paper has no counterpart: this exists for callers that
+ * cannot call cudaMalloc -- an I/O path whose device memory is wholly reserved by another allocator
+ * (a framework's caching pool or a pre-sized arena, where cudaMalloc fails or eats into that pool),
+ * or a latency-bound path that cannot take cudaMalloc's implicit device synchronisation.
+ *
+ * Scratch. The job descriptors, the tile list and two status words live in one fixed file-scope
+ * device array of 340 KiB (256 + PYRIT_NOALLOC_MAX_STRIPES * 848 + PYRIT_NOALLOC_MAX_TILES * 8
+ * bytes) inside the library's module image: every GPU that loads the library holds it until the
+ * process exits. The caller passes every input and output buffer; no cudaMalloc, cudaFree or other
+ * allocating routine is called (on the host, a decoding matrix for an erasure pattern that a plan has
+ * not seen is computed and kept in the plan's cache, as pyrit_decode does).
+ * Set-up. The first call on each device, with that device current, looks up the array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Sharing. Every call reuses the same array, which keeps the last call's contents; each call clears
+ * the status words and rewrites the descriptors on `stream` before its launches. Calls whose work
+ * overlaps on the GPU (for example on two streams at once) race on the array: order them on one
+ * stream or wait between them. Host callers are serialised by a lock.
+ * Errors. More than PYRIT_NOALLOC_MAX_STRIPES stripes or PYRIT_NOALLOC_MAX_TILES tiles returns
+ * PYRIT_E_SCRATCH_LIMIT before any device work; invalid stripes return the codes of
+ * pyrit_batch_create. A device-side bounded wait that gives up is recorded in the array's status
+ * words and is not reported by this call. Asynchronous on `stream` otherwise. */
+PYRIT_API int pyrit_code_stripes_noalloc(const pyrit_stripe_t* stripes, int count, pyrit_stream_t stream);
 
 /* ---- device status ----------------------------------------------------------------------- */
 

@@ -209,6 +209,7 @@ const char* pyrit_strerror(int s) {
     case PYRIT_E_BUDGET: return "request exceeds the admission budget";
     case PYRIT_E_TIMEOUT: return "bounded wait timed out";
     case PYRIT_E_BUSY: return "queue full";
+    case PYRIT_E_SCRATCH_LIMIT: return "request exceeds the fixed scratch of the no-allocation entry point";
     default: return "unknown status";
   }
 }

@@ -32,6 +32,9 @@ PYRIT_E_OOM = -7
 PYRIT_E_BUDGET = -8
 PYRIT_E_TIMEOUT = -9
 PYRIT_E_BUSY = -10
+PYRIT_E_SCRATCH_LIMIT = -11
+PYRIT_NOALLOC_MAX_STRIPES = 256
+PYRIT_NOALLOC_MAX_TILES = 16384
 PYRIT_MAX_K = 32
 PYRIT_MAX_M = 8
 PYRIT_OP_ENCODE = 0
@@ -243,3 +246,22 @@ def pyrit_batch_stats(batch):
 
 def pyrit_batch_destroy(batch):
     _lib.pyrit_batch_destroy(batch)
+
+
+# ---- coding without device allocation ---------------------------------------------------------
+
+_NOALLOC_SIGS = {"pyrit_code_stripes_noalloc": (_i, [ctypes.POINTER(pyrit_stripe_t), _i, _vp])}
+_bind(_NOALLOC_SIGS)
+EXPORTS = EXPORTS + tuple(_NOALLOC_SIGS)
+
+
+def pyrit_code_stripes_noalloc(stripes, stream=None):
+    """Codes stripes (list of (plan, op, erasures, P, block_ptrs[k+m])) with the library's fixed
+    device scratch instead of any device allocation, for callers that cannot call cudaMalloc."""
+    arr = (pyrit_stripe_t * max(1, len(stripes)))()
+    keep = []
+    for i, (plan, op, er, P, blocks) in enumerate(stripes):
+        ba = _ptr_array(blocks)
+        keep.append(ba)
+        arr[i] = pyrit_stripe_t(plan, op, er, P, ctypes.cast(ba, ctypes.POINTER(ctypes.c_void_p)))
+    return _check(_lib.pyrit_code_stripes_noalloc(arr, len(stripes), _stream(stream)), "pyrit_code_stripes_noalloc")

@@ -1,0 +1,96 @@
+"""The no-allocation entry point against the batched entry point.
+
+pyrit_code_stripes_noalloc is for callers that cannot call cudaMalloc (their device memory is held
+by another allocator, or their request path cannot take cudaMalloc's device synchronisation): it
+keeps its scratch in a fixed device array instead. Here it is called through the C ABI twice in a
+row, on different stripe sets, and each result must equal, byte for byte (the tolerance of every
+coding test here), what pyrit_batch_create + pyrit_batch_run write for the same stripes.
+
+This file is named to be collected last, and it builds all of its own state, so it runs the same
+alone in a fresh process and after the other tests.
+"""
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pyrit():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1709_00178_gb300 import pyrit as p
+    return p
+
+
+def _layout(specs):
+    offs, total = [], 0
+    for (w, k, m, P, op, er) in specs:
+        offs.append(total)
+        total += ((k + m) * w * P + 255) // 256 * 256
+    return offs, total
+
+
+def _stripes(pyrit, plans, specs, base, offs):
+    out = []
+    for (w, k, m, P, op, er), o in zip(specs, offs):
+        blocks = [base + o + e * w * P for e in range(k + m)]
+        out.append((plans[(w, k, m)], op, er, P, blocks))
+    return out
+
+
+def _run_both(pyrit, plans, specs, seed):
+    offs, total = _layout(specs)
+    init = torch.empty(total, dtype=torch.uint8, device="cuda")
+    pyrit.pyrit_synth_fill(init.data_ptr(), total, seed)
+    ref = init.clone()
+    got = init.clone()
+    b = pyrit.pyrit_batch_create(_stripes(pyrit, plans, specs, ref.data_ptr(), offs))
+    pyrit.pyrit_batch_run(b)
+    torch.cuda.synchronize()
+    pyrit.pyrit_batch_destroy(b)
+    pyrit.pyrit_code_stripes_noalloc(_stripes(pyrit, plans, specs, got.data_ptr(), offs))
+    torch.cuda.synchronize()
+    assert not torch.equal(ref, init), "the reference did no work"
+    return ref, got
+
+
+def test_noalloc_matches_batched_entry_on_two_calls(pyrit):
+    D = pyrit.PYRIT_OP_DECODE
+    E = pyrit.PYRIT_OP_ENCODE
+    codes = [(10, 10, 4), (4, 4, 2), (12, 16, 4)]
+    plans = {c: pyrit.pyrit_plan_create(c[0], c[0] + 1, c[1], c[2]) for c in codes}
+    try:
+        # First call: encodes and decodes over three fields, ragged tiles and one odd packet size
+        # (plain-load kernel). The decode of a stripe whose other blocks are random bytes still has
+        # one defined output, which both entry points must produce.
+        first = [(10, 10, 4, 8192 + 16, E, 0)] * 4 + [(4, 4, 2, 4096, E, 0), (12, 16, 4, 2048, E, 0),
+                                                      (10, 10, 4, 1000, E, 0), (10, 10, 4, 4096, D, 0b1011),
+                                                      (4, 4, 2, 2048, D, 0b100001), (12, 16, 4, 1024, D, 0xF0000)]
+        ref, got = _run_both(pyrit, plans, first, 0xA11C)
+        assert torch.equal(ref, got), "first call differs from the batched entry point"
+        # Second call right after, on fewer and different stripes: the scratch still holds the first
+        # call's descriptors and must not leak into this result.
+        second = [(12, 16, 4, 4096 + 32, E, 0), (10, 10, 4, 2048, D, 0b11 << 10), (4, 4, 2, 64, E, 0)]
+        ref, got = _run_both(pyrit, plans, second, 0xB22D)
+        assert torch.equal(ref, got), "second call differs from the batched entry point"
+    finally:
+        for p in plans.values():
+            pyrit.pyrit_plan_destroy(p)
+
+
+def test_noalloc_rejects_more_than_its_scratch(pyrit):
+    plan = pyrit.pyrit_plan_create(4, 5, 4, 2)
+    try:
+        fake = [256 * (i + 1) for i in range(6)]
+        too_many = [(plan, pyrit.PYRIT_OP_ENCODE, 0, 64, fake)] * (pyrit.PYRIT_NOALLOC_MAX_STRIPES + 1)
+        with pytest.raises(pyrit.PyritError) as ei:
+            pyrit.pyrit_code_stripes_noalloc(too_many)
+        assert ei.value.status == pyrit.PYRIT_E_SCRATCH_LIMIT
+        # GF(16) stripes use 2 KiB tiles: 32 stripes of (1 MiB + 2 KiB) packets need 32 * 513 tiles,
+        # more than the scratch's tile list holds (checked before any device work)
+        big = [(plan, pyrit.PYRIT_OP_ENCODE, 0, (1 << 20) + 2048, fake)] * 32
+        with pytest.raises(pyrit.PyritError) as ei:
+            pyrit.pyrit_code_stripes_noalloc(big)
+        assert ei.value.status == pyrit.PYRIT_E_SCRATCH_LIMIT
+    finally:
+        pyrit.pyrit_plan_destroy(plan)
