@@ -165,6 +165,7 @@ typedef struct {
   int words;        /* 32-bit words per consumer thread per packet (1 or 2)              */
   int mg;           /* outputs accumulated per consumer warp (2, 4 or 8)                 */
   int minb;         /* CTAs per multiprocessor the kernel's registers are sized for      */
+  int nc;           /* consumer warps per CTA (8 or 16)                                  */
   int dispatch;     /* 0: uniform test per ring shift; 1: switch per set mask bit        */
   int stages;       /* shared-memory pipeline depth (2..8)                               */
   int ctas_per_sm;  /* persistent grid = multiprocessors x ctas_per_sm                   */

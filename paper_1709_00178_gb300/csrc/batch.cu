@@ -82,6 +82,7 @@ int pyrit_batch_create(const pyrit_stripe_t* stripes, int count, const pyrit_til
     hint.words = tile->words;
     hint.mg = tile->mg;
     hint.minb = tile->minb;
+    hint.nc = tile->nc;
     hint.dispatch = tile->dispatch;
     hint.stages = tile->stages;
     hint.ctas_per_sm = tile->ctas_per_sm;

@@ -145,10 +145,10 @@ extern "C" int pyrit_code_stripes_noalloc(const pyrit_stripe_t* stripes, int cou
     a.groups = (uint32_t)L.shape.groups;
     a.stages = (uint32_t)L.shape.stages;
     a.err = reinterpret_cast<int*>(scratch);
-    const size_t smem = (size_t)L.shape.stages * (L.shape.v->n - 1) * L.shape.tw + 2 * sizeof(uint64_t) * L.shape.stages;
+    const size_t smem = staged_smem_bytes(L.shape.stages, L.shape.v->n - 1, L.shape.tw);
     const int grid = (int)(L.ntiles < (uint32_t)L.shape.grid ? L.ntiles : (uint32_t)L.shape.grid);
     void* args[] = {&a};
-    if (cudaLaunchKernel(L.shape.v->fn, dim3(grid), dim3((kConsumerWarps + 1) * 32), args, smem, st) != cudaSuccess)
+    if (cudaLaunchKernel(L.shape.v->fn, dim3(grid), dim3((L.shape.v->nc + 1) * 32), args, smem, st) != cudaSuccess)
       return PYRIT_E_CUDA;
   }
   for (int i = 0; i < count; ++i)

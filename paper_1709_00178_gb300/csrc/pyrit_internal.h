@@ -28,6 +28,11 @@ struct alignas(16) JobDesc {
   int32_t nin, nout;
 };
 
+// Dynamic shared memory of the staged kernel: S stages of W packets x tw bytes and 2 S mbarriers.
+inline size_t staged_smem_bytes(int stages, int w, int tw) {
+  return (size_t)stages * w * tw + 2 * sizeof(uint64_t) * stages;
+}
+
 // Launch arguments of the staged ring kernel. Tiles are (job, column range [col0, col0 + tw)).
 // With tiles == nullptr every job has the same P and tiles_per_job = ceil(P / tw) tiles, tile t
 // covering job t / tiles_per_job.
@@ -49,7 +54,8 @@ struct Variant {
   int words;     // 32-bit words per consumer thread per packet
   int mg;        // outputs accumulated per consumer warp
   int minb;      // CTAs per SM the register budget is sized for
-  int dispatch;  // 0: uniform test per shift; 1: switch per set bit
+  int dispatch;  // 0: uniform test per shift; 1: switch per set bit; 2: pairing automaton
+  int nc;        // consumer warps per CTA (one more warp is the producer)
   const void* fn;
 };
 
@@ -68,6 +74,7 @@ struct ShapeHint {
   int dispatch = -1;
   int mg = 0;
   int minb = 0;
+  int nc = 0;
   int stages = 0;
   int ctas_per_sm = 0;
 };
@@ -109,7 +116,7 @@ void make_decode_job(const pyrit_plan_s* p, const DecodeEntry& e, void* const* b
 // ---- kernels (device launchers) --------------------------------------------------------------
 // Registered variants (all translation units).
 const Variant* variants(int* count);
-const Variant* find_variant(int n, int words, int dispatch, int mg, int minb);
+const Variant* find_variant(int n, int words, int dispatch, int mg, int minb, int nc);
 // True when every pointer of the job is 16-byte aligned and P is a multiple of 16.
 bool job_is_staged(const JobDesc& j);
 // Tile shape for ring size n, the largest output count of the launch's jobs and optional hints.

@@ -13,9 +13,9 @@
 // The extra ring packet is never written to memory, as in the paper's register scheme (Sec. 3).
 //
 // GB300 mapping (prior art: the paper's x86 SIMD register schedule). A CTA owns a column tile of
-// `tw` bytes of one job. One producer thread streams the job's source blocks, one block (W packets
-// x tw bytes) per pipeline stage, into a shared-memory ring with bulk asynchronous copies
-// (cp.async.bulk, completion counted on an mbarrier); NC consumer warps read their 4*WORDS bytes
+// `tw` bytes of one job. A producer warp streams the job's source blocks, one block (W packets
+// x tw bytes, one lane per packet) per pipeline stage, into a shared-memory ring with bulk
+// asynchronous copies (cp.async.bulk, completion counted on an mbarrier); NC consumer warps (8 or 16) read their 4*WORDS bytes
 // of every packet into registers and release the stage, then run the XOR network out of registers.
 // When a job has more outputs than one warp's accumulators hold (MG), the consumer warps split
 // into output groups that read the same staged tile, so every source byte leaves HBM once.
@@ -28,7 +28,6 @@
 
 namespace pyrit {
 
-constexpr int kConsumerWarps = 8;  // consumer warps per CTA (plus one producer warp)
 
 // acc += x^S * d in R_{2,N}: packet q of the embedded source lands in accumulator (q + S) mod N.
 template <int N, int WORDS, int S>
@@ -64,10 +63,34 @@ __device__ __forceinline__ void xor_rotated_dyn(uint32_t (&acc)[N][WORDS], const
   }
 }
 
+// acc += (x^S1 + x^S2) * d in R_{2,N} in one pass: accumulator t receives d[t - S1] ^ d[t - S2]
+// (one three-input XOR), or a single term where the other index is the zero packet d[N-1].
+template <int N, int WORDS, int S1, int S2>
+__device__ __forceinline__ void xor_pair(uint32_t (&acc)[N][WORDS], const uint32_t (&d)[N - 1][WORDS]) {
+  constexpr int W = N - 1;
+#pragma unroll
+  for (int t = 0; t < N; ++t) {
+    const int q1 = (t - S1 + N) % N, q2 = (t - S2 + N) % N;
+#pragma unroll
+    for (int x = 0; x < WORDS; ++x) {
+      if (q1 < W && q2 < W)
+        acc[t][x] ^= d[q1][x] ^ d[q2][x];
+      else if (q1 < W)
+        acc[t][x] ^= d[q1][x];
+      else if (q2 < W)
+        acc[t][x] ^= d[q2][x];
+    }
+  }
+}
+
+#include "ring_network.inc"
+
 // acc_i += r_ij * d for every output i of the group, one rotation per set bit of r_ij. The masks
 // arrive as warp-uniform 32-bit words (two 16-bit masks each), so every branch below is uniform.
 //   DISPATCH 0: one uniform test per shift S (static code per (i, S); no indirect jump).
 //   DISPATCH 1: iterate over the set bits and jump to the rotation's code through a switch.
+//   DISPATCH 2: the generated pairing automaton: consecutive set bits fused into one pass of
+//               three-input XORs, static forward branches only (ring_network.inc).
 template <int N, int WORDS, int MG, int DISPATCH>
 __device__ __forceinline__ void ring_mac(uint32_t (&acc)[MG][N][WORDS], const uint32_t (&d)[N - 1][WORDS],
                                          const uint32_t (&mu)[(MG + 1) / 2]) {
@@ -84,6 +107,8 @@ __device__ __forceinline__ void ring_mac(uint32_t (&acc)[MG][N][WORDS], const ui
             for (int x = 0; x < WORDS; ++x) acc[i][(q + s) % N][x] ^= d[q][x];
         }
       }
+    } else if constexpr (DISPATCH == 2) {
+      ring_mac_pairs<N, WORDS>(acc[i], d, m);
     } else {
       uint32_t r = m;
       while (r) {
@@ -118,12 +143,36 @@ template <>
 struct Vec<2> {
   using T = uint2;
 };
+template <>
+struct Vec<4> {
+  using T = uint4;
+};
 
-template <int N, int WORDS, int MG, int MINB, int DISPATCH>
-__global__ void __launch_bounds__((kConsumerWarps + 1) * 32, MINB)
-    ring_staged_kernel(const __grid_constant__ CodeArgs a) {
+// Word x of a 1-, 2- or 4-word vector, and the vector of WORDS words.
+template <int WORDS>
+__device__ __forceinline__ uint32_t vword(const typename Vec<WORDS>::T& v, int x) {
+  if constexpr (WORDS == 1) {
+    return v;
+  } else if constexpr (WORDS == 2) {
+    return x == 0 ? v.x : v.y;
+  } else {
+    return x == 0 ? v.x : x == 1 ? v.y : x == 2 ? v.z : v.w;
+  }
+}
+template <int WORDS>
+__device__ __forceinline__ typename Vec<WORDS>::T vmake(const uint32_t (&w)[WORDS]) {
+  if constexpr (WORDS == 1) {
+    return w[0];
+  } else if constexpr (WORDS == 2) {
+    return make_uint2(w[0], w[1]);
+  } else {
+    return make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
+template <int N, int WORDS, int MG, int MINB, int DISPATCH, int NC>
+__global__ void __launch_bounds__((NC + 1) * 32, MINB) ring_staged_kernel(const __grid_constant__ CodeArgs a) {
   constexpr int W = N - 1;
-  constexpr int NC = kConsumerWarps;
   constexpr int MW = (MG + 1) / 2;  // 32-bit mask words per source for MG outputs
   using V = typename Vec<WORDS>::T;
   extern __shared__ __align__(128) uint8_t smem[];
@@ -143,8 +192,9 @@ __global__ void __launch_bounds__((kConsumerWarps + 1) * 32, MINB)
   __syncthreads();
 
   if (warp == NC) {
-    // ---- producer: one thread streams source blocks into the stage ring -------------------
-    if (lane != 0) return;
+    // ---- producer warp: streams source blocks into the stage ring --------------------------
+    // Lane 0 waits for the stage to be free and arms its barrier with the stage's byte count;
+    // then lane q issues the bulk copy of packet q, so the W copies of a stage leave together.
     const uint64_t pol = l2_evict_first_policy();
     uint32_t stage = 0, phase = 0;
     uint64_t armed = 0;  // stages armed so far
@@ -156,15 +206,15 @@ __global__ void __launch_bounds__((kConsumerWarps + 1) * 32, MINB)
       const uint32_t width = (uint32_t)(P - col0 < (uint64_t)TW ? P - col0 : (uint64_t)TW);
       const int nin = J->nin;
       for (int j = 0; j < nin; ++j) {
-        if (!mbar_wait(&empty[stage], phase ^ 1u, a.err, 1)) {
-          ok = false;
-          break;
+        bool free_ok = true;
+        if (lane == 0) {
+          free_ok = mbar_wait(&empty[stage], phase ^ 1u, a.err, 1);
+          if (free_ok) mbar_arrive_expect_tx(&full[stage], (uint32_t)W * width);
         }
-        mbar_arrive_expect_tx(&full[stage], (uint32_t)W * width);
-        const uint8_t* src = J->in[j] + col0;
-        uint8_t* dst = buf + (size_t)stage * W * TW;
-#pragma unroll 1
-        for (int q = 0; q < W; ++q) bulk_load(dst + (size_t)q * TW, src + (size_t)q * P, width, &full[stage], pol);
+        ok = __all_sync(0xFFFFFFFFu, free_ok);  // also orders the arming before the copies
+        if (!ok) break;
+        if (lane < W)
+          bulk_load(buf + ((size_t)stage * W + lane) * TW, J->in[j] + col0 + (size_t)lane * P, width, &full[stage], pol);
         ++armed;
         if (++stage == S) {
           stage = 0;
@@ -172,13 +222,14 @@ __global__ void __launch_bounds__((kConsumerWarps + 1) * 32, MINB)
         }
       }
     }
-    // Drain: wait (bounded) until every copy this thread issued has landed, so that no bulk copy
+    // Drain: wait (bounded) until every copy this warp issued has landed, so that no bulk copy
     // is still writing shared memory when the CTA exits, on the normal and the error path alike.
-    for (uint32_t s = 0; s < S; ++s) {
-      if (armed <= s) break;
-      const uint64_t times = (armed - 1 - s) / S + 1;
-      mbar_wait(&full[s], (uint32_t)((times - 1) & 1u), a.err, 3);
-    }
+    if (lane == 0)
+      for (uint32_t s = 0; s < S; ++s) {
+        if (armed <= s) break;
+        const uint64_t times = (armed - 1 - s) / S + 1;
+        mbar_wait(&full[s], (uint32_t)((times - 1) & 1u), a.err, 3);
+      }
     return;
   }
 
@@ -201,10 +252,17 @@ __global__ void __launch_bounds__((kConsumerWarps + 1) * 32, MINB)
     {
       uint4 row = make_uint4(0u, 0u, 0u, 0u);
       if (lane < nin) row = *reinterpret_cast<const uint4*>(&J->mask[lane][0]);
+      if constexpr (MG == 1) {
+        // one output per warp: output g's mask is half (g & 1) of word g / 2
+        const int wi = g >> 1;
+        const uint32_t wv = wi == 0 ? row.x : wi == 1 ? row.y : wi == 2 ? row.z : row.w;
+        rw[0] = (wv >> (16 * (g & 1))) & 0xFFFFu;
+      } else {
 #pragma unroll
-      for (int x = 0; x < MW; ++x) {
-        const int idx = g * MW + x;
-        rw[x] = idx == 0 ? row.x : idx == 1 ? row.y : idx == 2 ? row.z : idx == 3 ? row.w : 0u;
+        for (int x = 0; x < MW; ++x) {
+          const int idx = g * MW + x;
+          rw[x] = idx == 0 ? row.x : idx == 1 ? row.y : idx == 2 ? row.z : idx == 3 ? row.w : 0u;
+        }
       }
     }
 
@@ -230,12 +288,8 @@ __global__ void __launch_bounds__((kConsumerWarps + 1) * 32, MINB)
         } else {
           v = V{};
         }
-        if constexpr (WORDS == 1) {
-          d[q][0] = v;
-        } else {
-          d[q][0] = v.x;
-          d[q][1] = v.y;
-        }
+#pragma unroll
+        for (int x = 0; x < WORDS; ++x) d[q][x] = vword<WORDS>(v, x);
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[stage]);
@@ -260,13 +314,10 @@ __global__ void __launch_bounds__((kConsumerWarps + 1) * 32, MINB)
           uint8_t* dst = J->out[o] + col0 + off;
 #pragma unroll
           for (int r = 0; r < W; ++r) {
-            V v;
-            if constexpr (WORDS == 1) {
-              v = acc[i][r][0] ^ acc[i][W][0];
-            } else {
-              v = make_uint2(acc[i][r][0] ^ acc[i][W][0], acc[i][r][1] ^ acc[i][W][1]);
-            }
-            *reinterpret_cast<V*>(dst + (size_t)r * P) = v;
+            uint32_t o4[WORDS];
+#pragma unroll
+            for (int x = 0; x < WORDS; ++x) o4[x] = acc[i][r][x] ^ acc[i][W][x];
+            *reinterpret_cast<V*>(dst + (size_t)r * P) = vmake<WORDS>(o4);
           }
         }
       }

@@ -60,14 +60,12 @@ void ensure_attr(const Variant* v) {
   }
 }
 
-size_t smem_bytes(const TileShape& s) {
-  return (size_t)s.stages * (s.v->n - 1) * s.tw + 2 * (size_t)s.stages * sizeof(uint64_t);
-}
+size_t smem_bytes(const TileShape& s) { return staged_smem_bytes(s.stages, s.v->n - 1, s.tw); }
 
 int occupancy(const TileShape& s) {
   ensure_attr(s.v);
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, s.v->fn, (kConsumerWarps + 1) * 32, smem_bytes(s)) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, s.v->fn, (s.v->nc + 1) * 32, smem_bytes(s)) !=
       cudaSuccess)
     return 1;
   return std::max(nb, 1);
@@ -80,13 +78,13 @@ const Variant* variants(int* count) {
   return registry().all;
 }
 
-const Variant* find_variant(int n, int words, int dispatch, int mg, int minb) {
+const Variant* find_variant(int n, int words, int dispatch, int mg, int minb, int nc) {
   const Registry& r = registry();
   const Variant* best = nullptr;
   for (int i = 0; i < r.count; ++i) {
     const Variant& v = r.all[i];
     if (v.n != n || (words && v.words != words) || (dispatch >= 0 && v.dispatch != dispatch) || (mg && v.mg != mg) ||
-        (minb && v.minb != minb))
+        (minb && v.minb != minb) || (nc && v.nc != nc))
       continue;
     if (!best) best = &v;  // the first registered match is the preferred one
   }
@@ -130,19 +128,19 @@ bool job_is_staged(const JobDesc& j) {
 }
 
 bool choose_shape(int n, int max_nout, const ShapeHint& h, TileShape* out) {
-  // Defaults: two 32-bit words per thread with uniform per-shift dispatch; the first registered
-  // variant of each ring size is the one measured fastest on its workload.
-  const int words = h.words ? h.words : 2;
-  const int dispatch = h.dispatch >= 0 ? h.dispatch : 0;
-  const Variant* v = find_variant(n, words, dispatch, h.mg, h.minb);
-  if (!v) v = find_variant(n, 0, -1, 0, 0);
+  // Default: the first registered variant of the ring size, the one measured fastest on its
+  // workload (hints narrow the choice).
+  const int words = h.words;
+  const int dispatch = h.dispatch;
+  const Variant* v = find_variant(n, words, dispatch, h.mg, h.minb, h.nc);
+  if (!v) v = find_variant(n, 0, -1, 0, 0, 0);
   if (!v) return false;
   TileShape s;
   s.v = v;
   int groups = 1;
-  while (groups * v->mg < max_nout && groups < kConsumerWarps) groups *= 2;
+  while (groups * v->mg < max_nout && groups < v->nc) groups *= 2;
   s.groups = groups;
-  s.tw = (kConsumerWarps / groups) * 32 * 4 * v->words;
+  s.tw = (v->nc / groups) * 32 * 4 * v->words;
   const int w = n - 1;
   const int budget = (226 * 1024) / v->minb - 1024;  // shared memory per CTA at the target occupancy
   s.stages = h.stages > 0 ? h.stages : std::max(2, std::min(8, budget / (w * s.tw)));
@@ -179,7 +177,7 @@ int launch_staged(const TileShape& sh, const JobDesc* job0, const JobDesc* jobs_
   int grid = sh.grid > 0 ? sh.grid : sm_count() * occupancy(sh);
   grid = (int)std::min<uint32_t>((uint32_t)grid, ntiles);
   void* args[] = {&a};
-  const cudaError_t e = cudaLaunchKernel(sh.v->fn, dim3(grid), dim3((kConsumerWarps + 1) * 32), args, smem_bytes(sh),
+  const cudaError_t e = cudaLaunchKernel(sh.v->fn, dim3(grid), dim3((sh.v->nc + 1) * 32), args, smem_bytes(sh),
                                          stream);
   return e == cudaSuccess ? PYRIT_OK : PYRIT_E_CUDA;
 }

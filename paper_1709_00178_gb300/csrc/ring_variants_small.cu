@@ -2,7 +2,7 @@
 #include "ring_kernel.cuh"
 
 #define PYRIT_VARIANT_LIST(X) \
-  X(3, 2, 8, 2, 0) X(3, 1, 8, 3, 0) X(5, 2, 4, 2, 0) X(5, 2, 8, 1, 0) X(5, 1, 8, 2, 0) X(5, 1, 8, 3, 0) \
-      X(5, 1, 8, 3, 1)
+  X(3, 2, 8, 2, 0, 8) X(3, 1, 4, 2, 0, 16) X(5, 2, 4, 2, 0, 8) X(5, 1, 2, 2, 0, 16) X(5, 1, 4, 2, 0, 16) \
+      X(5, 1, 2, 4, 0, 8) X(5, 2, 4, 1, 0, 16) X(5, 2, 8, 1, 0, 8)
 #define PYRIT_VARIANT_TABLE variants_small
 #include "ring_variants.inc"

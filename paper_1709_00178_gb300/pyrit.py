@@ -198,8 +198,8 @@ class pyrit_stripe_t(ctypes.Structure):
 
 
 class pyrit_tile_t(ctypes.Structure):
-    _fields_ = [("words", ctypes.c_int), ("mg", ctypes.c_int), ("minb", ctypes.c_int), ("dispatch", ctypes.c_int),
-                ("stages", ctypes.c_int), ("ctas_per_sm", ctypes.c_int)]
+    _fields_ = [("words", ctypes.c_int), ("mg", ctypes.c_int), ("minb", ctypes.c_int), ("nc", ctypes.c_int),
+                ("dispatch", ctypes.c_int), ("stages", ctypes.c_int), ("ctas_per_sm", ctypes.c_int)]
 
 
 _BATCH_SIGS = {
@@ -215,7 +215,7 @@ EXPORTS = EXPORTS + tuple(_BATCH_SIGS)
 
 def pyrit_batch_create(stripes, tile=None):
     """stripes: list of (plan, op, erasures, P, block_ptrs[k+m]); tile: None or dict of overrides
-    (words, mg, minb, dispatch, stages, ctas_per_sm). Returns an opaque batch handle."""
+    (words, mg, minb, nc, dispatch, stages, ctas_per_sm). Returns an opaque batch handle."""
     arr = (pyrit_stripe_t * max(1, len(stripes)))()
     keep = []
     for i, (plan, op, er, P, blocks) in enumerate(stripes):
@@ -224,8 +224,8 @@ def pyrit_batch_create(stripes, tile=None):
         arr[i] = pyrit_stripe_t(plan, op, er, P, ctypes.cast(ba, ctypes.POINTER(ctypes.c_void_p)))
     t = None
     if tile is not None:
-        t = pyrit_tile_t(tile.get("words", 0), tile.get("mg", 0), tile.get("minb", 0), tile.get("dispatch", -1),
-                         tile.get("stages", 0), tile.get("ctas_per_sm", 0))
+        t = pyrit_tile_t(tile.get("words", 0), tile.get("mg", 0), tile.get("minb", 0), tile.get("nc", 0),
+                         tile.get("dispatch", -1), tile.get("stages", 0), tile.get("ctas_per_sm", 0))
     h = ctypes.c_void_p()
     _check(_lib.pyrit_batch_create(arr, len(stripes), ctypes.byref(t) if t is not None else None, ctypes.byref(h)),
            "pyrit_batch_create")

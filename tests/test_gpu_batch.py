@@ -107,11 +107,14 @@ def test_mixed_batch_encode_then_decode(pyrit):
             pyrit.pyrit_plan_destroy(p)
 
 
-TILES = [None, dict(words=1, mg=4, minb=2, dispatch=0), dict(words=1, mg=4, minb=2, dispatch=1),
-         dict(words=2, mg=2, minb=2, dispatch=0), dict(words=2, mg=4, minb=1, dispatch=0),
-         dict(words=1, mg=4, minb=3, dispatch=0), dict(words=1, mg=2, minb=3, dispatch=0),
-         dict(words=2, mg=8, minb=1, dispatch=0), dict(words=1, mg=8, minb=3, dispatch=1),
-         dict(stages=2), dict(stages=7, ctas_per_sm=1)]
+# Every registered variant shape (hints that match no variant of a ring size fall back to its default).
+TILES = [None, dict(stages=2), dict(stages=7, ctas_per_sm=1),
+         dict(words=2, mg=2, minb=1, nc=16, dispatch=0), dict(words=1, mg=2, minb=2, nc=16),
+         dict(words=1, mg=2, minb=4, nc=8), dict(words=2, mg=1, minb=3, nc=8), dict(words=1, mg=2, minb=3, nc=8),
+         dict(words=1, mg=2, minb=1, nc=24), dict(words=2, mg=2, minb=1, nc=16, dispatch=2),
+         dict(words=2, mg=2, minb=2, nc=8), dict(words=1, mg=4, minb=2, nc=8), dict(words=2, mg=4, minb=2, nc=8),
+         dict(words=1, mg=4, minb=2, nc=16), dict(words=2, mg=4, minb=1, nc=16), dict(words=2, mg=8, minb=1, nc=8),
+         dict(words=2, mg=8, minb=2, nc=8), dict(words=1, mg=4, minb=2, nc=16)]
 
 
 @pytest.mark.parametrize("w,k,m,P,S", [(10, 10, 4, 4096 + 48, 6), (12, 16, 4, 2048, 5), (4, 4, 2, 8192, 4)])
@@ -154,12 +157,14 @@ def test_every_variant_is_bit_exact(pyrit, w, k, m, P, S):
 
 def test_batch_rejects_bad_stripes(pyrit):
     plan = pyrit.pyrit_plan_create(4, 5, 4, 2)
+    # real device blocks, so that a request that slipped through validation could not fault
+    mem = torch.zeros(6 * 4 * 64, dtype=torch.uint8, device="cuda")
     try:
-        fake = [256 * (i + 1) for i in range(6)]
-        for bad, code in [((plan, 1, 0b111, 64, fake), pyrit.PYRIT_E_TOO_MANY_ERASURES),
-                          ((plan, 2, 0, 64, fake), pyrit.PYRIT_E_INVALID_ARG),
-                          ((plan, 0, 0, 0, fake), pyrit.PYRIT_E_INVALID_ARG),
-                          ((plan, 0, 0, 64, fake[:5] + [0]), pyrit.PYRIT_E_INVALID_ARG)]:
+        blocks = [mem.data_ptr() + e * 4 * 64 for e in range(6)]
+        for bad, code in [((plan, 1, 0b111, 64, blocks), pyrit.PYRIT_E_TOO_MANY_ERASURES),
+                          ((plan, 2, 0, 64, blocks), pyrit.PYRIT_E_INVALID_ARG),
+                          ((plan, 0, 0, 0, blocks), pyrit.PYRIT_E_INVALID_ARG),
+                          ((plan, 0, 0, 64, blocks[:5] + [0]), pyrit.PYRIT_E_INVALID_ARG)]:
             with pytest.raises(pyrit.PyritError) as ei:
                 pyrit.pyrit_batch_create([bad])
             assert ei.value.status == code

@@ -79,18 +79,26 @@ def test_noalloc_matches_batched_entry_on_two_calls(pyrit):
 
 
 def test_noalloc_rejects_more_than_its_scratch(pyrit):
-    plan = pyrit.pyrit_plan_create(4, 5, 4, 2)
+    # Every stripe points into one real device buffer, so that even a call that failed to reject
+    # would only touch valid memory. Both requests must be refused before any device work.
+    w, k, m, P = 4, 4, 2, 64 << 20
+    plan = pyrit.pyrit_plan_create(w, w + 1, k, m)
+    buf = torch.zeros((k + m) * w * P, dtype=torch.uint8, device="cuda")
     try:
-        fake = [256 * (i + 1) for i in range(6)]
-        too_many = [(plan, pyrit.PYRIT_OP_ENCODE, 0, 64, fake)] * (pyrit.PYRIT_NOALLOC_MAX_STRIPES + 1)
+        before = buf[:4096].clone()
+        blocks = [buf.data_ptr() + e * w * P for e in range(k + m)]
+        too_many = [(plan, pyrit.PYRIT_OP_ENCODE, 0, 64, blocks)] * (pyrit.PYRIT_NOALLOC_MAX_STRIPES + 1)
         with pytest.raises(pyrit.PyritError) as ei:
             pyrit.pyrit_code_stripes_noalloc(too_many)
         assert ei.value.status == pyrit.PYRIT_E_SCRATCH_LIMIT
-        # GF(16) stripes use 2 KiB tiles: 32 stripes of (1 MiB + 2 KiB) packets need 32 * 513 tiles,
-        # more than the scratch's tile list holds (checked before any device work)
-        big = [(plan, pyrit.PYRIT_OP_ENCODE, 0, (1 << 20) + 2048, fake)] * 32
+        # 32 stripes of 64 MiB packets: at least 32 * 1024 column tiles for any tile width up to
+        # 64 KiB, more than the scratch's tile list holds
+        big = [(plan, pyrit.PYRIT_OP_ENCODE, 0, P, blocks)] * 32
         with pytest.raises(pyrit.PyritError) as ei:
             pyrit.pyrit_code_stripes_noalloc(big)
         assert ei.value.status == pyrit.PYRIT_E_SCRATCH_LIMIT
+        torch.cuda.synchronize()
+        assert torch.equal(buf[:4096], before)
     finally:
         pyrit.pyrit_plan_destroy(plan)
+        del buf
