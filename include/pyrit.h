@@ -187,6 +187,23 @@ PYRIT_API int pyrit_batch_create(const pyrit_stripe_t* stripes, int count, const
  * captured once into a CUDA graph on first use and replayed from then on. */
 PYRIT_API int pyrit_batch_run(pyrit_batch_t batch, pyrit_stream_t stream, int graph);
 
+/* Autotunes the batch: for every launch group, times each compiled kernel variant of its ring size
+ * (one warm-up and `iters` timed launches of the real work, on `stream`; coding is idempotent, so
+ * the caller's outputs end up as one run leaves them) and keeps the fastest shape. The choice is
+ * recorded in the process-wide tuning table, keyed by ring size, shared-or-mixed masks, output
+ * count and packet-size class, which later pyrit_batch_create calls without tile overrides use.
+ * Synchronises `stream`; drops a captured graph. */
+PYRIT_API int pyrit_batch_tune(pyrit_batch_t batch, pyrit_stream_t stream, int iters);
+
+/* Saves / loads the tuning table as JSON (one object per key). Load returns the number of entries
+ * read (>= 0) or a negative status. */
+PYRIT_API int pyrit_tune_save(const char* path);
+PYRIT_API int pyrit_tune_load(const char* path);
+
+/* The compiled kernel variants, for introspection and tuning: writes up to `cap` rows of six ints
+ * (n, words, mg, minb, dispatch, nc) into params_out (host) and returns the total count. */
+PYRIT_API int pyrit_variants(int* params_out, int cap);
+
 /* Algorithmic HBM bytes of one run ((k + m) * w * P per encoded stripe, (k + e) * w * P per
  * decoded stripe with e erasures), source bytes (k * w * P per stripe), launches per run and
  * column tiles. Any pointer may be NULL. */

@@ -16,10 +16,47 @@ namespace {
 
 struct Group {
   TileShape shape;
-  size_t jobs_off = 0, tiles_off = 0;  // offsets into the batch's device allocation
+  size_t jobs_off = 0;           // offset of the group's jobs in the batch's device allocation
+  std::vector<uint64_t> job_P;   // packet size of every job (the tiling depends on the tile width)
+  uint2* tiles_dev = nullptr;    // explicit tile list when the jobs' P differ (own allocation)
   uint32_t njobs = 0, ntiles = 0, tiles_per_job = 0;
-  bool explicit_tiles = false;
+  int max_nout = 0;
+  TuneKey key;
 };
+
+// Tiling of a group's jobs under a shape: with one P for all jobs, tile t covers job
+// t / tiles_per_job; otherwise an explicit list {job, col0} is built and copied to the device.
+int make_tiling(const Group& g, const TileShape& sh, uint2** tiles_dev, uint32_t* ntiles, uint32_t* tpj) {
+  *tiles_dev = nullptr;
+  bool same = true;
+  for (uint64_t P : g.job_P) same = same && P == g.job_P[0];
+  if (same) {
+    *tpj = tiles_for(g.job_P[0], sh);
+    *ntiles = *tpj * g.njobs;
+    return PYRIT_OK;
+  }
+  std::vector<uint2> tl;
+  for (uint32_t ji = 0; ji < g.njobs; ++ji)
+    for (uint64_t c = 0; c < g.job_P[ji]; c += (uint64_t)sh.tw) tl.push_back(make_uint2(ji, (uint32_t)c));
+  *tpj = 0;
+  *ntiles = (uint32_t)tl.size();
+  if (cudaMalloc(tiles_dev, tl.size() * sizeof(uint2)) != cudaSuccess) return PYRIT_E_OOM;
+  if (cudaMemcpy(*tiles_dev, tl.data(), tl.size() * sizeof(uint2), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(*tiles_dev);
+    *tiles_dev = nullptr;
+    return PYRIT_E_CUDA;
+  }
+  return PYRIT_OK;
+}
+
+int log2_floor(uint64_t v) {
+  int r = -1;
+  while (v) {
+    v >>= 1;
+    ++r;
+  }
+  return r;
+}
 
 }  // namespace
 
@@ -59,8 +96,7 @@ int build_job(const pyrit_stripe_t& s, JobDesc* job, uint64_t* alg, uint64_t* sr
 int enqueue(pyrit_batch_s* b, cudaStream_t st) {
   for (const Group& g : b->groups) {
     const JobDesc* jobs = reinterpret_cast<const JobDesc*>(b->dev + g.jobs_off);
-    const uint2* tiles = g.explicit_tiles ? reinterpret_cast<const uint2*>(b->dev + g.tiles_off) : nullptr;
-    const int rc = launch_staged(g.shape, nullptr, jobs, tiles, g.ntiles, g.tiles_per_job, st);
+    const int rc = launch_staged(g.shape, nullptr, jobs, g.tiles_dev, g.ntiles, g.tiles_per_job, st);
     if (rc != PYRIT_OK) return rc;
   }
   for (const auto& pj : b->plain) {
@@ -124,29 +160,28 @@ int pyrit_batch_create(const pyrit_stripe_t* stripes, int count, const pyrit_til
     if (jobs.empty()) continue;
     Group g;
     int max_nout = 0;
-    bool same_p = true;
+    bool same_p = true, shared = true;
     for (const JobDesc& j : jobs) {
       max_nout = std::max(max_nout, (int)j.nout);
       same_p = same_p && j.P == jobs[0].P;
+      shared = shared && std::memcmp(j.mask, jobs[0].mask, sizeof(j.mask)) == 0;
     }
-    if (!choose_shape(n, max_nout, hint, &g.shape)) {
+    g.max_nout = max_nout;
+    g.key = TuneKey{n, shared ? 1 : 0, max_nout, same_p ? log2_floor(jobs[0].P) : -1};
+    TuneVal tv;
+    const Variant* tuned = nullptr;
+    if (!tile && tune_lookup(g.key, &tv)) tuned = find_variant(n, tv.words, tv.dispatch, tv.mg, tv.minb, tv.nc);
+    if (tuned) {
+      ShapeHint th;
+      th.stages = tv.stages;
+      shape_for_variant(tuned, max_nout, th, &g.shape);
+    } else if (!choose_shape(n, max_nout, hint, &g.shape, shared)) {
       delete b;
       return PYRIT_E_UNSUPPORTED_FIELD;
     }
     g.njobs = (uint32_t)jobs.size();
     g.jobs_off = place(jobs.data(), jobs.size() * sizeof(JobDesc));
-    if (same_p) {
-      g.tiles_per_job = tiles_for(jobs[0].P, g.shape);
-      g.ntiles = g.tiles_per_job * g.njobs;
-    } else {
-      std::vector<uint2> tl;
-      for (uint32_t ji = 0; ji < g.njobs; ++ji)
-        for (uint64_t c = 0; c < jobs[ji].P; c += (uint64_t)g.shape.tw) tl.push_back(make_uint2(ji, (uint32_t)c));
-      g.explicit_tiles = true;
-      g.ntiles = (uint32_t)tl.size();
-      g.tiles_off = place(tl.data(), tl.size() * sizeof(uint2));
-    }
-    b->tiles += g.ntiles;
+    for (const JobDesc& j : jobs) g.job_P.push_back(j.P);
     b->groups.push_back(g);
   }
   b->launches = (int)(b->groups.size() + b->plain.size());
@@ -162,14 +197,21 @@ int pyrit_batch_create(const pyrit_stripe_t* stripes, int count, const pyrit_til
       return PYRIT_E_CUDA;
     }
   }
-  // Resolve grids and one-time device state now, so that a later graph capture makes no
+  // Tilings, grids and one-time device state now, so that a later graph capture makes no
   // allocation or attribute call.
   if (!device_error_word()) {
-    cudaFree(b->dev);
-    delete b;
+    pyrit_batch_destroy(b);
     return PYRIT_E_CUDA;
   }
-  for (Group& g : b->groups) resolve_grid(&g.shape);
+  for (Group& g : b->groups) {
+    resolve_grid(&g.shape);
+    const int rc = make_tiling(g, g.shape, &g.tiles_dev, &g.ntiles, &g.tiles_per_job);
+    if (rc != PYRIT_OK) {
+      pyrit_batch_destroy(b);
+      return rc;
+    }
+    b->tiles += g.ntiles;
+  }
   *out = b;
   return PYRIT_OK;
 }
@@ -197,6 +239,67 @@ int pyrit_batch_run(pyrit_batch_t b, pyrit_stream_t stream, int graph) {
   return cudaGraphLaunch(b->exec, st) == cudaSuccess ? PYRIT_OK : PYRIT_E_CUDA;
 }
 
+int pyrit_batch_tune(pyrit_batch_t b, pyrit_stream_t stream, int iters) {
+  if (!b || iters < 1) return PYRIT_E_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return PYRIT_E_CUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return PYRIT_E_CUDA;
+  }
+  int rc = PYRIT_OK;
+  int nv = 0;
+  const Variant* all = variants(&nv);
+  for (Group& g : b->groups) {
+    const JobDesc* jobs = reinterpret_cast<const JobDesc*>(b->dev + g.jobs_off);
+    float best = 1e30f;
+    TileShape best_shape = g.shape;
+    for (int i = 0; i < nv && rc == PYRIT_OK; ++i) {
+      if (all[i].n != g.key.n) continue;
+      TileShape sh;
+      if (!shape_for_variant(&all[i], g.max_nout, ShapeHint(), &sh)) continue;
+      resolve_grid(&sh);
+      uint2* tiles = nullptr;  // the tiling depends on the candidate's tile width
+      uint32_t ntiles = 0, tpj = 0;
+      rc = make_tiling(g, sh, &tiles, &ntiles, &tpj);
+      if (rc != PYRIT_OK) break;
+      rc = launch_staged(sh, nullptr, jobs, tiles, ntiles, tpj, st);  // warm-up
+      if (rc == PYRIT_OK) {
+        cudaEventRecord(e0, st);
+        for (int it = 0; it < iters && rc == PYRIT_OK; ++it) rc = launch_staged(sh, nullptr, jobs, tiles, ntiles, tpj, st);
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) rc = PYRIT_E_CUDA;
+      }
+      if (tiles) cudaFree(tiles);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      ms /= (float)iters;
+      if (rc == PYRIT_OK && ms < best) {
+        best = ms;
+        best_shape = sh;
+      }
+    }
+    if (rc != PYRIT_OK) break;
+    if (g.tiles_dev) cudaFree(g.tiles_dev);
+    g.tiles_dev = nullptr;
+    g.shape = best_shape;
+    b->tiles -= g.ntiles;
+    rc = make_tiling(g, g.shape, &g.tiles_dev, &g.ntiles, &g.tiles_per_job);
+    if (rc != PYRIT_OK) break;
+    b->tiles += g.ntiles;
+    const Variant* v = best_shape.v;
+    tune_record(g.key, TuneVal{v->words, v->mg, v->minb, v->nc, v->dispatch, best_shape.stages, best});
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (b->exec) {  // the captured launches used the old shapes
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  return rc;
+}
+
 int pyrit_batch_stats(pyrit_batch_t b, uint64_t* alg_bytes, uint64_t* src_bytes, int* launches, uint64_t* tiles) {
   if (!b) return PYRIT_E_INVALID_ARG;
   if (alg_bytes) *alg_bytes = b->alg_bytes;
@@ -209,6 +312,8 @@ int pyrit_batch_stats(pyrit_batch_t b, uint64_t* alg_bytes, uint64_t* src_bytes,
 void pyrit_batch_destroy(pyrit_batch_t b) {
   if (!b) return;
   if (b->exec) cudaGraphExecDestroy(b->exec);
+  for (Group& g : b->groups)
+    if (g.tiles_dev) cudaFree(g.tiles_dev);
   if (b->dev) cudaFree(b->dev);
   delete b;
 }

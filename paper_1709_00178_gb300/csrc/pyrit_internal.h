@@ -119,9 +119,27 @@ const Variant* variants(int* count);
 const Variant* find_variant(int n, int words, int dispatch, int mg, int minb, int nc);
 // True when every pointer of the job is 16-byte aligned and P is a multiple of 16.
 bool job_is_staged(const JobDesc& j);
-// Tile shape for ring size n, the largest output count of the launch's jobs and optional hints.
-// Returns false if no compiled variant matches.
-bool choose_shape(int n, int max_nout, const ShapeHint& hint, TileShape* out);
+// Tile shape for ring size n, the largest output count of the launch's jobs and optional hints;
+// shared_masks: every job of the launch has the same masks. Returns false if no variant matches.
+bool choose_shape(int n, int max_nout, const ShapeHint& hint, TileShape* out, bool shared_masks = false);
+// Tile shape of a given variant.
+bool shape_for_variant(const Variant* v, int max_nout, const ShapeHint& hint, TileShape* out);
+
+// ---- autotuner table (process-wide) ---------------------------------------------------------
+// A launch group is keyed by ring size, whether its jobs share masks, its largest output count
+// and its packet-size class (log2 P, or -1 when P varies).
+struct TuneKey {
+  int n, shared, nout, plog2;
+  bool operator<(const TuneKey& o) const {
+    return n != o.n ? n < o.n : shared != o.shared ? shared < o.shared : nout != o.nout ? nout < o.nout : plog2 < o.plog2;
+  }
+};
+struct TuneVal {
+  int words, mg, minb, nc, dispatch, stages;
+  float ms;
+};
+bool tune_lookup(const TuneKey& k, TuneVal* v);
+void tune_record(const TuneKey& k, const TuneVal& v);
 // Fills shape->grid (SMs x occupancy) if it is 0; makes the one-time per-device attribute calls.
 void resolve_grid(TileShape* shape);
 // Tiles of one job of packet size P under a shape.

@@ -203,6 +203,7 @@ __global__ void __launch_bounds__((NC + 1) * 32, MINB) ring_staged_kernel(const 
       uint32_t col0;
       const JobDesc* J = tile_job(a, t, col0);
       const uint64_t P = J->P;
+      if (col0 >= P) continue;  // a tiling that does not match the tile width codes nothing past P
       const uint32_t width = (uint32_t)(P - col0 < (uint64_t)TW ? P - col0 : (uint64_t)TW);
       const int nin = J->nin;
       for (int j = 0; j < nin; ++j) {
@@ -242,6 +243,7 @@ __global__ void __launch_bounds__((NC + 1) * 32, MINB) ring_staged_kernel(const 
     uint32_t col0;
     const JobDesc* J = tile_job(a, t, col0);
     const uint64_t P = J->P;
+    if (col0 >= P) continue;  // same rule as the producer: such a tile has no stages
     const uint32_t width = (uint32_t)(P - col0 < (uint64_t)TW ? P - col0 : (uint64_t)TW);
     const bool valid = off < width;
     const int nin = J->nin, nout = J->nout;

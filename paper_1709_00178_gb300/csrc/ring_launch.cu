@@ -127,13 +127,7 @@ bool job_is_staged(const JobDesc& j) {
   return true;
 }
 
-bool choose_shape(int n, int max_nout, const ShapeHint& h, TileShape* out) {
-  // Default: the first registered variant of the ring size, the one measured fastest on its
-  // workload (hints narrow the choice).
-  const int words = h.words;
-  const int dispatch = h.dispatch;
-  const Variant* v = find_variant(n, words, dispatch, h.mg, h.minb, h.nc);
-  if (!v) v = find_variant(n, 0, -1, 0, 0, 0);
+bool shape_for_variant(const Variant* v, int max_nout, const ShapeHint& h, TileShape* out) {
   if (!v) return false;
   TileShape s;
   s.v = v;
@@ -141,13 +135,28 @@ bool choose_shape(int n, int max_nout, const ShapeHint& h, TileShape* out) {
   while (groups * v->mg < max_nout && groups < v->nc) groups *= 2;
   s.groups = groups;
   s.tw = (v->nc / groups) * 32 * 4 * v->words;
-  const int w = n - 1;
+  const int w = v->n - 1;
   const int budget = (226 * 1024) / v->minb - 1024;  // shared memory per CTA at the target occupancy
   s.stages = h.stages > 0 ? h.stages : std::max(2, std::min(8, budget / (w * s.tw)));
   s.grid = 0;
   if (h.ctas_per_sm > 0) s.grid = h.ctas_per_sm * sm_count();
   *out = s;
   return true;
+}
+
+bool choose_shape(int n, int max_nout, const ShapeHint& h, TileShape* out, bool shared_masks) {
+  // Default: the first registered variant of the ring size, the one measured fastest on its
+  // workload; hints narrow the choice. When every job of the launch has the same masks, all warps
+  // walk the same branches and the larger pairing network (dispatch 2) pays off, so a variant of
+  // the default's shape with that dispatch is preferred.
+  const Variant* v = find_variant(n, h.words, h.dispatch, h.mg, h.minb, h.nc);
+  if (!v) v = find_variant(n, 0, -1, 0, 0, 0);
+  if (!v) return false;
+  if (shared_masks && h.dispatch < 0 && v->dispatch != 2) {
+    const Variant* p = find_variant(n, v->words, 2, v->mg, v->minb, v->nc);
+    if (p) v = p;
+  }
+  return shape_for_variant(v, max_nout, h, out);
 }
 
 void resolve_grid(TileShape* s) {
@@ -197,3 +206,18 @@ int launch_plain(int n, const JobDesc& job, cudaStream_t stream) {
 }
 
 }  // namespace pyrit
+
+extern "C" int pyrit_variants(int* params_out, int cap) {
+  int n = 0;
+  const pyrit::Variant* v = pyrit::variants(&n);
+  for (int i = 0; i < n && i < cap && params_out; ++i) {
+    int* r = params_out + 6 * i;
+    r[0] = v[i].n;
+    r[1] = v[i].words;
+    r[2] = v[i].mg;
+    r[3] = v[i].minb;
+    r[4] = v[i].dispatch;
+    r[5] = v[i].nc;
+  }
+  return n;
+}

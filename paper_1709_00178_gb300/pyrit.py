@@ -208,6 +208,10 @@ _BATCH_SIGS = {
     "pyrit_batch_run": (_i, [_vp, _vp, _i]),
     "pyrit_batch_stats": (_i, [_vp, _vp, _vp, _vp, _vp]),
     "pyrit_batch_destroy": (None, [_vp]),
+    "pyrit_batch_tune": (_i, [_vp, _vp, _i]),
+    "pyrit_tune_save": (_i, [ctypes.c_char_p]),
+    "pyrit_tune_load": (_i, [ctypes.c_char_p]),
+    "pyrit_variants": (_i, [_vp, _i]),
 }
 _bind(_BATCH_SIGS)
 EXPORTS = EXPORTS + tuple(_BATCH_SIGS)
@@ -246,6 +250,27 @@ def pyrit_batch_stats(batch):
 
 def pyrit_batch_destroy(batch):
     _lib.pyrit_batch_destroy(batch)
+
+
+def pyrit_batch_tune(batch, stream=None, iters=3):
+    return _check(_lib.pyrit_batch_tune(batch, _stream(stream), iters), "pyrit_batch_tune")
+
+
+def pyrit_variants():
+    """List of dicts (n, words, mg, minb, dispatch, nc), one per compiled kernel variant."""
+    n = _lib.pyrit_variants(None, 0)
+    buf = np.zeros(6 * max(1, n), np.int32)
+    _lib.pyrit_variants(_np_ptr(buf), n)
+    keys = ("n", "words", "mg", "minb", "dispatch", "nc")
+    return [dict(zip(keys, (int(x) for x in buf[6 * i:6 * i + 6]))) for i in range(n)]
+
+
+def pyrit_tune_save(path):
+    return _check(_lib.pyrit_tune_save(os.fsencode(path)), "pyrit_tune_save")
+
+
+def pyrit_tune_load(path):
+    return _check(_lib.pyrit_tune_load(os.fsencode(path)), "pyrit_tune_load")
 
 
 # ---- coding without device allocation ---------------------------------------------------------

@@ -188,3 +188,14 @@ def test_invalid_coding_calls_fail_before_device_work():
         assert pyrit.pyrit_decode(plan, fake, 0, 64) == 0  # nothing erased: no work
     finally:
         pyrit.pyrit_plan_destroy(plan)
+
+
+def test_tune_table_save_load_roundtrip(tmp_path):
+    # Host-only: an entry written in the documented format loads back and saves identically.
+    path = tmp_path / "t.json"
+    path.write_text('[\n  {"n": 13, "shared": 0, "nout": 4, "plog2": 15, "words": 4, "mg": 1, "minb": 1, '
+                    '"nc": 12, "dispatch": 0, "stages": 4, "ms": 0.250000}\n]\n')
+    assert pyrit.pyrit_tune_load(str(path)) == 1
+    out = tmp_path / "o.json"
+    pyrit.pyrit_tune_save(str(out))
+    assert '"n": 13, "shared": 0, "nout": 4, "plog2": 15, "words": 4' in out.read_text()

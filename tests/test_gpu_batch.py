@@ -107,17 +107,17 @@ def test_mixed_batch_encode_then_decode(pyrit):
             pyrit.pyrit_plan_destroy(p)
 
 
-# Every registered variant shape (hints that match no variant of a ring size fall back to its default).
-TILES = [None, dict(stages=2), dict(stages=7, ctas_per_sm=1),
-         dict(words=2, mg=2, minb=1, nc=16, dispatch=0), dict(words=1, mg=2, minb=2, nc=16),
-         dict(words=1, mg=2, minb=4, nc=8), dict(words=2, mg=1, minb=3, nc=8), dict(words=1, mg=2, minb=3, nc=8),
-         dict(words=1, mg=2, minb=1, nc=24), dict(words=2, mg=2, minb=1, nc=16, dispatch=2),
-         dict(words=2, mg=2, minb=2, nc=8), dict(words=1, mg=4, minb=2, nc=8), dict(words=2, mg=4, minb=2, nc=8),
-         dict(words=1, mg=4, minb=2, nc=16), dict(words=2, mg=4, minb=1, nc=16), dict(words=2, mg=8, minb=1, nc=8),
-         dict(words=2, mg=8, minb=2, nc=8), dict(words=1, mg=4, minb=2, nc=16)]
+def _all_tiles(pyrit, n):
+    """Hints that select exactly each compiled variant of ring size n, plus stage overrides."""
+    out = [None, dict(stages=2), dict(stages=7, ctas_per_sm=1)]
+    for v in pyrit.pyrit_variants():
+        if v["n"] == n:
+            out.append({k: v[k] for k in ("words", "mg", "minb", "dispatch", "nc")})
+    return out
 
 
-@pytest.mark.parametrize("w,k,m,P,S", [(10, 10, 4, 4096 + 48, 6), (12, 16, 4, 2048, 5), (4, 4, 2, 8192, 4)])
+@pytest.mark.parametrize("w,k,m,P,S", [(10, 10, 4, 4096 + 48, 6), (12, 16, 4, 2048, 5), (4, 4, 2, 8192, 4),
+                                       (2, 2, 2, 4096 + 16, 3), (12, 32, 8, 2048, 3)])
 def test_every_variant_is_bit_exact(pyrit, w, k, m, P, S):
     specs = [(w, k, m, P)] * S
     pool = Pool(specs, 3)
@@ -130,7 +130,7 @@ def test_every_variant_is_bit_exact(pyrit, w, k, m, P, S):
             full.append(np.concatenate([data, oracle.encode(w, k, m, G, data, nthreads=NCPU)]))
         rng = np.random.default_rng(w)
         pats = [sum(1 << int(x) for x in rng.choice(k + m, m, replace=False)) for _ in range(S)]
-        for t in TILES:
+        for t in _all_tiles(pyrit, w + 1):
             for i in range(S):
                 arr = full[i].copy()
                 arr[k:] = 0
@@ -173,5 +173,82 @@ def test_batch_rejects_bad_stripes(pyrit):
         assert pyrit.pyrit_batch_stats(b)["launches"] == 0
         pyrit.pyrit_batch_run(b)
         pyrit.pyrit_batch_destroy(b)
+    finally:
+        pyrit.pyrit_plan_destroy(plan)
+
+
+def test_autotune_keeps_results_and_records_choice(pyrit, tmp_path):
+    # Tuning runs every variant on the batch's own buffers; the coding is idempotent, so the
+    # buffers must still hold the oracle's result afterwards, and the table must hold the key.
+    w, k, m, P, S = 10, 10, 4, 8192, 8
+    specs = [(w, k, m, P)] * S
+    pool = Pool(specs, 11)
+    plan = pyrit.pyrit_plan_create(w, w + 1, k, m)
+    try:
+        G = pyrit.pyrit_plan_generator(plan)
+        full = []
+        for i in range(S):
+            data = synth_bytes(700 + i, 0, k * w * P).reshape(k, w, P)
+            full.append(np.concatenate([data, oracle.encode(w, k, m, G, data, nthreads=NCPU)]))
+            arr = full[i].copy()
+            arr[k:] = 0
+            pool.put(i, arr)
+        b = pyrit.pyrit_batch_create([(plan, 0, 0, P, pool.blocks(i)) for i in range(S)])
+        pyrit.pyrit_batch_tune(b, iters=2)
+        for i in range(S):
+            assert np.array_equal(pool.host(i), full[i])
+        pyrit.pyrit_batch_run(b, graph=True)
+        for i in range(S):
+            assert np.array_equal(pool.host(i), full[i])
+        pyrit.pyrit_batch_destroy(b)
+        path = str(tmp_path / "tune.json")
+        pyrit.pyrit_tune_save(path)
+        text = open(path).read()
+        assert '"n": 11, "shared": 1, "nout": 4, "plog2": 13' in text
+        assert pyrit.pyrit_tune_load(path) >= 1
+        # a later batch with the same key is built with the tuned shape and stays bit-exact
+        b = pyrit.pyrit_batch_create([(plan, 0, 0, P, pool.blocks(i)) for i in range(S)])
+        pyrit.pyrit_batch_run(b)
+        pyrit.pyrit_batch_destroy(b)
+        for i in range(S):
+            assert np.array_equal(pool.host(i), full[i])
+    finally:
+        pyrit.pyrit_plan_destroy(plan)
+
+
+def test_autotune_mixed_packet_sizes_and_decode(pyrit):
+    # Explicit tile lists (packet sizes differ) are rebuilt for every candidate tile width; after
+    # tuning an encode and a decode batch, every stripe still equals the oracle.
+    specs = [(12, 16, 4, 2048), (12, 16, 4, 4096 + 32), (12, 16, 4, 1024), (12, 16, 4, 8192)]
+    pool = Pool(specs, 5)
+    plan = pyrit.pyrit_plan_create(12, 13, 16, 4)
+    try:
+        G = pyrit.pyrit_plan_generator(plan)
+        full = []
+        for i, (w, k, m, P) in enumerate(specs):
+            data = synth_bytes(800 + i, 0, k * w * P).reshape(k, w, P)
+            full.append(np.concatenate([data, oracle.encode(w, k, m, G, data, nthreads=NCPU)]))
+            arr = full[i].copy()
+            arr[k:] = 0
+            pool.put(i, arr)
+        b = pyrit.pyrit_batch_create([(plan, 0, 0, P, pool.blocks(i)) for i, (w, k, m, P) in enumerate(specs)])
+        pyrit.pyrit_batch_tune(b, iters=1)
+        pyrit.pyrit_batch_destroy(b)
+        for i in range(len(specs)):
+            assert np.array_equal(pool.host(i), full[i]), ("encode", i)
+        pats = [0b1011, 0xF0000, 0b11 << 15, 1]
+        for i, (w, k, m, P) in enumerate(specs):
+            arr = full[i].copy()
+            for x in range(k + m):
+                if (pats[i] >> x) & 1:
+                    arr[x] = 0x77
+            pool.put(i, arr)
+        b = pyrit.pyrit_batch_create([(plan, 1, pats[i], P, pool.blocks(i)) for i, (w, k, m, P) in enumerate(specs)])
+        pyrit.pyrit_batch_tune(b, iters=1)
+        pyrit.pyrit_batch_run(b, graph=True)
+        pyrit.pyrit_batch_destroy(b)
+        for i in range(len(specs)):
+            assert np.array_equal(pool.host(i), full[i]), ("decode", i)
+        assert pyrit.pyrit_device_status() == (0, 0)
     finally:
         pyrit.pyrit_plan_destroy(plan)
