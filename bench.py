@@ -143,8 +143,8 @@ def run_reference(args):
     G = oracle.cauchy(W, K, M)
     pats = patterns(BASE_SEED + 1, STRIPES, K, M)
     blk = W * P
-    stripe_bytes = (K + M) * blk
-    data = [synth_bytes(BASE_SEED + 1, s * stripe_bytes, K * blk).reshape(K, W, P) for s in range(sample)]
+    # the same bytes as the GPU arm's first stripes: data blocks are contiguous in the stream
+    data = [synth_bytes(BASE_SEED + 1, s * K * blk, K * blk).reshape(K, W, P) for s in range(sample)]
 
     def step():
         for s in range(sample):
@@ -205,11 +205,15 @@ def main():
 
     blk = W * P
     stripe_bytes = (K + M) * blk
+    # Layout: every stripe's k data blocks contiguous in a data region, its m parity blocks in a
+    # parity region, so host<->device transfers of a run of stripes are single copies.
     buf = torch.empty(STRIPES * stripe_bytes, dtype=torch.uint8, device=dev)
     pyrit.pyrit_synth_fill(buf.data_ptr(), buf.numel(), BASE_SEED + 1, rank * buf.numel())
     torch.cuda.synchronize(dev)
     base = buf.data_ptr()
-    blocks = [[base + s * stripe_bytes + e * blk for e in range(K + M)] for s in range(STRIPES)]
+    par0 = STRIPES * K * blk
+    blocks = [[base + (s * K + j) * blk for j in range(K)] + [base + par0 + (s * M + i) * blk for i in range(M)]
+              for s in range(STRIPES)]
     pats = patterns(BASE_SEED + 1 + 1000 * rank, STRIPES, K, M)
     plan = pyrit.pyrit_plan_create(W, N, K, M)
     enc = pyrit.pyrit_batch_create([(plan, pyrit.PYRIT_OP_ENCODE, 0, P, blocks[s]) for s in range(STRIPES)])
@@ -238,6 +242,7 @@ def main():
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize(dev)
+    nvtx = torch.cuda.nvtx
     code, where = pyrit.pyrit_device_status()
     if code != 0:
         raise RuntimeError("device status %d at site %d after warm-up" % (code, where))
@@ -256,11 +261,13 @@ def main():
         torch.cuda.synchronize(dev)
     barrier()
     torch.cuda.synchronize(dev)
+    nvtx.range_push("timed")
     t0.record(stream)
     for i in range(args.steps):
         step(evs[i])
     t1.record(stream)
     torch.cuda.synchronize(dev)
+    nvtx.range_pop()
     clk = clocks.stop()
     barrier()
     ms = t0.elapsed_time(t1)
@@ -281,29 +288,27 @@ def main():
         raise RuntimeError("device status %d at site %d" % (code, where))
 
     # ---- end to end: data from pinned host memory, parity back, every step ----
-    CH = 8  # chunks of stripes, each on its own stream slot
+    CH = 16  # chunks of stripes; chunk c's data and parity are each one contiguous copy
     per = STRIPES // CH
-    host = torch.empty(STRIPES * stripe_bytes, dtype=torch.uint8, pin_memory=True)
-    host.copy_(buf)
+    host = torch.empty(STRIPES * K * blk, dtype=torch.uint8, pin_memory=True)
+    host.copy_(buf[:par0])
     host_par = torch.empty(STRIPES * M * blk, dtype=torch.uint8, pin_memory=True)
     cenc = [pyrit.pyrit_batch_create([(plan, 0, 0, P, blocks[s]) for s in range(c * per, (c + 1) * per)])
             for c in range(CH)]
     cdec = [pyrit.pyrit_batch_create([(plan, 1, pats[s], P, blocks[s]) for s in range(c * per, (c + 1) * per)])
             for c in range(CH)]
-    streams = [torch.cuda.Stream(device=dev) for _ in range(3)]
+    streams = [torch.cuda.Stream(device=dev) for _ in range(4)]
 
     def e2e_step():
         for c in range(CH):
             st = streams[c % len(streams)]
+            d0, d1 = c * per * K * blk, (c + 1) * per * K * blk
+            p0, p1 = c * per * M * blk, (c + 1) * per * M * blk
             with torch.cuda.stream(st):
-                for s in range(c * per, (c + 1) * per):
-                    o = s * stripe_bytes
-                    buf[o:o + K * blk].copy_(host[o:o + K * blk], non_blocking=True)
+                buf[d0:d1].copy_(host[d0:d1], non_blocking=True)
                 pyrit.pyrit_batch_run(cenc[c], st, graph=True)
                 pyrit.pyrit_batch_run(cdec[c], st, graph=True)
-                for s in range(c * per, (c + 1) * per):
-                    o = s * stripe_bytes + K * blk
-                    host_par[s * M * blk:(s + 1) * M * blk].copy_(buf[o:o + M * blk], non_blocking=True)
+                host_par[p0:p1].copy_(buf[par0 + p0:par0 + p1], non_blocking=True)
 
     def e2e_timed(steps):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -321,15 +326,16 @@ def main():
 
     e2e_timed(2)
     barrier()
+    nvtx.range_push("e2e")
     e2e_ms = e2e_timed(args.steps)
+    nvtx.range_pop()
     if world > 1:
         t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_ms = float(t.item())
     e2e_val = world * src_per_step / (e2e_ms / args.steps * 1e-3) / 1e9
     # every parity read back must equal the device-resident result
-    par_dev = torch.cat([buf[s * stripe_bytes + K * blk:s * stripe_bytes + (K + M) * blk] for s in range(STRIPES)])
-    e2e_ok = bool(torch.equal(par_dev.cpu(), host_par))
+    e2e_ok = bool(torch.equal(buf[par0:].cpu(), host_par))
 
     out = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
@@ -367,16 +373,17 @@ def cpu_baseline(buf, blocks, pats, plan, pyrit):
     sample = 16
     cores = os.cpu_count() or 1
     blk = W * P
-    stripe_bytes = (K + M) * blk
     G = pyrit.pyrit_plan_generator(plan)
-    host = buf[:sample * stripe_bytes].cpu().numpy().reshape(sample, K + M, W, P)
+    data = buf[:sample * K * blk].cpu().numpy().reshape(sample, K, W, P)
+    par0 = STRIPES * K * blk
+    gpar = buf[par0:par0 + sample * M * blk].cpu().numpy().reshape(sample, M, W, P)
     t0 = time.perf_counter()
     match = True
     for s in range(sample):
-        par = oracle.encode(W, K, M, G, host[s, :K], nthreads=cores)
-        full = np.concatenate([host[s, :K], par])
+        par = oracle.encode(W, K, M, G, data[s], nthreads=cores)
+        full = np.concatenate([data[s], par])
         rebuilt = oracle.decode(W, K, M, G, full, pats[s], nthreads=cores)
-        match = match and np.array_equal(par, host[s, K:]) and np.array_equal(rebuilt, full)
+        match = match and np.array_equal(par, gpar[s]) and np.array_equal(rebuilt, full)
     dt = time.perf_counter() - t0
     return {"value": 2 * sample * K * blk / dt / 1e9, "unit": "GB/s", "cores": cores, "kind": "oracle",
             "sample": "first %d of the %d stripes, encode + decode (same erasure patterns), %.1f s" % (
