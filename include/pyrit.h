@@ -213,6 +213,60 @@ PYRIT_API int pyrit_batch_stats(pyrit_batch_t batch, uint64_t* alg_bytes, uint64
 /* Frees the batch's device memory and graph (synchronises the device). */
 PYRIT_API void pyrit_batch_destroy(pyrit_batch_t batch);
 
+/* ---- served coding: continuous batching ---------------------------------------------------- */
+
+typedef struct pyrit_server_s* pyrit_server_t;
+
+/* One served request: a stripe (any plan, operation and packet size; P a multiple of 16 and
+ * 16-byte aligned blocks), the caller's tag, and its arrival time on the server clock (ns since the
+ * server was created; <= 0: the time of submission). */
+typedef struct {
+  pyrit_stripe_t stripe;
+  uint64_t tag;
+  int64_t arrival_ns;
+} pyrit_request_t;
+
+/* A finished request: times on the server clock. start_ns / done_ns are device-timeline times of
+ * the beginning and end of the batch that coded it. */
+typedef struct {
+  uint64_t tag;
+  int status;
+  int64_t arrival_ns, start_ns, done_ns;
+} pyrit_completion_t;
+
+/* Starts a server on the current device. A scheduler thread admits submitted requests in arrival
+ * order while the device bytes of the requests in flight ((k+m) w P each) stay within hbm_budget,
+ * and whenever one of `slots` stream slots is free it packs the admitted requests (at most
+ * max_batch) into one batch: their jobs are copied into the slot's device descriptor table and
+ * coded by one persistent launch of the staged ring kernel per ring size on the slot's stream.
+ * Batches on different slots overlap on the device; new arrivals join the next free slot
+ * (continuous batching). Decoding matrices come from the plans' caches; launch shapes from the
+ * autotuner's table when it has the key. queue_cap bounds the requests waiting for admission.
+ * Allocates its slots' device tables and pinned staging. */
+PYRIT_API int pyrit_server_create(size_t hbm_budget, int max_batch, int slots, int queue_cap, pyrit_server_t* out);
+
+/* Validates and enqueues requests (all or none). Errors before any device work: the codes of
+ * pyrit_batch_create, PYRIT_E_BUDGET for a stripe larger than the budget, PYRIT_E_INVALID_ARG
+ * for a misaligned stripe or one too large for a slot, PYRIT_E_BUSY when the queue is full. */
+PYRIT_API int pyrit_server_submit(pyrit_server_t server, const pyrit_request_t* reqs, int count);
+
+/* Moves up to `cap` completions into out (host array); returns how many. */
+PYRIT_API int pyrit_server_poll(pyrit_server_t server, pyrit_completion_t* out, int cap);
+
+/* Waits until every submitted request has completed, for at most timeout_ms: PYRIT_OK, or
+ * PYRIT_E_TIMEOUT when the limit passes first (the requests keep running). */
+PYRIT_API int pyrit_server_drain(pyrit_server_t server, int timeout_ms);
+
+/* The server clock: ns since the server was created (host steady clock). */
+PYRIT_API int64_t pyrit_server_now_ns(pyrit_server_t server);
+
+/* stats_out[7]: submitted, completed, batches, launches, bytes in flight, largest bytes in flight
+ * observed, budget. */
+PYRIT_API int pyrit_server_stats(pyrit_server_t server, uint64_t* stats_out);
+
+/* Waits for every submitted request, stops the scheduler and frees the server. */
+PYRIT_API void pyrit_server_destroy(pyrit_server_t server);
+
 /* ---- coding without device allocation --------------------------------------------------- */
 
 #define PYRIT_NOALLOC_MAX_STRIPES 256  /* stripes per call                                       */

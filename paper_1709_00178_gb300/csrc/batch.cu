@@ -72,27 +72,6 @@ struct pyrit_batch_s {
 
 namespace {
 
-int build_job(const pyrit_stripe_t& s, JobDesc* job, uint64_t* alg, uint64_t* src) {
-  pyrit_plan_s* p = s.plan;
-  if (!p || !s.blocks || s.packet_bytes == 0 || s.packet_bytes > (1ull << 40)) return PYRIT_E_INVALID_ARG;
-  if (s.op != PYRIT_OP_ENCODE && s.op != PYRIT_OP_DECODE) return PYRIT_E_INVALID_ARG;
-  for (int b = 0; b < p->k + p->m; ++b)
-    if (!s.blocks[b]) return PYRIT_E_INVALID_ARG;
-  const uint64_t blk = (uint64_t)p->w * s.packet_bytes;
-  *src = (uint64_t)p->k * blk;
-  if (s.op == PYRIT_OP_ENCODE) {
-    make_encode_job(p, s.blocks, s.blocks + p->k, s.packet_bytes, job);
-    *alg = (uint64_t)(p->k + p->m) * blk;
-    return PYRIT_OK;
-  }
-  DecodeEntry e;
-  const int rc = plan_decode_entry(p, s.erasures, &e);
-  if (rc != PYRIT_OK) return rc;
-  make_decode_job(p, e, s.blocks, s.packet_bytes, job);
-  *alg = (uint64_t)(p->k + e.ne) * blk;
-  return PYRIT_OK;
-}
-
 int enqueue(pyrit_batch_s* b, cudaStream_t st) {
   for (const Group& g : b->groups) {
     const JobDesc* jobs = reinterpret_cast<const JobDesc*>(b->dev + g.jobs_off);
@@ -132,7 +111,7 @@ int pyrit_batch_create(const pyrit_stripe_t* stripes, int count, const pyrit_til
   for (int i = 0; i < count; ++i) {
     JobDesc job;
     uint64_t alg = 0, src = 0;
-    const int rc = build_job(stripes[i], &job, &alg, &src);
+    const int rc = stripe_job(stripes[i], &job, &alg, &src);
     if (rc != PYRIT_OK) {
       delete b;
       return rc;

@@ -190,6 +190,30 @@ void make_decode_job(const pyrit_plan_s* p, const DecodeEntry& e, void* const* b
     for (int s = 0; s < p->k; ++s) job->mask[s][r] = e.mask[r][s];
 }
 
+
+// Validates a stripe request and builds its coding job; alg / src receive its algorithmic and
+// source bytes.
+int stripe_job(const pyrit_stripe_t& s, JobDesc* job, uint64_t* alg, uint64_t* src) {
+  pyrit_plan_s* p = s.plan;
+  if (!p || !s.blocks || s.packet_bytes == 0 || s.packet_bytes > (1ull << 40)) return PYRIT_E_INVALID_ARG;
+  if (s.op != PYRIT_OP_ENCODE && s.op != PYRIT_OP_DECODE) return PYRIT_E_INVALID_ARG;
+  for (int b = 0; b < p->k + p->m; ++b)
+    if (!s.blocks[b]) return PYRIT_E_INVALID_ARG;
+  const uint64_t blk = (uint64_t)p->w * s.packet_bytes;
+  *src = (uint64_t)p->k * blk;
+  if (s.op == PYRIT_OP_ENCODE) {
+    make_encode_job(p, s.blocks, s.blocks + p->k, s.packet_bytes, job);
+    *alg = (uint64_t)(p->k + p->m) * blk;
+    return PYRIT_OK;
+  }
+  DecodeEntry e;
+  const int rc = plan_decode_entry(p, s.erasures, &e);
+  if (rc != PYRIT_OK) return rc;
+  make_decode_job(p, e, s.blocks, s.packet_bytes, job);
+  *alg = (uint64_t)(p->k + e.ne) * blk;
+  return PYRIT_OK;
+}
+
 }  // namespace pyrit
 
 using namespace pyrit;

@@ -109,6 +109,8 @@ int plan_decode_entry(pyrit_plan_s* p, uint64_t erasures, DecodeEntry* out);
 // Fills a job for encoding one stripe.
 void make_encode_job(const pyrit_plan_s* p, const void* const* data, void* const* parity, size_t P,
                      JobDesc* job);
+// Validates a stripe request and builds its coding job (alg / src: algorithmic and source bytes).
+int stripe_job(const pyrit_stripe_t& s, JobDesc* job, uint64_t* alg, uint64_t* src);
 // Fills a job for decoding one stripe with a decode entry.
 void make_decode_job(const pyrit_plan_s* p, const DecodeEntry& e, void* const* blocks, size_t P,
                      JobDesc* job);

@@ -290,3 +290,71 @@ def pyrit_code_stripes_noalloc(stripes, stream=None):
         keep.append(ba)
         arr[i] = pyrit_stripe_t(plan, op, er, P, ctypes.cast(ba, ctypes.POINTER(ctypes.c_void_p)))
     return _check(_lib.pyrit_code_stripes_noalloc(arr, len(stripes), _stream(stream)), "pyrit_code_stripes_noalloc")
+
+
+# ---- served coding -----------------------------------------------------------------------------
+
+class pyrit_request_t(ctypes.Structure):
+    _fields_ = [("stripe", pyrit_stripe_t), ("tag", ctypes.c_uint64), ("arrival_ns", ctypes.c_int64)]
+
+
+class pyrit_completion_t(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_uint64), ("status", ctypes.c_int), ("arrival_ns", ctypes.c_int64),
+                ("start_ns", ctypes.c_int64), ("done_ns", ctypes.c_int64)]
+
+
+_SERVER_SIGS = {
+    "pyrit_server_create": (_i, [_sz, _i, _i, _i, ctypes.POINTER(_vp)]),
+    "pyrit_server_submit": (_i, [_vp, ctypes.POINTER(pyrit_request_t), _i]),
+    "pyrit_server_poll": (_i, [_vp, ctypes.POINTER(pyrit_completion_t), _i]),
+    "pyrit_server_drain": (_i, [_vp, _i]),
+    "pyrit_server_now_ns": (ctypes.c_int64, [_vp]),
+    "pyrit_server_stats": (_i, [_vp, _vp]),
+    "pyrit_server_destroy": (None, [_vp]),
+}
+_bind(_SERVER_SIGS)
+EXPORTS = EXPORTS + tuple(_SERVER_SIGS)
+
+
+def pyrit_server_create(hbm_budget, max_batch=64, slots=4, queue_cap=1 << 20):
+    h = ctypes.c_void_p()
+    _check(_lib.pyrit_server_create(hbm_budget, max_batch, slots, queue_cap, ctypes.byref(h)), "pyrit_server_create")
+    return h.value
+
+
+def pyrit_server_submit(server, requests):
+    """requests: list of (plan, op, erasures, P, block_ptrs[k+m], tag, arrival_ns)."""
+    arr = (pyrit_request_t * max(1, len(requests)))()
+    keep = []
+    for i, (plan, op, er, P, blocks, tag, arrival) in enumerate(requests):
+        ba = _ptr_array(blocks)
+        keep.append(ba)
+        arr[i] = pyrit_request_t(pyrit_stripe_t(plan, op, er, P, ctypes.cast(ba, ctypes.POINTER(ctypes.c_void_p))),
+                                 tag, arrival)
+    return _check(_lib.pyrit_server_submit(server, arr, len(requests)), "pyrit_server_submit")
+
+
+def pyrit_server_poll(server, cap=4096):
+    """List of (tag, status, arrival_ns, start_ns, done_ns)."""
+    buf = (pyrit_completion_t * cap)()
+    n = _check(_lib.pyrit_server_poll(server, buf, cap), "pyrit_server_poll")
+    return [(c.tag, c.status, c.arrival_ns, c.start_ns, c.done_ns) for c in buf[:n]]
+
+
+def pyrit_server_drain(server, timeout_ms):
+    return _check(_lib.pyrit_server_drain(server, timeout_ms), "pyrit_server_drain")
+
+
+def pyrit_server_now_ns(server):
+    return int(_lib.pyrit_server_now_ns(server))
+
+
+def pyrit_server_stats(server):
+    s = np.zeros(7, np.uint64)
+    _check(_lib.pyrit_server_stats(server, _np_ptr(s)), "pyrit_server_stats")
+    keys = ("submitted", "completed", "batches", "launches", "inflight", "max_inflight", "budget")
+    return {k: int(v) for k, v in zip(keys, s)}
+
+
+def pyrit_server_destroy(server):
+    _lib.pyrit_server_destroy(server)
