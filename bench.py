@@ -178,10 +178,16 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--stripes", type=int, default=STRIPES,
                     help="stripes per GPU (default 256; smaller values make profiling cases)")
+    ap.add_argument("--workload", default="coding", choices=["coding", "sweep", "mixed", "served"],
+                    help="coding: the default line; sweep: GF(2^12) k=16 m=4 packet sweep 4 KiB-1 MiB; mixed: "
+                         "4096 uneven stripes batched vs per-stripe launches; served: Poisson arrivals")
+    ap.add_argument("--seconds", type=float, default=10.0, help="served: arrival window")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "coding":
+        return {"sweep": run_sweep, "mixed": run_mixed, "served": run_served}[args.workload](args)
     if args.stripes != STRIPES:
         STRIPES = max(8, args.stripes // 8 * 8)
         CONFIG["stripes"] = STRIPES
@@ -389,6 +395,230 @@ def cpu_baseline(buf, blocks, pats, plan, pyrit):
             "sample": "first %d of the %d stripes, encode + decode (same erasure patterns), %.1f s" % (
                 sample, STRIPES, dt),
             "gpu_parity_on_sample": match}
+
+
+# ---------------------------------------------------------------------------------------------
+# Further measured workloads (one JSON line each; not the default line)
+# ---------------------------------------------------------------------------------------------
+
+def _setup_gpu():
+    import torch
+    from paper_1709_00178_gb300 import pyrit
+    torch.cuda.set_device(0)
+    return torch, pyrit, torch.device("cuda", 0)
+
+
+def _time_batch(torch, pyrit, batch, stream, steps):
+    for _ in range(3):
+        pyrit.pyrit_batch_run(batch, stream, graph=True)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        pyrit.pyrit_batch_run(batch, stream, graph=True)
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / steps
+
+
+def run_sweep(args):
+    """GF(2^12) (n=13), Cauchy k=16 m=4: packet sizes 4 KiB..1 MiB, stripes filling ~8 GiB of
+    source data; encode and 4-erasure decode per point, batched and autotuned."""
+    torch, pyrit, dev = _setup_gpu()
+    from paper_1709_00178_gb300.synth import BASE_SEED
+    import numpy as np
+    w, k, m = 12, 16, 4
+    peak, _ = peak_hbm()
+    plan = pyrit.pyrit_plan_create(w, w + 1, k, m)
+    stream = torch.cuda.Stream(device=dev)
+    for e in range(12, 21):
+        P = 1 << e
+        S = (8 << 30) // (k * w * P)
+        blk = w * P
+        buf = torch.empty(S * (k + m) * blk, dtype=torch.uint8, device=dev)
+        pyrit.pyrit_synth_fill(buf.data_ptr(), buf.numel(), BASE_SEED + 2, 0)
+        torch.cuda.synchronize()
+        base, par0 = buf.data_ptr(), S * k * blk
+        blocks = [[base + (s * k + j) * blk for j in range(k)] + [base + par0 + (s * m + i) * blk for i in range(m)]
+                  for s in range(S)]
+        rng = np.random.default_rng(BASE_SEED + 2 + e)
+        pats = [sum(1 << int(x) for x in rng.choice(k + m, m, replace=False)) for _ in range(S)]
+        enc = pyrit.pyrit_batch_create([(plan, 0, 0, P, blocks[s]) for s in range(S)])
+        dec = pyrit.pyrit_batch_create([(plan, 1, pats[s], P, blocks[s]) for s in range(S)])
+        pyrit.pyrit_batch_tune(enc, stream, 2)
+        pyrit.pyrit_batch_tune(dec, stream, 2)
+        te = _time_batch(torch, pyrit, enc, stream, args.steps)
+        td = _time_batch(torch, pyrit, dec, stream, args.steps)
+        es, ds = pyrit.pyrit_batch_stats(enc), pyrit.pyrit_batch_stats(dec)
+        ae, ad = es["alg_bytes"] / te / 1e6, ds["alg_bytes"] / td / 1e6
+        print(json.dumps({
+            "metric": "encode+decode GB/s of source data", "workload": "sweep",
+            "value": (es["src_bytes"] + ds["src_bytes"]) / (te + td) / 1e6, "unit": "GB/s",
+            "config": {"workload": "GF(2^12) n=13 Cauchy k=16 m=4, 4-erasure decode", "packet_bytes": P, "stripes": S},
+            "encode_ms": te, "decode_ms": td, "encode_roofline_frac": ae / peak, "decode_roofline_frac": ad / peak,
+            "encode_alg_gbs": ae, "decode_alg_gbs": ad, "dtype": "u8", "data": "synthetic"}), flush=True)
+        pyrit.pyrit_batch_destroy(enc)
+        pyrit.pyrit_batch_destroy(dec)
+        del buf
+        torch.cuda.empty_cache()
+    pyrit.pyrit_plan_destroy(plan)
+
+
+def run_mixed(args):
+    """4096 uneven stripes: ring n uniform in {5, 11, 13}, k in 4..32, m in 2..8 (redrawn until
+    k+m <= 2^w), P log-uniform 512 B..256 KiB (multiple of 16), half encode, half decode with 1..m
+    erasures. The batched persistent launch (autotuned) against 4096 per-stripe launches of the
+    same kernel; both must write the same bytes."""
+    torch, pyrit, dev = _setup_gpu()
+    from paper_1709_00178_gb300.synth import BASE_SEED
+    import numpy as np
+    rng = np.random.default_rng(BASE_SEED + 3)
+    S = 4096
+    specs = []
+    for _ in range(S):
+        n = int(rng.choice([5, 11, 13]))
+        w = n - 1
+        while True:
+            k, m = int(rng.integers(4, 33)), int(rng.integers(2, 9))
+            if k + m <= (1 << w):
+                break
+        P = max(16, int(2 ** rng.uniform(9, 18)) // 16 * 16)
+        op = int(rng.integers(0, 2))
+        er = 0
+        if op:
+            e = int(rng.integers(1, m + 1))
+            er = sum(1 << int(x) for x in rng.choice(k + m, e, replace=False))
+        specs.append((w, k, m, P, op, er))
+    offs, total = [], 0
+    for (w, k, m, P, op, er) in specs:
+        offs.append(total)
+        total += ((k + m) * w * P + 255) // 256 * 256
+    buf = torch.empty(total, dtype=torch.uint8, device=dev)
+    pyrit.pyrit_synth_fill(buf.data_ptr(), total, BASE_SEED + 3, 0)
+    torch.cuda.synchronize()
+    plans = {}
+    for (w, k, m, P, op, er) in specs:
+        if (w, k, m) not in plans:
+            plans[(w, k, m)] = pyrit.pyrit_plan_create(w, w + 1, k, m)
+    base = buf.data_ptr()
+    stripes = [(plans[(w, k, m)], op, er, P, [base + o + e * w * P for e in range(k + m)])
+               for (w, k, m, P, op, er), o in zip(specs, offs)]
+    stream = torch.cuda.Stream(device=dev)
+    batch = pyrit.pyrit_batch_create(stripes)
+    st = pyrit.pyrit_batch_stats(batch)
+    pyrit.pyrit_batch_tune(batch, stream, 2)
+    t_batch = _time_batch(torch, pyrit, batch, stream, args.steps)
+    after_batch = buf.clone()
+
+    ks = [spec[1] for spec in specs]
+
+    def per_stripe():
+        for (plan, op, er, P, blocks), kk in zip(stripes, ks):
+            if op == 0:
+                pyrit.pyrit_encode(plan, blocks[:kk], blocks[kk:], P, stream)
+            else:
+                pyrit.pyrit_decode(plan, blocks, er, P, stream)
+
+    per_stripe()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = max(1, min(5, args.steps))
+    a.record(stream)
+    for _ in range(reps):
+        per_stripe()
+    b.record(stream)
+    torch.cuda.synchronize()
+    t_per = a.elapsed_time(b) / reps
+    same = bool(torch.equal(after_batch, buf))
+    peak, _ = peak_hbm()
+    print(json.dumps({
+        "metric": "encode+decode GB/s of source data", "workload": "mixed", "unit": "GB/s",
+        "value": st["src_bytes"] / t_batch / 1e6,
+        "config": {"workload": "4096 uneven stripes, n in {5,11,13}, k 4-32, m 2-8, P 512 B-256 KiB, half decode",
+                   "stripes": S, "alg_bytes": st["alg_bytes"], "launches": st["launches"], "tiles": st["tiles"]},
+        "batched_ms": t_batch, "per_stripe_ms": t_per, "speedup_vs_per_stripe": t_per / t_batch,
+        "batched_roofline_frac": st["alg_bytes"] / t_batch / 1e6 / peak, "same_bytes": same,
+        "dtype": "u8", "data": "synthetic"}), flush=True)
+    pyrit.pyrit_batch_destroy(batch)
+    for p in plans.values():
+        pyrit.pyrit_plan_destroy(p)
+
+
+def run_served(args):
+    """Poisson arrivals (seeded, 20 000 requests/s) of GF(2^12) k=16 m=4 requests, P one of
+    4 KiB..1 MiB (powers of two, uniform), half encode and half 4-erasure decode, served with
+    continuous batching under a 16 GiB budget; payloads pre-generated in device memory."""
+    torch, pyrit, dev = _setup_gpu()
+    from paper_1709_00178_gb300.synth import BASE_SEED
+    import numpy as np
+    w, k, m = 12, 16, 4
+    rate = 20000.0
+    rng = np.random.default_rng(BASE_SEED + 4)
+    POOL = 512
+    pool_P = [1 << int(e) for e in rng.integers(12, 21, POOL)]
+    pool_pat = [sum(1 << int(x) for x in rng.choice(k + m, m, replace=False)) for _ in range(POOL)]
+    offs, total = [], 0
+    for P in pool_P:
+        offs.append(total)
+        total += (k + m) * w * P
+    buf = torch.empty(total, dtype=torch.uint8, device=dev)
+    pyrit.pyrit_synth_fill(buf.data_ptr(), total, BASE_SEED + 4, 0)
+    torch.cuda.synchronize()
+    plan = pyrit.pyrit_plan_create(w, w + 1, k, m)
+    for pat in set(pool_pat):  # the plan caches every decoding matrix before the timed window
+        pyrit.pyrit_plan_decode_masks(plan, pat)
+    base = buf.data_ptr()
+    nreq = int(rate * args.seconds)
+    gaps = rng.exponential(1e9 / rate, nreq)
+    arrivals = np.cumsum(gaps).astype(np.int64)
+    ops = rng.integers(0, 2, nreq)
+    reqs, src_bytes = [], 0
+    for i in range(nreq):
+        s = i % POOL
+        P = pool_P[s]
+        blocks = [base + offs[s] + e * w * P for e in range(k + m)]
+        reqs.append((plan, int(ops[i]), pool_pat[s] if ops[i] else 0, P, blocks, i, 0))
+        src_bytes += k * w * P
+    arr, keep = pyrit.pyrit_requests_array(reqs)
+    srv = pyrit.pyrit_server_create(16 << 30, max_batch=64, slots=4)
+    # warm the launch shapes and the device with a short unmeasured burst
+    pyrit.pyrit_server_submit_slice(srv, arr, 0, min(64, nreq))
+    pyrit.pyrit_server_drain(srv, 60000)
+    pyrit.pyrit_server_poll(srv, 1 << 20)
+    clocks = Clocks(0)
+    clocks.start()
+    t0 = pyrit.pyrit_server_now_ns(srv) + 2000000
+    for i in range(nreq):
+        arr[i].arrival_ns = int(t0 + arrivals[i])
+    i = 0
+    while i < nreq:
+        now = pyrit.pyrit_server_now_ns(srv)
+        j = i
+        while j < nreq and arr[j].arrival_ns <= now:
+            j += 1
+        if j > i:
+            pyrit.pyrit_server_submit_slice(srv, arr, i, j - i)
+            i = j
+    pyrit.pyrit_server_drain(srv, 600000)
+    clk = clocks.stop()
+    done = pyrit.pyrit_server_poll(srv, nreq + 64)
+    st = pyrit.pyrit_server_stats(srv)
+    pyrit.pyrit_server_destroy(srv)
+    lat = np.array([d[4] - d[2] for d in done if d[0] < nreq], dtype=np.float64) / 1e3  # us
+    t_first = min(d[2] for d in done)
+    t_last = max(d[4] for d in done)
+    ok = all(d[1] == 0 for d in done)
+    print(json.dumps({
+        "metric": "served p50/p99 latency", "workload": "served", "unit": "us",
+        "value": float(np.percentile(lat, 99)), "p50_us": float(np.percentile(lat, 50)),
+        "p99_us": float(np.percentile(lat, 99)), "p999_us": float(np.percentile(lat, 99.9)),
+        "max_us": float(lat.max()), "requests": len(lat), "all_ok": ok,
+        "sustained_gbs": src_bytes / ((t_last - t_first) * 1e-9) / 1e9,
+        "offered_gbs": src_bytes / (arrivals[-1] * 1e-9) / 1e9,
+        "batches": st["batches"], "launches": st["launches"], "max_inflight_bytes": st["max_inflight"],
+        "config": {"workload": "Poisson 20k req/s, GF(2^12) k=16 m=4, P 4 KiB-1 MiB, half 4-erasure decode, "
+                               "16 GiB budget, 4 stream slots, batches up to 64", "seconds": args.seconds},
+        "clocks": clk, "higher_is_better": False, "dtype": "u8", "data": "synthetic"}), flush=True)
+    pyrit.pyrit_plan_destroy(plan)
 
 
 if __name__ == "__main__":

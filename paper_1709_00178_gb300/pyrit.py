@@ -358,3 +358,22 @@ def pyrit_server_stats(server):
 
 def pyrit_server_destroy(server):
     _lib.pyrit_server_destroy(server)
+
+
+def pyrit_requests_array(requests):
+    """A prebuilt ctypes array of requests (plan, op, erasures, P, block_ptrs, tag, arrival_ns) and the
+    pointer arrays it references, for pyrit_server_submit_slice."""
+    arr = (pyrit_request_t * max(1, len(requests)))()
+    keep = []
+    for i, (plan, op, er, P, blocks, tag, arrival) in enumerate(requests):
+        ba = _ptr_array(blocks)
+        keep.append(ba)
+        arr[i] = pyrit_request_t(pyrit_stripe_t(plan, op, er, P, ctypes.cast(ba, ctypes.POINTER(ctypes.c_void_p))),
+                                 tag, arrival)
+    return arr, keep
+
+
+def pyrit_server_submit_slice(server, arr, start, count):
+    """Submits arr[start:start + count] of a prebuilt request array without copying it."""
+    ptr = ctypes.cast(ctypes.byref(arr, start * ctypes.sizeof(pyrit_request_t)), ctypes.POINTER(pyrit_request_t))
+    return _check(_lib.pyrit_server_submit(server, ptr, count), "pyrit_server_submit")
