@@ -65,6 +65,8 @@ typedef struct CUstream_st* pyrit_stream_t;
 #define PYRIT_E_BUSY -10              /* server: request queue full, retry later               */
 #define PYRIT_E_SCRATCH_LIMIT -11     /* more stripes or tiles than pyrit_code_stripes_noalloc's
                                          fixed scratch holds                                     */
+#define PYRIT_E_JIT -12               /* run-time compilation or loading of a plan-specialised
+                                         network failed (pyrit_jit_log has the compiler's log)  */
 
 /* Limits of this build. */
 #define PYRIT_MAX_K 32 /* data blocks per stripe                   */
@@ -133,7 +135,8 @@ PYRIT_API uint32_t pyrit_gf_mul(int w, uint32_t a, uint32_t b);
  *   P      : packet bytes, >= 1.
  * The fused ring kernel stages the sources through shared memory with bulk-async copies,
  * embeds them (phi_E), accumulates XORs of packet rotations for every set bit of phi_S(G[k+i][j])
- * and reduces mod p (phi_E^{-1}) before storing. No device memory is allocated. */
+ * and reduces mod p (phi_E^{-1}) before storing. No coding state is allocated on the device (the
+ * first use of a generated network loads its module: see "plan-specialised networks"). */
 PYRIT_API int pyrit_encode(pyrit_plan_t plan, const void* const* data, void* const* parity, size_t P,
                  pyrit_stream_t stream);
 
@@ -166,7 +169,9 @@ typedef struct {
   int mg;           /* outputs accumulated per consumer warp (2, 4 or 8)                 */
   int minb;         /* CTAs per multiprocessor the kernel's registers are sized for      */
   int nc;           /* consumer warps per CTA (8 or 16)                                  */
-  int dispatch;     /* 0: uniform test per ring shift; 1: switch per set mask bit        */
+  int dispatch;     /* 0: uniform test per ring shift; 1: switch per set mask bit;
+                       2: pairing automaton; 3 (PYRIT_DISPATCH_NETWORK): a network generated
+                       for the group's mask table (every stripe of the group must share it)  */
   int stages;       /* shared-memory pipeline depth (2..8)                               */
   int ctas_per_sm;  /* persistent grid = multiprocessors x ctas_per_sm                   */
 } pyrit_tile_t;
@@ -200,6 +205,9 @@ PYRIT_API int pyrit_batch_tune(pyrit_batch_t batch, pyrit_stream_t stream, int i
 PYRIT_API int pyrit_tune_save(const char* path);
 PYRIT_API int pyrit_tune_load(const char* path);
 
+/* Forgets every tuned shape (later batches use the automatic choice); returns how many there were. */
+PYRIT_API int pyrit_tune_clear(void);
+
 /* The compiled kernel variants, for introspection and tuning: writes up to `cap` rows of six ints
  * (n, words, mg, minb, dispatch, nc) into params_out (host) and returns the total count. */
 PYRIT_API int pyrit_variants(int* params_out, int cap);
@@ -210,8 +218,69 @@ PYRIT_API int pyrit_variants(int* params_out, int cap);
 PYRIT_API int pyrit_batch_stats(pyrit_batch_t batch, uint64_t* alg_bytes, uint64_t* src_bytes, int* launches,
                       uint64_t* tiles);
 
+/* The launch shape of group `group` (0-based, groups ordered by ring size) of a batch, as ten ints:
+ * n, words, mg, minb, dispatch, nc, output groups, tile bytes, pipeline stages, grid CTAs.
+ * dispatch 3 marks a plan-specialised network. PYRIT_E_INVALID_ARG past the last group. */
+PYRIT_API int pyrit_batch_shape(pyrit_batch_t batch, int group, int* params_out);
+
 /* Frees the batch's device memory and graph (synchronises the device). */
 PYRIT_API void pyrit_batch_destroy(pyrit_batch_t batch);
+
+/* ---- plan-specialised networks (run-time compilation) ---------------------------------------
+ *
+ * The generic kernels test every bit of phi_S(u) at run time to decide which packet rotations to
+ * XOR (Sec. 3). When every job of a launch shares one mask table -- the stripes of one code and
+ * operation, or decodes of one erasure pattern -- the library can instead generate the kernel's
+ * multiply-accumulate step for that table: per source, each ring accumulator receives one XOR
+ * expression over the rotated source packets that the coefficient's set bits select, with no bit
+ * tested. The generated step is compiled with NVRTC into an sm_103a cubin together with the same
+ * staging, phi_E^{-1} and store code as the generic kernels, cached per (shape, mask table) for the
+ * life of the process (at most 1024 networks, never unloaded) and loaded as a CUDA library.
+ *
+ * Where it is used. pyrit_batch_create specialises every launch group whose stripes share one mask
+ * table, compiling in the calling thread (about a second per new table), unless the policy is
+ * PYRIT_JIT_OFF or tile overrides are given (tile->dispatch = 3 asks for a network with the
+ * tile's words, mg, minb and nc); pyrit_batch_tune times the network shapes beside the generic
+ * variants. pyrit_encode / pyrit_decode and the server use a network
+ * when one for the job's table is already compiled; otherwise, under PYRIT_JIT_ASYNC, they queue
+ * it for a background compiler thread (at most 16 waiting) and run the generic kernel meanwhile.
+ * pyrit_code_stripes_noalloc never uses networks (loading one allocates device memory).
+ * A network that fails to compile or load leaves the generic kernel in use (pyrit_jit_stats counts
+ * the failure; pyrit_jit_log has the log), except where tile overrides ask for dispatch 3, which
+ * then fails with PYRIT_E_JIT. */
+#define PYRIT_DISPATCH_NETWORK 3
+#define PYRIT_JIT_OFF 0   /* generic kernels only                                              */
+#define PYRIT_JIT_SYNC 1  /* compile a missing network in the calling thread, then use it     */
+#define PYRIT_JIT_ASYNC 2 /* default: batches compile in the caller; single calls and the
+                             server queue a missing network and use the generic kernel meanwhile */
+
+/* Sets the process-wide policy (PYRIT_JIT_*) and returns the previous one; mode < 0 only queries. */
+PYRIT_API int pyrit_jit_mode(int mode);
+
+/* Compiles (host only, no device call) the network of a plan's encode (op PYRIT_OP_ENCODE) or of
+ * its decode for an erasure pattern (PYRIT_OP_DECODE) into the cache, so that later calls find it.
+ * tile: NULL for the default shape, else its words, mg, minb and nc (0 = default) select one.
+ * PYRIT_OK (also when there is nothing to code), a planning error, or PYRIT_E_JIT. */
+PYRIT_API int pyrit_plan_specialise(pyrit_plan_t plan, int op, uint64_t erasures, const pyrit_tile_t* tile);
+
+/* Waits up to timeout_ms for the background compiler to finish its queue: PYRIT_OK or
+ * PYRIT_E_TIMEOUT. */
+PYRIT_API int pyrit_jit_wait(int timeout_ms);
+
+/* stats_out[8]: networks cached, compiled, failed, compilations pending, lookups that returned a
+ * network, networks loaded, total compile time (us), specs ever queued for the background. */
+PYRIT_API int pyrit_jit_stats(uint64_t* stats_out);
+
+/* Copies the log of the last failed compilation or load (NUL-terminated, truncated to cap - 1)
+ * into buf; returns its full length. */
+PYRIT_API int pyrit_jit_log(char* buf, int cap);
+
+/* The CUDA C++ source generated for a mask table (masks[o*nin + j] = phi_S mask of output o,
+ * source j, as in pyrit_plan_encode_masks) over R_{2,n}, under the default shape or tile's
+ * overrides. Copies it NUL-terminated (truncated to cap - 1) into buf and returns its length, or
+ * PYRIT_E_INVALID_ARG. For inspection and tests; host only. */
+PYRIT_API int pyrit_jit_source(int n, int nin, int nout, const uint16_t* masks, const pyrit_tile_t* tile, char* buf,
+                     int cap);
 
 /* ---- served coding: continuous batching ---------------------------------------------------- */
 

@@ -56,6 +56,13 @@ int pyrit_tune_save(const char* path) {
   return PYRIT_OK;
 }
 
+int pyrit_tune_clear(void) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  const int n = (int)table().size();
+  table().clear();
+  return n;
+}
+
 int pyrit_tune_load(const char* path) {
   if (!path) return PYRIT_E_INVALID_ARG;
   FILE* f = std::fopen(path, "r");

@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cstring>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "pyrit_internal.h"
@@ -22,6 +23,8 @@ struct Group {
   uint32_t njobs = 0, ntiles = 0, tiles_per_job = 0;
   int max_nout = 0;
   TuneKey key;
+  bool netable = false;  // every job has the same nin, nout and masks: a generated network applies
+  JobDesc job0{};        // host copy of the group's first job (its mask table)
 };
 
 // Tiling of a group's jobs under a shape: with one P for all jobs, tile t covers job
@@ -145,15 +148,42 @@ int pyrit_batch_create(const pyrit_stripe_t* stripes, int count, const pyrit_til
       same_p = same_p && j.P == jobs[0].P;
       shared = shared && std::memcmp(j.mask, jobs[0].mask, sizeof(j.mask)) == 0;
     }
+    bool same_io = true;
+    for (const JobDesc& j : jobs) same_io = same_io && j.nin == jobs[0].nin && j.nout == jobs[0].nout;
     g.max_nout = max_nout;
     g.key = TuneKey{n, shared ? 1 : 0, max_nout, same_p ? log2_floor(jobs[0].P) : -1};
+    g.netable = shared && same_io;
+    g.job0 = jobs[0];
+    const bool jit_on = jit_mode() != PYRIT_JIT_OFF;
+    const Variant* v = nullptr;
+    ShapeHint sh_hint = hint;
     TuneVal tv;
-    const Variant* tuned = nullptr;
-    if (!tile && tune_lookup(g.key, &tv)) tuned = find_variant(n, tv.words, tv.dispatch, tv.mg, tv.minb, tv.nc);
-    if (tuned) {
-      ShapeHint th;
-      th.stages = tv.stages;
-      shape_for_variant(tuned, max_nout, th, &g.shape);
+    if (!tile && tune_lookup(g.key, &tv)) {
+      sh_hint = ShapeHint();
+      sh_hint.stages = tv.stages;
+      if (tv.dispatch != PYRIT_DISPATCH_NETWORK)
+        v = find_variant(n, tv.words, tv.dispatch, tv.mg, tv.minb, tv.nc);
+      else if (g.netable && jit_on)
+        v = net_variant(net_spec(n, jobs[0], tv.words, tv.mg, tv.minb, tv.nc), true);
+    }
+    if (!v && tile && hint.dispatch == PYRIT_DISPATCH_NETWORK) {
+      // an explicit request for a generated network must be honoured or fail
+      if (!g.netable) {
+        delete b;
+        return PYRIT_E_INVALID_ARG;
+      }
+      v = jit_on ? net_variant(net_spec(n, jobs[0], hint.words, hint.mg, hint.minb, hint.nc), true) : nullptr;
+      if (!v) {
+        delete b;
+        return PYRIT_E_JIT;
+      }
+    }
+    if (!v && !tile && g.netable && jit_on) {
+      sh_hint = ShapeHint();
+      v = net_variant(net_spec(n, jobs[0], 0, 0, 0, 0), true);  // a failure leaves the generic kernel
+    }
+    if (v) {
+      shape_for_variant(v, max_nout, sh_hint, &g.shape);
     } else if (!choose_shape(n, max_nout, hint, &g.shape, shared)) {
       delete b;
       return PYRIT_E_UNSUPPORTED_FIELD;
@@ -232,12 +262,25 @@ int pyrit_batch_tune(pyrit_batch_t b, pyrit_stream_t stream, int iters) {
   const Variant* all = variants(&nv);
   for (Group& g : b->groups) {
     const JobDesc* jobs = reinterpret_cast<const JobDesc*>(b->dev + g.jobs_off);
+    std::vector<const Variant*> cands;
+    for (int i = 0; i < nv; ++i)
+      if (all[i].n == g.key.n) cands.push_back(&all[i]);
+    if (g.netable && jit_mode() != PYRIT_JIT_OFF) {
+      // the network shapes, compiled side by side (host threads) before they are loaded and timed
+      NetSpec specs[8];
+      const int ns = net_candidate_shapes(g.key.n, g.job0.nout, specs, 8);
+      for (int i = 0; i < ns; ++i) specs[i] = net_spec(g.key.n, g.job0, specs[i].words, specs[i].mg, specs[i].minb, specs[i].nc);
+      std::vector<std::thread> th;
+      for (int i = 0; i < ns; ++i) th.emplace_back([&specs, i] { net_compile(specs[i]); });
+      for (auto& t : th) t.join();
+      for (int i = 0; i < ns; ++i)
+        if (const Variant* v = net_variant(specs[i], true)) cands.push_back(v);
+    }
     float best = 1e30f;
     TileShape best_shape = g.shape;
-    for (int i = 0; i < nv && rc == PYRIT_OK; ++i) {
-      if (all[i].n != g.key.n) continue;
+    for (size_t i = 0; i < cands.size() && rc == PYRIT_OK; ++i) {
       TileShape sh;
-      if (!shape_for_variant(&all[i], g.max_nout, ShapeHint(), &sh)) continue;
+      if (!shape_for_variant(cands[i], g.max_nout, ShapeHint(), &sh)) continue;
       resolve_grid(&sh);
       uint2* tiles = nullptr;  // the tiling depends on the candidate's tile width
       uint32_t ntiles = 0, tpj = 0;
@@ -285,6 +328,15 @@ int pyrit_batch_stats(pyrit_batch_t b, uint64_t* alg_bytes, uint64_t* src_bytes,
   if (src_bytes) *src_bytes = b->src_bytes;
   if (launches) *launches = b->launches;
   if (tiles) *tiles = b->tiles;
+  return PYRIT_OK;
+}
+
+int pyrit_batch_shape(pyrit_batch_t b, int group, int* params_out) {
+  if (!b || !params_out || group < 0 || group >= (int)b->groups.size()) return PYRIT_E_INVALID_ARG;
+  const TileShape& s = b->groups[(size_t)group].shape;
+  const Variant* v = s.v;
+  const int r[10] = {v->n, v->words, v->mg, v->minb, v->dispatch, v->nc, s.groups, s.tw, s.stages, s.grid};
+  std::memcpy(params_out, r, sizeof(r));
   return PYRIT_OK;
 }
 

@@ -8,12 +8,18 @@ using namespace pyrit;
 namespace {
 
 // Codes one job: the staged kernel when P and every pointer allow 16-byte bulk copies, else the
-// plain-load kernel. The job travels in the kernel's parameters: nothing is allocated.
+// plain-load kernel. The staged kernel is the generated network of the job's mask table when one
+// is compiled (a missing one is queued under PYRIT_JIT_ASYNC), else the generic one. The job
+// travels in the kernel's parameters: no coding state is allocated.
 int run_job(int n, const JobDesc& job, cudaStream_t stream) {
   if (job.nout == 0) return PYRIT_OK;
   if (job_is_staged(job)) {
     TileShape sh;
-    if (!choose_shape(n, job.nout, ShapeHint(), &sh)) return PYRIT_E_UNSUPPORTED_FIELD;
+    const Variant* net = net_variant(net_spec(n, job, 0, 0, 0, 0), false);
+    if (net)
+      shape_for_variant(net, job.nout, ShapeHint(), &sh);
+    else if (!choose_shape(n, job.nout, ShapeHint(), &sh))
+      return PYRIT_E_UNSUPPORTED_FIELD;
     const uint32_t tpj = tiles_for(job.P, sh);
     return launch_staged(sh, &job, nullptr, nullptr, tpj, tpj, stream);
   }

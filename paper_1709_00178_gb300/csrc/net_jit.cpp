@@ -1,0 +1,433 @@
+// Plan-specialised ring networks: the staged kernel with its multiply-accumulate step generated
+// for one mask table, compiled at run time (NVRTC) and loaded as a CUDA library.
+//
+// The generic kernels apply a coefficient r = phi_S(u) by testing its bits at run time: one XOR of
+// the source rotated by s packets per set bit s (paper Sec. 3). When every job of a launch has the
+// same mask table (all stripes of one code and operation: an encode batch, or decodes of one
+// erasure pattern) those tests are known before the launch. The generated step writes them out:
+// for source j and output i, ring accumulator t receives the XOR of the source packets
+// q = t - s (mod N) over the set bits s of r_ij, where q = W (the zero packet that phi_E pads,
+// Sec. 2.3.2) drops out -- one XOR expression per accumulator, no bit tested. Per source the
+// kernel takes one warp-uniform branch (a switch on the source index) into that straight-line
+// code. Staging, phi_E^{-1} and the stores are the generic kernels' own text (ring_staged.cuh).
+//
+// Compiled networks are cached per NetSpec (shape + mask table) for the life of the process and
+// never unloaded (a captured graph may still launch them). Compilation runs in the caller's thread
+// when it blocks, else in one background thread that takes queued specs in order.
+#include <cuda_runtime.h>
+#include <nvrtc.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "jit_sources.inc"
+#include "pyrit_internal.h"
+
+namespace pyrit {
+namespace {
+
+constexpr const char* kKernelName = "ring_staged_net";
+constexpr const char* kArch = "-arch=sm_103a";
+constexpr size_t kMaxEntries = 1024;  // networks kept per process
+constexpr size_t kMaxQueued = 16;     // specs waiting for the background compiler
+
+enum State { kPending, kReady, kFailed };
+
+struct Entry {
+  NetSpec spec;
+  State state = kPending;
+  bool queued = false;  // waiting in the background queue (not yet taken)
+  std::vector<char> cubin;
+  cudaLibrary_t lib = nullptr;
+  bool loaded = false;
+  Variant v{};
+};
+
+struct Jit {
+  std::mutex mu;
+  std::condition_variable cv;
+  std::map<std::string, std::unique_ptr<Entry>> cache;
+  std::deque<Entry*> queue;
+  std::thread worker;
+  int busy = 0;  // compilations running
+  bool stop = false;
+  std::atomic<int> mode{PYRIT_JIT_ASYNC};
+  uint64_t compiled = 0, failed = 0, hits = 0, queued_total = 0, loaded = 0, compile_us = 0;
+  std::string last_log;
+
+  ~Jit() {
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      stop = true;
+      queue.clear();
+    }
+    cv.notify_all();
+    if (worker.joinable()) worker.join();
+  }
+};
+
+Jit& jit() {
+  static Jit j;
+  return j;
+}
+
+std::string key_of(const NetSpec& s) { return std::string(reinterpret_cast<const char*>(&s), sizeof(s)); }
+
+void put(std::string& o, const char* fmt, long a = 0, long b = 0, long c = 0, long d = 0) {
+  char buf[256];
+  std::snprintf(buf, sizeof(buf), fmt, a, b, c, d);
+  o += buf;
+}
+
+// CUDA C++ source of a network (compiled together with the embedded ring_staged.cuh).
+std::string net_source(const NetSpec& s) {
+  const int N = s.n, W = N - 1;
+  const int groups = output_groups(s.mg, s.nout, s.nc);
+  std::string o;
+  o += "#include \"ring_staged.cuh\"\n"
+       "namespace pyrit {\n"
+       "struct NetMac {\n"
+       "  __device__ __forceinline__ void tile(const JobDesc*, int, int) {}\n"
+       "  template <int N, int WORDS, int MG>\n"
+       "  __device__ __forceinline__ void apply(uint32_t (&acc)[MG][N][WORDS], const uint32_t (&d)[N - 1][WORDS],\n"
+       "                                        int j, int g, int) {\n";
+  put(o, "    switch (g * %ld + j) {\n", s.nin);
+  for (int g = 0; g < groups; ++g) {
+    for (int j = 0; j < s.nin; ++j) {
+      put(o, "      case %ld: {\n#pragma unroll\n        for (int x = 0; x < WORDS; ++x) {\n", g * s.nin + j);
+      for (int ii = 0; ii < s.mg; ++ii) {
+        const int out = g * s.mg + ii;
+        if (out >= s.nout) break;
+        const uint32_t r = s.mask[j][out];
+        for (int t = 0; t < N; ++t) {
+          std::string terms;
+          for (int sh = 0; sh < N; ++sh) {
+            if (!((r >> sh) & 1u)) continue;
+            const int q = (t - sh + N) % N;
+            if (q == W) continue;  // the zero packet of the embedding
+            char buf[32];
+            std::snprintf(buf, sizeof(buf), " ^ d[%d][x]", q);
+            terms += buf;
+          }
+          if (terms.empty()) continue;
+          put(o, "          acc[%ld][%ld][x] ^=", ii, t);
+          o += terms.substr(2);
+          o += ";\n";
+        }
+      }
+      o += "        }\n      } break;\n";
+    }
+  }
+  o += "      default: break;\n    }\n  }\n};\n}  // namespace pyrit\n\n";
+  put(o, "extern \"C\" __global__ void __launch_bounds__(%ld, %ld)\n", (s.nc + 1) * 32, s.minb);
+  o += kKernelName;
+  o += "(const __grid_constant__ pyrit::CodeArgs a) {\n";
+  put(o, "  pyrit::ring_staged_body<%ld, %ld, %ld, %ld, pyrit::NetMac>(a);\n}\n", N, s.words, s.mg, s.nc);
+  return o;
+}
+
+// Compiles one spec into a cubin. Returns PYRIT_OK or PYRIT_E_JIT (log filled).
+int compile_spec(const NetSpec& s, std::vector<char>* cubin, std::string* log, uint64_t* us) {
+  const auto t0 = std::chrono::steady_clock::now();
+  const std::string src = net_source(s);
+  nvrtcProgram prog;
+  if (nvrtcCreateProgram(&prog, src.c_str(), "ring_staged_net.cu", kJitHeaderCount, kJitHeaders, kJitHeaderNames) !=
+      NVRTC_SUCCESS) {
+    *log = "nvrtcCreateProgram failed";
+    return PYRIT_E_JIT;
+  }
+  const char* opts[] = {kArch, "-std=c++17", "-lineinfo"};
+  const nvrtcResult r = nvrtcCompileProgram(prog, 3, opts);
+  size_t ls = 0;
+  nvrtcGetProgramLogSize(prog, &ls);
+  log->assign(ls, '\0');
+  if (ls) nvrtcGetProgramLog(prog, &(*log)[0]);
+  int rc = PYRIT_E_JIT;
+  size_t cs = 0;
+  if (r == NVRTC_SUCCESS && nvrtcGetCUBINSize(prog, &cs) == NVRTC_SUCCESS && cs > 0) {
+    cubin->resize(cs);
+    if (nvrtcGetCUBIN(prog, cubin->data()) == NVRTC_SUCCESS) rc = PYRIT_OK;
+  }
+  if (r != NVRTC_SUCCESS) *log = std::string(nvrtcGetErrorString(r)) + "\n" + *log;
+  nvrtcDestroyProgram(&prog);
+  *us = (uint64_t)std::chrono::duration_cast<std::chrono::microseconds>(std::chrono::steady_clock::now() - t0).count();
+  return rc;
+}
+
+// Records a finished compilation (lock held).
+void finish(Jit& J, Entry* e, int rc, std::vector<char>& cubin, const std::string& log, uint64_t us) {
+  J.compile_us += us;
+  if (rc == PYRIT_OK) {
+    e->cubin.swap(cubin);
+    e->state = kReady;
+    ++J.compiled;
+  } else {
+    e->state = kFailed;
+    J.last_log = log;
+    ++J.failed;
+  }
+}
+
+// Compiles `e` in this thread (lock held on entry and exit, released meanwhile).
+void compile_here(Jit& J, Entry* e, std::unique_lock<std::mutex>& lk) {
+  ++J.busy;
+  lk.unlock();
+  std::vector<char> cubin;
+  std::string log;
+  uint64_t us = 0;
+  const int rc = compile_spec(e->spec, &cubin, &log, &us);
+  lk.lock();
+  finish(J, e, rc, cubin, log, us);
+  --J.busy;
+  J.cv.notify_all();
+}
+
+void worker_main(Jit* J) {
+  std::unique_lock<std::mutex> lk(J->mu);
+  while (true) {
+    J->cv.wait(lk, [&] { return J->stop || !J->queue.empty(); });
+    if (J->stop) return;
+    Entry* e = J->queue.front();
+    J->queue.pop_front();
+    e->queued = false;
+    compile_here(*J, e, lk);
+  }
+}
+
+// The cache entry of `s` after the policy's step: compiled (or failed) when `block`, else possibly
+// still pending. nullptr when the cache is full or the queue has no room.
+Entry* obtain(Jit& J, const NetSpec& s, bool block, std::unique_lock<std::mutex>& lk) {
+  const std::string key = key_of(s);
+  auto it = J.cache.find(key);
+  Entry* e = it == J.cache.end() ? nullptr : it->second.get();
+  if (!e) {
+    if (J.cache.size() >= kMaxEntries || (!block && J.queue.size() >= kMaxQueued)) return nullptr;
+    std::unique_ptr<Entry> up(new Entry);
+    up->spec = s;
+    e = up.get();
+    J.cache.emplace(key, std::move(up));
+    if (!block) {
+      e->queued = true;
+      J.queue.push_back(e);
+      ++J.queued_total;
+      if (!J.worker.joinable()) J.worker = std::thread(worker_main, &J);
+      J.cv.notify_all();
+      return e;
+    }
+    compile_here(J, e, lk);
+    return e;
+  }
+  if (e->state == kPending && block) {
+    if (e->queued) {  // not started: take it out of the queue and compile it here
+      J.queue.erase(std::find(J.queue.begin(), J.queue.end(), e));
+      e->queued = false;
+      compile_here(J, e, lk);
+    } else {
+      J.cv.wait(lk, [&] { return e->state != kPending; });
+    }
+  }
+  return e;
+}
+
+struct Shape4 {
+  int words, half, minb, nc;  // half: mg = ceil(nout / 2) (two output groups) instead of nout
+};
+
+// Registers a consumer thread may use at (nc + 1) warps and minb CTAs per SM.
+int reg_cap(int nc, int minb) {
+  const int r = (65536 / ((nc + 1) * 32 * minb)) & ~7;
+  return r > 255 ? 255 : r;
+}
+
+}  // namespace
+
+int jit_mode() { return jit().mode.load(); }
+
+int net_candidate_shapes(int n, int nout, NetSpec* out, int cap) {
+  static const Shape4 big[] = {{1, 0, 1, 24}, {1, 0, 1, 16}, {1, 1, 1, 16}, {2, 0, 1, 8}, {1, 1, 1, 24}};
+  static const Shape4 small[] = {{1, 0, 1, 24}, {2, 0, 1, 16}, {4, 0, 1, 8}, {2, 0, 1, 8}, {1, 0, 1, 16}};
+  const Shape4* list = n >= 11 ? big : small;
+  int count = 0;
+  for (int i = 0; i < 5 && count < cap; ++i) {
+    const Shape4& c = list[i];
+    const int mg = c.half ? (nout + 1) / 2 : nout;
+    if (mg < 1 || (c.half && nout < 2)) continue;
+    const int groups = output_groups(mg, nout, c.nc);
+    if (c.nc % groups != 0 || groups * mg < nout) continue;
+    // accumulators + one staged source + addressing and loop state
+    if (mg * n * c.words + (n - 1) * c.words + 24 > reg_cap(c.nc, c.minb)) continue;
+    NetSpec s;
+    std::memset(&s, 0, sizeof(s));
+    s.n = n;
+    s.nout = nout;
+    s.words = c.words;
+    s.mg = mg;
+    s.minb = c.minb;
+    s.nc = c.nc;
+    out[count++] = s;
+  }
+  return count;
+}
+
+NetSpec net_spec(int n, const JobDesc& job, int words, int mg, int minb, int nc) {
+  NetSpec s;
+  std::memset(&s, 0, sizeof(s));
+  NetSpec def[1];
+  if (net_candidate_shapes(n, job.nout, def, 1) == 1) s = def[0];
+  s.n = n;
+  s.nin = job.nin;
+  s.nout = job.nout;
+  if (words) s.words = words;
+  if (mg) s.mg = mg;
+  if (minb) s.minb = minb;
+  if (nc) s.nc = nc;
+  if (!s.words) s.words = 1;
+  if (!s.mg) s.mg = job.nout;
+  if (!s.minb) s.minb = 1;
+  if (!s.nc) s.nc = 16;
+  for (int j = 0; j < job.nin; ++j)
+    for (int o = 0; o < job.nout; ++o) s.mask[j][o] = job.mask[j][o];
+  return s;
+}
+
+static bool spec_valid(const NetSpec& s) {
+  const bool words_ok = s.words == 1 || s.words == 2 || s.words == 4;
+  const bool nc_ok = s.nc >= 1 && s.nc <= 31;
+  return (s.n == 3 || s.n == 5 || s.n == 11 || s.n == 13) && s.nin >= 1 && s.nin <= kMaxIn && s.nout >= 1 &&
+         s.nout <= kMaxOut && words_ok && s.mg >= 1 && s.mg <= kMaxOut && s.minb >= 1 && s.minb <= 4 && nc_ok &&
+         output_groups(s.mg, s.nout, s.nc) * s.mg >= s.nout && s.nc % output_groups(s.mg, s.nout, s.nc) == 0;
+}
+
+int net_compile(const NetSpec& s) {
+  if (!spec_valid(s)) return PYRIT_E_INVALID_ARG;
+  Jit& J = jit();
+  std::unique_lock<std::mutex> lk(J.mu);
+  Entry* e = obtain(J, s, true, lk);
+  return e && e->state == kReady ? PYRIT_OK : PYRIT_E_JIT;
+}
+
+const Variant* net_variant(const NetSpec& s, bool block) {
+  Jit& J = jit();
+  const int mode = J.mode.load();
+  if (mode == PYRIT_JIT_OFF || !spec_valid(s)) return nullptr;
+  if (mode == PYRIT_JIT_SYNC) block = true;
+  std::unique_lock<std::mutex> lk(J.mu);
+  Entry* e = obtain(J, s, block, lk);
+  if (!e || e->state != kReady) return nullptr;
+  if (!e->loaded) {
+    // cudaLibraryLoadData makes the module available on every device of the process.
+    cudaKernel_t k = nullptr;
+    if (cudaLibraryLoadData(&e->lib, e->cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0) != cudaSuccess ||
+        cudaLibraryGetKernel(&k, e->lib, kKernelName) != cudaSuccess) {
+      cudaGetLastError();  // load failures are not sticky; clear them for the caller
+      e->state = kFailed;
+      J.last_log = "cudaLibraryLoadData / cudaLibraryGetKernel failed";
+      ++J.failed;
+      return nullptr;
+    }
+    e->v = Variant{s.n, s.words, s.mg, s.minb, PYRIT_DISPATCH_NETWORK, s.nc, reinterpret_cast<const void*>(k)};
+    e->loaded = true;
+    ++J.loaded;
+  }
+  ++J.hits;
+  return &e->v;
+}
+
+}  // namespace pyrit
+
+using namespace pyrit;
+
+extern "C" {
+
+int pyrit_jit_mode(int mode) {
+  Jit& J = jit();
+  if (mode < 0) return J.mode.load();
+  if (mode > PYRIT_JIT_ASYNC) return PYRIT_E_INVALID_ARG;
+  return J.mode.exchange(mode);
+}
+
+int pyrit_jit_wait(int timeout_ms) {
+  Jit& J = jit();
+  std::unique_lock<std::mutex> lk(J.mu);
+  const bool done = J.cv.wait_for(lk, std::chrono::milliseconds(timeout_ms < 0 ? 0 : timeout_ms),
+                                  [&] { return J.queue.empty() && J.busy == 0; });
+  return done ? PYRIT_OK : PYRIT_E_TIMEOUT;
+}
+
+int pyrit_jit_stats(uint64_t* stats_out) {
+  if (!stats_out) return PYRIT_E_INVALID_ARG;
+  Jit& J = jit();
+  std::lock_guard<std::mutex> lk(J.mu);
+  stats_out[0] = J.cache.size();
+  stats_out[1] = J.compiled;
+  stats_out[2] = J.failed;
+  stats_out[3] = J.queue.size() + (uint64_t)J.busy;
+  stats_out[4] = J.hits;
+  stats_out[5] = J.loaded;
+  stats_out[6] = J.compile_us;
+  stats_out[7] = J.queued_total;
+  return PYRIT_OK;
+}
+
+int pyrit_jit_log(char* buf, int cap) {
+  Jit& J = jit();
+  std::lock_guard<std::mutex> lk(J.mu);
+  const int len = (int)J.last_log.size();
+  if (buf && cap > 0) {
+    const int c = std::min(len, cap - 1);
+    std::memcpy(buf, J.last_log.data(), (size_t)c);
+    buf[c] = '\0';
+  }
+  return len;
+}
+
+int pyrit_plan_specialise(pyrit_plan_t plan, int op, uint64_t erasures, const pyrit_tile_t* tile) {
+  if (!plan) return PYRIT_E_INVALID_ARG;
+  std::vector<void*> none((size_t)(plan->k + plan->m), nullptr);  // only the masks are used
+  JobDesc job;
+  if (op == PYRIT_OP_ENCODE) {
+    if (plan->m == 0) return PYRIT_OK;
+    make_encode_job(plan, none.data(), none.data() + plan->k, 16, &job);
+  } else if (op == PYRIT_OP_DECODE) {
+    DecodeEntry e;
+    const int rc = plan_decode_entry(plan, erasures, &e);
+    if (rc != PYRIT_OK) return rc;
+    if (e.ne == 0) return PYRIT_OK;
+    make_decode_job(plan, e, none.data(), 16, &job);
+  } else {
+    return PYRIT_E_INVALID_ARG;
+  }
+  const NetSpec s = tile ? net_spec(plan->n, job, tile->words, tile->mg, tile->minb, tile->nc)
+                         : net_spec(plan->n, job, 0, 0, 0, 0);
+  return net_compile(s);
+}
+
+int pyrit_jit_source(int n, int nin, int nout, const uint16_t* masks, const pyrit_tile_t* tile, char* buf, int cap) {
+  if (!masks || nin < 1 || nin > kMaxIn || nout < 1 || nout > kMaxOut) return PYRIT_E_INVALID_ARG;
+  JobDesc job;
+  std::memset(&job, 0, sizeof(job));
+  job.nin = nin;
+  job.nout = nout;
+  for (int o = 0; o < nout; ++o)
+    for (int j = 0; j < nin; ++j) job.mask[j][o] = masks[o * nin + j];
+  const NetSpec s = tile ? net_spec(n, job, tile->words, tile->mg, tile->minb, tile->nc) : net_spec(n, job, 0, 0, 0, 0);
+  if (!spec_valid(s)) return PYRIT_E_INVALID_ARG;
+  const std::string src = net_source(s);
+  if (buf && cap > 0) {
+    const int c = std::min((int)src.size(), cap - 1);
+    std::memcpy(buf, src.data(), (size_t)c);
+    buf[c] = '\0';
+  }
+  return (int)src.size();
+}
+
+}  // extern "C"

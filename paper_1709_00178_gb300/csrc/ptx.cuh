@@ -2,7 +2,7 @@
 // through shared-memory mbarriers) and the global timer used to bound every wait.
 #pragma once
 
-#include <cstdint>
+#include "ring_abi.h"
 
 namespace pyrit {
 

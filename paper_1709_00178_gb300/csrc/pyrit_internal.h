@@ -10,43 +10,16 @@
 #include <cuda_runtime_api.h>
 
 #include "../../include/pyrit.h"
+#include "ring_abi.h"
 
 namespace pyrit {
 
-constexpr int kMaxIn = PYRIT_MAX_K;   // sources of one coding job (data blocks or survivors)
-constexpr int kMaxOut = PYRIT_MAX_M;  // destinations of one coding job (parity or erased blocks)
-
-// One coding job: out[i] = sum_j u_ij * in[j] over GF(2^w) in every symbol lane, where the
-// coefficient u_ij is given by its ring representative mask[j][i] (bit s = coefficient of x^s).
-// Encoding a stripe is the job (data -> parity, the generator's parity rows); decoding is the job
-// (survivors -> erased blocks, the decoding matrix). Lives in kernel parameters or device memory.
-struct alignas(16) JobDesc {
-  const uint8_t* in[kMaxIn];
-  uint8_t* out[kMaxOut];
-  uint16_t mask[kMaxIn][kMaxOut];  // source-major so one 16-byte load gives every output's mask
-  uint64_t P;                      // packet bytes
-  int32_t nin, nout;
-};
+static_assert(kMaxIn == PYRIT_MAX_K && kMaxOut == PYRIT_MAX_M, "job limits follow the C ABI's");
 
 // Dynamic shared memory of the staged kernel: S stages of W packets x tw bytes and 2 S mbarriers.
 inline size_t staged_smem_bytes(int stages, int w, int tw) {
   return (size_t)stages * w * tw + 2 * sizeof(uint64_t) * stages;
 }
-
-// Launch arguments of the staged ring kernel. Tiles are (job, column range [col0, col0 + tw)).
-// With tiles == nullptr every job has the same P and tiles_per_job = ceil(P / tw) tiles, tile t
-// covering job t / tiles_per_job.
-struct CodeArgs {
-  const JobDesc* jobs;  // device array; nullptr: the single job `job0`
-  const uint2* tiles;   // optional explicit tile list {job, col0}
-  uint32_t ntiles;
-  uint32_t tiles_per_job;
-  uint32_t tw;          // tile width in bytes (multiple of 16)
-  uint32_t groups;      // consumer warps are split into this many output groups
-  uint32_t stages;      // shared-memory pipeline depth
-  int* err;             // device error word (code, site) or nullptr
-  JobDesc job0;
-};
 
 // A compiled instance of the staged ring kernel.
 struct Variant {
@@ -54,10 +27,19 @@ struct Variant {
   int words;     // 32-bit words per consumer thread per packet
   int mg;        // outputs accumulated per consumer warp
   int minb;      // CTAs per SM the register budget is sized for
-  int dispatch;  // 0: uniform test per shift; 1: switch per set bit; 2: pairing automaton
+  int dispatch;  // 0: uniform test per shift; 1: switch per set bit; 2: pairing automaton;
+                 // 3: a network generated for one mask table (PYRIT_DISPATCH_NETWORK)
   int nc;        // consumer warps per CTA (one more warp is the producer)
   const void* fn;
 };
+
+// Output groups of a launch: the smallest power of two g with g * mg >= nout (and g < nc); the
+// consumer warps split evenly into them. Generated networks are compiled for this same split.
+inline int output_groups(int mg, int nout, int nc) {
+  int g = 1;
+  while (g * mg < nout && g < nc) g *= 2;
+  return g;
+}
 
 // Tile-shape choice of one launch.
 struct TileShape {
@@ -142,6 +124,28 @@ struct TuneVal {
 };
 bool tune_lookup(const TuneKey& k, TuneVal* v);
 void tune_record(const TuneKey& k, const TuneVal& v);
+// ---- plan-specialised networks (net_jit.cpp) ------------------------------------------------
+// A network is the staged kernel with its multiply-accumulate step generated for one mask table:
+// the XOR of rotated source packets that every (source, output) coefficient contributes is written
+// out as straight-line code, so no mask bit is tested at run time. Generated, compiled (NVRTC) and
+// cached per NetSpec; `mask` holds the table for j < nin, o < nout and zeros elsewhere.
+struct NetSpec {
+  int32_t n, nin, nout, words, mg, minb, nc, pad;
+  uint16_t mask[kMaxIn][kMaxOut];
+};
+// The network spec of a job under a shape (zero fields: the default shape for (n, nout)).
+NetSpec net_spec(int n, const JobDesc& job, int words, int mg, int minb, int nc);
+// Candidate shapes for (n, nout), the default first; returns how many were written (<= cap).
+int net_candidate_shapes(int n, int nout, NetSpec* out, int cap);
+// Run-time compilation policy (PYRIT_JIT_*).
+int jit_mode();
+// The compiled network of `s` loaded on the current device, or nullptr. With block, a missing
+// network is compiled now (or a pending one awaited); without, a missing one is queued for the
+// background compiler when the policy is PYRIT_JIT_ASYNC and nullptr is returned until it is ready.
+const Variant* net_variant(const NetSpec& s, bool block);
+// Compiles a spec into the cache (host only, no device call). PYRIT_OK or PYRIT_E_JIT.
+int net_compile(const NetSpec& s);
+
 // Fills shape->grid (SMs x occupancy) if it is 0; makes the one-time per-device attribute calls.
 void resolve_grid(TileShape* shape);
 // Tiles of one job of packet size P under a shape.

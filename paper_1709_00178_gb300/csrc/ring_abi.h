@@ -1,0 +1,52 @@
+// Plain-data types shared by the host library and every device compilation of the ring kernels:
+// nvcc for the generic kernels and the run-time compiler (NVRTC) for plan-specialised networks.
+// Both compilers see this exact text, so the layouts agree by construction.
+#pragma once
+
+#ifdef __CUDACC_RTC__
+// The run-time compiler has no C++ standard headers; LP64 (x86_64 and aarch64 Linux) widths.
+typedef unsigned char uint8_t;
+typedef unsigned short uint16_t;
+typedef unsigned int uint32_t;
+typedef int int32_t;
+typedef unsigned long uint64_t;
+typedef unsigned long uintptr_t;
+#else
+#include <cstddef>
+#include <cstdint>
+#include <vector_types.h>
+#endif
+
+namespace pyrit {
+
+constexpr int kMaxIn = 32;  // sources of one coding job (data blocks or survivors)
+constexpr int kMaxOut = 8;  // destinations of one coding job (parity or erased blocks)
+
+// One coding job: out[i] = sum_j u_ij * in[j] over GF(2^w) in every symbol lane, where the
+// coefficient u_ij is given by its ring representative mask[j][i] (bit s = coefficient of x^s).
+// Encoding a stripe is the job (data -> parity, the generator's parity rows); decoding is the job
+// (survivors -> erased blocks, the decoding matrix). Lives in kernel parameters or device memory.
+struct alignas(16) JobDesc {
+  const uint8_t* in[kMaxIn];
+  uint8_t* out[kMaxOut];
+  uint16_t mask[kMaxIn][kMaxOut];  // source-major so one 16-byte load gives every output's mask
+  uint64_t P;                      // packet bytes
+  int32_t nin, nout;
+};
+
+// Launch arguments of the staged ring kernel. Tiles are (job, column range [col0, col0 + tw)).
+// With tiles == nullptr every job has the same P and tiles_per_job = ceil(P / tw) tiles, tile t
+// covering job t / tiles_per_job.
+struct CodeArgs {
+  const JobDesc* jobs;  // device array; nullptr: the single job `job0`
+  const uint2* tiles;   // optional explicit tile list {job, col0}
+  uint32_t ntiles;
+  uint32_t tiles_per_job;
+  uint32_t tw;          // tile width in bytes (multiple of 16)
+  uint32_t groups;      // consumer warps are split into this many output groups
+  uint32_t stages;      // shared-memory pipeline depth
+  int* err;             // device error word (code, site) or nullptr
+  JobDesc job0;
+};
+
+}  // namespace pyrit

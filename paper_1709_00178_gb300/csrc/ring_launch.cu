@@ -5,6 +5,8 @@
 #include <algorithm>
 #include <cstring>
 #include <mutex>
+#include <set>
+#include <utility>
 
 #include "ring_kernel.cuh"
 
@@ -43,21 +45,16 @@ const Registry& registry() {
   return r;
 }
 
-// One-time per (variant, device) opt-in to the large dynamic shared-memory carve-out.
+// One-time per (kernel, device) opt-in to the large dynamic shared-memory carve-out; kernels are
+// the registered variants and the loaded generated networks.
 std::mutex g_attr_mu;
-bool g_attr_done[kMaxVariants][kMaxDevices];
-
-int variant_index(const Variant* v) { return (int)(v - registry().all); }
+std::set<std::pair<const void*, int>> g_attr_done;
 
 void ensure_attr(const Variant* v) {
   const int dev = current_device();
-  const int vi = variant_index(v);
-  if (dev < 0 || dev >= kMaxDevices || vi < 0 || vi >= kMaxVariants) return;
   std::lock_guard<std::mutex> lk(g_attr_mu);
-  if (!g_attr_done[vi][dev]) {
+  if (g_attr_done.insert({v->fn, dev}).second)
     cudaFuncSetAttribute(v->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    g_attr_done[vi][dev] = true;
-  }
 }
 
 size_t smem_bytes(const TileShape& s) { return staged_smem_bytes(s.stages, s.v->n - 1, s.tw); }
@@ -131,8 +128,7 @@ bool shape_for_variant(const Variant* v, int max_nout, const ShapeHint& h, TileS
   if (!v) return false;
   TileShape s;
   s.v = v;
-  int groups = 1;
-  while (groups * v->mg < max_nout && groups < v->nc) groups *= 2;
+  const int groups = output_groups(v->mg, max_nout, v->nc);
   s.groups = groups;
   s.tw = (v->nc / groups) * 32 * 4 * v->words;
   const int w = v->n - 1;

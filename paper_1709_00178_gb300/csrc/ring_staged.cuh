@@ -1,0 +1,223 @@
+// The staged ring-transform coding pipeline (paper Sec. 2.3.2 and Sec. 3), shared by the generic
+// kernels (compiled by nvcc) and the plan-specialised ones (generated at run time and compiled by
+// NVRTC). It is written for both compilers: no standard headers, only ring_abi.h and ptx.cuh.
+//
+// A coding job computes out[i] = sum_j u_ij in[j] over GF(2^w), w = N - 1, for every symbol lane
+// of bit-sliced blocks (packet q of a block holds coefficient q). Each coefficient arrives as its
+// ring representative r_ij = phi_S(u_ij) (an N-bit mask, Sec. 2.2). Per 32-bit column word the
+// pipeline:
+//   1. embeds the source block in R_{2,N} (phi_E): its W packets plus an implicit zero packet;
+//   2. for every set bit s of r_ij, XORs the source rotated by s packets into the N ring
+//      accumulators of output i (x^s times a ring element is a cyclic shift of its coefficients;
+//      the zero packet contributes nothing, so each set bit costs W XORs -- Sec. 3); this step is
+//      the policy `Mac`, either driven by the masks at run time or a network fixed at compile time;
+//   3. reduces each accumulator mod p (phi_E^{-1}): out[t] = acc[t] ^ acc[W] (Sec. 2.3.2), then
+//      stores the W field packets.
+// The extra ring packet is never written to memory, as in the paper's register scheme (Sec. 3).
+//
+// GB300 mapping (prior art: the paper's x86 SIMD register schedule). A CTA owns a column tile of
+// `tw` bytes of one job. A producer warp streams the job's source blocks, one block (W packets
+// x tw bytes, one lane per packet) per pipeline stage, into a shared-memory ring with bulk
+// asynchronous copies (cp.async.bulk, completion counted on an mbarrier); NC consumer warps read
+// their 4*WORDS bytes of every packet into registers and release the stage, then run the XOR
+// network out of registers. When a job has more outputs than one warp's accumulators hold (MG),
+// the consumer warps split into output groups that read the same staged tile, so every source
+// byte leaves HBM once.
+//
+// The policy Mac provides, per consumer warp:
+//   void tile(const JobDesc* J, int g, int lane);      // once per tile (e.g. load the masks)
+//   template <int N, int WORDS, int MG>
+//   void apply(uint32_t (&acc)[MG][N][WORDS], const uint32_t (&d)[N - 1][WORDS], int j, int g,
+//              int lane);                             // acc_i += r_ij * d for the group's outputs
+#pragma once
+
+#include "ptx.cuh"
+#include "ring_abi.h"
+
+namespace pyrit {
+
+__device__ __forceinline__ const JobDesc* tile_job(const CodeArgs& a, uint32_t t, uint32_t& col0) {
+  uint32_t jid;
+  if (a.tiles) {
+    const uint2 v = a.tiles[t];
+    jid = v.x;
+    col0 = v.y;
+  } else {
+    jid = t / a.tiles_per_job;
+    col0 = (t - jid * a.tiles_per_job) * a.tw;
+  }
+  return a.jobs ? a.jobs + jid : &a.job0;
+}
+
+template <int WORDS>
+struct Vec;
+template <>
+struct Vec<1> {
+  using T = uint32_t;
+};
+template <>
+struct Vec<2> {
+  using T = uint2;
+};
+template <>
+struct Vec<4> {
+  using T = uint4;
+};
+
+// Word x of a 1-, 2- or 4-word vector, and the vector of WORDS words.
+template <int WORDS>
+__device__ __forceinline__ uint32_t vword(const typename Vec<WORDS>::T& v, int x) {
+  if constexpr (WORDS == 1) {
+    return v;
+  } else if constexpr (WORDS == 2) {
+    return x == 0 ? v.x : v.y;
+  } else {
+    return x == 0 ? v.x : x == 1 ? v.y : x == 2 ? v.z : v.w;
+  }
+}
+template <int WORDS>
+__device__ __forceinline__ typename Vec<WORDS>::T vmake(const uint32_t (&w)[WORDS]) {
+  if constexpr (WORDS == 1) {
+    return w[0];
+  } else if constexpr (WORDS == 2) {
+    return make_uint2(w[0], w[1]);
+  } else {
+    return make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
+template <int N, int WORDS, int MG, int NC, class Mac>
+__device__ __forceinline__ void ring_staged_body(const CodeArgs& a) {
+  constexpr int W = N - 1;
+  using V = typename Vec<WORDS>::T;
+  extern __shared__ __align__(128) uint8_t smem[];
+  const uint32_t S = a.stages, TW = a.tw;
+  uint8_t* buf = smem;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)S * W * TW);
+  uint64_t* empty = full + S;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (uint32_t s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], NC);
+    }
+    mbar_fence_init();
+  }
+  __syncthreads();
+
+  if (warp == NC) {
+    // ---- producer warp: streams source blocks into the stage ring --------------------------
+    // Lane 0 waits for the stage to be free and arms its barrier with the stage's byte count;
+    // then lane q issues the bulk copy of packet q, so the W copies of a stage leave together.
+    const uint64_t pol = l2_evict_first_policy();
+    uint32_t stage = 0, phase = 0;
+    uint64_t armed = 0;  // stages armed so far
+    bool ok = true;
+    for (uint32_t t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
+      uint32_t col0;
+      const JobDesc* J = tile_job(a, t, col0);
+      const uint64_t P = J->P;
+      if (col0 >= P) continue;  // a tiling that does not match the tile width codes nothing past P
+      const uint32_t width = (uint32_t)(P - col0 < (uint64_t)TW ? P - col0 : (uint64_t)TW);
+      const int nin = J->nin;
+      for (int j = 0; j < nin; ++j) {
+        bool free_ok = true;
+        if (lane == 0) {
+          free_ok = mbar_wait(&empty[stage], phase ^ 1u, a.err, 1);
+          if (free_ok) mbar_arrive_expect_tx(&full[stage], (uint32_t)W * width);
+        }
+        ok = __all_sync(0xFFFFFFFFu, free_ok);  // also orders the arming before the copies
+        if (!ok) break;
+        if (lane < W)
+          bulk_load(buf + ((size_t)stage * W + lane) * TW, J->in[j] + col0 + (size_t)lane * P, width, &full[stage], pol);
+        ++armed;
+        if (++stage == S) {
+          stage = 0;
+          phase ^= 1u;
+        }
+      }
+    }
+    // Drain: wait (bounded) until every copy this warp issued has landed, so that no bulk copy
+    // is still writing shared memory when the CTA exits, on the normal and the error path alike.
+    if (lane == 0)
+      for (uint32_t s = 0; s < S; ++s) {
+        if (armed <= s) break;
+        const uint64_t times = (armed - 1 - s) / S + 1;
+        mbar_wait(&full[s], (uint32_t)((times - 1) & 1u), a.err, 3);
+      }
+    return;
+  }
+
+  // ---- consumers -------------------------------------------------------------------------
+  const int wpg = NC / (int)a.groups;  // warps per output group
+  const int g = warp / wpg;
+  const uint32_t off = (uint32_t)((warp % wpg) * 32 + lane) * (4u * WORDS);
+  uint32_t stage = 0, phase = 0;
+  for (uint32_t t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+    uint32_t col0;
+    const JobDesc* J = tile_job(a, t, col0);
+    const uint64_t P = J->P;
+    if (col0 >= P) continue;  // same rule as the producer: such a tile has no stages
+    const uint32_t width = (uint32_t)(P - col0 < (uint64_t)TW ? P - col0 : (uint64_t)TW);
+    const bool valid = off < width;
+    const int nin = J->nin, nout = J->nout;
+
+    Mac mac;
+    mac.tile(J, g, lane);
+
+    uint32_t acc[MG][N][WORDS];
+#pragma unroll
+    for (int i = 0; i < MG; ++i)
+#pragma unroll
+      for (int r = 0; r < N; ++r)
+#pragma unroll
+        for (int x = 0; x < WORDS; ++x) acc[i][r][x] = 0u;
+
+    for (int j = 0; j < nin; ++j) {
+      // Every lane observes the phase (so the staged bytes are visible to it); the give-up
+      // decision is made warp-uniform before anyone leaves.
+      if (!__all_sync(0xFFFFFFFFu, mbar_wait(&full[stage], phase, a.err, 2))) return;
+      uint32_t d[W][WORDS];
+      const uint8_t* sb = buf + (size_t)stage * W * TW + off;
+#pragma unroll
+      for (int q = 0; q < W; ++q) {
+        V v;
+        if (valid) {
+          v = *reinterpret_cast<const V*>(sb + (size_t)q * TW);
+        } else {
+          v = V{};
+        }
+#pragma unroll
+        for (int x = 0; x < WORDS; ++x) d[q][x] = vword<WORDS>(v, x);
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[stage]);
+      if (++stage == S) {
+        stage = 0;
+        phase ^= 1u;
+      }
+      mac.template apply<N, WORDS, MG>(acc, d, j, g, lane);
+    }
+
+    // phi_E^{-1}: reduce mod the AOP and store the W field packets of every output.
+    if (valid) {
+#pragma unroll
+      for (int i = 0; i < MG; ++i) {
+        const int o = g * MG + i;
+        if (o < nout) {
+          uint8_t* dst = J->out[o] + col0 + off;
+#pragma unroll
+          for (int r = 0; r < W; ++r) {
+            uint32_t o4[WORDS];
+#pragma unroll
+            for (int x = 0; x < WORDS; ++x) o4[x] = acc[i][r][x] ^ acc[i][W][x];
+            *reinterpret_cast<V*>(dst + (size_t)r * P) = vmake<WORDS>(o4);
+          }
+        }
+      }
+    }
+  }
+}
+
+}  // namespace pyrit

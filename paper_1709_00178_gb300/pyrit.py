@@ -33,6 +33,11 @@ PYRIT_E_BUDGET = -8
 PYRIT_E_TIMEOUT = -9
 PYRIT_E_BUSY = -10
 PYRIT_E_SCRATCH_LIMIT = -11
+PYRIT_E_JIT = -12
+PYRIT_DISPATCH_NETWORK = 3
+PYRIT_JIT_OFF = 0
+PYRIT_JIT_SYNC = 1
+PYRIT_JIT_ASYNC = 2
 PYRIT_NOALLOC_MAX_STRIPES = 256
 PYRIT_NOALLOC_MAX_TILES = 16384
 PYRIT_MAX_K = 32
@@ -211,7 +216,9 @@ _BATCH_SIGS = {
     "pyrit_batch_tune": (_i, [_vp, _vp, _i]),
     "pyrit_tune_save": (_i, [ctypes.c_char_p]),
     "pyrit_tune_load": (_i, [ctypes.c_char_p]),
+    "pyrit_tune_clear": (_i, []),
     "pyrit_variants": (_i, [_vp, _i]),
+    "pyrit_batch_shape": (_i, [_vp, _i, _vp]),
 }
 _bind(_BATCH_SIGS)
 EXPORTS = EXPORTS + tuple(_BATCH_SIGS)
@@ -265,12 +272,88 @@ def pyrit_variants():
     return [dict(zip(keys, (int(x) for x in buf[6 * i:6 * i + 6]))) for i in range(n)]
 
 
+def pyrit_batch_shape(batch, group=0):
+    """Launch shape of one group of a batch: dict of n, words, mg, minb, dispatch, nc, groups, tw,
+    stages, grid (dispatch 3 = a plan-specialised network)."""
+    buf = np.zeros(10, np.int32)
+    _check(_lib.pyrit_batch_shape(batch, group, _np_ptr(buf)), "pyrit_batch_shape")
+    keys = ("n", "words", "mg", "minb", "dispatch", "nc", "groups", "tw", "stages", "grid")
+    return dict(zip(keys, (int(x) for x in buf)))
+
+
 def pyrit_tune_save(path):
     return _check(_lib.pyrit_tune_save(os.fsencode(path)), "pyrit_tune_save")
 
 
 def pyrit_tune_load(path):
     return _check(_lib.pyrit_tune_load(os.fsencode(path)), "pyrit_tune_load")
+
+
+def pyrit_tune_clear():
+    return _check(_lib.pyrit_tune_clear(), "pyrit_tune_clear")
+
+
+# ---- plan-specialised networks (run-time compilation) ------------------------------------------
+
+_JIT_SIGS = {
+    "pyrit_jit_mode": (_i, [_i]),
+    "pyrit_plan_specialise": (_i, [_vp, _i, _u64, ctypes.POINTER(pyrit_tile_t)]),
+    "pyrit_jit_wait": (_i, [_i]),
+    "pyrit_jit_stats": (_i, [_vp]),
+    "pyrit_jit_log": (_i, [ctypes.c_char_p, _i]),
+    "pyrit_jit_source": (_i, [_i, _i, _i, _vp, ctypes.POINTER(pyrit_tile_t), ctypes.c_char_p, _i]),
+}
+_bind(_JIT_SIGS)
+EXPORTS = EXPORTS + tuple(_JIT_SIGS)
+
+
+def _tile(tile):
+    if tile is None:
+        return None
+    return pyrit_tile_t(tile.get("words", 0), tile.get("mg", 0), tile.get("minb", 0), tile.get("nc", 0),
+                        tile.get("dispatch", -1), tile.get("stages", 0), tile.get("ctas_per_sm", 0))
+
+
+def pyrit_jit_mode(mode=-1):
+    """Sets the run-time compilation policy (PYRIT_JIT_*) and returns the previous one."""
+    return _check(_lib.pyrit_jit_mode(mode), "pyrit_jit_mode")
+
+
+def pyrit_plan_specialise(plan, op=PYRIT_OP_ENCODE, erasures=0, tile=None):
+    t = _tile(tile)
+    return _check(_lib.pyrit_plan_specialise(plan, op, erasures, ctypes.byref(t) if t is not None else None),
+                  "pyrit_plan_specialise")
+
+
+def pyrit_jit_wait(timeout_ms=60000):
+    return _check(_lib.pyrit_jit_wait(timeout_ms), "pyrit_jit_wait")
+
+
+def pyrit_jit_stats():
+    buf = np.zeros(8, np.uint64)
+    _check(_lib.pyrit_jit_stats(_np_ptr(buf)), "pyrit_jit_stats")
+    keys = ("cached", "compiled", "failed", "pending", "hits", "loaded", "compile_us", "queued_total")
+    return dict(zip(keys, (int(x) for x in buf)))
+
+
+def pyrit_jit_log():
+    n = _lib.pyrit_jit_log(None, 0)
+    buf = ctypes.create_string_buffer(n + 1)
+    _lib.pyrit_jit_log(buf, n + 1)
+    return buf.value.decode(errors="replace")
+
+
+def pyrit_jit_source(n, masks, tile=None):
+    """Generated CUDA source for a mask table (2-D array, masks[o][j] = phi_S mask of output o,
+    source j) over R_{2,n}."""
+    m = np.ascontiguousarray(np.asarray(masks, dtype=np.uint16))
+    nout, nin = m.shape
+    t = _tile(tile)
+    size = _check(_lib.pyrit_jit_source(n, nin, nout, _np_ptr(m), ctypes.byref(t) if t is not None else None, None, 0),
+                  "pyrit_jit_source")
+    buf = ctypes.create_string_buffer(size + 1)
+    _lib.pyrit_jit_source(n, nin, nout, _np_ptr(m), ctypes.byref(t) if t is not None else None, buf, size + 1)
+    return buf.value.decode()
 
 
 # ---- coding without device allocation ---------------------------------------------------------

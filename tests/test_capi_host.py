@@ -199,3 +199,8 @@ def test_tune_table_save_load_roundtrip(tmp_path):
     out = tmp_path / "o.json"
     pyrit.pyrit_tune_save(str(out))
     assert '"n": 13, "shared": 0, "nout": 4, "plog2": 15, "words": 4' in out.read_text()
+    # clearing forgets every entry
+    assert pyrit.pyrit_tune_clear() >= 1
+    pyrit.pyrit_tune_save(str(out))
+    assert '"n": 13' not in out.read_text()
+    assert pyrit.pyrit_tune_clear() == 0

@@ -1,0 +1,171 @@
+"""Plan-specialised networks on the host (no GPU).
+
+The library writes, for a mask table, the multiply-accumulate step of the staged kernel as
+straight-line XORs (one expression per ring accumulator and output, per source). These tests read
+that generated source back, interpret its XOR lists on single symbol lanes and compare them with the
+oracle: the network of mask r must be multiplication by r in R_{2,n} (paper Sec. 2.3.2 / Sec. 3),
+and after the phi_E^{-1} fold (out_t = acc_t + acc_w) the field product by the coefficient whose
+sparse representative r is (Sec. 2.2). The map is linear in the source, so checking every basis
+vector x^q (q < w) is exhaustive. They also run the run-time compiler (NVRTC) for sm_103a, which
+needs no device.
+"""
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1709_00178_gb300 import pyrit
+
+
+def _parse(src):
+    nin = int(re.search(r"switch \(g \* (\d+) \+ j\)", src).group(1))
+    n, words, mg, nc = map(int, re.search(r"ring_staged_body<(\d+), (\d+), (\d+), (\d+),", src).groups())
+    cases, cur = {}, None
+    for line in src.splitlines():
+        c = re.match(r"\s*case (\d+): \{", line)
+        if c:
+            cur = int(c.group(1))
+            cases[cur] = []
+            continue
+        a = re.match(r"\s*acc\[(\d+)\]\[(\d+)\]\[x\] \^= (.*);", line)
+        if a:
+            assert cur is not None
+            qs = [int(q) for q in re.findall(r"d\[(\d+)\]\[x\]", a.group(3))]
+            cases[cur].append((int(a.group(1)), int(a.group(2)), qs))
+        if "} break;" in line:
+            cur = None
+    return dict(nin=nin, n=n, words=words, mg=mg, nc=nc, cases=cases)
+
+
+def _ring_columns(entries, ii, n, w):
+    """Ring accumulators of output slot ii for each basis source x^q: list of n-bit ints."""
+    cols = []
+    for q in range(w):
+        acc = 0
+        for (i, t, qs) in entries:
+            if i == ii:
+                for qq in qs:
+                    assert 0 <= qq < w, "the zero packet of the embedding must not be read"
+                    if qq == q:
+                        acc ^= 1 << t
+        cols.append(acc)
+    return cols
+
+
+def _check_network(src, masks, n):
+    """masks[o][j]: the table the source was generated for. Every (j, o) must be covered once."""
+    net = _parse(src)
+    w = n - 1
+    nout, nin = masks.shape
+    assert net["n"] == n and net["nin"] == nin
+    mg = net["mg"]
+    seen = set()
+    for case, entries in net["cases"].items():
+        g, j = divmod(case, nin)
+        for ii in range(mg):
+            o = g * mg + ii
+            if o >= nout:
+                assert not [e for e in entries if e[0] == ii], "a slot past the outputs is written"
+                continue
+            seen.add((j, o))
+            cols = _ring_columns(entries, ii, n, w)
+            for q in range(w):
+                assert cols[q] == oracle.ring_mul(n, int(masks[o][j]), 1 << q), (case, ii, q)
+    assert seen == {(j, o) for j in range(nin) for o in range(nout)}
+    return net
+
+
+def _oracle_parity_masks(w, k, m):
+    G = oracle.cauchy(w, k, m)
+    C = G[k:]
+    masks = np.array([[oracle.sparse_rep(w, w + 1, int(C[o][j])) for j in range(k)] for o in range(m)], np.uint16)
+    return C, masks
+
+
+@pytest.mark.parametrize("w,k,m", [(10, 10, 4), (12, 16, 4), (4, 8, 8), (2, 1, 2), (10, 32, 8)])
+def test_generated_network_is_the_field_product(w, k, m):
+    n = w + 1
+    C, masks = _oracle_parity_masks(w, k, m)
+    net = _check_network(pyrit.pyrit_jit_source(n, masks), masks, n)
+    # phi_E^{-1} of the ring columns gives the field product by the Cauchy coefficient
+    for case, entries in net["cases"].items():
+        g, j = divmod(case, k)
+        for ii in range(net["mg"]):
+            o = g * net["mg"] + ii
+            if o >= m:
+                continue
+            for q, col in enumerate(_ring_columns(entries, ii, n, w)):
+                top = (col >> w) & 1
+                field = (col ^ (((1 << n) - 1) if top else 0)) & ((1 << w) - 1)
+                assert field == oracle.gf_mul_slow(w, int(C[o][j]), 1 << q)
+
+
+@pytest.mark.parametrize("n", [3, 5, 11, 13])
+def test_generated_network_random_masks_and_shapes(n):
+    rng = np.random.default_rng(1000 + n)
+    shapes = [None, {"mg": 0, "nc": 16}, {"words": 2, "nc": 8}]
+    for trial in range(6):
+        nin = int(rng.integers(1, 33))
+        nout = int(rng.integers(1, 9))
+        masks = rng.integers(0, 1 << n, size=(nout, nin)).astype(np.uint16)
+        masks[0][0] = 0                 # a zero coefficient writes nothing
+        masks[-1][-1] = (1 << n) - 1    # every shift
+        tile = shapes[trial % len(shapes)]
+        if trial == 5 and nout >= 2:
+            tile = {"mg": (nout + 1) // 2, "nc": 16}  # two output groups
+        _check_network(pyrit.pyrit_jit_source(n, masks, tile), masks, n)
+
+
+def test_output_groups_split_the_outputs():
+    C, masks = _oracle_parity_masks(10, 10, 8)
+    net = _check_network(pyrit.pyrit_jit_source(11, masks, {"mg": 4, "nc": 16}), masks, 11)
+    assert net["mg"] == 4 and max(net["cases"]) == 2 * 10 - 1
+
+
+def test_jit_source_rejects_bad_tables():
+    masks = np.zeros((4, 10), np.uint16)
+    for bad in [(7, masks, None), (11, np.zeros((9, 10), np.uint16), None), (11, np.zeros((4, 33), np.uint16), None),
+                (11, masks, {"words": 3}), (11, masks, {"nc": 40})]:
+        with pytest.raises(pyrit.PyritError) as ei:
+            pyrit.pyrit_jit_source(*bad)
+        assert ei.value.status == pyrit.PYRIT_E_INVALID_ARG
+
+
+def test_jit_mode_roundtrip():
+    prev = pyrit.pyrit_jit_mode()
+    try:
+        assert pyrit.pyrit_jit_mode(pyrit.PYRIT_JIT_OFF) == prev
+        assert pyrit.pyrit_jit_mode(pyrit.PYRIT_JIT_SYNC) == pyrit.PYRIT_JIT_OFF
+        assert pyrit.pyrit_jit_mode() == pyrit.PYRIT_JIT_SYNC
+        with pytest.raises(pyrit.PyritError):
+            pyrit.pyrit_jit_mode(7)
+    finally:
+        pyrit.pyrit_jit_mode(prev)
+
+
+@pytest.mark.parametrize("w,k,m", [(2, 1, 2), (4, 8, 4), (10, 10, 4), (12, 16, 4)])
+def test_runtime_compiler_builds_networks_without_a_device(w, k, m):
+    plan = pyrit.pyrit_plan_create(w, w + 1, k, m)
+    try:
+        before = pyrit.pyrit_jit_stats()
+        pyrit.pyrit_plan_specialise(plan)
+        pyrit.pyrit_plan_specialise(plan, pyrit.PYRIT_OP_DECODE, 0b11)
+        mid = pyrit.pyrit_jit_stats()
+        assert mid["failed"] == before["failed"], pyrit.pyrit_jit_log()
+        # the same tables again are cache hits: nothing new is compiled
+        pyrit.pyrit_plan_specialise(plan)
+        pyrit.pyrit_plan_specialise(plan, pyrit.PYRIT_OP_DECODE, 0b11)
+        after = pyrit.pyrit_jit_stats()
+        assert after["compiled"] == mid["compiled"] and after["cached"] == mid["cached"]
+        assert mid["cached"] - before["cached"] <= 2
+        # nothing erased: nothing to specialise
+        pyrit.pyrit_plan_specialise(plan, pyrit.PYRIT_OP_DECODE, 0)
+        with pytest.raises(pyrit.PyritError) as ei:
+            pyrit.pyrit_plan_specialise(plan, pyrit.PYRIT_OP_DECODE, (1 << (m + 1)) - 1)
+        assert ei.value.status == pyrit.PYRIT_E_TOO_MANY_ERASURES
+        with pytest.raises(pyrit.PyritError) as ei:
+            pyrit.pyrit_plan_specialise(plan, tile={"words": 3})
+        assert ei.value.status == pyrit.PYRIT_E_INVALID_ARG
+    finally:
+        pyrit.pyrit_plan_destroy(plan)
