@@ -75,6 +75,7 @@ typedef struct CUstream_st* pyrit_stream_t;
 /* Operations. */
 #define PYRIT_OP_ENCODE 0
 #define PYRIT_OP_DECODE 1
+#define PYRIT_OP_DECODE_ANY 2 /* pyrit_plan_specialise only: the plan's syndrome-decode network */
 
 /* Name of a status code (static string). */
 PYRIT_API const char* pyrit_strerror(int status);
@@ -118,6 +119,16 @@ PYRIT_API int pyrit_plan_encode_masks(pyrit_plan_t plan, uint16_t* masks_out);
  * Computed once per (plan, pattern) and cached in the plan. */
 PYRIT_API int pyrit_plan_decode_masks(pyrit_plan_t plan, uint64_t erasures, int* survivors_out,
                             int* erased_out, uint16_t* masks_out, int* ne_out);
+
+/* The syndrome form of the decoding for an erasure pattern (used by the plan's syndrome-decode
+ * network; requires k + m <= PYRIT_MAX_K). With U the first a surviving parity rows (a = erased
+ * data blocks) and, for parity row r, acc_r = (sum of C[r][j] d_j over surviving data j) + p_r
+ * when r is in U, every erased block (ascending, as in pyrit_plan_decode_masks) is a sum of the
+ * rows' values: output o = acc_{base-1} (when base = syn_out[8*8 + o] > 0: an erased parity block
+ * adds its own partial sum) + sum over rows r of phi_S^{-1}(syn_out[r*8 + o]) * acc_r.
+ * syn_out: host array of 9 x 8 uint16 (rows r = 0..7, then the base row), zero past the erased
+ * count *ne_out. Host only. */
+PYRIT_API int pyrit_plan_syndrome_masks(pyrit_plan_t plan, uint64_t erasures, uint16_t* syn_out, int* ne_out);
 
 /* phi_S of one field element u < 2^w: the lighter of its two ring representatives u and
  * u + p(x) (Sec. 2.2; for an AOP and odd n the weights differ, so there is no tie).
@@ -218,9 +229,10 @@ PYRIT_API int pyrit_variants(int* params_out, int cap);
 PYRIT_API int pyrit_batch_stats(pyrit_batch_t batch, uint64_t* alg_bytes, uint64_t* src_bytes, int* launches,
                       uint64_t* tiles);
 
-/* The launch shape of group `group` (0-based, groups ordered by ring size) of a batch, as ten ints:
- * n, words, mg, minb, dispatch, nc, output groups, tile bytes, pipeline stages, grid CTAs.
- * dispatch 3 marks a plan-specialised network. PYRIT_E_INVALID_ARG past the last group. */
+/* The launch shape of group `group` (0-based, groups ordered by ring size) of a batch, as eleven
+ * ints: n, words, mg, minb, dispatch, nc, output groups, tile bytes, pipeline stages, grid CTAs,
+ * network mode. dispatch 3 marks a plan-specialised network, of the group's own mask table (mode
+ * 0) or a plan's syndrome decode (mode 1). PYRIT_E_INVALID_ARG past the last group. */
 PYRIT_API int pyrit_batch_shape(pyrit_batch_t batch, int group, int* params_out);
 
 /* Frees the batch's device memory and graph (synchronises the device). */
@@ -257,8 +269,10 @@ PYRIT_API void pyrit_batch_destroy(pyrit_batch_t batch);
 /* Sets the process-wide policy (PYRIT_JIT_*) and returns the previous one; mode < 0 only queries. */
 PYRIT_API int pyrit_jit_mode(int mode);
 
-/* Compiles (host only, no device call) the network of a plan's encode (op PYRIT_OP_ENCODE) or of
- * its decode for an erasure pattern (PYRIT_OP_DECODE) into the cache, so that later calls find it.
+/* Compiles (host only, no device call) the network of a plan's encode (op PYRIT_OP_ENCODE), of
+ * its decode for one erasure pattern (PYRIT_OP_DECODE), or its syndrome-decode network, which
+ * serves every erasure pattern (PYRIT_OP_DECODE_ANY; requires k + m <= PYRIT_MAX_K), into the
+ * cache, so that later calls find it.
  * tile: NULL for the default shape, else its words, mg, minb and nc (0 = default) select one.
  * PYRIT_OK (also when there is nothing to code), a planning error, or PYRIT_E_JIT. */
 PYRIT_API int pyrit_plan_specialise(pyrit_plan_t plan, int op, uint64_t erasures, const pyrit_tile_t* tile);

@@ -25,7 +25,14 @@ struct Group {
   TuneKey key;
   bool netable = false;  // every job has the same nin, nout and masks: a generated network applies
   JobDesc job0{};        // host copy of the group's first job (its mask table)
+  const pyrit_plan_s* syn_plan = nullptr;  // all jobs decode this plan: its syndrome network applies
+  size_t syn_off = 0;                      // the syndrome-form jobs in the device allocation
 };
+
+// The group's device job array for a variant (syndrome networks take syndrome-form jobs).
+const JobDesc* group_jobs(const uint8_t* dev, const Group& g, const Variant* v) {
+  return reinterpret_cast<const JobDesc*>(dev + (v && v->mode == 1 ? g.syn_off : g.jobs_off));
+}
 
 // Tiling of a group's jobs under a shape: with one P for all jobs, tile t covers job
 // t / tiles_per_job; otherwise an explicit list {job, col0} is built and copied to the device.
@@ -77,8 +84,8 @@ namespace {
 
 int enqueue(pyrit_batch_s* b, cudaStream_t st) {
   for (const Group& g : b->groups) {
-    const JobDesc* jobs = reinterpret_cast<const JobDesc*>(b->dev + g.jobs_off);
-    const int rc = launch_staged(g.shape, nullptr, jobs, g.tiles_dev, g.ntiles, g.tiles_per_job, st);
+    const int rc = launch_staged(g.shape, nullptr, group_jobs(b->dev, g, g.shape.v), g.tiles_dev, g.ntiles,
+                                 g.tiles_per_job, st);
     if (rc != PYRIT_OK) return rc;
   }
   for (const auto& pj : b->plain) {
@@ -109,8 +116,9 @@ int pyrit_batch_create(const pyrit_stripe_t* stripes, int count, const pyrit_til
   if (!b) return PYRIT_E_OOM;
   cudaGetDevice(&b->device);
 
-  // Jobs per ring size, in stripe order.
+  // Jobs per ring size, in stripe order (with the stripe each came from).
   std::vector<std::vector<JobDesc>> by_n(16);
+  std::vector<std::vector<int>> src_of(16);
   for (int i = 0; i < count; ++i) {
     JobDesc job;
     uint64_t alg = 0, src = 0;
@@ -123,9 +131,10 @@ int pyrit_batch_create(const pyrit_stripe_t* stripes, int count, const pyrit_til
     if (job.nout == 0) continue;
     b->alg_bytes += alg;
     const int n = stripes[i].plan->n;
-    if (job_is_staged(job))
+    if (job_is_staged(job)) {
       by_n[n].push_back(job);
-    else
+      src_of[n].push_back(i);
+    } else
       b->plain.emplace_back(n, job);
   }
 
@@ -154,6 +163,24 @@ int pyrit_batch_create(const pyrit_stripe_t* stripes, int count, const pyrit_til
     g.key = TuneKey{n, shared ? 1 : 0, max_nout, same_p ? log2_floor(jobs[0].P) : -1};
     g.netable = shared && same_io;
     g.job0 = jobs[0];
+    // Syndrome decoding: every job decodes a stripe of one plan whose columns fit a job.
+    const pyrit_plan_s* plan0 = stripes[src_of[n][0]].plan;
+    bool syn = plan0->k + plan0->m <= kMaxIn;
+    for (int si : src_of[n]) syn = syn && stripes[si].op == PYRIT_OP_DECODE && stripes[si].plan == plan0;
+    std::vector<JobDesc> syn_jobs;
+    if (syn) {
+      for (int si : src_of[n]) {
+        DecodeEntry e;
+        if (plan_decode_entry(stripes[si].plan, stripes[si].erasures, &e) != PYRIT_OK || !e.syn_ok) {
+          syn = false;
+          break;
+        }
+        JobDesc sj;
+        make_syndrome_job(plan0, e, stripes[si].blocks, stripes[si].packet_bytes, &sj);
+        syn_jobs.push_back(sj);
+      }
+    }
+    if (syn) g.syn_plan = plan0;
     const bool jit_on = jit_mode() != PYRIT_JIT_OFF;
     const Variant* v = nullptr;
     ShapeHint sh_hint = hint;
@@ -165,22 +192,31 @@ int pyrit_batch_create(const pyrit_stripe_t* stripes, int count, const pyrit_til
         v = find_variant(n, tv.words, tv.dispatch, tv.mg, tv.minb, tv.nc);
       else if (g.netable && jit_on)
         v = net_variant(net_spec(n, jobs[0], tv.words, tv.mg, tv.minb, tv.nc), true);
+      else if (g.syn_plan && jit_on)
+        v = net_variant(net_spec_syndrome(g.syn_plan, tv.words, tv.minb, tv.nc), true);
     }
     if (!v && tile && hint.dispatch == PYRIT_DISPATCH_NETWORK) {
-      // an explicit request for a generated network must be honoured or fail
-      if (!g.netable) {
+      // an explicit request for a generated network must be honoured or fail: the group's own
+      // table when its jobs share one, else the plan's syndrome network
+      if (!g.netable && !g.syn_plan) {
         delete b;
         return PYRIT_E_INVALID_ARG;
       }
-      v = jit_on ? net_variant(net_spec(n, jobs[0], hint.words, hint.mg, hint.minb, hint.nc), true) : nullptr;
+      if (jit_on)
+        v = g.netable ? net_variant(net_spec(n, jobs[0], hint.words, hint.mg, hint.minb, hint.nc), true)
+                      : net_variant(net_spec_syndrome(g.syn_plan, hint.words, hint.minb, hint.nc), true);
       if (!v) {
         delete b;
         return PYRIT_E_JIT;
       }
     }
-    if (!v && !tile && g.netable && jit_on) {
+    if (!v && !tile && jit_on) {
       sh_hint = ShapeHint();
-      v = net_variant(net_spec(n, jobs[0], 0, 0, 0, 0), true);  // a failure leaves the generic kernel
+      // a failure leaves the generic kernel
+      if (g.netable)
+        v = net_variant(net_spec(n, jobs[0], 0, 0, 0, 0), true);
+      else if (g.syn_plan)
+        v = net_variant(net_spec_syndrome(g.syn_plan, 0, 0, 0), true);
     }
     if (v) {
       shape_for_variant(v, max_nout, sh_hint, &g.shape);
@@ -190,6 +226,7 @@ int pyrit_batch_create(const pyrit_stripe_t* stripes, int count, const pyrit_til
     }
     g.njobs = (uint32_t)jobs.size();
     g.jobs_off = place(jobs.data(), jobs.size() * sizeof(JobDesc));
+    if (g.syn_plan) g.syn_off = place(syn_jobs.data(), syn_jobs.size() * sizeof(JobDesc));
     for (const JobDesc& j : jobs) g.job_P.push_back(j.P);
     b->groups.push_back(g);
   }
@@ -261,7 +298,6 @@ int pyrit_batch_tune(pyrit_batch_t b, pyrit_stream_t stream, int iters) {
   int nv = 0;
   const Variant* all = variants(&nv);
   for (Group& g : b->groups) {
-    const JobDesc* jobs = reinterpret_cast<const JobDesc*>(b->dev + g.jobs_off);
     std::vector<const Variant*> cands;
     for (int i = 0; i < nv; ++i)
       if (all[i].n == g.key.n) cands.push_back(&all[i]);
@@ -270,6 +306,14 @@ int pyrit_batch_tune(pyrit_batch_t b, pyrit_stream_t stream, int iters) {
       NetSpec specs[8];
       const int ns = net_candidate_shapes(g.key.n, g.job0.nout, specs, 8);
       for (int i = 0; i < ns; ++i) specs[i] = net_spec(g.key.n, g.job0, specs[i].words, specs[i].mg, specs[i].minb, specs[i].nc);
+      std::vector<std::thread> th;
+      for (int i = 0; i < ns; ++i) th.emplace_back([&specs, i] { net_compile(specs[i]); });
+      for (auto& t : th) t.join();
+      for (int i = 0; i < ns; ++i)
+        if (const Variant* v = net_variant(specs[i], true)) cands.push_back(v);
+    } else if (g.syn_plan && jit_mode() != PYRIT_JIT_OFF) {
+      NetSpec specs[8];
+      const int ns = net_syndrome_shapes(g.syn_plan, specs, 8);
       std::vector<std::thread> th;
       for (int i = 0; i < ns; ++i) th.emplace_back([&specs, i] { net_compile(specs[i]); });
       for (auto& t : th) t.join();
@@ -286,6 +330,7 @@ int pyrit_batch_tune(pyrit_batch_t b, pyrit_stream_t stream, int iters) {
       uint32_t ntiles = 0, tpj = 0;
       rc = make_tiling(g, sh, &tiles, &ntiles, &tpj);
       if (rc != PYRIT_OK) break;
+      const JobDesc* jobs = group_jobs(b->dev, g, cands[i]);
       rc = launch_staged(sh, nullptr, jobs, tiles, ntiles, tpj, st);  // warm-up
       if (rc == PYRIT_OK) {
         cudaEventRecord(e0, st);
@@ -335,7 +380,7 @@ int pyrit_batch_shape(pyrit_batch_t b, int group, int* params_out) {
   if (!b || !params_out || group < 0 || group >= (int)b->groups.size()) return PYRIT_E_INVALID_ARG;
   const TileShape& s = b->groups[(size_t)group].shape;
   const Variant* v = s.v;
-  const int r[10] = {v->n, v->words, v->mg, v->minb, v->dispatch, v->nc, s.groups, s.tw, s.stages, s.grid};
+  const int r[11] = {v->n, v->words, v->mg, v->minb, v->dispatch, v->nc, s.groups, s.tw, s.stages, s.grid, v->mode};
   std::memcpy(params_out, r, sizeof(r));
   return PYRIT_OK;
 }

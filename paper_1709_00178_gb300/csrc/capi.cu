@@ -53,7 +53,19 @@ int pyrit_decode(pyrit_plan_t plan, void* const* blocks, uint64_t erasures, size
   if (e.ne == 0) return PYRIT_OK;
   JobDesc job;
   make_decode_job(plan, e, blocks, P, &job);
-  return run_job(plan->n, job, reinterpret_cast<cudaStream_t>(stream));
+  const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  // The plan's syndrome-decode network serves every erasure pattern: used once compiled.
+  if (e.syn_ok && job_is_staged(job)) {
+    if (const Variant* net = net_variant(net_spec_syndrome(plan, 0, 0, 0), false)) {
+      JobDesc sj;
+      make_syndrome_job(plan, e, blocks, P, &sj);
+      TileShape sh;
+      shape_for_variant(net, plan->m, ShapeHint(), &sh);
+      const uint32_t tpj = tiles_for(P, sh);
+      return launch_staged(sh, &sj, nullptr, nullptr, tpj, tpj, st);
+    }
+  }
+  return run_job(plan->n, job, st);
 }
 
 int pyrit_device_status(int* code_out, int* where_out) {

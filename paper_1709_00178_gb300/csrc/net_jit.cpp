@@ -95,19 +95,33 @@ std::string net_source(const NetSpec& s) {
   std::string o;
   o += "#include \"ring_staged.cuh\"\n"
        "namespace pyrit {\n"
-       "struct NetMac {\n"
-       "  __device__ __forceinline__ void tile(const JobDesc*, int, int) {}\n"
-       "  template <int N, int WORDS, int MG>\n"
+       "struct NetMac : ";
+  o += s.mode == 1 ? "SyndromeStore" : "DirectStore";
+  o += " {\n";
+  if (s.mode == 1) {
+    // syndrome decode: only the rows a tile's erasure pattern uses are accumulated
+    o += "  uint32_t need;\n"
+         "  __device__ __forceinline__ void tile(const JobDesc* J, int, int) { need = J->mask[kSyndromeNeedRow][0]; }\n";
+  } else {
+    o += "  __device__ __forceinline__ void tile(const JobDesc*, int, int) {}\n";
+  }
+  o += "  template <int N, int WORDS, int MG>\n"
        "  __device__ __forceinline__ void apply(uint32_t (&acc)[MG][N][WORDS], const uint32_t (&d)[N - 1][WORDS],\n"
        "                                        int j, int g, int) {\n";
+  // Syndrome networks guard each parity row with one warp-uniform test of the tile's needed rows
+  // (a switch on the needed-row set with one block per set measured no faster and compiled
+  // several times longer).
+  const bool guard = s.mode == 1;
   put(o, "    switch (g * %ld + j) {\n", s.nin);
   for (int g = 0; g < groups; ++g) {
     for (int j = 0; j < s.nin; ++j) {
-      put(o, "      case %ld: {\n#pragma unroll\n        for (int x = 0; x < WORDS; ++x) {\n", g * s.nin + j);
+      put(o, "      case %ld: {\n", g * s.nin + j);
+      if (!guard) o += "#pragma unroll\n        for (int x = 0; x < WORDS; ++x) {\n";
       for (int ii = 0; ii < s.mg; ++ii) {
         const int out = g * s.mg + ii;
         if (out >= s.nout) break;
         const uint32_t r = s.mask[j][out];
+        std::string lines;
         for (int t = 0; t < N; ++t) {
           std::string terms;
           for (int sh = 0; sh < N; ++sh) {
@@ -119,12 +133,21 @@ std::string net_source(const NetSpec& s) {
             terms += buf;
           }
           if (terms.empty()) continue;
-          put(o, "          acc[%ld][%ld][x] ^=", ii, t);
-          o += terms.substr(2);
-          o += ";\n";
+          put(lines, "          acc[%ld][%ld][x] ^=", ii, t);
+          lines += terms.substr(2);
+          lines += ";\n";
+        }
+        if (lines.empty()) continue;
+        if (guard) {
+          put(o, "        if (need & %ldu) {\n#pragma unroll\n        for (int x = 0; x < WORDS; ++x) {\n", 1L << ii);
+          o += lines;
+          o += "        }\n        }\n";
+        } else {
+          o += lines;
         }
       }
-      o += "        }\n      } break;\n";
+      if (!guard) o += "        }\n";
+      o += "      } break;\n";
     }
   }
   o += "      default: break;\n    }\n  }\n};\n}  // namespace pyrit\n\n";
@@ -252,19 +275,26 @@ int reg_cap(int nc, int minb) {
 
 int jit_mode() { return jit().mode.load(); }
 
+int shapes_for(int n, int nout, bool syndrome, NetSpec* out, int cap);
+
 int net_candidate_shapes(int n, int nout, NetSpec* out, int cap) {
-  static const Shape4 big[] = {{1, 0, 1, 24}, {1, 0, 1, 16}, {1, 1, 1, 16}, {2, 0, 1, 8}, {1, 1, 1, 24}};
-  static const Shape4 small[] = {{1, 0, 1, 24}, {2, 0, 1, 16}, {4, 0, 1, 8}, {2, 0, 1, 8}, {1, 0, 1, 16}};
+  return shapes_for(n, nout, false, out, cap);
+}
+
+int shapes_for(int n, int nout, bool syndrome, NetSpec* out, int cap) {
+  static const Shape4 big[] = {{1, 0, 1, 24}, {2, 0, 1, 12}, {1, 0, 1, 16}, {2, 0, 1, 8}, {1, 1, 1, 16}, {1, 1, 1, 24}};
+  static const Shape4 small[] = {{1, 0, 1, 24}, {2, 0, 1, 16}, {4, 0, 1, 8}, {2, 0, 1, 8}, {1, 0, 1, 16}, {2, 0, 1, 12}};
   const Shape4* list = n >= 11 ? big : small;
   int count = 0;
-  for (int i = 0; i < 5 && count < cap; ++i) {
+  for (int i = 0; i < 6 && count < cap; ++i) {
     const Shape4& c = list[i];
     const int mg = c.half ? (nout + 1) / 2 : nout;
-    if (mg < 1 || (c.half && nout < 2)) continue;
+    if (mg < 1 || (c.half && (nout < 2 || syndrome))) continue;  // syndrome decode needs every row
     const int groups = output_groups(mg, nout, c.nc);
     if (c.nc % groups != 0 || groups * mg < nout) continue;
-    // accumulators + one staged source + addressing and loop state
-    if (mg * n * c.words + (n - 1) * c.words + 24 > reg_cap(c.nc, c.minb)) continue;
+    // accumulators + one staged source + addressing and loop state (+ an output under
+    // construction for syndrome decoding)
+    if ((mg + (syndrome ? 1 : 0)) * n * c.words + (n - 1) * c.words + 24 > reg_cap(c.nc, c.minb)) continue;
     NetSpec s;
     std::memset(&s, 0, sizeof(s));
     s.n = n;
@@ -299,9 +329,43 @@ NetSpec net_spec(int n, const JobDesc& job, int words, int mg, int minb, int nc)
   return s;
 }
 
+NetSpec net_spec_syndrome(const pyrit_plan_s* p, int words, int minb, int nc) {
+  NetSpec s;
+  std::memset(&s, 0, sizeof(s));
+  NetSpec def[1];
+  if (shapes_for(p->n, p->m, true, def, 1) == 1) s = def[0];
+  s.n = p->n;
+  s.mode = 1;
+  s.nin = p->k + p->m;
+  s.nout = p->m;
+  s.mg = p->m;
+  if (words) s.words = words;
+  if (minb) s.minb = minb;
+  if (nc) s.nc = nc;
+  if (!s.words) s.words = 1;
+  if (!s.minb) s.minb = 1;
+  if (!s.nc) s.nc = 8;
+  if (s.nin > kMaxIn) return s;  // rejected by spec_valid
+  // H = [C | I_m]: data column j carries the parity rows' coefficients, parity column k + r only
+  // its own row with coefficient 1 (mask x^0)
+  for (int r = 0; r < p->m; ++r) {
+    for (int j = 0; j < p->k; ++j) s.mask[j][r] = p->enc_mask[r * p->k + j];
+    s.mask[p->k + r][r] = 1;
+  }
+  return s;
+}
+
+int net_syndrome_shapes(const pyrit_plan_s* p, NetSpec* out, int cap) {
+  NetSpec shapes[8];
+  const int c = shapes_for(p->n, p->m, true, shapes, cap < 8 ? cap : 8);
+  for (int i = 0; i < c; ++i) out[i] = net_spec_syndrome(p, shapes[i].words, shapes[i].minb, shapes[i].nc);
+  return c;
+}
+
 static bool spec_valid(const NetSpec& s) {
   const bool words_ok = s.words == 1 || s.words == 2 || s.words == 4;
   const bool nc_ok = s.nc >= 1 && s.nc <= 31;
+  if (s.mode != 0 && !(s.mode == 1 && s.mg == s.nout && s.nout <= kSyndromeBaseRow)) return false;
   return (s.n == 3 || s.n == 5 || s.n == 11 || s.n == 13) && s.nin >= 1 && s.nin <= kMaxIn && s.nout >= 1 &&
          s.nout <= kMaxOut && words_ok && s.mg >= 1 && s.mg <= kMaxOut && s.minb >= 1 && s.minb <= 4 && nc_ok &&
          output_groups(s.mg, s.nout, s.nc) * s.mg >= s.nout && s.nc % output_groups(s.mg, s.nout, s.nc) == 0;
@@ -334,7 +398,7 @@ const Variant* net_variant(const NetSpec& s, bool block) {
       ++J.failed;
       return nullptr;
     }
-    e->v = Variant{s.n, s.words, s.mg, s.minb, PYRIT_DISPATCH_NETWORK, s.nc, reinterpret_cast<const void*>(k)};
+    e->v = Variant{s.n, s.words, s.mg, s.minb, PYRIT_DISPATCH_NETWORK, s.nc, reinterpret_cast<const void*>(k), s.mode};
     e->loaded = true;
     ++J.loaded;
   }
@@ -397,6 +461,11 @@ int pyrit_plan_specialise(pyrit_plan_t plan, int op, uint64_t erasures, const py
   if (op == PYRIT_OP_ENCODE) {
     if (plan->m == 0) return PYRIT_OK;
     make_encode_job(plan, none.data(), none.data() + plan->k, 16, &job);
+  } else if (op == PYRIT_OP_DECODE_ANY) {
+    if (plan->m == 0) return PYRIT_OK;
+    if (plan->k + plan->m > kMaxIn) return PYRIT_E_INVALID_ARG;
+    return net_compile(tile ? net_spec_syndrome(plan, tile->words, tile->minb, tile->nc)
+                            : net_spec_syndrome(plan, 0, 0, 0));
   } else if (op == PYRIT_OP_DECODE) {
     DecodeEntry e;
     const int rc = plan_decode_entry(plan, erasures, &e);

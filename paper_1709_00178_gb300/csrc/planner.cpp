@@ -115,6 +115,44 @@ static double binom(int a, int b) {
   return r;
 }
 
+// The syndrome form of a decode entry (see SyndromeStore in ring_staged.cuh): with D the lost
+// data blocks (a of them), U the first a surviving parity rows and X = (C_{U,D})^{-1}, lost data
+// block D_i is row i of X applied to the syndromes of U, and lost parity row r is its partial
+// sum plus (C_{r,D} X) applied to them. C_{U,D} is a square submatrix of the parity part of an MDS
+// systematic generator, hence invertible whenever the survivors' matrix is.
+static void syndrome_entry(const pyrit_plan_s* p, DecodeEntry* e) {
+  const int k = p->k, m = p->m, w = p->w, n = p->n;
+  e->syn_ok = false;
+  std::memset(e->syn, 0, sizeof(e->syn));
+  if (k + m > kMaxIn) return;
+  int D[kMaxOut], U[kMaxOut], a = 0, nu = 0;
+  for (int r = 0; r < e->ne; ++r)
+    if (e->erased[r] < k) D[a++] = e->erased[r];
+  for (int s = 0; s < k; ++s)
+    if (e->surv[s] >= k) U[nu++] = e->surv[s] - k;
+  if (nu != a) return;
+  uint32_t A[kMaxOut * kMaxOut], X[kMaxOut * kMaxOut];
+  for (int i = 0; i < a; ++i)
+    for (int j = 0; j < a; ++j) A[i * a + j] = p->G[(k + U[i]) * k + D[j]];
+  if (a > 0 && !invert(w, a, A, X)) return;
+  for (int o = 0; o < e->ne; ++o) {
+    const int b = e->erased[o];
+    for (int s = 0; s < a; ++s) {
+      uint32_t v = 0;
+      if (b < k) {
+        int i = 0;
+        while (D[i] != b) ++i;
+        v = X[i * a + s];
+      } else {
+        for (int i = 0; i < a; ++i) v ^= gf_mul(w, p->G[b * k + D[i]], X[i * a + s]);
+      }
+      e->syn[U[s]][o] = (uint16_t)sparse_rep(w, n, v);
+    }
+    e->syn[kSyndromeBaseRow][o] = (uint16_t)(b < k ? 0 : b - k + 1);
+  }
+  e->syn_ok = true;
+}
+
 int plan_decode_entry(pyrit_plan_s* p, uint64_t erasures, DecodeEntry* out) {
   const int k = p->k, m = p->m, w = p->w, n = p->n;
   if (k + m < 64 && (erasures >> (k + m)) != 0) return PYRIT_E_INVALID_ARG;
@@ -156,6 +194,7 @@ int plan_decode_entry(pyrit_plan_s* p, uint64_t erasures, DecodeEntry* out) {
           e.mask[r][s] = (uint16_t)sparse_rep(w, n, v);
         }
       }
+      syndrome_entry(p, &e);
     }
   }
   {
@@ -190,6 +229,24 @@ void make_decode_job(const pyrit_plan_s* p, const DecodeEntry& e, void* const* b
     for (int s = 0; s < p->k; ++s) job->mask[s][r] = e.mask[r][s];
 }
 
+void make_syndrome_job(const pyrit_plan_s* p, const DecodeEntry& e, void* const* blocks, size_t P, JobDesc* job) {
+  std::memset(job, 0, sizeof(*job));
+  const int k = p->k, m = p->m;
+  job->nin = k + m;
+  job->nout = e.ne;
+  job->P = P;
+  for (int s = 0; s < k; ++s) job->in[e.surv[s]] = static_cast<const uint8_t*>(blocks[e.surv[s]]);
+  for (int o = 0; o < e.ne; ++o) job->out[o] = static_cast<uint8_t*>(blocks[e.erased[o]]);
+  uint32_t need = 0;  // parity rows that are syndromes or partial sums of this pattern
+  for (int o = 0; o < e.ne; ++o) {
+    for (int r = 0; r < m; ++r)
+      if (e.syn[r][o]) need |= 1u << r;
+    if (e.syn[kSyndromeBaseRow][o]) need |= 1u << (e.syn[kSyndromeBaseRow][o] - 1);
+  }
+  for (int r = 0; r <= kSyndromeBaseRow; ++r)
+    for (int o = 0; o < e.ne; ++o) job->mask[r][o] = e.syn[r][o];
+  job->mask[kSyndromeNeedRow][0] = (uint16_t)need;
+}
 
 // Validates a stripe request and builds its coding job; alg / src receive its algorithmic and
 // source bytes.
@@ -298,6 +355,18 @@ int pyrit_plan_generator(pyrit_plan_t p, uint32_t* G_out) {
 int pyrit_plan_encode_masks(pyrit_plan_t p, uint16_t* masks_out) {
   if (!p || !masks_out) return PYRIT_E_INVALID_ARG;
   std::memcpy(masks_out, p->enc_mask.data(), p->enc_mask.size() * sizeof(uint16_t));
+  return PYRIT_OK;
+}
+
+int pyrit_plan_syndrome_masks(pyrit_plan_t p, uint64_t erasures, uint16_t* syn_out, int* ne_out) {
+  if (!p || !syn_out) return PYRIT_E_INVALID_ARG;
+  DecodeEntry e;
+  const int rc = plan_decode_entry(p, erasures, &e);
+  if (rc != PYRIT_OK) return rc;
+  if (!e.syn_ok && e.ne > 0) return PYRIT_E_INVALID_ARG;
+  for (int r = 0; r <= kSyndromeBaseRow; ++r)
+    for (int o = 0; o < kMaxOut; ++o) syn_out[r * kMaxOut + o] = o < e.ne ? e.syn[r][o] : 0;
+  if (ne_out) *ne_out = e.ne;
   return PYRIT_OK;
 }
 

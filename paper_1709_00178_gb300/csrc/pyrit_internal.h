@@ -31,6 +31,7 @@ struct Variant {
                  // 3: a network generated for one mask table (PYRIT_DISPATCH_NETWORK)
   int nc;        // consumer warps per CTA (one more warp is the producer)
   const void* fn;
+  int mode;      // generated networks: 0 direct table, 1 syndrome decode (takes syndrome-form jobs)
 };
 
 // Output groups of a launch: the smallest power of two g with g * mg >= nout (and g < nc); the
@@ -73,6 +74,11 @@ struct DecodeEntry {
   int surv[kMaxIn];
   int erased[kMaxOut];
   uint16_t mask[kMaxOut][kMaxIn];  // row r = erased block erased[r], column s = survivor surv[s]
+  // Syndrome form (k + m <= kMaxIn): syn[r][o] = phi_S of the coefficient of parity row r's
+  // accumulator for output o; syn[kSyndromeBaseRow][o] = 1 + the row whose partial sum output o
+  // adds (an erased parity block), 0 for an erased data block.
+  bool syn_ok = false;
+  uint16_t syn[kSyndromeBaseRow + 1][kMaxOut];
 };
 
 }  // namespace pyrit
@@ -96,6 +102,9 @@ int stripe_job(const pyrit_stripe_t& s, JobDesc* job, uint64_t* alg, uint64_t* s
 // Fills a job for decoding one stripe with a decode entry.
 void make_decode_job(const pyrit_plan_s* p, const DecodeEntry& e, void* const* blocks, size_t P,
                      JobDesc* job);
+// Fills the syndrome-form decode job (requires e.syn_ok): sources are the k + m block columns in
+// index order, absent (null) unless they are survivors; outputs are the erased blocks.
+void make_syndrome_job(const pyrit_plan_s* p, const DecodeEntry& e, void* const* blocks, size_t P, JobDesc* job);
 
 // ---- kernels (device launchers) --------------------------------------------------------------
 // Registered variants (all translation units).
@@ -130,11 +139,16 @@ void tune_record(const TuneKey& k, const TuneVal& v);
 // out as straight-line code, so no mask bit is tested at run time. Generated, compiled (NVRTC) and
 // cached per NetSpec; `mask` holds the table for j < nin, o < nout and zeros elsewhere.
 struct NetSpec {
-  int32_t n, nin, nout, words, mg, minb, nc, pad;
+  int32_t n, nin, nout, words, mg, minb, nc;
+  int32_t mode;  // 0: direct (the job's own table); 1: syndrome decode of a plan (table [C | I])
   uint16_t mask[kMaxIn][kMaxOut];
 };
 // The network spec of a job under a shape (zero fields: the default shape for (n, nout)).
 NetSpec net_spec(int n, const JobDesc& job, int words, int mg, int minb, int nc);
+// The syndrome-decode network spec of a plan (requires k + m <= kMaxIn; zero fields: default).
+NetSpec net_spec_syndrome(const pyrit_plan_s* p, int words, int minb, int nc);
+// Candidate shapes of a plan's syndrome network, the default first.
+int net_syndrome_shapes(const pyrit_plan_s* p, NetSpec* out, int cap);
 // Candidate shapes for (n, nout), the default first; returns how many were written (<= cap).
 int net_candidate_shapes(int n, int nout, NetSpec* out, int cap);
 // Run-time compilation policy (PYRIT_JIT_*).

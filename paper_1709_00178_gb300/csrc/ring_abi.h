@@ -21,6 +21,11 @@ namespace pyrit {
 
 constexpr int kMaxIn = 32;  // sources of one coding job (data blocks or survivors)
 constexpr int kMaxOut = 8;  // destinations of one coding job (parity or erased blocks)
+// Syndrome-form decode jobs keep, for output o, 1 + the row of their partial sum (0: none) in
+// mask[kSyndromeBaseRow][o]; rows 0..kMaxOut-1 hold the per-row coefficients.
+constexpr int kSyndromeBaseRow = kMaxOut;
+// ... and in mask[kSyndromeNeedRow][0] the bit set of parity rows whose accumulators are used.
+constexpr int kSyndromeNeedRow = kMaxOut + 1;
 
 // One coding job: out[i] = sum_j u_ij * in[j] over GF(2^w) in every symbol lane, where the
 // coefficient u_ij is given by its ring representative mask[j][i] (bit s = coefficient of x^s).

@@ -107,7 +107,7 @@ __device__ __forceinline__ void ring_mac(uint32_t (&acc)[MG][N][WORDS], const ui
 // outputs 0..7); each source's masks are broadcast from lane j by a warp OR-reduction, uniform
 // across the warp by construction, which keeps the dispatch on uniform branches.
 template <int MG, int DISPATCH>
-struct MaskMac {
+struct MaskMac : DirectStore {
   static constexpr int MW = (MG + 1) / 2;  // 32-bit mask words per source for MG outputs
   uint32_t rw[MW];
 

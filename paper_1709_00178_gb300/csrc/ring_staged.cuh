@@ -29,6 +29,11 @@
 //   template <int N, int WORDS, int MG>
 //   void apply(uint32_t (&acc)[MG][N][WORDS], const uint32_t (&d)[N - 1][WORDS], int j, int g,
 //              int lane);                             // acc_i += r_ij * d for the group's outputs
+//   template <int N, int WORDS, int MG>
+//   void store(uint32_t (&acc)[MG][N][WORDS], const JobDesc* J, int g, uint32_t col0,
+//              uint32_t off);                          // phi_E^{-1} and the stores of the tile
+//   static constexpr bool kSparse;                     // sources with a null pointer are absent
+// DirectStore supplies the usual store (output g*MG + i is acc[i] reduced) and kSparse = false.
 #pragma once
 
 #include "ptx.cuh"
@@ -86,6 +91,110 @@ __device__ __forceinline__ typename Vec<WORDS>::T vmake(const uint32_t (&w)[WORD
   }
 }
 
+// phi_E^{-1} and the stores of a direct job: output g*MG + i is acc[i] reduced mod the AOP
+// (out[t] = acc[t] ^ acc[W], Sec. 2.3.2); its W field packets are stored at column col0 + off.
+struct DirectStore {
+  static constexpr bool kSparse = false;
+
+  template <int N, int WORDS, int MG>
+  __device__ __forceinline__ void store(uint32_t (&acc)[MG][N][WORDS], const JobDesc* J, int g, uint32_t col0,
+                                        uint32_t off) {
+    constexpr int W = N - 1;
+    using V = typename Vec<WORDS>::T;
+    const uint64_t P = J->P;
+    const int nout = J->nout;
+#pragma unroll
+    for (int i = 0; i < MG; ++i) {
+      const int o = g * MG + i;
+      if (o < nout) {
+        uint8_t* dst = J->out[o] + col0 + off;
+#pragma unroll
+        for (int r = 0; r < W; ++r) {
+          uint32_t o4[WORDS];
+#pragma unroll
+          for (int x = 0; x < WORDS; ++x) o4[x] = acc[i][r][x] ^ acc[i][W][x];
+          *reinterpret_cast<V*>(dst + (size_t)r * P) = vmake<WORDS>(o4);
+        }
+      }
+    }
+  }
+};
+
+// Syndrome-form decoding (the second phase of a decode network; the first phase is a network for
+// the plan's parity-check matrix H = [C | I_m], which depends only on the plan).
+//
+// A systematic code has parity p_r = sum_j C_rj d_j. When blocks E are lost, decoding reads the
+// survivors S = the first k blocks not in E: the surviving data D_s and the first a surviving
+// parity rows U (a = number of lost data blocks). The first phase accumulates, for every parity
+// row r, acc_r = sum over j in D_s of C_rj d_j, plus p_r when r is in U. For r in U this is the
+// syndrome s_r = sum over lost data j of C_rj d_j; for a lost parity row r it is the partial sum
+// t_r over the surviving data. Then (Sec. 4.3: the decoding matrix depends on the loss pattern)
+//   lost data     d_E = X s_U,            X = (C restricted to rows U, lost data columns)^{-1}
+//   lost parity   p_r = t_r + (C_{r, lost data} X) s_U,
+// every square submatrix of C being invertible for an MDS code. The small per-pattern matrices
+// arrive in the job: for output o, mask[r][o] (r < MG) is phi_S of the coefficient of acc_r and
+// mask[kSyndromeBaseRow][o] is 1 + the row whose partial sum is added (0: none). Rows are first
+// reduced in place (phi_E^{-1}), products are formed in the ring with the reduced rows embedded
+// (phi_E), and each output is reduced once more before its store.
+struct SyndromeStore {
+  static constexpr bool kSparse = true;  // erased columns and unused parity are absent sources
+
+  template <int N, int WORDS, int MG>
+  __device__ __forceinline__ void store(uint32_t (&acc)[MG][N][WORDS], const JobDesc* J, int, uint32_t col0,
+                                        uint32_t off) {
+    constexpr int W = N - 1;
+    using V = typename Vec<WORDS>::T;
+#pragma unroll
+    for (int r = 0; r < MG; ++r)
+#pragma unroll
+      for (int t = 0; t < W; ++t)
+#pragma unroll
+        for (int x = 0; x < WORDS; ++x) acc[r][t][x] ^= acc[r][W][x];
+    const uint64_t P = J->P;
+    const int nout = J->nout;
+    for (int o = 0; o < nout; ++o) {
+      const uint32_t base = J->mask[kSyndromeBaseRow][o];
+      uint32_t res[N][WORDS];
+#pragma unroll
+      for (int t = 0; t < N; ++t)
+#pragma unroll
+        for (int x = 0; x < WORDS; ++x) res[t][x] = 0u;
+#pragma unroll
+      for (int r = 0; r < MG; ++r) {
+        if (base == (uint32_t)(r + 1)) {
+#pragma unroll
+          for (int t = 0; t < W; ++t)
+#pragma unroll
+            for (int x = 0; x < WORDS; ++x) res[t][x] = acc[r][t][x];
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < MG; ++r) {
+        const uint32_t c = J->mask[r][o];
+        if (c == 0u) continue;
+        // res += c * acc_r: one rotation of the reduced row per set bit of c
+#pragma unroll
+        for (int sh = 0; sh < N; ++sh) {
+          if (c & (1u << sh)) {
+#pragma unroll
+            for (int q = 0; q < W; ++q)
+#pragma unroll
+              for (int x = 0; x < WORDS; ++x) res[(q + sh) % N][x] ^= acc[r][q][x];
+          }
+        }
+      }
+      uint8_t* dst = J->out[o] + col0 + off;
+#pragma unroll
+      for (int t = 0; t < W; ++t) {
+        uint32_t o4[WORDS];
+#pragma unroll
+        for (int x = 0; x < WORDS; ++x) o4[x] = res[t][x] ^ res[W][x];
+        *reinterpret_cast<V*>(dst + (size_t)t * P) = vmake<WORDS>(o4);
+      }
+    }
+  }
+};
+
 template <int N, int WORDS, int MG, int NC, class Mac>
 __device__ __forceinline__ void ring_staged_body(const CodeArgs& a) {
   constexpr int W = N - 1;
@@ -122,6 +231,9 @@ __device__ __forceinline__ void ring_staged_body(const CodeArgs& a) {
       const uint32_t width = (uint32_t)(P - col0 < (uint64_t)TW ? P - col0 : (uint64_t)TW);
       const int nin = J->nin;
       for (int j = 0; j < nin; ++j) {
+        if constexpr (Mac::kSparse) {
+          if (J->in[j] == nullptr) continue;
+        }
         bool free_ok = true;
         if (lane == 0) {
           free_ok = mbar_wait(&empty[stage], phase ^ 1u, a.err, 1);
@@ -161,7 +273,7 @@ __device__ __forceinline__ void ring_staged_body(const CodeArgs& a) {
     if (col0 >= P) continue;  // same rule as the producer: such a tile has no stages
     const uint32_t width = (uint32_t)(P - col0 < (uint64_t)TW ? P - col0 : (uint64_t)TW);
     const bool valid = off < width;
-    const int nin = J->nin, nout = J->nout;
+    const int nin = J->nin;
 
     Mac mac;
     mac.tile(J, g, lane);
@@ -175,6 +287,9 @@ __device__ __forceinline__ void ring_staged_body(const CodeArgs& a) {
         for (int x = 0; x < WORDS; ++x) acc[i][r][x] = 0u;
 
     for (int j = 0; j < nin; ++j) {
+      if constexpr (Mac::kSparse) {
+        if (J->in[j] == nullptr) continue;  // the producer staged nothing for it either
+      }
       // Every lane observes the phase (so the staged bytes are visible to it); the give-up
       // decision is made warp-uniform before anyone leaves.
       if (!__all_sync(0xFFFFFFFFu, mbar_wait(&full[stage], phase, a.err, 2))) return;
@@ -200,23 +315,7 @@ __device__ __forceinline__ void ring_staged_body(const CodeArgs& a) {
       mac.template apply<N, WORDS, MG>(acc, d, j, g, lane);
     }
 
-    // phi_E^{-1}: reduce mod the AOP and store the W field packets of every output.
-    if (valid) {
-#pragma unroll
-      for (int i = 0; i < MG; ++i) {
-        const int o = g * MG + i;
-        if (o < nout) {
-          uint8_t* dst = J->out[o] + col0 + off;
-#pragma unroll
-          for (int r = 0; r < W; ++r) {
-            uint32_t o4[WORDS];
-#pragma unroll
-            for (int x = 0; x < WORDS; ++x) o4[x] = acc[i][r][x] ^ acc[i][W][x];
-            *reinterpret_cast<V*>(dst + (size_t)r * P) = vmake<WORDS>(o4);
-          }
-        }
-      }
-    }
+    if (valid) mac.template store<N, WORDS, MG>(acc, J, g, col0, off);
   }
 }
 

@@ -44,6 +44,7 @@ PYRIT_MAX_K = 32
 PYRIT_MAX_M = 8
 PYRIT_OP_ENCODE = 0
 PYRIT_OP_DECODE = 1
+PYRIT_OP_DECODE_ANY = 2
 
 _i, _u32, _u64, _sz, _vp = ctypes.c_int, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_size_t, ctypes.c_void_p
 
@@ -55,6 +56,7 @@ _SIGS = {
     "pyrit_plan_generator": (_i, [_vp, _vp]),
     "pyrit_plan_encode_masks": (_i, [_vp, _vp]),
     "pyrit_plan_decode_masks": (_i, [_vp, _u64, _vp, _vp, _vp, _vp]),
+    "pyrit_plan_syndrome_masks": (_i, [_vp, _u64, _vp, _vp]),
     "pyrit_sparse_transform": (_u32, [_i, _i, _u32]),
     "pyrit_gf_mul": (_u32, [_i, _u32, _u32]),
     "pyrit_encode": (_i, [_vp, _vp, _vp, _sz, _vp]),
@@ -167,6 +169,15 @@ def pyrit_plan_decode_masks(plan, erasures):
     return surv, er[:ne.value].copy(), M[:ne.value].copy()
 
 
+def pyrit_plan_syndrome_masks(plan, erasures):
+    """(syn, ne): syn is a 9 x 8 uint16 array (rows r = parity rows, row 8 = 1 + base row)."""
+    syn = np.zeros((9, 8), np.uint16)
+    ne = ctypes.c_int()
+    _check(_lib.pyrit_plan_syndrome_masks(plan, erasures, _np_ptr(syn), ctypes.byref(ne)),
+           "pyrit_plan_syndrome_masks")
+    return syn, ne.value
+
+
 def pyrit_sparse_transform(w, n, u):
     return int(_lib.pyrit_sparse_transform(w, n, u))
 
@@ -274,10 +285,10 @@ def pyrit_variants():
 
 def pyrit_batch_shape(batch, group=0):
     """Launch shape of one group of a batch: dict of n, words, mg, minb, dispatch, nc, groups, tw,
-    stages, grid (dispatch 3 = a plan-specialised network)."""
-    buf = np.zeros(10, np.int32)
+    stages, grid, mode (dispatch 3 = a plan-specialised network; mode 1 = syndrome decode)."""
+    buf = np.zeros(11, np.int32)
     _check(_lib.pyrit_batch_shape(batch, group, _np_ptr(buf)), "pyrit_batch_shape")
-    keys = ("n", "words", "mg", "minb", "dispatch", "nc", "groups", "tw", "stages", "grid")
+    keys = ("n", "words", "mg", "minb", "dispatch", "nc", "groups", "tw", "stages", "grid", "mode")
     return dict(zip(keys, (int(x) for x in buf)))
 
 

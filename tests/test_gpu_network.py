@@ -194,7 +194,8 @@ def test_single_calls_sync_and_background(pyrit, jit_mode):
         s2 = pyrit.pyrit_jit_stats()
         assert s2["hits"] > s1["hits"]
         np.testing.assert_array_equal(st.host(0), st.full(0))
-        # synchronous policy: a decode pattern never seen is compiled in the call and used at once
+        # synchronous policy: the plan's syndrome-decode network (compiled in the call if no earlier
+        # call compiled it) decodes a pattern never seen
         pyrit.pyrit_jit_mode(pyrit.PYRIT_JIT_SYNC)
         erasures = 0b101 | (1 << 17)
         for e in range(st.k + st.m):
@@ -202,7 +203,7 @@ def test_single_calls_sync_and_background(pyrit, jit_mode):
                 st.view(0)[e * 12 * st.P:(e + 1) * 12 * st.P].fill_(0xA5)
         pyrit.pyrit_decode(st.plan, st.blocks(0), erasures, st.P)
         s3 = pyrit.pyrit_jit_stats()
-        assert s3["compiled"] > s2["compiled"] and s3["hits"] > s2["hits"]
+        assert s3["hits"] > s2["hits"] and s3["failed"] == s2["failed"]
         np.testing.assert_array_equal(st.host(0), st.full(0))
     finally:
         pyrit.pyrit_plan_destroy(st.plan)
@@ -234,5 +235,108 @@ def test_tuner_times_networks_and_keeps_parity(pyrit, jit_mode, tmp_path):
             pyrit.pyrit_batch_destroy(b)
         path = str(tmp_path / "tune.json")
         assert pyrit.pyrit_tune_save(path) >= 0
+    finally:
+        pyrit.pyrit_plan_destroy(st.plan)
+
+
+def _decode_batch_matches(pyrit, st, pats, tile=None, expect_mode=1, graph=False):
+    """Writes every stripe's codeword with its pattern's blocks wiped, decodes them in one batch
+    and compares every stripe with the oracle's codeword."""
+    full = [st.full(s) for s in range(st.count)]
+    for s in range(st.count):
+        arr = full[s].copy()
+        for e in range(st.k + st.m):
+            if (pats[s] >> e) & 1:
+                arr[e] = 0xC3
+        st.view(s).copy_(torch.from_numpy(arr.reshape(-1)).cuda())
+    b = pyrit.pyrit_batch_create([(st.plan, pyrit.PYRIT_OP_DECODE, pats[s], st.P, st.blocks(s)) for s in range(st.count)],
+                                 tile)
+    try:
+        shape = pyrit.pyrit_batch_shape(b, 0)
+        if expect_mode is not None:
+            assert shape["dispatch"] == pyrit.PYRIT_DISPATCH_NETWORK and shape["mode"] == expect_mode, shape
+        pyrit.pyrit_batch_run(b, graph=graph)
+        if graph:
+            pyrit.pyrit_batch_run(b, graph=True)
+        for s in range(st.count):
+            np.testing.assert_array_equal(st.host(s), full[s], err_msg="stripe %d pattern %#x" % (s, pats[s]))
+    finally:
+        pyrit.pyrit_batch_destroy(b)
+    return shape
+
+
+def _random_patterns(rng, count, k, m):
+    out = []
+    for _ in range(count):
+        e = int(rng.integers(1, m + 1))
+        out.append(sum(1 << int(x) for x in rng.choice(k + m, e, replace=False)))
+    return out
+
+
+@pytest.mark.parametrize("w,k,m,P,count", [(10, 10, 4, 8192 + 16, 24), (12, 16, 4, 4096 + 32, 12), (4, 4, 2, 2048, 16),
+                                           (10, 24, 8, 1024 + 16, 10), (2, 2, 2, 512, 8)])
+def test_syndrome_network_mixed_patterns(pyrit, jit_mode, w, k, m, P, count):
+    """Every stripe has its own random erasure pattern: the batch runs the plan's syndrome network."""
+    rng = np.random.default_rng(0x5E + w + k)
+    st = Stripes(pyrit, w, k, m, P, count, 0x5E00 + w * 100 + k)
+    try:
+        _decode_batch_matches(pyrit, st, _random_patterns(rng, count, k, m), graph=(k == 16))
+    finally:
+        pyrit.pyrit_plan_destroy(st.plan)
+
+
+def test_syndrome_network_every_pattern(pyrit, jit_mode):
+    """All erasure patterns of at most m blocks of a small code, one stripe each, in one launch."""
+    from itertools import combinations
+    w, k, m, P = 4, 4, 2, 1024 + 16
+    pats = [sum(1 << b for b in c) for e in range(1, m + 1) for c in combinations(range(k + m), e)]
+    st = Stripes(pyrit, w, k, m, P, len(pats), 0xA11)
+    try:
+        _decode_batch_matches(pyrit, st, pats)
+    finally:
+        pyrit.pyrit_plan_destroy(st.plan)
+
+
+@pytest.mark.parametrize("shape", [dict(words=1, nc=16), dict(words=1, nc=24), dict(words=2, nc=8), dict(words=2, nc=12),
+                                   dict(words=4, nc=8), dict(words=1, nc=8, minb=2)],
+                         ids=lambda d: "-".join("%s%d" % kv for kv in d.items()))
+def test_every_syndrome_shape(pyrit, jit_mode, shape):
+    rng = np.random.default_rng(0x5A)
+    st = Stripes(pyrit, 10, 10, 4, 8192 + 16, 12, 0x5A5)
+    try:
+        got = _decode_batch_matches(pyrit, st, _random_patterns(rng, 12, 10, 4),
+                                    dict(shape, dispatch=pyrit.PYRIT_DISPATCH_NETWORK))
+        assert (got["words"], got["nc"], got["mg"], got["groups"]) == (shape["words"], shape["nc"], 4, 1)
+    finally:
+        pyrit.pyrit_plan_destroy(st.plan)
+
+
+def test_wide_code_decodes_on_the_generic_kernel(pyrit, jit_mode):
+    # k + m = 36 columns do not fit a job: the generic kernel decodes, still bit-exact
+    rng = np.random.default_rng(0x36)
+    st = Stripes(pyrit, 12, 30, 6, 2048, 4, 0x360)
+    try:
+        shape = _decode_batch_matches(pyrit, st, _random_patterns(rng, 4, 30, 6), expect_mode=None)
+        assert shape["dispatch"] != pyrit.PYRIT_DISPATCH_NETWORK
+    finally:
+        pyrit.pyrit_plan_destroy(st.plan)
+
+
+def test_single_decode_uses_the_syndrome_network(pyrit, jit_mode):
+    pyrit.pyrit_jit_mode(pyrit.PYRIT_JIT_SYNC)
+    rng = np.random.default_rng(0x51D)
+    st = Stripes(pyrit, 10, 10, 4, 4096 + 16, 1, 0x51D0)
+    try:
+        full = st.full(0)
+        for pat in _random_patterns(rng, 6, 10, 4):
+            arr = full.copy()
+            for e in range(14):
+                if (pat >> e) & 1:
+                    arr[e] = 0x3C
+            st.view(0).copy_(torch.from_numpy(arr.reshape(-1)).cuda())
+            before = pyrit.pyrit_jit_stats()["hits"]
+            pyrit.pyrit_decode(st.plan, st.blocks(0), pat, st.P)
+            assert pyrit.pyrit_jit_stats()["hits"] > before
+            np.testing.assert_array_equal(st.host(0), full, err_msg="pattern %#x" % pat)
     finally:
         pyrit.pyrit_plan_destroy(st.plan)

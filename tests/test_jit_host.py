@@ -169,3 +169,61 @@ def test_runtime_compiler_builds_networks_without_a_device(w, k, m):
         assert ei.value.status == pyrit.PYRIT_E_INVALID_ARG
     finally:
         pyrit.pyrit_plan_destroy(plan)
+
+
+def _field_of_mask(w, mask):
+    """The field element a ring representative stands for: its remainder mod the AOP."""
+    return int(oracle.poly_mod(mask, oracle.aop(w)))
+
+
+@pytest.mark.parametrize("w,k,m", [(4, 4, 2), (10, 10, 4), (12, 16, 4), (4, 6, 4), (10, 24, 8)])
+def test_syndrome_tables_rebuild_every_erasure_pattern(w, k, m):
+    """The planner's syndrome-form decode (second phase of the syndrome network), checked with the
+    oracle's field arithmetic only: random symbols are encoded with the oracle's Cauchy generator,
+    the first phase's row sums are formed from the survivors, and every erased symbol must come
+    back from the per-pattern coefficients."""
+    from itertools import combinations
+    rng = np.random.default_rng(77 + w * k + m)
+    G = oracle.cauchy(w, k, m)
+    C = G[k:]
+    plan = pyrit.pyrit_plan_create(w, w + 1, k, m)
+    try:
+        patterns = []
+        for e in range(1, m + 1):
+            combos = list(combinations(range(k + m), e))
+            if len(combos) > 300:
+                combos = [combos[i] for i in rng.choice(len(combos), 300, replace=False)]
+            patterns += combos
+        for pat in patterns:
+            er = sum(1 << b for b in pat)
+            d = [int(x) for x in rng.integers(0, 1 << w, size=k)]
+            p = [0] * m
+            for r in range(m):
+                for j in range(k):
+                    p[r] ^= oracle.gf_mul_slow(w, int(C[r][j]), d[j])
+            block = d + p
+            erased = sorted(pat)
+            survivors = [b for b in range(k + m) if b not in pat][:k]
+            U = [b - k for b in survivors if b >= k]
+            acc = []
+            for r in range(m):
+                v = 0
+                for j in range(k):
+                    if j not in pat:
+                        v ^= oracle.gf_mul_slow(w, int(C[r][j]), d[j])
+                if r in U:
+                    v ^= p[r]
+                acc.append(v)
+            syn, ne = pyrit.pyrit_plan_syndrome_masks(plan, er)
+            assert ne == len(erased)
+            for o, b in enumerate(erased):
+                base = int(syn[8][o])
+                v = acc[base - 1] if base else 0
+                assert (base == 0) == (b < k)
+                for r in range(m):
+                    if syn[r][o]:
+                        assert r in U, "only syndrome rows carry coefficients"
+                        v ^= oracle.gf_mul_slow(w, _field_of_mask(w, int(syn[r][o])), acc[r])
+                assert v == block[b], (pat, b)
+    finally:
+        pyrit.pyrit_plan_destroy(plan)
