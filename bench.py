@@ -10,9 +10,10 @@ blocks (rebuilt in place), each as one persistent batched launch replayed from a
            inputs resident in HBM (2.19 GiB of stripes, larger than L2; no flush needed).
   e2e      the same metric with the data blocks uploaded from pinned host memory and the parity
            read back every step (chunked over streams so copies overlap the kernels).
-  roofline the coding kernel's algorithmic bytes ((k+m)wP per encoded stripe, (k+e)wP per decoded
-           stripe with e erasures) per launch over its event-timed duration, against the measured
-           HBM copy bandwidth.
+  roofline for each timed kernel (the encode and the decode launch), its algorithmic bytes
+           ((k+m)wP per encoded stripe, (k+e)wP per decoded stripe with e erasures) per launch over
+           its event-timed duration, against the measured HBM copy bandwidth; the headline object
+           is the kernel with the larger share of the step.
 
 `--impl reference` times the CPU oracle (the plain log/antilog coder) on a bounded sample of the
 same workload. Multi-GPU (torchrun): every rank codes its own 256 stripes (weak scaling, no
@@ -56,18 +57,52 @@ def kernel_source_digest():
     return h.hexdigest()[:16]
 
 
+TRAFFIC_RECORD = os.path.join(ROOT, "profiles", "coding_kernels_config2_traffic.json")
+
+
 def recorded_traffic():
-    """DRAM bytes per launch of the coding kernel from the committed ncu summary, if the kernel
-    sources have not changed since it was taken."""
-    p = os.path.join(ROOT, "profiles", "ring_staged_traffic.json")
+    """DRAM bytes per launch of the timed encode and decode kernels ({"encode": B, "decode": B})
+    from the committed ncu record, if the kernel sources have not changed since it was taken."""
     try:
-        with open(p) as f:
+        with open(TRAFFIC_RECORD) as f:
             rec = json.load(f)
     except Exception:
-        return None
+        return {}
     if rec.get("kernel_src_digest") != kernel_source_digest():
-        return None
-    return rec.get("traffic_bytes_per_launch")
+        return {}
+    return rec.get("traffic_bytes_per_launch", {})
+
+
+def kernel_name(shape):
+    """Name of the kernel a batch group launches, as ncu lists it."""
+    if shape["dispatch"] == 3:
+        return "ring_staged_net (%s network, words %d, %d consumer warps)" % (
+            "syndrome-decode" if shape["mode"] == 1 else "direct", shape["words"], shape["nc"])
+    return "ring_staged_kernel<%d, %d, %d, %d, %d, %d>" % (shape["n"], shape["words"], shape["mg"], shape["minb"],
+                                                          shape["dispatch"], shape["nc"])
+
+
+def rank_shard(rank, stripe_bytes, stripes):
+    """What rank `rank` codes (weak scaling, no data-path collective): its stripes' bytes are the
+    synthetic stream's bytes [rank * S * B, (rank + 1) * S * B) and its erasure patterns come from
+    their own seed. Returns (stream offset, pattern seed)."""
+    from paper_1709_00178_gb300.synth import BASE_SEED
+    return rank * stripes * stripe_bytes, BASE_SEED + 1 + 1000 * rank
+
+
+def max_over_ranks(value, world, dist, device):
+    """The maximum of a per-rank float over all ranks (the job is as slow as its slowest rank)."""
+    if world <= 1:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gbs(world, src_bytes_per_rank_step, ms_per_step):
+    """Whole-job throughput: every rank's source bytes per step over the slowest rank's step time."""
+    return world * src_bytes_per_rank_step / (ms_per_step * 1e-3) / 1e9
 
 
 def patterns(seed, stripes, k, m):
@@ -182,6 +217,8 @@ def main():
                     help="coding: the default line; sweep: GF(2^12) k=16 m=4 packet sweep 4 KiB-1 MiB; mixed: "
                          "4096 uneven stripes batched vs per-stripe launches; served: Poisson arrivals")
     ap.add_argument("--seconds", type=float, default=10.0, help="served: arrival window")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="skip the autotuner: time the automatic shapes (profiling cases of a fixed kernel)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -214,22 +251,25 @@ def main():
     # Layout: every stripe's k data blocks contiguous in a data region, its m parity blocks in a
     # parity region, so host<->device transfers of a run of stripes are single copies.
     buf = torch.empty(STRIPES * stripe_bytes, dtype=torch.uint8, device=dev)
-    pyrit.pyrit_synth_fill(buf.data_ptr(), buf.numel(), BASE_SEED + 1, rank * buf.numel())
+    shard_off, pat_seed = rank_shard(rank, stripe_bytes, STRIPES)
+    pyrit.pyrit_synth_fill(buf.data_ptr(), buf.numel(), BASE_SEED + 1, shard_off)
     torch.cuda.synchronize(dev)
     base = buf.data_ptr()
     par0 = STRIPES * K * blk
     blocks = [[base + (s * K + j) * blk for j in range(K)] + [base + par0 + (s * M + i) * blk for i in range(M)]
               for s in range(STRIPES)]
-    pats = patterns(BASE_SEED + 1 + 1000 * rank, STRIPES, K, M)
+    pats = patterns(pat_seed, STRIPES, K, M)
     plan = pyrit.pyrit_plan_create(W, N, K, M)
     enc = pyrit.pyrit_batch_create([(plan, pyrit.PYRIT_OP_ENCODE, 0, P, blocks[s]) for s in range(STRIPES)])
     dec = pyrit.pyrit_batch_create([(plan, pyrit.PYRIT_OP_DECODE, pats[s], P, blocks[s]) for s in range(STRIPES)])
     es, ds = pyrit.pyrit_batch_stats(enc), pyrit.pyrit_batch_stats(dec)
     launches_per_step = es["launches"] + ds["launches"]
     stream = torch.cuda.Stream(device=dev)
-    # The library's autotuner times every kernel variant on these batches and keeps the fastest.
-    pyrit.pyrit_batch_tune(enc, stream, 3)
-    pyrit.pyrit_batch_tune(dec, stream, 3)
+    # The library's autotuner times every kernel variant (and generated network shape) on these
+    # batches and keeps the fastest.
+    if not args.no_tune:
+        pyrit.pyrit_batch_tune(enc, stream, 6)
+        pyrit.pyrit_batch_tune(dec, stream, 6)
 
     def step(evs=None):
         if evs is not None:
@@ -276,19 +316,21 @@ def main():
     nvtx.range_pop()
     clk = clocks.stop()
     barrier()
-    ms = t0.elapsed_time(t1)
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(t0.elapsed_time(t1), world, dist, dev)
     ms_step = ms / args.steps
     src_per_step = es["src_bytes"] + ds["src_bytes"]
-    value = world * src_per_step / (ms_step * 1e-3) / 1e9
+    value = whole_job_gbs(world, src_per_step, ms_step)
     enc_ms = sum(e[0].elapsed_time(e[1]) for e in evs) / args.steps
     dec_ms = sum(e[1].elapsed_time(e[2]) for e in evs) / args.steps
-    alg_per_launch = (es["alg_bytes"] + ds["alg_bytes"]) / 2
-    achieved = alg_per_launch / ((enc_ms + dec_ms) / 2 * 1e-3) / 1e9
     peak, peak_kind = peak_hbm()
+    traffic = recorded_traffic()
+    kernels = []
+    for role, batch, st_, kms in (("encode", enc, es, enc_ms), ("decode", dec, ds, dec_ms)):
+        ach = st_["alg_bytes"] / (kms * 1e-3) / 1e9
+        kernels.append({"role": role, "kernel": kernel_name(pyrit.pyrit_batch_shape(batch, 0)), "ms": kms,
+                        "alg_bytes_per_launch": st_["alg_bytes"], "achieved": ach, "frac": ach / peak,
+                        "traffic": traffic.get(role)})
+    dominant = max(kernels, key=lambda kk: kk["ms"])
     code, where = pyrit.pyrit_device_status()
     if code != 0:
         raise RuntimeError("device status %d at site %d" % (code, where))
@@ -335,11 +377,8 @@ def main():
     nvtx.range_push("e2e")
     e2e_ms = e2e_timed(args.steps)
     nvtx.range_pop()
-    if world > 1:
-        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_val = world * src_per_step / (e2e_ms / args.steps * 1e-3) / 1e9
+    e2e_ms = max_over_ranks(e2e_ms, world, dist, dev)
+    e2e_val = whole_job_gbs(world, src_per_step, e2e_ms / args.steps)
     # every parity read back must equal the device-resident result
     e2e_ok = bool(torch.equal(buf[par0:].cpu(), host_par))
 
@@ -350,12 +389,13 @@ def main():
         "e2e": {"value": e2e_val, "unit": "GB/s", "h2d_bytes_per_step": STRIPES * K * blk,
                 "d2h_bytes_per_step": STRIPES * M * blk, "parity_readback_matches": e2e_ok},
         "gpu_launches": launches_per_step * args.steps,
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": recorded_traffic(),
+        "roofline": {"bound": "hbm", "achieved": dominant["achieved"], "peak": peak, "unit": "GB/s",
+                     "frac": dominant["frac"], "traffic": dominant["traffic"],
                      "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind if peak_kind == "measured"
                      else "fallback 6800 GB/s",
-                     "kernel": "ring_staged_kernel", "alg_bytes_per_launch": alg_per_launch,
-                     "encode_ms": enc_ms, "decode_ms": dec_ms},
+                     "kernel": dominant["kernel"], "role": dominant["role"],
+                     "alg_bytes_per_launch": dominant["alg_bytes_per_launch"], "kernels": kernels,
+                     "step_frac": (es["alg_bytes"] + ds["alg_bytes"]) / ((enc_ms + dec_ms) * 1e-3) / 1e9 / peak},
         "clocks": clk,
     }
 
@@ -467,8 +507,10 @@ def run_mixed(args):
     """4096 uneven stripes: ring n uniform in {5, 11, 13}, k in 4..32, m in 2..8 (redrawn until
     k+m <= 2^w), P log-uniform 512 B..256 KiB (multiple of 16), half encode, half decode with 1..m
     erasures. The batched persistent launch (autotuned) against 4096 per-stripe launches of the
-    same kernel; both must write the same bytes."""
+    same kernel; both must write the same bytes. The stripes' mask tables differ, so both arms run
+    the generic kernels (run-time compiled networks are switched off for the comparison)."""
     torch, pyrit, dev = _setup_gpu()
+    pyrit.pyrit_jit_mode(pyrit.PYRIT_JIT_OFF)
     from paper_1709_00178_gb300.synth import BASE_SEED
     import numpy as np
     rng = np.random.default_rng(BASE_SEED + 3)

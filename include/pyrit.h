@@ -281,6 +281,11 @@ PYRIT_API int pyrit_plan_specialise(pyrit_plan_t plan, int op, uint64_t erasures
  * PYRIT_E_TIMEOUT. */
 PYRIT_API int pyrit_jit_wait(int timeout_ms);
 
+/* Drops the background compiler's queued specs (they are compiled again when next needed) and
+ * waits up to timeout_ms for a compilation in progress: PYRIT_OK or PYRIT_E_TIMEOUT. For process
+ * shutdown (the Python binding calls it at interpreter exit) and for tests. */
+PYRIT_API int pyrit_jit_quiesce(int timeout_ms);
+
 /* stats_out[8]: networks cached, compiled, failed, compilations pending, lookups that returned a
  * network, networks loaded, total compile time (us), specs ever queued for the background. */
 PYRIT_API int pyrit_jit_stats(uint64_t* stats_out);

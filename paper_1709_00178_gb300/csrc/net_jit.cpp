@@ -82,9 +82,9 @@ Jit& jit() {
 
 std::string key_of(const NetSpec& s) { return std::string(reinterpret_cast<const char*>(&s), sizeof(s)); }
 
-void put(std::string& o, const char* fmt, long a = 0, long b = 0, long c = 0, long d = 0) {
+void put(std::string& o, const char* fmt, long a = 0, long b = 0, long c = 0, long d = 0, long e = 0, long f = 0) {
   char buf[256];
-  std::snprintf(buf, sizeof(buf), fmt, a, b, c, d);
+  std::snprintf(buf, sizeof(buf), fmt, a, b, c, d, e, f);
   o += buf;
 }
 
@@ -100,8 +100,7 @@ std::string net_source(const NetSpec& s) {
   o += " {\n";
   if (s.mode == 1) {
     // syndrome decode: only the rows a tile's erasure pattern uses are accumulated
-    o += "  uint32_t need;\n"
-         "  __device__ __forceinline__ void tile(const JobDesc* J, int, int) { need = J->mask[kSyndromeNeedRow][0]; }\n";
+    o += "  __device__ __forceinline__ void tile(const JobDesc* J, int, int) { load_rows(J); }\n";
   } else {
     o += "  __device__ __forceinline__ void tile(const JobDesc*, int, int) {}\n";
   }
@@ -123,19 +122,18 @@ std::string net_source(const NetSpec& s) {
         const uint32_t r = s.mask[j][out];
         std::string lines;
         for (int t = 0; t < N; ++t) {
-          std::string terms;
+          // accumulator t receives d[t - s] for every set bit s (the zero packet q = W drops out),
+          // two terms per three-input XOR
+          int qs[32], nq = 0;
           for (int sh = 0; sh < N; ++sh) {
             if (!((r >> sh) & 1u)) continue;
             const int q = (t - sh + N) % N;
-            if (q == W) continue;  // the zero packet of the embedding
-            char buf[32];
-            std::snprintf(buf, sizeof(buf), " ^ d[%d][x]", q);
-            terms += buf;
+            if (q != W) qs[nq++] = q;
           }
-          if (terms.empty()) continue;
-          put(lines, "          acc[%ld][%ld][x] ^=", ii, t);
-          lines += terms.substr(2);
-          lines += ";\n";
+          for (int i = 0; i + 1 < nq; i += 2)
+            put(lines, "          acc[%ld][%ld][x] = xor3(acc[%ld][%ld][x], d[%ld][x], d[%ld][x]);\n", ii, t, ii, t, qs[i],
+                qs[i + 1]);
+          if (nq & 1) put(lines, "          acc[%ld][%ld][x] ^= d[%ld][x];\n", ii, t, qs[nq - 1]);
         }
         if (lines.empty()) continue;
         if (guard) {
@@ -282,19 +280,22 @@ int net_candidate_shapes(int n, int nout, NetSpec* out, int cap) {
 }
 
 int shapes_for(int n, int nout, bool syndrome, NetSpec* out, int cap) {
-  static const Shape4 big[] = {{1, 0, 1, 24}, {2, 0, 1, 12}, {1, 0, 1, 16}, {2, 0, 1, 8}, {1, 1, 1, 16}, {1, 1, 1, 24}};
-  static const Shape4 small[] = {{1, 0, 1, 24}, {2, 0, 1, 16}, {4, 0, 1, 8}, {2, 0, 1, 8}, {1, 0, 1, 16}, {2, 0, 1, 12}};
-  const Shape4* list = n >= 11 ? big : small;
+  // Per ring size, measured order (config-2 and GF(2^12) batches): the first shape that fits is
+  // the default, the rest are the tuner's other candidates.
+  static const Shape4 n11[] = {{2, 0, 1, 12}, {2, 0, 1, 8}, {1, 0, 1, 16}, {1, 0, 1, 24}, {1, 1, 1, 16}};
+  static const Shape4 n13[] = {{1, 0, 1, 16}, {2, 0, 1, 8}, {1, 0, 1, 24}, {2, 0, 1, 12}, {1, 1, 1, 16}};
+  static const Shape4 small[] = {{2, 0, 1, 16}, {4, 0, 1, 8}, {1, 0, 1, 24}, {2, 0, 1, 8}, {2, 0, 1, 12}};
+  const Shape4* list = n == 11 ? n11 : n == 13 ? n13 : small;
   int count = 0;
-  for (int i = 0; i < 6 && count < cap; ++i) {
+  for (int i = 0; i < 5 && count < cap; ++i) {
     const Shape4& c = list[i];
     const int mg = c.half ? (nout + 1) / 2 : nout;
     if (mg < 1 || (c.half && (nout < 2 || syndrome))) continue;  // syndrome decode needs every row
     const int groups = output_groups(mg, nout, c.nc);
     if (c.nc % groups != 0 || groups * mg < nout) continue;
-    // accumulators + one staged source + addressing and loop state (+ an output under
-    // construction for syndrome decoding)
-    if ((mg + (syndrome ? 1 : 0)) * n * c.words + (n - 1) * c.words + 24 > reg_cap(c.nc, c.minb)) continue;
+    // accumulators (+ an output under construction for syndrome decoding) and one staged source
+    // must fit the register budget of (nc + 1) warps with room for addressing and loop state
+    if ((mg + (syndrome ? 1 : 0)) * n * c.words + (n - 1) * c.words + 16 > reg_cap(c.nc, c.minb)) continue;
     NetSpec s;
     std::memset(&s, 0, sizeof(s));
     s.n = n;
@@ -424,6 +425,16 @@ int pyrit_jit_wait(int timeout_ms) {
   std::unique_lock<std::mutex> lk(J.mu);
   const bool done = J.cv.wait_for(lk, std::chrono::milliseconds(timeout_ms < 0 ? 0 : timeout_ms),
                                   [&] { return J.queue.empty() && J.busy == 0; });
+  return done ? PYRIT_OK : PYRIT_E_TIMEOUT;
+}
+
+int pyrit_jit_quiesce(int timeout_ms) {
+  Jit& J = jit();
+  std::unique_lock<std::mutex> lk(J.mu);
+  for (Entry* e : J.queue) J.cache.erase(key_of(e->spec));  // never started: forget them
+  J.queue.clear();
+  const bool done = J.cv.wait_for(lk, std::chrono::milliseconds(timeout_ms < 0 ? 0 : timeout_ms),
+                                  [&] { return J.busy == 0; });
   return done ? PYRIT_OK : PYRIT_E_TIMEOUT;
 }
 

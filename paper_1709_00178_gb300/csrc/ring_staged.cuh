@@ -31,7 +31,9 @@
 //              int lane);                             // acc_i += r_ij * d for the group's outputs
 //   template <int N, int WORDS, int MG>
 //   void store(uint32_t (&acc)[MG][N][WORDS], const JobDesc* J, int g, uint32_t col0,
-//              uint32_t off);                          // phi_E^{-1} and the stores of the tile
+//              uint32_t off, bool valid);              // phi_E^{-1} and the stores of the tile;
+//                                                      // called by every lane (warp-collective
+//                                                      // steps allowed), stores only if valid
 //   static constexpr bool kSparse;                     // sources with a null pointer are absent
 // DirectStore supplies the usual store (output g*MG + i is acc[i] reduced) and kSparse = false.
 #pragma once
@@ -52,6 +54,14 @@ __device__ __forceinline__ const JobDesc* tile_job(const CodeArgs& a, uint32_t t
     col0 = (t - jid * a.tiles_per_job) * a.tw;
   }
   return a.jobs ? a.jobs + jid : &a.job0;
+}
+
+// a ^ b ^ c in one three-input logic instruction (truth table 0x96). Generated networks spell
+// their XORs this way so that each instruction absorbs two source terms.
+__device__ __forceinline__ uint32_t xor3(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t r;
+  asm("lop3.b32 %0, %1, %2, %3, 0x96;" : "=r"(r) : "r"(a), "r"(b), "r"(c));
+  return r;
 }
 
 template <int WORDS>
@@ -98,9 +108,10 @@ struct DirectStore {
 
   template <int N, int WORDS, int MG>
   __device__ __forceinline__ void store(uint32_t (&acc)[MG][N][WORDS], const JobDesc* J, int g, uint32_t col0,
-                                        uint32_t off) {
+                                        uint32_t off, bool valid) {
     constexpr int W = N - 1;
     using V = typename Vec<WORDS>::T;
+    if (!valid) return;
     const uint64_t P = J->P;
     const int nout = J->nout;
 #pragma unroll
@@ -138,10 +149,14 @@ struct DirectStore {
 // (phi_E), and each output is reduced once more before its store.
 struct SyndromeStore {
   static constexpr bool kSparse = true;  // erased columns and unused parity are absent sources
+  uint32_t need;                         // rows the pattern uses (read once per tile)
+
+  __device__ __forceinline__ void load_rows(const JobDesc* J) { need = J->mask[kSyndromeNeedRow][0]; }
 
   template <int N, int WORDS, int MG>
   __device__ __forceinline__ void store(uint32_t (&acc)[MG][N][WORDS], const JobDesc* J, int, uint32_t col0,
-                                        uint32_t off) {
+                                        uint32_t off, bool valid) {
+    // lanes past the tile's width take part in nothing here but the stores they skip
     constexpr int W = N - 1;
     using V = typename Vec<WORDS>::T;
 #pragma unroll
@@ -183,13 +198,15 @@ struct SyndromeStore {
           }
         }
       }
-      uint8_t* dst = J->out[o] + col0 + off;
+      if (valid) {
+        uint8_t* dst = J->out[o] + col0 + off;
 #pragma unroll
-      for (int t = 0; t < W; ++t) {
-        uint32_t o4[WORDS];
+        for (int t = 0; t < W; ++t) {
+          uint32_t o4[WORDS];
 #pragma unroll
-        for (int x = 0; x < WORDS; ++x) o4[x] = res[t][x] ^ res[W][x];
-        *reinterpret_cast<V*>(dst + (size_t)t * P) = vmake<WORDS>(o4);
+          for (int x = 0; x < WORDS; ++x) o4[x] = res[t][x] ^ res[W][x];
+          *reinterpret_cast<V*>(dst + (size_t)t * P) = vmake<WORDS>(o4);
+        }
       }
     }
   }
@@ -315,7 +332,7 @@ __device__ __forceinline__ void ring_staged_body(const CodeArgs& a) {
       mac.template apply<N, WORDS, MG>(acc, d, j, g, lane);
     }
 
-    if (valid) mac.template store<N, WORDS, MG>(acc, J, g, col0, off);
+    mac.template store<N, WORDS, MG>(acc, J, g, col0, off, valid);
   }
 }
 

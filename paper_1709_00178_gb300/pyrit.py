@@ -8,6 +8,7 @@ arrays). A negative status raises :class:`PyritError`. Streams are ``cudaStream_
 Importing this module loads ``libpyrit.so`` and fails loudly if it has not been built
 (``python -c "import __graft_entry__ as g; g.build()"``); there is no fallback.
 """
+import atexit
 import ctypes
 import os
 
@@ -310,6 +311,7 @@ _JIT_SIGS = {
     "pyrit_jit_mode": (_i, [_i]),
     "pyrit_plan_specialise": (_i, [_vp, _i, _u64, ctypes.POINTER(pyrit_tile_t)]),
     "pyrit_jit_wait": (_i, [_i]),
+    "pyrit_jit_quiesce": (_i, [_i]),
     "pyrit_jit_stats": (_i, [_vp]),
     "pyrit_jit_log": (_i, [ctypes.c_char_p, _i]),
     "pyrit_jit_source": (_i, [_i, _i, _i, _vp, ctypes.POINTER(pyrit_tile_t), ctypes.c_char_p, _i]),
@@ -338,6 +340,17 @@ def pyrit_plan_specialise(plan, op=PYRIT_OP_ENCODE, erasures=0, tile=None):
 
 def pyrit_jit_wait(timeout_ms=60000):
     return _check(_lib.pyrit_jit_wait(timeout_ms), "pyrit_jit_wait")
+
+
+def pyrit_jit_quiesce(timeout_ms=60000):
+    return _check(_lib.pyrit_jit_quiesce(timeout_ms), "pyrit_jit_quiesce")
+
+
+@atexit.register
+def _quiesce_at_exit():
+    # No background compilation may still run while the interpreter and CUDA shut down.
+    _lib.pyrit_jit_mode(PYRIT_JIT_OFF)
+    _lib.pyrit_jit_quiesce(120000)
 
 
 def pyrit_jit_stats():

@@ -28,10 +28,15 @@ def _parse(src):
             cur = int(c.group(1))
             cases[cur] = []
             continue
+        # acc[i][t][x] ^= d[q][x];   or   acc[i][t][x] = xor3(acc[i][t][x], d[a][x], d[b][x]);
         a = re.match(r"\s*acc\[(\d+)\]\[(\d+)\]\[x\] \^= (.*);", line)
+        b = re.match(r"\s*acc\[(\d+)\]\[(\d+)\]\[x\] = xor3\(acc\[(\d+)\]\[(\d+)\]\[x\], (.*)\);", line)
+        if b:
+            assert b.group(1, 2) == b.group(3, 4), "a three-input XOR must update its own accumulator"
+            a = b
         if a:
             assert cur is not None
-            qs = [int(q) for q in re.findall(r"d\[(\d+)\]\[x\]", a.group(3))]
+            qs = [int(q) for q in re.findall(r"d\[(\d+)\]\[x\]", a.groups()[-1])]
             cases[cur].append((int(a.group(1)), int(a.group(2)), qs))
         if "} break;" in line:
             cur = None
