@@ -608,6 +608,10 @@ def run_served(args):
     plan = pyrit.pyrit_plan_create(w, w + 1, k, m)
     for pat in set(pool_pat):  # the plan caches every decoding matrix before the timed window
         pyrit.pyrit_plan_decode_masks(plan, pat)
+    # the plan's generated networks (encode table, syndrome decode) are compiled before serving;
+    # without this the server codes with the generic kernel until its background compiles finish
+    pyrit.pyrit_plan_specialise(plan, pyrit.PYRIT_OP_ENCODE)
+    pyrit.pyrit_plan_specialise(plan, pyrit.PYRIT_OP_DECODE_ANY)
     base = buf.data_ptr()
     nreq = int(rate * args.seconds)
     gaps = rng.exponential(1e9 / rate, nreq)
@@ -622,15 +626,29 @@ def run_served(args):
         src_bytes += k * w * P
     arr, keep = pyrit.pyrit_requests_array(reqs)
     srv = pyrit.pyrit_server_create(16 << 30, max_batch=64, slots=4)
-    # warm the launch shapes and the device with a short unmeasured burst
+    # The clock sampler starts before anything is timed: its startup queries the driver, which
+    # stalled the server's stream calls for tens of milliseconds when it coincided with the first
+    # arrivals. Then a short unmeasured burst warms the launch shapes and the device.
+    clocks = Clocks(0)
+    clocks.start()
     pyrit.pyrit_server_submit_slice(srv, arr, 0, min(64, nreq))
     pyrit.pyrit_server_drain(srv, 60000)
     pyrit.pyrit_server_poll(srv, 1 << 20)
-    clocks = Clocks(0)
-    clocks.start()
-    t0 = pyrit.pyrit_server_now_ns(srv) + 2000000
+    time.sleep(0.5)
+    # The load generator must not pause: a full collection over the request tables (millions of
+    # objects) would hold submissions back for tens of milliseconds and count as service latency.
+    import gc
+    gc.collect()
+    gc.freeze()
+    gc.disable()
+    # The arrival times are written first (200k ctypes fields take tens of milliseconds), with the
+    # first arrival far enough ahead that submission starts before it: arrivals must not pile up
+    # into a burst the load generator itself created.
+    t0 = pyrit.pyrit_server_now_ns(srv) + 1000000000
     for i in range(nreq):
         arr[i].arrival_ns = int(t0 + arrivals[i])
+    if pyrit.pyrit_server_now_ns(srv) >= t0:
+        raise RuntimeError("load generator set-up ran past the first arrival")
     i = 0
     while i < nreq:
         now = pyrit.pyrit_server_now_ns(srv)
@@ -641,6 +659,7 @@ def run_served(args):
             pyrit.pyrit_server_submit_slice(srv, arr, i, j - i)
             i = j
     pyrit.pyrit_server_drain(srv, 600000)
+    gc.enable()
     clk = clocks.stop()
     done = pyrit.pyrit_server_poll(srv, nreq + 64)
     st = pyrit.pyrit_server_stats(srv)

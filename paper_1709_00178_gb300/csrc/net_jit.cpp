@@ -399,7 +399,7 @@ const Variant* net_variant(const NetSpec& s, bool block) {
       ++J.failed;
       return nullptr;
     }
-    e->v = Variant{s.n, s.words, s.mg, s.minb, PYRIT_DISPATCH_NETWORK, s.nc, reinterpret_cast<const void*>(k), s.mode};
+    e->v = Variant{s.n, s.words, s.mg, s.minb, PYRIT_DISPATCH_NETWORK, s.nc, reinterpret_cast<const void*>(k), s.mode, s.nout};
     e->loaded = true;
     ++J.loaded;
   }

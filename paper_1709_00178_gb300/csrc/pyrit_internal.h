@@ -32,6 +32,7 @@ struct Variant {
   int nc;        // consumer warps per CTA (one more warp is the producer)
   const void* fn;
   int mode;      // generated networks: 0 direct table, 1 syndrome decode (takes syndrome-form jobs)
+  int nout;      // generated networks: the output count they were compiled for (0: generic)
 };
 
 // Output groups of a launch: the smallest power of two g with g * mg >= nout (and g < nc); the

@@ -4,10 +4,14 @@
 // scheduler thread admits them while the bytes of the requests in flight stay within an HBM budget
 // and, whenever one of its stream slots is free, packs everything admitted into one batch: the jobs
 // are copied into that slot's device descriptor table and coded by one persistent launch of the
-// staged ring kernel per ring size on the slot's stream. Batches on different slots overlap on the
-// device, so requests that arrive while others are running start as soon as a slot and budget free
-// up. Completion is timestamped on the device timeline (CUDA events measured against an origin
-// event), so a request's latency is its arrival to the end of the GPU work that coded it.
+// staged ring kernel per ring size on the slot's stream -- or, for requests whose plan has a
+// compiled generated network (its encode table, or its syndrome-decode network), one launch of
+// that network per plan and operation; a missing network is queued for the background compiler and
+// the generic kernel serves meanwhile, so the scheduler never waits for a compilation. Batches on
+// different slots overlap on the device, so requests that arrive while others are running start as
+// soon as a slot and budget free up. Completion is timestamped on the device timeline (CUDA events
+// measured against an origin event), so a request's latency is its arrival to the end of the GPU
+// work that coded it.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -18,6 +22,7 @@
 #include <deque>
 #include <mutex>
 #include <new>
+#include <map>
 #include <thread>
 #include <vector>
 
@@ -34,6 +39,10 @@ int64_t host_now_ns() {
 
 struct Pending {
   JobDesc job;
+  JobDesc syn_job;               // the syndrome form of a decode job (when syn)
+  const pyrit_plan_s* plan;
+  int op;
+  bool syn = false;
   int n;
   uint64_t bytes;    // device bytes of the stripe ((k+m) w P): what the admission budget counts
   uint64_t tag;
@@ -58,6 +67,7 @@ struct Slot {
 struct pyrit_server_s {
   TileShape shapes[16][kMaxOut + 1];  // launch shape per (ring size, largest output count), lazily
   bool shape_set[16][kMaxOut + 1] = {};
+  std::map<const Variant*, TileShape> net_shapes;  // launch shapes of the generated networks used
   size_t budget = 0;
   int max_batch = 0;
   uint32_t max_tiles = 0;
@@ -139,7 +149,30 @@ int slot_shape(pyrit_server_s* s, int n, int max_nout, TileShape* out) {
   return PYRIT_OK;
 }
 
-// Column tiles the slot's requests need, with their batch's launch shapes.
+// The generated network that would code request p now (nullptr: the generic kernel), queued for
+// the background compiler if it is missing.
+const Variant* request_network(const Pending& p) {
+  if (p.job.nout == 0 || jit_mode() == PYRIT_JIT_OFF) return nullptr;
+  if (p.op == PYRIT_OP_ENCODE) return net_variant(net_spec(p.n, p.job, 0, 0, 0, 0), false);
+  if (p.syn) return net_variant(net_spec_syndrome(p.plan, 0, 0, 0), false);
+  return nullptr;
+}
+
+// Launch shape of a generated network (cached).
+const TileShape& network_shape(pyrit_server_s* s, const Variant* v) {
+  auto it = s->net_shapes.find(v);
+  if (it == s->net_shapes.end()) {
+    TileShape sh;
+    shape_for_variant(v, v->nout, ShapeHint(), &sh);  // the output split it was compiled for
+    resolve_grid(&sh);
+    it = s->net_shapes.emplace(v, sh).first;
+  }
+  return it->second;
+}
+
+// Column tiles the slot's requests need: an upper bound whichever kernel codes each of them (the
+// narrowest tile width among its ring size's generic shape and the default network shapes), so
+// that a network finishing its compilation between admission and launch cannot overflow the table.
 uint64_t slot_tiles(pyrit_server_s* s, const std::vector<Pending>& reqs) {
   int max_nout[16] = {0};
   for (const Pending& p : reqs) max_nout[p.n] = std::max(max_nout[p.n], (int)p.job.nout);
@@ -148,13 +181,22 @@ uint64_t slot_tiles(pyrit_server_s* s, const std::vector<Pending>& reqs) {
     if (p.job.nout == 0) continue;
     TileShape sh;
     if (slot_shape(s, p.n, max_nout[p.n], &sh) != PYRIT_OK) return ~0ull;
-    t += (p.job.P + (uint64_t)sh.tw - 1) / (uint64_t)sh.tw;
+    uint64_t tw = (uint64_t)sh.tw;
+    NetSpec cand[8];
+    const int nc = p.syn ? net_syndrome_shapes(p.plan, cand, 8) : net_candidate_shapes(p.n, p.job.nout, cand, 8);
+    for (int i = 0; i < nc && i < 1; ++i) {  // the default network shape is the one served
+      const int groups = output_groups(cand[i].mg, cand[i].nout, cand[i].nc);
+      tw = std::min<uint64_t>(tw, (uint64_t)(cand[i].nc / groups) * 32u * 4u * (uint64_t)cand[i].words);
+    }
+    t += (p.job.P + tw - 1) / tw;
   }
   return t;
 }
 
-// Packs the slot's admitted requests into launches: jobs grouped by ring size, an explicit tile
-// list per group, both staged in pinned memory and copied on the slot's stream.
+// Packs the slot's admitted requests into launches: requests with a compiled network grouped by
+// that network (encode table or plan's syndrome decode), the rest by ring size on the generic
+// kernel; an explicit tile list per group; all staged in pinned memory and copied on the slot's
+// stream.
 int launch_slot(pyrit_server_s* s, Slot& sl) {
   uint32_t nj = 0, nt = 0;
   struct G {
@@ -162,19 +204,17 @@ int launch_slot(pyrit_server_s* s, Slot& sl) {
     uint32_t job0, njobs, tile0, ntiles;
   };
   std::vector<G> groups;
-  for (int n = 0; n < 16; ++n) {
+  std::vector<const Variant*> net(sl.reqs.size());
+  for (size_t i = 0; i < sl.reqs.size(); ++i) net[i] = request_network(sl.reqs[i]);
+  auto add_group = [&](const TileShape& shape, auto member, bool syn_form) -> int {
     G g{};
+    g.shape = shape;
     g.job0 = nj;
     g.tile0 = nt;
-    int max_nout = 0;
-    for (const Pending& p : sl.reqs)
-      if (p.n == n) max_nout = std::max(max_nout, (int)p.job.nout);
-    if (max_nout == 0) continue;
-    const int rc = slot_shape(s, n, max_nout, &g.shape);
-    if (rc != PYRIT_OK) return rc;
-    for (const Pending& p : sl.reqs) {
-      if (p.n != n || p.job.nout == 0) continue;
-      sl.host_jobs[nj] = p.job;
+    for (size_t i = 0; i < sl.reqs.size(); ++i) {
+      const Pending& p = sl.reqs[i];
+      if (p.job.nout == 0 || !member(i)) continue;
+      sl.host_jobs[nj] = syn_form ? p.syn_job : p.job;
       for (uint64_t c = 0; c < p.job.P; c += (uint64_t)g.shape.tw) {
         if (nt >= s->max_tiles) return PYRIT_E_INVALID_ARG;  // admission keeps batches within the table
         sl.host_tiles[nt++] = make_uint2(nj - g.job0, (uint32_t)c);
@@ -183,7 +223,28 @@ int launch_slot(pyrit_server_s* s, Slot& sl) {
     }
     g.njobs = nj - g.job0;
     g.ntiles = nt - g.tile0;
-    groups.push_back(g);
+    if (g.njobs) groups.push_back(g);
+    return PYRIT_OK;
+  };
+  // generated networks, one launch each
+  std::vector<const Variant*> used;
+  for (const Variant* v : net)
+    if (v && std::find(used.begin(), used.end(), v) == used.end()) used.push_back(v);
+  for (const Variant* v : used) {
+    const int rc = add_group(network_shape(s, v), [&](size_t i) { return net[i] == v; }, v->mode == 1);
+    if (rc != PYRIT_OK) return rc;
+  }
+  // the generic kernel per ring size for the rest
+  for (int n = 0; n < 16; ++n) {
+    int max_nout = 0;
+    for (size_t i = 0; i < sl.reqs.size(); ++i)
+      if (!net[i] && sl.reqs[i].n == n) max_nout = std::max(max_nout, (int)sl.reqs[i].job.nout);
+    if (max_nout == 0) continue;
+    TileShape sh;
+    const int rc = slot_shape(s, n, max_nout, &sh);
+    if (rc != PYRIT_OK) return rc;
+    const int rc2 = add_group(sh, [&](size_t i) { return !net[i] && sl.reqs[i].n == n; }, false);
+    if (rc2 != PYRIT_OK) return rc2;
   }
   cudaEventRecord(sl.start, sl.st);
   if (nj && cudaMemcpyAsync(sl.dev_jobs, sl.host_jobs, nj * sizeof(JobDesc), cudaMemcpyHostToDevice, sl.st) != cudaSuccess)
@@ -300,6 +361,15 @@ int pyrit_server_submit(pyrit_server_t s, const pyrit_request_t* reqs, int count
     const int rc = stripe_job(reqs[i].stripe, &p.job, &alg, &src);
     if (rc != PYRIT_OK) return rc;
     p.n = reqs[i].stripe.plan->n;
+    p.plan = reqs[i].stripe.plan;
+    p.op = reqs[i].stripe.op;
+    if (p.op == PYRIT_OP_DECODE && p.job.nout > 0) {
+      DecodeEntry e;
+      if (plan_decode_entry(reqs[i].stripe.plan, reqs[i].stripe.erasures, &e) == PYRIT_OK && e.syn_ok) {
+        make_syndrome_job(p.plan, e, reqs[i].stripe.blocks, reqs[i].stripe.packet_bytes, &p.syn_job);
+        p.syn = true;
+      }
+    }
     p.bytes = (uint64_t)(reqs[i].stripe.plan->k + reqs[i].stripe.plan->m) * reqs[i].stripe.plan->w *
               reqs[i].stripe.packet_bytes;
     if (p.bytes > s->budget) return PYRIT_E_BUDGET;
