@@ -419,7 +419,7 @@ def cpu_baseline(buf, blocks, pats, plan, pyrit):
     sample = 16
     cores = os.cpu_count() or 1
     blk = W * P
-    G = pyrit.pyrit_plan_generator(plan)
+    G = oracle.cauchy(W, K, M)
     data = buf[:sample * K * blk].cpu().numpy().reshape(sample, K, W, P)
     par0 = STRIPES * K * blk
     gpar = buf[par0:par0 + sample * M * blk].cpu().numpy().reshape(sample, M, W, P)

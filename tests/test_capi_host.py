@@ -115,7 +115,7 @@ def test_decode_masks_match_oracle(w, k, m, exhaustive):
     plan = pyrit.pyrit_plan_create(w, w + 1, k, m)
     sp = _brute_sparse(w, w + 1)
     try:
-        G = pyrit.pyrit_plan_generator(plan)
+        G = oracle.cauchy(w, k, m)  # the oracle's own generator (the library's is pinned equal above)
         if exhaustive:
             pats = [sum(1 << x for x in c) for e in range(0, m + 1) for c in itertools.combinations(range(k + m), e)]
         else:

@@ -74,7 +74,7 @@ def test_mixed_batch_encode_then_decode(pyrit):
             arr = np.zeros((k + m, w, P), np.uint8)
             arr[:k] = data
             pool.put(i, arr)
-            G = pyrit.pyrit_plan_generator(plans[(w, k, m)])
+            G = oracle.cauchy(w, k, m)
             full.append(np.concatenate([data, oracle.encode(w, k, m, G, data, nthreads=NCPU)]))
         enc = [(plans[(w, k, m)], pyrit.PYRIT_OP_ENCODE, 0, P, pool.blocks(i)) for i, (w, k, m, P) in enumerate(MIXED)]
         b = pyrit.pyrit_batch_create(enc)
@@ -123,7 +123,7 @@ def test_every_variant_is_bit_exact(pyrit, w, k, m, P, S):
     pool = Pool(specs, 3)
     plan = pyrit.pyrit_plan_create(w, w + 1, k, m)
     try:
-        G = pyrit.pyrit_plan_generator(plan)
+        G = oracle.cauchy(w, k, m)
         full = []
         for i in range(S):
             data = synth_bytes(300 + i, 0, k * w * P).reshape(k, w, P)
@@ -185,7 +185,7 @@ def test_autotune_keeps_results_and_records_choice(pyrit, tmp_path):
     pool = Pool(specs, 11)
     plan = pyrit.pyrit_plan_create(w, w + 1, k, m)
     try:
-        G = pyrit.pyrit_plan_generator(plan)
+        G = oracle.cauchy(w, k, m)
         full = []
         for i in range(S):
             data = synth_bytes(700 + i, 0, k * w * P).reshape(k, w, P)
@@ -223,7 +223,7 @@ def test_autotune_mixed_packet_sizes_and_decode(pyrit):
     pool = Pool(specs, 5)
     plan = pyrit.pyrit_plan_create(12, 13, 16, 4)
     try:
-        G = pyrit.pyrit_plan_generator(plan)
+        G = oracle.cauchy(12, 16, 4)
         full = []
         for i, (w, k, m, P) in enumerate(specs):
             data = synth_bytes(800 + i, 0, k * w * P).reshape(k, w, P)

@@ -41,7 +41,7 @@ class Stripes:
         self.stride = ((k + m) * w * P + 255) // 256 * 256
         self.buf = torch.zeros(count * self.stride, dtype=torch.uint8, device="cuda")
         self.plan = pyrit.pyrit_plan_create(w, w + 1, k, m)
-        self.G = pyrit.pyrit_plan_generator(self.plan)
+        self.G = oracle.cauchy(w, k, m)
         self.data = [synth_bytes(seed + s, 0, k * w * P).reshape(k, w, P) for s in range(count)]
         for s in range(count):
             self.view(s)[:k * w * P].copy_(torch.from_numpy(self.data[s].reshape(-1)).cuda())

@@ -70,7 +70,7 @@ class Stripe:
 def _encode_case(pyrit, w, k, m, P, seed, misalign=0):
     plan = pyrit.pyrit_plan_create(w, w + 1, k, m)
     try:
-        G = pyrit.pyrit_plan_generator(plan)
+        G = oracle.cauchy(w, k, m)
         data = synth_bytes(seed, 0, k * w * P).reshape(k, w, P)
         st = Stripe(k, m, w, P, misalign)
         for j in range(k):
@@ -123,7 +123,7 @@ def test_encode_zero_and_ones(pyrit):
     w, k, m, P = 10, 10, 4, 4096
     plan = pyrit.pyrit_plan_create(w, w + 1, k, m)
     try:
-        G = pyrit.pyrit_plan_generator(plan)
+        G = oracle.cauchy(w, k, m)
         for fill in (0x00, 0xFF):
             data = np.full((k, w, P), fill, np.uint8)
             st = Stripe(k, m, w, P)

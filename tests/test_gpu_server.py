@@ -93,7 +93,7 @@ def test_alone_equals_mix(pyrit):
             if op != 0 or i > 12:
                 continue
             stripe = h[offs[i]:offs[i] + (k + m) * w * P].reshape(k + m, w, P)
-            G = pyrit.pyrit_plan_generator(plans[(w, k, m)])
+            G = oracle.cauchy(w, k, m)
             assert np.array_equal(stripe[k:], oracle.encode(w, k, m, G, stripe[:k], nthreads=NCPU)), i
     finally:
         for p in plans.values():
