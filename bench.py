@@ -82,6 +82,15 @@ def kernel_name(shape):
                                                           shape["dispatch"], shape["nc"])
 
 
+def make_plan(pyrit, generator, w, k, m):
+    """The library plan of a code: the plain Cauchy generator, or the weight-optimised generalized
+    Cauchy one (the oracle legs compute their own copy; a CPU test pins the two equal)."""
+    if generator == "weighted":
+        G, _ = pyrit.pyrit_generator_weighted(w, w + 1, k, m)
+        return pyrit.pyrit_plan_create(w, w + 1, k, m, G)
+    return pyrit.pyrit_plan_create(w, w + 1, k, m)
+
+
 def rank_shard(rank, stripe_bytes, stripes):
     """What rank `rank` codes (weak scaling, no data-path collective): its stripes' bytes are the
     synthetic stream's bytes [rank * S * B, (rank + 1) * S * B) and its erasure patterns come from
@@ -175,7 +184,7 @@ def run_reference(args):
         return
     cores = os.cpu_count() or 1
     sample = 4  # stripes encoded and decoded per step
-    G = oracle.cauchy(W, K, M)
+    G = oracle.cauchy_weighted(W, K, M)[0] if args.generator == "weighted" else oracle.cauchy(W, K, M)
     pats = patterns(BASE_SEED + 1, STRIPES, K, M)
     blk = W * P
     # the same bytes as the GPU arm's first stripes: data blocks are contiguous in the stream
@@ -217,6 +226,9 @@ def main():
                     help="coding: the default line; sweep: GF(2^12) k=16 m=4 packet sweep 4 KiB-1 MiB; mixed: "
                          "4096 uneven stripes batched vs per-stripe launches; served: Poisson arrivals")
     ap.add_argument("--seconds", type=float, default=10.0, help="served: arrival window")
+    ap.add_argument("--generator", default="cauchy", choices=["cauchy", "weighted"],
+                    help="cauchy: the plain Cauchy code of the configurations; weighted: the same code "
+                         "family with weight-optimised row/column scalings (generalized Cauchy)")
     ap.add_argument("--no-tune", action="store_true",
                     help="skip the autotuner: time the automatic shapes (profiling cases of a fixed kernel)")
     args = ap.parse_args()
@@ -259,7 +271,8 @@ def main():
     blocks = [[base + (s * K + j) * blk for j in range(K)] + [base + par0 + (s * M + i) * blk for i in range(M)]
               for s in range(STRIPES)]
     pats = patterns(pat_seed, STRIPES, K, M)
-    plan = pyrit.pyrit_plan_create(W, N, K, M)
+    plan = make_plan(pyrit, args.generator, W, K, M)
+    CONFIG["generator"] = "plain Cauchy" if args.generator == "cauchy" else "weight-optimised generalized Cauchy"
     enc = pyrit.pyrit_batch_create([(plan, pyrit.PYRIT_OP_ENCODE, 0, P, blocks[s]) for s in range(STRIPES)])
     dec = pyrit.pyrit_batch_create([(plan, pyrit.PYRIT_OP_DECODE, pats[s], P, blocks[s]) for s in range(STRIPES)])
     es, ds = pyrit.pyrit_batch_stats(enc), pyrit.pyrit_batch_stats(dec)
@@ -400,7 +413,7 @@ def main():
     }
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(buf, blocks, pats, plan, pyrit)
+        out["cpu_baseline"] = cpu_baseline(buf, blocks, pats, plan, pyrit, args.generator)
     if rank == 0:
         print(json.dumps(out))
     for b in [enc, dec] + cenc + cdec:
@@ -410,7 +423,7 @@ def main():
         dist.destroy_process_group()
 
 
-def cpu_baseline(buf, blocks, pats, plan, pyrit):
+def cpu_baseline(buf, blocks, pats, plan, pyrit, generator="cauchy"):
     """The oracle, as it stands, on a bounded sample of the same stripes and patterns, on all host
     cores; its parity is also compared with the GPU's for those stripes."""
     import numpy as np
@@ -419,7 +432,7 @@ def cpu_baseline(buf, blocks, pats, plan, pyrit):
     sample = 16
     cores = os.cpu_count() or 1
     blk = W * P
-    G = oracle.cauchy(W, K, M)
+    G = oracle.cauchy_weighted(W, K, M)[0] if generator == "weighted" else oracle.cauchy(W, K, M)
     data = buf[:sample * K * blk].cpu().numpy().reshape(sample, K, W, P)
     par0 = STRIPES * K * blk
     gpar = buf[par0:par0 + sample * M * blk].cpu().numpy().reshape(sample, M, W, P)
@@ -468,7 +481,7 @@ def run_sweep(args):
     import numpy as np
     w, k, m = 12, 16, 4
     peak, _ = peak_hbm()
-    plan = pyrit.pyrit_plan_create(w, w + 1, k, m)
+    plan = make_plan(pyrit, args.generator, w, k, m)
     stream = torch.cuda.Stream(device=dev)
     for e in range(12, 21):
         P = 1 << e
@@ -493,7 +506,8 @@ def run_sweep(args):
         print(json.dumps({
             "metric": "encode+decode GB/s of source data", "workload": "sweep",
             "value": (es["src_bytes"] + ds["src_bytes"]) / (te + td) / 1e6, "unit": "GB/s",
-            "config": {"workload": "GF(2^12) n=13 Cauchy k=16 m=4, 4-erasure decode", "packet_bytes": P, "stripes": S},
+            "config": {"workload": "GF(2^12) n=13 Cauchy k=16 m=4, 4-erasure decode", "packet_bytes": P, "stripes": S,
+                       "generator": args.generator},
             "encode_ms": te, "decode_ms": td, "encode_roofline_frac": ae / peak, "decode_roofline_frac": ad / peak,
             "encode_alg_gbs": ae, "decode_alg_gbs": ad, "dtype": "u8", "data": "synthetic"}), flush=True)
         pyrit.pyrit_batch_destroy(enc)

@@ -100,6 +100,18 @@ typedef struct pyrit_plan_s* pyrit_plan_t;
 PYRIT_API int pyrit_plan_create(int w, int n, int k, int m, const uint32_t* G, pyrit_plan_t* out);
 PYRIT_API void pyrit_plan_destroy(pyrit_plan_t plan);
 
+/* A weight-optimised generalized Cauchy generator to pass to pyrit_plan_create (Sec. 3 codes with
+ * "generalized Cauchy matrices"; Sec. 2.2 makes the cost the number of ones of the sparse ring
+ * representatives). G_out[(k+m)*k] = [I_k ; C'] with C'[i][j] = a_i b_j / (x_i + y_j),
+ * x_i = k+i, y_j = j: row and column scalings of the default Cauchy matrix, which keep every
+ * square submatrix nonsingular (the code stays MDS). The scalings are chosen by coordinate descent
+ * on the total weight of phi_S over C': starting from a = b = 1, each round sets every b_j
+ * (ascending j), then every a_i (ascending i), to the nonzero element minimising the weight summed
+ * over its column (row), the smallest element on ties, until a round changes nothing (at most 8
+ * rounds). weights_out[2] (may be NULL): total weight of the default and of the returned parity
+ * part. Host only; deterministic. Errors: as pyrit_plan_create for (w, n, k, m). */
+PYRIT_API int pyrit_generator_weighted(int w, int n, int k, int m, uint32_t* G_out, uint64_t* weights_out);
+
 /* Plan parameters (any pointer may be NULL). */
 PYRIT_API int pyrit_plan_info(pyrit_plan_t plan, int* w, int* n, int* k, int* m);
 

@@ -37,6 +37,7 @@ def lib():
             "oracle_gf_tables": (i32, [i32, vp, vp, vp]),
             "oracle_gf_mul": (u32, [i32, u32, u32]),
             "oracle_cauchy": (i32, [i32, i32, i32, vp]),
+            "oracle_cauchy_weighted": (i32, [i32, i32, i32, vp, vp]),
             "oracle_gf_invert": (i32, [i32, i32, vp, vp]),
             "oracle_encode": (i32, [i32, i32, i32, vp, vp, vp, sz, i32]),
             "oracle_decode": (i32, [i32, i32, i32, vp, vp, u64, sz, i32]),
@@ -125,6 +126,16 @@ def cauchy(w, k, m):
     if rc:
         raise ValueError("oracle_cauchy(w=%d,k=%d,m=%d) -> %d" % (w, k, m, rc))
     return G
+
+
+def cauchy_weighted(w, k, m):
+    """Weight-optimised generalized Cauchy generator and its (plain, optimised) total weights."""
+    G = np.zeros((k + m, k), np.uint32)
+    wts = np.zeros(2, np.uint64)
+    rc = lib().oracle_cauchy_weighted(w, k, m, _p(G), wts.ctypes.data_as(ctypes.c_void_p))
+    if rc:
+        raise ValueError("oracle_cauchy_weighted(w=%d,k=%d,m=%d) -> %d" % (w, k, m, rc))
+    return G, (int(wts[0]), int(wts[1]))
 
 
 def gf_invert(w, A):

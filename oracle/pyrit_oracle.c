@@ -503,3 +503,105 @@ void oracle_ring_mul_vec(int n, const uint32_t* a, const uint32_t* b, uint32_t* 
 void oracle_poly_mod_vec(uint64_t p, const uint32_t* a, uint32_t* out, size_t cnt) {
   for (size_t i = 0; i < cnt; i++) out[i] = (uint32_t)oracle_poly_mod(a[i], p);
 }
+
+/* ------------------------------------------------------------------------------------------ */
+/* Weight-optimised generalized Cauchy generator (Sec. 3 names "generalized Cauchy matrices"   */
+/* and Sec. 2.2 makes the coding cost the number of ones of the sparse representatives)       */
+/* ------------------------------------------------------------------------------------------ */
+
+/* wt[u] = number of ones of phi_S(u), for every u < 2^w: the fewest ones over all ring elements
+ * r with r mod p = u, in one pass over the 2^n ring elements. */
+static void sparse_weights(int w, int n, int* wt) {
+  uint64_t p = oracle_aop(w);
+  for (uint32_t u = 0; u < (1u << w); u++) wt[u] = 99;
+  for (uint32_t r = 0; r < (1u << n); r++) {
+    uint32_t u = (uint32_t)oracle_poly_mod(r, p);
+    int c = popcount32(r);
+    if (c < wt[u]) wt[u] = c;
+  }
+}
+
+/* The generator [I_k ; C'] with C'[i][j] = a_i b_j / (x_i + y_j), x_i = k + i, y_j = j: scaling
+ * the rows and columns of a Cauchy matrix by nonzero elements keeps every square submatrix
+ * nonsingular, so the code stays MDS. The scalings minimise the total weight of phi_S over C' by
+ * coordinate descent: starting from a = b = 1, each round sets every b_j (j ascending), then
+ * every a_i (i ascending), to the element of 1..2^w-1 that minimises the weight summed over its
+ * column (row) -- the smallest such element on ties -- and the rounds stop when one changes
+ * nothing, or after 8. weights[0] / weights[1]: total weight before and after. */
+int oracle_cauchy_weighted(int w, int k, int m, uint32_t* G, uint64_t* weights) {
+  if (k < 1 || m < 0 || k > ORACLE_MAX_K || w < 2 || w > ORACLE_MAX_W) return -2;
+  if ((uint64_t)k + (uint64_t)m > ((uint64_t)1 << w)) return -2;
+  gf_t f;
+  if (gf_init(&f, w)) {
+    gf_free(&f);
+    return -1;
+  }
+  const int n = w + 1;
+  const uint32_t q = 1u << w;
+  int* wt = (int*)malloc(sizeof(int) * q);
+  uint32_t* c = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(m > 0 ? m : 1) * (size_t)k);
+  uint32_t a[64], b[64];
+  if (!wt || !c || m > 64) {
+    free(wt);
+    free(c);
+    gf_free(&f);
+    return -1;
+  }
+  sparse_weights(w, n, wt);
+  for (int i = 0; i < m; i++)
+    for (int j = 0; j < k; j++) c[i * k + j] = gf_inv(&f, (uint32_t)(k + i) ^ (uint32_t)j);
+  for (int i = 0; i < m; i++) a[i] = 1;
+  for (int j = 0; j < k; j++) b[j] = 1;
+  uint64_t w0 = 0;
+  for (int i = 0; i < m; i++)
+    for (int j = 0; j < k; j++) w0 += (uint64_t)wt[c[i * k + j]];
+  for (int round = 0; round < 8; round++) {
+    int changed = 0;
+    for (int j = 0; j < k; j++) {
+      uint32_t best = 0;
+      long bw = -1;
+      for (uint32_t s = 1; s < q; s++) {
+        long sum = 0;
+        for (int i = 0; i < m; i++) sum += wt[gf_mul(&f, gf_mul(&f, a[i], s), c[i * k + j])];
+        if (bw < 0 || sum < bw) {
+          bw = sum;
+          best = s;
+        }
+      }
+      if (best != b[j]) changed = 1;
+      b[j] = best;
+    }
+    for (int i = 0; i < m; i++) {
+      uint32_t best = 0;
+      long bw = -1;
+      for (uint32_t s = 1; s < q; s++) {
+        long sum = 0;
+        for (int j = 0; j < k; j++) sum += wt[gf_mul(&f, gf_mul(&f, s, b[j]), c[i * k + j])];
+        if (bw < 0 || sum < bw) {
+          bw = sum;
+          best = s;
+        }
+      }
+      if (best != a[i]) changed = 1;
+      a[i] = best;
+    }
+    if (!changed) break;
+  }
+  uint64_t w1 = 0;
+  for (int r = 0; r < k; r++)
+    for (int cc = 0; cc < k; cc++) G[r * k + cc] = (r == cc);
+  for (int i = 0; i < m; i++)
+    for (int j = 0; j < k; j++) {
+      uint32_t v = gf_mul(&f, gf_mul(&f, a[i], b[j]), c[i * k + j]);
+      G[(k + i) * k + j] = v;
+      w1 += (uint64_t)wt[v];
+    }
+  if (weights) {
+    weights[0] = w0;
+    weights[1] = w1;
+  }
+  free(wt);
+  free(c);
+  gf_free(&f);
+  return 0;
+}

@@ -358,6 +358,74 @@ int pyrit_plan_encode_masks(pyrit_plan_t p, uint16_t* masks_out) {
   return PYRIT_OK;
 }
 
+int pyrit_generator_weighted(int w, int n, int k, int m, uint32_t* G_out, uint64_t* weights_out) {
+  if (!G_out || k < 1 || k > kMaxIn || m < 0 || m > kMaxOut) return PYRIT_E_INVALID_ARG;
+  if (n != w + 1 || !aop_field_supported(w, n)) return PYRIT_E_UNSUPPORTED_FIELD;
+  if ((uint64_t)k + (uint64_t)m > (1ull << w)) return PYRIT_E_TOO_LONG;
+  const uint32_t q = 1u << w;
+  // weight of phi_S(u): an AOP element has the two representatives u and u + p (p = all n ones),
+  // so the sparse one has min(ones, n - ones) ones
+  std::vector<int> wt(q);
+  for (uint32_t u = 0; u < q; ++u) {
+    const int ones = __builtin_popcount(u);
+    wt[u] = ones < n - ones ? ones : n - ones;
+  }
+  std::vector<uint32_t> c((size_t)m * k);
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < k; ++j) c[(size_t)i * k + j] = gf_inv(w, (uint32_t)(k + i) ^ (uint32_t)j);
+  std::vector<uint32_t> a(m, 1u), b(k, 1u);
+  auto entry = [&](int i, int j, uint32_t ai, uint32_t bj) { return gf_mul(w, gf_mul(w, ai, bj), c[(size_t)i * k + j]); };
+  uint64_t before = 0;
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < k; ++j) before += (uint64_t)wt[c[(size_t)i * k + j]];
+  for (int round = 0; round < 8; ++round) {
+    bool changed = false;
+    for (int j = 0; j < k; ++j) {  // column scalings, then row scalings; smallest element on ties
+      uint32_t best = 0;
+      long bw = -1;
+      for (uint32_t sc = 1; sc < q; ++sc) {
+        long sum = 0;
+        for (int i = 0; i < m; ++i) sum += wt[entry(i, j, a[i], sc)];
+        if (bw < 0 || sum < bw) {
+          bw = sum;
+          best = sc;
+        }
+      }
+      changed = changed || best != b[j];
+      b[j] = best;
+    }
+    for (int i = 0; i < m; ++i) {
+      uint32_t best = 0;
+      long bw = -1;
+      for (uint32_t sc = 1; sc < q; ++sc) {
+        long sum = 0;
+        for (int j = 0; j < k; ++j) sum += wt[entry(i, j, sc, b[j])];
+        if (bw < 0 || sum < bw) {
+          bw = sum;
+          best = sc;
+        }
+      }
+      changed = changed || best != a[i];
+      a[i] = best;
+    }
+    if (!changed) break;
+  }
+  uint64_t after = 0;
+  for (int r = 0; r < k; ++r)
+    for (int cc = 0; cc < k; ++cc) G_out[r * k + cc] = r == cc ? 1u : 0u;
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < k; ++j) {
+      const uint32_t v = entry(i, j, a[i], b[j]);
+      G_out[(k + i) * k + j] = v;
+      after += (uint64_t)wt[v];
+    }
+  if (weights_out) {
+    weights_out[0] = before;
+    weights_out[1] = after;
+  }
+  return PYRIT_OK;
+}
+
 int pyrit_plan_syndrome_masks(pyrit_plan_t p, uint64_t erasures, uint16_t* syn_out, int* ne_out) {
   if (!p || !syn_out) return PYRIT_E_INVALID_ARG;
   DecodeEntry e;

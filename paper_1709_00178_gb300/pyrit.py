@@ -58,6 +58,7 @@ _SIGS = {
     "pyrit_plan_encode_masks": (_i, [_vp, _vp]),
     "pyrit_plan_decode_masks": (_i, [_vp, _u64, _vp, _vp, _vp, _vp]),
     "pyrit_plan_syndrome_masks": (_i, [_vp, _u64, _vp, _vp]),
+    "pyrit_generator_weighted": (_i, [_i, _i, _i, _i, _vp, _vp]),
     "pyrit_sparse_transform": (_u32, [_i, _i, _u32]),
     "pyrit_gf_mul": (_u32, [_i, _u32, _u32]),
     "pyrit_encode": (_i, [_vp, _vp, _vp, _sz, _vp]),
@@ -177,6 +178,14 @@ def pyrit_plan_syndrome_masks(plan, erasures):
     _check(_lib.pyrit_plan_syndrome_masks(plan, erasures, _np_ptr(syn), ctypes.byref(ne)),
            "pyrit_plan_syndrome_masks")
     return syn, ne.value
+
+
+def pyrit_generator_weighted(w, n, k, m):
+    """(G, (weight_default, weight_optimised)): a weight-optimised generalized Cauchy generator."""
+    G = np.zeros((k + m, k), np.uint32)
+    wts = np.zeros(2, np.uint64)
+    _check(_lib.pyrit_generator_weighted(w, n, k, m, _np_ptr(G), _np_ptr(wts)), "pyrit_generator_weighted")
+    return G, (int(wts[0]), int(wts[1]))
 
 
 def pyrit_sparse_transform(w, n, u):

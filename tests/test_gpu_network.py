@@ -36,12 +36,13 @@ def jit_mode(pyrit):
 class Stripes:
     """`count` stripes of one code in one device buffer, data filled from the synthetic stream."""
 
-    def __init__(self, pyrit, w, k, m, P, count, seed):
+    def __init__(self, pyrit, w, k, m, P, count, seed, weighted=False):
         self.w, self.k, self.m, self.P, self.count = w, k, m, P, count
         self.stride = ((k + m) * w * P + 255) // 256 * 256
         self.buf = torch.zeros(count * self.stride, dtype=torch.uint8, device="cuda")
-        self.plan = pyrit.pyrit_plan_create(w, w + 1, k, m)
-        self.G = oracle.cauchy(w, k, m)
+        # the oracle's own generator; the library plan is built from the same matrix
+        self.G = oracle.cauchy_weighted(w, k, m)[0] if weighted else oracle.cauchy(w, k, m)
+        self.plan = pyrit.pyrit_plan_create(w, w + 1, k, m, self.G if weighted else None)
         self.data = [synth_bytes(seed + s, 0, k * w * P).reshape(k, w, P) for s in range(count)]
         for s in range(count):
             self.view(s)[:k * w * P].copy_(torch.from_numpy(self.data[s].reshape(-1)).cuda())
@@ -338,5 +339,17 @@ def test_single_decode_uses_the_syndrome_network(pyrit, jit_mode):
             pyrit.pyrit_decode(st.plan, st.blocks(0), pat, st.P)
             assert pyrit.pyrit_jit_stats()["hits"] > before
             np.testing.assert_array_equal(st.host(0), full, err_msg="pattern %#x" % pat)
+    finally:
+        pyrit.pyrit_plan_destroy(st.plan)
+
+
+@pytest.mark.parametrize("w,k,m,P,count", [(10, 10, 4, 8192 + 16, 6), (12, 16, 4, 4096 + 32, 4), (4, 12, 4, 2048, 4)])
+def test_weighted_generator_encode_and_decode(pyrit, jit_mode, w, k, m, P, count):
+    """The weight-optimised generalized Cauchy generator through the direct and syndrome networks."""
+    st = Stripes(pyrit, w, k, m, P, count, 0x3E1 + w * 100 + k, weighted=True)
+    try:
+        _encode_batch_matches(pyrit, st)
+        rng = np.random.default_rng(0x3E2 + k)
+        _decode_batch_matches(pyrit, st, _random_patterns(rng, count, k, m))
     finally:
         pyrit.pyrit_plan_destroy(st.plan)
