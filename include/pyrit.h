@@ -67,6 +67,8 @@ typedef struct CUstream_st* pyrit_stream_t;
                                          fixed scratch holds                                     */
 #define PYRIT_E_JIT -12               /* run-time compilation or loading of a plan-specialised
                                          network failed (pyrit_jit_log has the compiler's log)  */
+#define PYRIT_E_UNSUPPORTED -13       /* the request needs a path this build does not provide for
+                                         it (the parity transform outside generated networks)   */
 
 /* Limits of this build. */
 #define PYRIT_MAX_K 32 /* data blocks per stripe                   */
@@ -111,6 +113,22 @@ PYRIT_API void pyrit_plan_destroy(pyrit_plan_t plan);
  * rounds). weights_out[2] (may be NULL): total weight of the default and of the returned parity
  * part. Host only; deterministic. Errors: as pyrit_plan_create for (w, n, k, m). */
 PYRIT_API int pyrit_generator_weighted(int w, int n, int k, int m, uint32_t* G_out, uint64_t* weights_out);
+
+/* Field-to-ring transform of a plan (Sec. 2.3.1-2.3.2). EMBEDDING (the default): phi_E pads each
+ * block with a zero packet and phi_E^{-1} reduces mod p; the code is the field code. PARITY:
+ * phi_P pads each source block with its parity packet and phi_P^{-1} drops the top packet; encoder
+ * and decoder must both use it, and the code is the field code conjugated symbol by symbol by
+ * psi(d) = d + par(d)(1 + x + ... + x^{w-1}). AUTO: the paper's rule, parity when k < m. The
+ * parity transform runs only on generated networks (pyrit_jit_mode must not be OFF): batches whose
+ * parity-transform stripes cannot use one (mixed tables of several plans, an unaligned stripe),
+ * the server and pyrit_code_stripes_noalloc return PYRIT_E_UNSUPPORTED for them. */
+#define PYRIT_TRANSFORM_EMBEDDING 0
+#define PYRIT_TRANSFORM_PARITY 1
+#define PYRIT_TRANSFORM_AUTO 2
+
+/* Sets the plan's transform (before it codes anything: a plan must not change code mid-stream).
+ * Returns the transform now in force (AUTO resolved) or PYRIT_E_INVALID_ARG. */
+PYRIT_API int pyrit_plan_set_transform(pyrit_plan_t plan, int transform);
 
 /* Plan parameters (any pointer may be NULL). */
 PYRIT_API int pyrit_plan_info(pyrit_plan_t plan, int* w, int* n, int* k, int* m);
@@ -308,10 +326,10 @@ PYRIT_API int pyrit_jit_log(char* buf, int cap);
 
 /* The CUDA C++ source generated for a mask table (masks[o*nin + j] = phi_S mask of output o,
  * source j, as in pyrit_plan_encode_masks) over R_{2,n}, under the default shape or tile's
- * overrides. Copies it NUL-terminated (truncated to cap - 1) into buf and returns its length, or
+ * overrides, for the embedding or the parity transform (PYRIT_TRANSFORM_*). Copies it NUL-terminated (truncated to cap - 1) into buf and returns its length, or
  * PYRIT_E_INVALID_ARG. For inspection and tests; host only. */
-PYRIT_API int pyrit_jit_source(int n, int nin, int nout, const uint16_t* masks, const pyrit_tile_t* tile, char* buf,
-                     int cap);
+PYRIT_API int pyrit_jit_source(int n, int nin, int nout, const uint16_t* masks, const pyrit_tile_t* tile,
+                               int transform, char* buf, int cap);
 
 /* ---- served coding: continuous batching ---------------------------------------------------- */
 

@@ -38,6 +38,8 @@ def lib():
             "oracle_gf_mul": (u32, [i32, u32, u32]),
             "oracle_cauchy": (i32, [i32, i32, i32, vp]),
             "oracle_cauchy_weighted": (i32, [i32, i32, i32, vp, vp]),
+            "oracle_encode_pt": (i32, [i32, i32, i32, vp, vp, sz, i32]),
+            "oracle_decode_pt": (i32, [i32, i32, i32, vp, vp, u64, sz, i32]),
             "oracle_gf_invert": (i32, [i32, i32, vp, vp]),
             "oracle_encode": (i32, [i32, i32, i32, vp, vp, vp, sz, i32]),
             "oracle_decode": (i32, [i32, i32, i32, vp, vp, u64, sz, i32]),
@@ -172,6 +174,30 @@ def decode(w, k, m, G, blocks, erased, nthreads=1):
     rc = lib().oracle_decode(w, k, m, _p(G), _p(out), erased, P, nthreads)
     if rc:
         raise ValueError("oracle_decode -> %d" % rc)
+    return out.reshape(k + m, w, P)
+
+
+def encode_pt(w, k, m, G, data, nthreads=1):
+    """Parity-transform encoding (Sec. 2.3.1). data: uint8 (k, w, P). Returns the parity (m, w, P)."""
+    G = _u32(G)
+    data = np.ascontiguousarray(data, dtype=np.uint8)
+    P = data.size // (k * w)
+    blocks = np.zeros((k + m, w, P), np.uint8)
+    blocks[:k] = data.reshape(k, w, P)
+    rc = lib().oracle_encode_pt(w, k, m, _p(G), _p(blocks), P, nthreads)
+    if rc:
+        raise ValueError("oracle_encode_pt -> %d" % rc)
+    return blocks[k:].copy()
+
+
+def decode_pt(w, k, m, G, blocks, erased, nthreads=1):
+    """Parity-transform decoding: blocks (k+m, w, P); erased blocks are rebuilt in a returned copy."""
+    G = _u32(G)
+    out = np.array(blocks, dtype=np.uint8, copy=True, order="C")
+    P = out.size // ((k + m) * w)
+    rc = lib().oracle_decode_pt(w, k, m, _p(G), _p(out), erased, P, nthreads)
+    if rc:
+        raise ValueError("oracle_decode_pt -> %d" % rc)
     return out.reshape(k + m, w, P)
 
 

@@ -605,3 +605,118 @@ int oracle_cauchy_weighted(int w, int k, int m, uint32_t* G, uint64_t* weights) 
   gf_free(&f);
   return 0;
 }
+
+/* ------------------------------------------------------------------------------------------ */
+/* The parity transform (Sec. 2.3.1), written literally in the ring                            */
+/* ------------------------------------------------------------------------------------------ */
+
+/* phi_P(b) = b + par(b) x^w: the field element padded with its parity bit, an even-weight ring
+ * element (an element of the ideal A_1). phi_P^{-1} drops the coefficient of x^w. */
+static uint32_t phi_P(int w, uint32_t b) { return b | ((uint32_t)(popcount32(b) & 1) << w); }
+static uint32_t phi_P_inv(int w, uint32_t r) { return r & ((1u << w) - 1); }
+
+typedef struct {
+  int w, k, nout;
+  const uint32_t* R;     /* nout x k ring masks (phi_S of the coefficients) */
+  const int* src;        /* block index of source s */
+  const int* dst;        /* block index of output o */
+  uint8_t* blocks;       /* all blocks, contiguous */
+  size_t P, t0, t1;
+} pt_job_t;
+
+/* out_o = phi_P^{-1}( sum_s R[o][s] * phi_P(y_s) ) in R_{2,w+1}, symbol lane by symbol lane. */
+static void* pt_run(void* arg) {
+  pt_job_t* J = (pt_job_t*)arg;
+  const int w = J->w, n = w + 1;
+  size_t blk = (size_t)w * J->P;
+  uint32_t y[ORACLE_MAX_K];
+  for (size_t t = J->t0; t < J->t1; t++)
+    for (int b = 0; b < 8; b++) {
+      for (int s = 0; s < J->k; s++) y[s] = phi_P(w, gather_symbol(J->blocks + (size_t)J->src[s] * blk, w, J->P, t, b));
+      for (int o = 0; o < J->nout; o++) {
+        uint32_t acc = 0;
+        for (int s = 0; s < J->k; s++) acc ^= oracle_ring_mul(n, J->R[o * J->k + s], y[s]);
+        scatter_symbol(J->blocks + (size_t)J->dst[o] * blk, w, J->P, t, b, phi_P_inv(w, acc));
+      }
+    }
+  return NULL;
+}
+
+static void pt_code(int w, int k, int nout, const uint32_t* R, const int* src, const int* dst, uint8_t* blocks,
+                    size_t P, int nthreads) {
+  if (nthreads < 1) nthreads = 1;
+  if ((size_t)nthreads > P) nthreads = (int)P;
+  if (nthreads > 256) nthreads = 256;
+  pt_job_t jobs[256];
+  for (int i = 0; i < nthreads; i++)
+    jobs[i] = (pt_job_t){w, k, nout, R, src, dst, blocks, P, P * (size_t)i / (size_t)nthreads,
+                         P * (size_t)(i + 1) / (size_t)nthreads};
+  run_threads(pt_run, jobs, sizeof(pt_job_t), nthreads);
+}
+
+/* Encoding with the parity transform (both encoder and decoder must use it, Sec. 2.3.1).
+ * blocks: k+m blocks of w*P bytes, contiguous; the m parity blocks are written.
+ * Returns 0, -1 unsupported field, -3 bad sizes. */
+int oracle_encode_pt(int w, int k, int m, const uint32_t* G, uint8_t* blocks, size_t P, int nthreads) {
+  if (k < 1 || k > ORACLE_MAX_K || m < 0 || m > 64 || P == 0) return -3;
+  if (!oracle_aop_irreducible(w)) return -1;
+  const int n = w + 1;
+  uint32_t* R = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(m > 0 ? m : 1) * (size_t)k);
+  int src[ORACLE_MAX_K], dst[64];
+  for (int i = 0; i < m; i++)
+    for (int j = 0; j < k; j++) R[i * k + j] = oracle_sparse_rep(w, n, G[(k + i) * k + j]);
+  for (int j = 0; j < k; j++) src[j] = j;
+  for (int i = 0; i < m; i++) dst[i] = k + i;
+  pt_code(w, k, m, R, src, dst, blocks, P, nthreads);
+  free(R);
+  return 0;
+}
+
+/* Decoding with the parity transform: the erased blocks (bit e of `erased`) are rebuilt from the
+ * first k survivors with the pattern's decoding matrix (erased data e: row e of the survivors'
+ * inverse; erased parity e: G[e] times it), each coefficient through phi_S as in encoding.
+ * Returns 0, -1 unsupported field, -3 bad sizes, -4 too many erasures, -5 singular. */
+int oracle_decode_pt(int w, int k, int m, const uint32_t* G, uint8_t* blocks, uint64_t erased, size_t P,
+                     int nthreads) {
+  if (k < 1 || k > ORACLE_MAX_K || m < 0 || k + m > 64 || P == 0) return -3;
+  if ((erased >> (k + m)) != 0 && k + m < 64) return -3;
+  int ne = 0, er[64], surv[ORACLE_MAX_K], ns = 0;
+  for (int e = 0; e < k + m; e++) {
+    if ((erased >> e) & 1)
+      er[ne++] = e;
+    else if (ns < k)
+      surv[ns++] = e;
+  }
+  if (ne > m) return -4;
+  if (ne == 0) return 0;
+  gf_t f;
+  if (gf_init(&f, w)) {
+    gf_free(&f);
+    return -1;
+  }
+  const int n = w + 1;
+  uint32_t* Gs = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)k * (size_t)k);
+  uint32_t* Inv = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)k * (size_t)k);
+  uint32_t* R = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)ne * (size_t)k);
+  for (int s = 0; s < k; s++)
+    for (int c = 0; c < k; c++) Gs[s * k + c] = G[surv[s] * k + c];
+  int rc = gf_invert(&f, k, Gs, Inv) == 0 ? 0 : -5;
+  if (rc == 0) {
+    for (int r = 0; r < ne; r++)
+      for (int s = 0; s < k; s++) {
+        uint32_t v = 0;
+        if (er[r] < k) {
+          v = Inv[er[r] * k + s];
+        } else {
+          for (int j = 0; j < k; j++) v ^= gf_mul(&f, G[er[r] * k + j], Inv[j * k + s]);
+        }
+        R[r * k + s] = oracle_sparse_rep(w, n, v);
+      }
+    pt_code(w, k, ne, R, surv, er, blocks, P, nthreads);
+  }
+  free(Gs);
+  free(Inv);
+  free(R);
+  gf_free(&f);
+  return rc;
+}

@@ -27,11 +27,12 @@ struct Group {
   JobDesc job0{};        // host copy of the group's first job (its mask table)
   const pyrit_plan_s* syn_plan = nullptr;  // all jobs decode this plan: its syndrome network applies
   size_t syn_off = 0;                      // the syndrome-form jobs in the device allocation
+  int transform = PYRIT_TRANSFORM_EMBEDDING;  // the group's stripes all use this transform
 };
 
 // The group's device job array for a variant (syndrome networks take syndrome-form jobs).
 const JobDesc* group_jobs(const uint8_t* dev, const Group& g, const Variant* v) {
-  return reinterpret_cast<const JobDesc*>(dev + (v && v->mode == 1 ? g.syn_off : g.jobs_off));
+  return reinterpret_cast<const JobDesc*>(dev + (v && syndrome_mode(v->mode) ? g.syn_off : g.jobs_off));
 }
 
 // Tiling of a group's jobs under a shape: with one P for all jobs, tile t covers job
@@ -116,9 +117,10 @@ int pyrit_batch_create(const pyrit_stripe_t* stripes, int count, const pyrit_til
   if (!b) return PYRIT_E_OOM;
   cudaGetDevice(&b->device);
 
-  // Jobs per ring size, in stripe order (with the stripe each came from).
-  std::vector<std::vector<JobDesc>> by_n(16);
-  std::vector<std::vector<int>> src_of(16);
+  // Jobs per (ring size, transform), in stripe order (with the stripe each came from): slot n for
+  // the embedding transform, 16 + n for the parity transform.
+  std::vector<std::vector<JobDesc>> by_n(32);
+  std::vector<std::vector<int>> src_of(32);
   for (int i = 0; i < count; ++i) {
     JobDesc job;
     uint64_t alg = 0, src = 0;
@@ -131,9 +133,13 @@ int pyrit_batch_create(const pyrit_stripe_t* stripes, int count, const pyrit_til
     if (job.nout == 0) continue;
     b->alg_bytes += alg;
     const int n = stripes[i].plan->n;
+    const bool parity = stripes[i].plan->transform == PYRIT_TRANSFORM_PARITY;
     if (job_is_staged(job)) {
-      by_n[n].push_back(job);
-      src_of[n].push_back(i);
+      by_n[n + (parity ? 16 : 0)].push_back(job);
+      src_of[n + (parity ? 16 : 0)].push_back(i);
+    } else if (parity) {  // the plain-load kernel has no parity transform
+      delete b;
+      return PYRIT_E_UNSUPPORTED;
     } else
       b->plain.emplace_back(n, job);
   }
@@ -146,10 +152,13 @@ int pyrit_batch_create(const pyrit_stripe_t* stripes, int count, const pyrit_til
     std::memcpy(image.data() + off, src, bytes);
     return off;
   };
-  for (int n = 0; n < 16; ++n) {
-    std::vector<JobDesc>& jobs = by_n[n];
+  for (int slot = 0; slot < 32; ++slot) {
+    std::vector<JobDesc>& jobs = by_n[slot];
     if (jobs.empty()) continue;
+    const int n = slot & 15;
     Group g;
+    g.transform = slot >= 16 ? PYRIT_TRANSFORM_PARITY : PYRIT_TRANSFORM_EMBEDDING;
+    const bool parity = slot >= 16;
     int max_nout = 0;
     bool same_p = true, shared = true;
     for (const JobDesc& j : jobs) {
@@ -164,12 +173,12 @@ int pyrit_batch_create(const pyrit_stripe_t* stripes, int count, const pyrit_til
     g.netable = shared && same_io;
     g.job0 = jobs[0];
     // Syndrome decoding: every job decodes a stripe of one plan whose columns fit a job.
-    const pyrit_plan_s* plan0 = stripes[src_of[n][0]].plan;
+    const pyrit_plan_s* plan0 = stripes[src_of[slot][0]].plan;
     bool syn = plan0->k + plan0->m <= kMaxIn;
-    for (int si : src_of[n]) syn = syn && stripes[si].op == PYRIT_OP_DECODE && stripes[si].plan == plan0;
+    for (int si : src_of[slot]) syn = syn && stripes[si].op == PYRIT_OP_DECODE && stripes[si].plan == plan0;
     std::vector<JobDesc> syn_jobs;
     if (syn) {
-      for (int si : src_of[n]) {
+      for (int si : src_of[slot]) {
         DecodeEntry e;
         if (plan_decode_entry(stripes[si].plan, stripes[si].erasures, &e) != PYRIT_OK || !e.syn_ok) {
           syn = false;
@@ -185,13 +194,18 @@ int pyrit_batch_create(const pyrit_stripe_t* stripes, int count, const pyrit_til
     const Variant* v = nullptr;
     ShapeHint sh_hint = hint;
     TuneVal tv;
+    if (parity && (!jit_on || (!g.netable && !g.syn_plan) || (tile && hint.dispatch != PYRIT_DISPATCH_NETWORK))) {
+      // only a generated network codes under the parity transform
+      delete b;
+      return PYRIT_E_UNSUPPORTED;
+    }
     if (!tile && tune_lookup(g.key, &tv)) {
       sh_hint = ShapeHint();
       sh_hint.stages = tv.stages;
-      if (tv.dispatch != PYRIT_DISPATCH_NETWORK)
-        v = find_variant(n, tv.words, tv.dispatch, tv.mg, tv.minb, tv.nc);
-      else if (g.netable && jit_on)
-        v = net_variant(net_spec(n, jobs[0], tv.words, tv.mg, tv.minb, tv.nc), true);
+      if (tv.dispatch != PYRIT_DISPATCH_NETWORK) {
+        if (!parity) v = find_variant(n, tv.words, tv.dispatch, tv.mg, tv.minb, tv.nc);
+      } else if (g.netable && jit_on)
+        v = net_variant(net_spec(n, jobs[0], tv.words, tv.mg, tv.minb, tv.nc, g.transform), true);
       else if (g.syn_plan && jit_on)
         v = net_variant(net_spec_syndrome(g.syn_plan, tv.words, tv.minb, tv.nc), true);
     }
@@ -203,7 +217,7 @@ int pyrit_batch_create(const pyrit_stripe_t* stripes, int count, const pyrit_til
         return PYRIT_E_INVALID_ARG;
       }
       if (jit_on)
-        v = g.netable ? net_variant(net_spec(n, jobs[0], hint.words, hint.mg, hint.minb, hint.nc), true)
+        v = g.netable ? net_variant(net_spec(n, jobs[0], hint.words, hint.mg, hint.minb, hint.nc, g.transform), true)
                       : net_variant(net_spec_syndrome(g.syn_plan, hint.words, hint.minb, hint.nc), true);
       if (!v) {
         delete b;
@@ -212,11 +226,15 @@ int pyrit_batch_create(const pyrit_stripe_t* stripes, int count, const pyrit_til
     }
     if (!v && !tile && jit_on) {
       sh_hint = ShapeHint();
-      // a failure leaves the generic kernel
+      // a failure leaves the generic kernel (under the parity transform: an error)
       if (g.netable)
-        v = net_variant(net_spec(n, jobs[0], 0, 0, 0, 0), true);
+        v = net_variant(net_spec(n, jobs[0], 0, 0, 0, 0, g.transform), true);
       else if (g.syn_plan)
         v = net_variant(net_spec_syndrome(g.syn_plan, 0, 0, 0), true);
+    }
+    if (parity && !v) {
+      delete b;
+      return PYRIT_E_JIT;
     }
     if (v) {
       shape_for_variant(v, max_nout, sh_hint, &g.shape);
@@ -299,13 +317,15 @@ int pyrit_batch_tune(pyrit_batch_t b, pyrit_stream_t stream, int iters) {
   const Variant* all = variants(&nv);
   for (Group& g : b->groups) {
     std::vector<const Variant*> cands;
-    for (int i = 0; i < nv; ++i)
+    const bool parity = g.transform == PYRIT_TRANSFORM_PARITY;  // generated networks only
+    for (int i = 0; i < nv && !parity; ++i)
       if (all[i].n == g.key.n) cands.push_back(&all[i]);
     if (g.netable && jit_mode() != PYRIT_JIT_OFF) {
       // the network shapes, compiled side by side (host threads) before they are loaded and timed
       NetSpec specs[8];
       const int ns = net_candidate_shapes(g.key.n, g.job0.nout, specs, 8);
-      for (int i = 0; i < ns; ++i) specs[i] = net_spec(g.key.n, g.job0, specs[i].words, specs[i].mg, specs[i].minb, specs[i].nc);
+      for (int i = 0; i < ns; ++i)
+        specs[i] = net_spec(g.key.n, g.job0, specs[i].words, specs[i].mg, specs[i].minb, specs[i].nc, g.transform);
       std::vector<std::thread> th;
       for (int i = 0; i < ns; ++i) th.emplace_back([&specs, i] { net_compile(specs[i]); });
       for (auto& t : th) t.join();

@@ -9,20 +9,27 @@ namespace {
 
 // Codes one job: the staged kernel when P and every pointer allow 16-byte bulk copies, else the
 // plain-load kernel. The staged kernel is the generated network of the job's mask table when one
-// is compiled (a missing one is queued under PYRIT_JIT_ASYNC), else the generic one. The job
-// travels in the kernel's parameters: no coding state is allocated.
-int run_job(int n, const JobDesc& job, cudaStream_t stream) {
+// is compiled (a missing one is queued under PYRIT_JIT_ASYNC), else the generic one. Under the
+// parity transform only a generated network codes the job: it is compiled in the call if
+// missing, and anything else is PYRIT_E_UNSUPPORTED. The job travels in the kernel's parameters:
+// no coding state is allocated.
+int run_job(const pyrit_plan_s* plan, const JobDesc& job, cudaStream_t stream) {
   if (job.nout == 0) return PYRIT_OK;
+  const int n = plan->n;
+  const bool parity = plan->transform == PYRIT_TRANSFORM_PARITY;
   if (job_is_staged(job)) {
     TileShape sh;
-    const Variant* net = net_variant(net_spec(n, job, 0, 0, 0, 0), false);
+    const Variant* net = net_variant(net_spec(n, job, 0, 0, 0, 0, plan->transform), parity);
     if (net)
       shape_for_variant(net, job.nout, ShapeHint(), &sh);
+    else if (parity)
+      return PYRIT_E_UNSUPPORTED;
     else if (!choose_shape(n, job.nout, ShapeHint(), &sh))
       return PYRIT_E_UNSUPPORTED_FIELD;
     const uint32_t tpj = tiles_for(job.P, sh);
     return launch_staged(sh, &job, nullptr, nullptr, tpj, tpj, stream);
   }
+  if (parity) return PYRIT_E_UNSUPPORTED;
   return launch_plain(n, job, stream);
 }
 
@@ -39,7 +46,7 @@ int pyrit_encode(pyrit_plan_t plan, const void* const* data, void* const* parity
   if (plan->m == 0) return PYRIT_OK;
   JobDesc job;
   make_encode_job(plan, data, parity, P, &job);
-  return run_job(plan->n, job, reinterpret_cast<cudaStream_t>(stream));
+  return run_job(plan, job, reinterpret_cast<cudaStream_t>(stream));
 }
 
 int pyrit_decode(pyrit_plan_t plan, void* const* blocks, uint64_t erasures, size_t P, pyrit_stream_t stream) {
@@ -54,9 +61,11 @@ int pyrit_decode(pyrit_plan_t plan, void* const* blocks, uint64_t erasures, size
   JobDesc job;
   make_decode_job(plan, e, blocks, P, &job);
   const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  // The plan's syndrome-decode network serves every erasure pattern: used once compiled.
+  // The plan's syndrome-decode network serves every erasure pattern: used once compiled (compiled
+  // in the call under the parity transform, which has no generic kernel).
   if (e.syn_ok && job_is_staged(job)) {
-    if (const Variant* net = net_variant(net_spec_syndrome(plan, 0, 0, 0), false)) {
+    const bool block = plan->transform == PYRIT_TRANSFORM_PARITY;
+    if (const Variant* net = net_variant(net_spec_syndrome(plan, 0, 0, 0), block)) {
       JobDesc sj;
       make_syndrome_job(plan, e, blocks, P, &sj);
       TileShape sh;
@@ -65,7 +74,7 @@ int pyrit_decode(pyrit_plan_t plan, void* const* blocks, uint64_t erasures, size
       return launch_staged(sh, &sj, nullptr, nullptr, tpj, tpj, st);
     }
   }
-  return run_job(plan->n, job, st);
+  return run_job(plan, job, st);
 }
 
 int pyrit_device_status(int* code_out, int* where_out) {

@@ -96,9 +96,13 @@ std::string net_source(const NetSpec& s) {
   o += "#include \"ring_staged.cuh\"\n"
        "namespace pyrit {\n"
        "struct NetMac : ";
-  o += s.mode == 1 ? "SyndromeStore" : "DirectStore";
+  // modes: 0 direct / 1 syndrome under the embedding transform, 2 direct / 3 syndrome under the
+  // parity transform (each source enters the ring with its parity packet as packet W)
+  static const char* const kStore[4] = {"DirectStore", "SyndromeStore", "ParityStore", "SyndromePsiStore"};
+  const bool syndrome = s.mode == 1 || s.mode == 3, parity = s.mode >= 2;
+  o += kStore[s.mode];
   o += " {\n";
-  if (s.mode == 1) {
+  if (syndrome) {
     // syndrome decode: only the rows a tile's erasure pattern uses are accumulated
     o += "  __device__ __forceinline__ void tile(const JobDesc* J, int, int) { load_rows(J); }\n";
   } else {
@@ -107,10 +111,18 @@ std::string net_source(const NetSpec& s) {
   o += "  template <int N, int WORDS, int MG>\n"
        "  __device__ __forceinline__ void apply(uint32_t (&acc)[MG][N][WORDS], const uint32_t (&d)[N - 1][WORDS],\n"
        "                                        int j, int g, int) {\n";
+  if (parity) {
+    // phi_P: the source's parity packet, i.e. the XOR of its W packets
+    o += "    uint32_t dp[WORDS];\n#pragma unroll\n    for (int x = 0; x < WORDS; ++x) {\n      dp[x] = d[0][x];\n";
+    int q = 1;
+    for (; q + 1 < W; q += 2) put(o, "      dp[x] = xor3(dp[x], d[%ld][x], d[%ld][x]);\n", q, q + 1);
+    if (q < W) put(o, "      dp[x] ^= d[%ld][x];\n", q);
+    o += "    }\n";
+  }
   // Syndrome networks guard each parity row with one warp-uniform test of the tile's needed rows
   // (a switch on the needed-row set with one block per set measured no faster and compiled
   // several times longer).
-  const bool guard = s.mode == 1;
+  const bool guard = syndrome;
   put(o, "    switch (g * %ld + j) {\n", s.nin);
   for (int g = 0; g < groups; ++g) {
     for (int j = 0; j < s.nin; ++j) {
@@ -122,18 +134,28 @@ std::string net_source(const NetSpec& s) {
         const uint32_t r = s.mask[j][out];
         std::string lines;
         for (int t = 0; t < N; ++t) {
-          // accumulator t receives d[t - s] for every set bit s (the zero packet q = W drops out),
-          // two terms per three-input XOR
-          int qs[32], nq = 0;
+          // under the parity transform a direct network never builds the top accumulator
+          // (phi_P^{-1} drops it)
+          if (parity && !syndrome && t == W) continue;
+          // accumulator t receives packet t - s for every set bit s, two terms per three-input
+          // XOR; packet W is the zero packet of phi_E (dropped) or the parity packet of phi_P
+          std::vector<std::string> terms;
           for (int sh = 0; sh < N; ++sh) {
             if (!((r >> sh) & 1u)) continue;
             const int q = (t - sh + N) % N;
-            if (q != W) qs[nq++] = q;
+            if (q < W) {
+              char buf[32];
+              std::snprintf(buf, sizeof(buf), "d[%d][x]", q);
+              terms.push_back(buf);
+            } else if (parity) {
+              terms.push_back("dp[x]");
+            }
           }
-          for (int i = 0; i + 1 < nq; i += 2)
-            put(lines, "          acc[%ld][%ld][x] = xor3(acc[%ld][%ld][x], d[%ld][x], d[%ld][x]);\n", ii, t, ii, t, qs[i],
-                qs[i + 1]);
-          if (nq & 1) put(lines, "          acc[%ld][%ld][x] ^= d[%ld][x];\n", ii, t, qs[nq - 1]);
+          char acc[32];
+          std::snprintf(acc, sizeof(acc), "acc[%d][%d][x]", ii, t);
+          for (size_t i = 0; i + 1 < terms.size(); i += 2)
+            lines += std::string("          ") + acc + " = xor3(" + acc + ", " + terms[i] + ", " + terms[i + 1] + ");\n";
+          if (terms.size() & 1) lines += std::string("          ") + acc + " ^= " + terms.back() + ";\n";
         }
         if (lines.empty()) continue;
         if (guard) {
@@ -309,7 +331,7 @@ int shapes_for(int n, int nout, bool syndrome, NetSpec* out, int cap) {
   return count;
 }
 
-NetSpec net_spec(int n, const JobDesc& job, int words, int mg, int minb, int nc) {
+NetSpec net_spec(int n, const JobDesc& job, int words, int mg, int minb, int nc, int transform) {
   NetSpec s;
   std::memset(&s, 0, sizeof(s));
   NetSpec def[1];
@@ -325,6 +347,7 @@ NetSpec net_spec(int n, const JobDesc& job, int words, int mg, int minb, int nc)
   if (!s.mg) s.mg = job.nout;
   if (!s.minb) s.minb = 1;
   if (!s.nc) s.nc = 16;
+  s.mode = transform == PYRIT_TRANSFORM_PARITY ? 2 : 0;
   for (int j = 0; j < job.nin; ++j)
     for (int o = 0; o < job.nout; ++o) s.mask[j][o] = job.mask[j][o];
   return s;
@@ -336,7 +359,7 @@ NetSpec net_spec_syndrome(const pyrit_plan_s* p, int words, int minb, int nc) {
   NetSpec def[1];
   if (shapes_for(p->n, p->m, true, def, 1) == 1) s = def[0];
   s.n = p->n;
-  s.mode = 1;
+  s.mode = p->transform == PYRIT_TRANSFORM_PARITY ? 3 : 1;
   s.nin = p->k + p->m;
   s.nout = p->m;
   s.mg = p->m;
@@ -366,7 +389,8 @@ int net_syndrome_shapes(const pyrit_plan_s* p, NetSpec* out, int cap) {
 static bool spec_valid(const NetSpec& s) {
   const bool words_ok = s.words == 1 || s.words == 2 || s.words == 4;
   const bool nc_ok = s.nc >= 1 && s.nc <= 31;
-  if (s.mode != 0 && !(s.mode == 1 && s.mg == s.nout && s.nout <= kSyndromeBaseRow)) return false;
+  if (s.mode < 0 || s.mode > 3) return false;
+  if ((s.mode == 1 || s.mode == 3) && !(s.mg == s.nout && s.nout <= kSyndromeBaseRow)) return false;
   return (s.n == 3 || s.n == 5 || s.n == 11 || s.n == 13) && s.nin >= 1 && s.nin <= kMaxIn && s.nout >= 1 &&
          s.nout <= kMaxOut && words_ok && s.mg >= 1 && s.mg <= kMaxOut && s.minb >= 1 && s.minb <= 4 && nc_ok &&
          output_groups(s.mg, s.nout, s.nc) * s.mg >= s.nout && s.nc % output_groups(s.mg, s.nout, s.nc) == 0;
@@ -486,20 +510,23 @@ int pyrit_plan_specialise(pyrit_plan_t plan, int op, uint64_t erasures, const py
   } else {
     return PYRIT_E_INVALID_ARG;
   }
-  const NetSpec s = tile ? net_spec(plan->n, job, tile->words, tile->mg, tile->minb, tile->nc)
-                         : net_spec(plan->n, job, 0, 0, 0, 0);
+  const NetSpec s = tile ? net_spec(plan->n, job, tile->words, tile->mg, tile->minb, tile->nc, plan->transform)
+                         : net_spec(plan->n, job, 0, 0, 0, 0, plan->transform);
   return net_compile(s);
 }
 
-int pyrit_jit_source(int n, int nin, int nout, const uint16_t* masks, const pyrit_tile_t* tile, char* buf, int cap) {
+int pyrit_jit_source(int n, int nin, int nout, const uint16_t* masks, const pyrit_tile_t* tile, int transform,
+                     char* buf, int cap) {
   if (!masks || nin < 1 || nin > kMaxIn || nout < 1 || nout > kMaxOut) return PYRIT_E_INVALID_ARG;
+  if (transform != PYRIT_TRANSFORM_EMBEDDING && transform != PYRIT_TRANSFORM_PARITY) return PYRIT_E_INVALID_ARG;
   JobDesc job;
   std::memset(&job, 0, sizeof(job));
   job.nin = nin;
   job.nout = nout;
   for (int o = 0; o < nout; ++o)
     for (int j = 0; j < nin; ++j) job.mask[j][o] = masks[o * nin + j];
-  const NetSpec s = tile ? net_spec(n, job, tile->words, tile->mg, tile->minb, tile->nc) : net_spec(n, job, 0, 0, 0, 0);
+  const NetSpec s = tile ? net_spec(n, job, tile->words, tile->mg, tile->minb, tile->nc, transform)
+                         : net_spec(n, job, 0, 0, 0, 0, transform);
   if (!spec_valid(s)) return PYRIT_E_INVALID_ARG;
   const std::string src = net_source(s);
   if (buf && cap > 0) {

@@ -57,6 +57,8 @@ int stripe_job(const pyrit_stripe_t& s, JobDesc* job) {
   if (s.op != PYRIT_OP_ENCODE && s.op != PYRIT_OP_DECODE) return PYRIT_E_INVALID_ARG;
   for (int b = 0; b < p->k + p->m; ++b)
     if (!s.blocks[b]) return PYRIT_E_INVALID_ARG;
+  // the fixed kernels have no parity transform (it runs only on generated networks)
+  if (p->transform == PYRIT_TRANSFORM_PARITY) return PYRIT_E_UNSUPPORTED;
   if (s.op == PYRIT_OP_ENCODE) {
     make_encode_job(p, s.blocks, s.blocks + p->k, s.packet_bytes, job);
     return PYRIT_OK;

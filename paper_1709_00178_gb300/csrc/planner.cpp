@@ -291,6 +291,8 @@ const char* pyrit_strerror(int s) {
     case PYRIT_E_TIMEOUT: return "bounded wait timed out";
     case PYRIT_E_BUSY: return "queue full";
     case PYRIT_E_SCRATCH_LIMIT: return "request exceeds the fixed scratch of the no-allocation entry point";
+    case PYRIT_E_JIT: return "run-time compilation or loading of a generated network failed";
+    case PYRIT_E_UNSUPPORTED: return "the parity transform runs only on generated networks";
     default: return "unknown status";
   }
 }
@@ -336,6 +338,14 @@ int pyrit_plan_create(int w, int n, int k, int m, const uint32_t* G, pyrit_plan_
 }
 
 void pyrit_plan_destroy(pyrit_plan_t p) { delete p; }
+
+int pyrit_plan_set_transform(pyrit_plan_t p, int transform) {
+  if (!p) return PYRIT_E_INVALID_ARG;
+  if (transform == PYRIT_TRANSFORM_AUTO) transform = p->k < p->m ? PYRIT_TRANSFORM_PARITY : PYRIT_TRANSFORM_EMBEDDING;
+  if (transform != PYRIT_TRANSFORM_EMBEDDING && transform != PYRIT_TRANSFORM_PARITY) return PYRIT_E_INVALID_ARG;
+  p->transform = transform;
+  return transform;
+}
 
 int pyrit_plan_info(pyrit_plan_t p, int* w, int* n, int* k, int* m) {
   if (!p) return PYRIT_E_INVALID_ARG;

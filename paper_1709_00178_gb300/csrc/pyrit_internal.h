@@ -31,12 +31,15 @@ struct Variant {
                  // 3: a network generated for one mask table (PYRIT_DISPATCH_NETWORK)
   int nc;        // consumer warps per CTA (one more warp is the producer)
   const void* fn;
-  int mode;      // generated networks: 0 direct table, 1 syndrome decode (takes syndrome-form jobs)
+  int mode;      // generated networks: NetSpec mode (syndrome modes take syndrome-form jobs)
   int nout;      // generated networks: the output count they were compiled for (0: generic)
 };
 
 // Output groups of a launch: the smallest power of two g with g * mg >= nout (and g < nc); the
 // consumer warps split evenly into them. Generated networks are compiled for this same split.
+// Generated networks whose jobs are in syndrome form (modes 1 and 3).
+inline bool syndrome_mode(int mode) { return mode == 1 || mode == 3; }
+
 inline int output_groups(int mg, int nout, int nc) {
   int g = 1;
   while (g * mg < nout && g < nc) g *= 2;
@@ -86,6 +89,7 @@ struct DecodeEntry {
 
 struct pyrit_plan_s {
   int w, n, k, m;
+  int transform = PYRIT_TRANSFORM_EMBEDDING;
   std::vector<uint32_t> G;         // (k+m) x k
   std::vector<uint16_t> enc_mask;  // m x k
   std::mutex mu;
@@ -141,12 +145,15 @@ void tune_record(const TuneKey& k, const TuneVal& v);
 // cached per NetSpec; `mask` holds the table for j < nin, o < nout and zeros elsewhere.
 struct NetSpec {
   int32_t n, nin, nout, words, mg, minb, nc;
-  int32_t mode;  // 0: direct (the job's own table); 1: syndrome decode of a plan (table [C | I])
+  int32_t mode;  // 0 / 2: direct (the job's own table), 1 / 3: syndrome decode of a plan (table
+                 // [C | I]); 0 and 1 under the embedding transform, 2 and 3 under the parity one
   uint16_t mask[kMaxIn][kMaxOut];
 };
-// The network spec of a job under a shape (zero fields: the default shape for (n, nout)).
-NetSpec net_spec(int n, const JobDesc& job, int words, int mg, int minb, int nc);
-// The syndrome-decode network spec of a plan (requires k + m <= kMaxIn; zero fields: default).
+// The network spec of a job under a shape (zero fields: the default shape for (n, nout)) and a
+// transform (PYRIT_TRANSFORM_EMBEDDING or _PARITY).
+NetSpec net_spec(int n, const JobDesc& job, int words, int mg, int minb, int nc, int transform);
+// The syndrome-decode network spec of a plan, under its transform (requires k + m <= kMaxIn;
+// zero fields: default).
 NetSpec net_spec_syndrome(const pyrit_plan_s* p, int words, int minb, int nc);
 // Candidate shapes of a plan's syndrome network, the default first.
 int net_syndrome_shapes(const pyrit_plan_s* p, NetSpec* out, int cap);

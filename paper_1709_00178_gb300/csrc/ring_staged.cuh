@@ -147,7 +147,12 @@ struct DirectStore {
 // mask[kSyndromeBaseRow][o] is 1 + the row whose partial sum is added (0: none). Rows are first
 // reduced in place (phi_E^{-1}), products are formed in the ring with the reduced rows embedded
 // (phi_E), and each output is reduced once more before its store.
-struct SyndromeStore {
+// PSI: the jobs code under the parity transform (Sec. 2.3.1). The first phase's rows then reduce
+// to field values in the psi domain (psi(d) = phi_P(d) mod p = d + par(d) (1 + ... + x^{W-1})), the
+// second phase is the same linear algebra there, and each output finally goes through psi^{-1} =
+// psi (an involution for even W): its parity is XORed into every packet.
+template <bool PSI>
+struct SyndromeStoreT {
   static constexpr bool kSparse = true;  // erased columns and unused parity are absent sources
   uint32_t need;                         // rows the pattern uses (read once per tile)
 
@@ -200,13 +205,50 @@ struct SyndromeStore {
       }
       if (valid) {
         uint8_t* dst = J->out[o] + col0 + off;
+        uint32_t par[WORDS];
+#pragma unroll
+        for (int x = 0; x < WORDS; ++x) par[x] = 0u;
+        if constexpr (PSI) {
+#pragma unroll
+          for (int t = 0; t < W; ++t)
+#pragma unroll
+            for (int x = 0; x < WORDS; ++x) par[x] ^= res[t][x] ^ res[W][x];
+        }
 #pragma unroll
         for (int t = 0; t < W; ++t) {
           uint32_t o4[WORDS];
 #pragma unroll
-          for (int x = 0; x < WORDS; ++x) o4[x] = res[t][x] ^ res[W][x];
+          for (int x = 0; x < WORDS; ++x) o4[x] = res[t][x] ^ res[W][x] ^ par[x];
           *reinterpret_cast<V*>(dst + (size_t)t * P) = vmake<WORDS>(o4);
         }
+      }
+    }
+  }
+};
+using SyndromeStore = SyndromeStoreT<false>;
+using SyndromePsiStore = SyndromeStoreT<true>;
+
+// phi_P^{-1} and the stores of a direct job under the parity transform (Sec. 2.3.1): every source
+// entered the ring padded with its parity packet, so each ring result lies in the ideal A_1 and
+// its field packets are its first W coefficients (the top one is dropped, never computed).
+struct ParityStore {
+  static constexpr bool kSparse = false;
+
+  template <int N, int WORDS, int MG>
+  __device__ __forceinline__ void store(uint32_t (&acc)[MG][N][WORDS], const JobDesc* J, int g, uint32_t col0,
+                                        uint32_t off, bool valid) {
+    constexpr int W = N - 1;
+    using V = typename Vec<WORDS>::T;
+    if (!valid) return;
+    const uint64_t P = J->P;
+    const int nout = J->nout;
+#pragma unroll
+    for (int i = 0; i < MG; ++i) {
+      const int o = g * MG + i;
+      if (o < nout) {
+        uint8_t* dst = J->out[o] + col0 + off;
+#pragma unroll
+        for (int r = 0; r < W; ++r) *reinterpret_cast<V*>(dst + (size_t)r * P) = vmake<WORDS>(acc[i][r]);
       }
     }
   }

@@ -153,7 +153,7 @@ int slot_shape(pyrit_server_s* s, int n, int max_nout, TileShape* out) {
 // the background compiler if it is missing.
 const Variant* request_network(const Pending& p) {
   if (p.job.nout == 0 || jit_mode() == PYRIT_JIT_OFF) return nullptr;
-  if (p.op == PYRIT_OP_ENCODE) return net_variant(net_spec(p.n, p.job, 0, 0, 0, 0), false);
+  if (p.op == PYRIT_OP_ENCODE) return net_variant(net_spec(p.n, p.job, 0, 0, 0, 0, PYRIT_TRANSFORM_EMBEDDING), false);
   if (p.syn) return net_variant(net_spec_syndrome(p.plan, 0, 0, 0), false);
   return nullptr;
 }
@@ -231,7 +231,7 @@ int launch_slot(pyrit_server_s* s, Slot& sl) {
   for (const Variant* v : net)
     if (v && std::find(used.begin(), used.end(), v) == used.end()) used.push_back(v);
   for (const Variant* v : used) {
-    const int rc = add_group(network_shape(s, v), [&](size_t i) { return net[i] == v; }, v->mode == 1);
+    const int rc = add_group(network_shape(s, v), [&](size_t i) { return net[i] == v; }, syndrome_mode(v->mode));
     if (rc != PYRIT_OK) return rc;
   }
   // the generic kernel per ring size for the rest
@@ -360,6 +360,8 @@ int pyrit_server_submit(pyrit_server_t s, const pyrit_request_t* reqs, int count
     uint64_t alg = 0, src = 0;
     const int rc = stripe_job(reqs[i].stripe, &p.job, &alg, &src);
     if (rc != PYRIT_OK) return rc;
+    // requests wait for no compilation, and only a generated network has the parity transform
+    if (reqs[i].stripe.plan->transform == PYRIT_TRANSFORM_PARITY) return PYRIT_E_UNSUPPORTED;
     p.n = reqs[i].stripe.plan->n;
     p.plan = reqs[i].stripe.plan;
     p.op = reqs[i].stripe.op;

@@ -35,6 +35,7 @@ PYRIT_E_TIMEOUT = -9
 PYRIT_E_BUSY = -10
 PYRIT_E_SCRATCH_LIMIT = -11
 PYRIT_E_JIT = -12
+PYRIT_E_UNSUPPORTED = -13
 PYRIT_DISPATCH_NETWORK = 3
 PYRIT_JIT_OFF = 0
 PYRIT_JIT_SYNC = 1
@@ -46,6 +47,9 @@ PYRIT_MAX_M = 8
 PYRIT_OP_ENCODE = 0
 PYRIT_OP_DECODE = 1
 PYRIT_OP_DECODE_ANY = 2
+PYRIT_TRANSFORM_EMBEDDING = 0
+PYRIT_TRANSFORM_PARITY = 1
+PYRIT_TRANSFORM_AUTO = 2
 
 _i, _u32, _u64, _sz, _vp = ctypes.c_int, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_size_t, ctypes.c_void_p
 
@@ -54,6 +58,7 @@ _SIGS = {
     "pyrit_plan_create": (_i, [_i, _i, _i, _i, _vp, ctypes.POINTER(_vp)]),
     "pyrit_plan_destroy": (None, [_vp]),
     "pyrit_plan_info": (_i, [_vp, _vp, _vp, _vp, _vp]),
+    "pyrit_plan_set_transform": (_i, [_vp, _i]),
     "pyrit_plan_generator": (_i, [_vp, _vp]),
     "pyrit_plan_encode_masks": (_i, [_vp, _vp]),
     "pyrit_plan_decode_masks": (_i, [_vp, _u64, _vp, _vp, _vp, _vp]),
@@ -178,6 +183,11 @@ def pyrit_plan_syndrome_masks(plan, erasures):
     _check(_lib.pyrit_plan_syndrome_masks(plan, erasures, _np_ptr(syn), ctypes.byref(ne)),
            "pyrit_plan_syndrome_masks")
     return syn, ne.value
+
+
+def pyrit_plan_set_transform(plan, transform):
+    """Sets the plan's transform (PYRIT_TRANSFORM_*); returns the one in force (AUTO resolved)."""
+    return _check(_lib.pyrit_plan_set_transform(plan, transform), "pyrit_plan_set_transform")
 
 
 def pyrit_generator_weighted(w, n, k, m):
@@ -323,7 +333,7 @@ _JIT_SIGS = {
     "pyrit_jit_quiesce": (_i, [_i]),
     "pyrit_jit_stats": (_i, [_vp]),
     "pyrit_jit_log": (_i, [ctypes.c_char_p, _i]),
-    "pyrit_jit_source": (_i, [_i, _i, _i, _vp, ctypes.POINTER(pyrit_tile_t), ctypes.c_char_p, _i]),
+    "pyrit_jit_source": (_i, [_i, _i, _i, _vp, ctypes.POINTER(pyrit_tile_t), _i, ctypes.c_char_p, _i]),
 }
 _bind(_JIT_SIGS)
 EXPORTS = EXPORTS + tuple(_JIT_SIGS)
@@ -376,16 +386,16 @@ def pyrit_jit_log():
     return buf.value.decode(errors="replace")
 
 
-def pyrit_jit_source(n, masks, tile=None):
+def pyrit_jit_source(n, masks, tile=None, transform=PYRIT_TRANSFORM_EMBEDDING):
     """Generated CUDA source for a mask table (2-D array, masks[o][j] = phi_S mask of output o,
-    source j) over R_{2,n}."""
+    source j) over R_{2,n}, for the embedding or the parity transform."""
     m = np.ascontiguousarray(np.asarray(masks, dtype=np.uint16))
     nout, nin = m.shape
     t = _tile(tile)
-    size = _check(_lib.pyrit_jit_source(n, nin, nout, _np_ptr(m), ctypes.byref(t) if t is not None else None, None, 0),
-                  "pyrit_jit_source")
+    tp = ctypes.byref(t) if t is not None else None
+    size = _check(_lib.pyrit_jit_source(n, nin, nout, _np_ptr(m), tp, transform, None, 0), "pyrit_jit_source")
     buf = ctypes.create_string_buffer(size + 1)
-    _lib.pyrit_jit_source(n, nin, nout, _np_ptr(m), ctypes.byref(t) if t is not None else None, buf, size + 1)
+    _lib.pyrit_jit_source(n, nin, nout, _np_ptr(m), tp, transform, buf, size + 1)
     return buf.value.decode()
 
 

@@ -36,7 +36,9 @@ def _parse(src):
             a = b
         if a:
             assert cur is not None
-            qs = [int(q) for q in re.findall(r"d\[(\d+)\]\[x\]", a.groups()[-1])]
+            # d[q][x] is packet q of the source; dp[x] (the parity transform's padding packet, the
+            # XOR of the source's packets) is recorded as q = -1
+            qs = [int(q) if q else -1 for q in re.findall(r"d(?:\[(\d+)\]|p)\[x\]", a.groups()[-1])]
             cases[cur].append((int(a.group(1)), int(a.group(2)), qs))
         if "} break;" in line:
             cur = None
@@ -230,5 +232,109 @@ def test_syndrome_tables_rebuild_every_erasure_pattern(w, k, m):
                         assert r in U, "only syndrome rows carry coefficients"
                         v ^= oracle.gf_mul_slow(w, _field_of_mask(w, int(syn[r][o])), acc[r])
                 assert v == block[b], (pat, b)
+    finally:
+        pyrit.pyrit_plan_destroy(plan)
+
+
+def _psi(w, d):
+    """phi_P(d) mod p (Sec. 2.3.1): every coefficient of d flipped by its parity bit."""
+    return d ^ ((1 << w) - 1 if bin(d).count("1") & 1 else 0)
+
+
+def _parity_columns(entries, ii, n, w):
+    """Ring rows of output slot ii for each basis source x^q under the parity transform: the
+    source's padding packet (its parity) is 1 for every basis vector."""
+    cols = []
+    for q in range(w):
+        acc = 0
+        for (i, t, qs) in entries:
+            if i != ii:
+                continue
+            assert t < w, "the parity transform drops the top ring row: it must not be accumulated"
+            for qq in qs:
+                assert -1 <= qq < w
+                if qq == q or qq == -1:
+                    acc ^= 1 << t
+        cols.append(acc)
+    return cols
+
+
+@pytest.mark.parametrize("w,k,m", [(10, 10, 4), (12, 16, 4), (4, 8, 8), (2, 1, 2), (10, 32, 8)])
+def test_generated_parity_network_is_the_conjugated_field_product(w, k, m):
+    """Under the parity transform the network of mask r maps a source d to the low w coefficients
+    of r * phi_P(d) in R_{2,n} (phi_P pads d with its parity bit, phi_P^{-1} drops the top one);
+    that is psi(u * psi(d)) for the field coefficient u, psi(d) = phi_P(d) mod p."""
+    n = w + 1
+    C, masks = _oracle_parity_masks(w, k, m)
+    net = _parse(pyrit.pyrit_jit_source(n, masks, None, pyrit.PYRIT_TRANSFORM_PARITY))
+    assert net["n"] == n and net["nin"] == k
+    seen = set()
+    for case, entries in net["cases"].items():
+        g, j = divmod(case, k)
+        for ii in range(net["mg"]):
+            o = g * net["mg"] + ii
+            if o >= m:
+                assert not [e for e in entries if e[0] == ii]
+                continue
+            seen.add((j, o))
+            for q, col in enumerate(_parity_columns(entries, ii, n, w)):
+                ring = oracle.ring_mul(n, int(masks[o][j]), (1 << q) | (1 << w)) & ((1 << w) - 1)
+                assert col == ring, (case, ii, q)
+                assert col == _psi(w, oracle.gf_mul_slow(w, int(C[o][j]), _psi(w, 1 << q)))
+    assert seen == {(j, o) for j in range(k) for o in range(m)}
+
+
+@pytest.mark.parametrize("n", [3, 5, 11, 13])
+def test_generated_parity_network_random_masks(n):
+    rng = np.random.default_rng(2000 + n)
+    w = n - 1
+    for trial in range(4):
+        nin = int(rng.integers(1, 33))
+        nout = int(rng.integers(1, 9))
+        masks = rng.integers(0, 1 << n, size=(nout, nin)).astype(np.uint16)
+        masks[-1][-1] = (1 << n) - 1
+        tile = [None, {"mg": 0, "nc": 16}, {"words": 2, "nc": 8}, None][trial]
+        net = _parse(pyrit.pyrit_jit_source(n, masks, tile, pyrit.PYRIT_TRANSFORM_PARITY))
+        for case, entries in net["cases"].items():
+            g, j = divmod(case, nin)
+            for ii in range(net["mg"]):
+                o = g * net["mg"] + ii
+                if o >= nout:
+                    continue
+                for q, col in enumerate(_parity_columns(entries, ii, n, w)):
+                    assert col == oracle.ring_mul(n, int(masks[o][j]), (1 << q) | (1 << w)) & ((1 << w) - 1)
+
+
+def test_plan_transform_setting():
+    plan = pyrit.pyrit_plan_create(10, 11, 10, 4)
+    try:
+        assert pyrit.pyrit_plan_set_transform(plan, pyrit.PYRIT_TRANSFORM_PARITY) == pyrit.PYRIT_TRANSFORM_PARITY
+        assert pyrit.pyrit_plan_set_transform(plan, pyrit.PYRIT_TRANSFORM_EMBEDDING) == pyrit.PYRIT_TRANSFORM_EMBEDDING
+        # AUTO: the parity transform when k < m (Sec. 2.3.1), else the embedding
+        assert pyrit.pyrit_plan_set_transform(plan, pyrit.PYRIT_TRANSFORM_AUTO) == pyrit.PYRIT_TRANSFORM_EMBEDDING
+        with pytest.raises(pyrit.PyritError) as ei:
+            pyrit.pyrit_plan_set_transform(plan, 5)
+        assert ei.value.status == pyrit.PYRIT_E_INVALID_ARG
+    finally:
+        pyrit.pyrit_plan_destroy(plan)
+    plan = pyrit.pyrit_plan_create(4, 5, 2, 6)
+    try:
+        assert pyrit.pyrit_plan_set_transform(plan, pyrit.PYRIT_TRANSFORM_AUTO) == pyrit.PYRIT_TRANSFORM_PARITY
+    finally:
+        pyrit.pyrit_plan_destroy(plan)
+    with pytest.raises(pyrit.PyritError):
+        pyrit.pyrit_jit_source(11, np.ones((2, 2), np.uint16), None, 3)
+
+
+def test_runtime_compiler_builds_parity_networks_without_a_device():
+    plan = pyrit.pyrit_plan_create(10, 11, 10, 4)
+    try:
+        pyrit.pyrit_plan_set_transform(plan, pyrit.PYRIT_TRANSFORM_PARITY)
+        before = pyrit.pyrit_jit_stats()
+        pyrit.pyrit_plan_specialise(plan)
+        pyrit.pyrit_plan_specialise(plan, pyrit.PYRIT_OP_DECODE, 0b1001)
+        pyrit.pyrit_plan_specialise(plan, pyrit.PYRIT_OP_DECODE_ANY)
+        after = pyrit.pyrit_jit_stats()
+        assert after["failed"] == before["failed"], pyrit.pyrit_jit_log()
     finally:
         pyrit.pyrit_plan_destroy(plan)
