@@ -77,18 +77,30 @@ def kernel_name(shape):
     """Name of the kernel a batch group launches, as ncu lists it."""
     if shape["dispatch"] == 3:
         return "ring_staged_net (%s network, words %d, %d consumer warps)" % (
-            "syndrome-decode" if shape["mode"] == 1 else "direct", shape["words"], shape["nc"])
+            ("syndrome-decode" if shape["mode"] in (1, 3) else "direct") +
+            (", parity transform" if shape["mode"] in (2, 3) else ""), shape["words"], shape["nc"])
     return "ring_staged_kernel<%d, %d, %d, %d, %d, %d>" % (shape["n"], shape["words"], shape["mg"], shape["minb"],
                                                           shape["dispatch"], shape["nc"])
 
 
-def make_plan(pyrit, generator, w, k, m):
+def make_plan(pyrit, generator, w, k, m, transform="embedding"):
     """The library plan of a code: the plain Cauchy generator, or the weight-optimised generalized
-    Cauchy one (the oracle legs compute their own copy; a CPU test pins the two equal)."""
+    Cauchy one (the oracle legs compute their own copy; a CPU test pins the two equal), under the
+    embedding or the parity transform (Sec. 2.3)."""
     if generator == "weighted":
         G, _ = pyrit.pyrit_generator_weighted(w, w + 1, k, m)
-        return pyrit.pyrit_plan_create(w, w + 1, k, m, G)
-    return pyrit.pyrit_plan_create(w, w + 1, k, m)
+        plan = pyrit.pyrit_plan_create(w, w + 1, k, m, G)
+    else:
+        plan = pyrit.pyrit_plan_create(w, w + 1, k, m)
+    if transform == "parity":
+        pyrit.pyrit_plan_set_transform(plan, pyrit.PYRIT_TRANSFORM_PARITY)
+    return plan
+
+
+def oracle_codec(transform):
+    """The oracle's (encode, decode) pair for a transform."""
+    import oracle
+    return (oracle.encode_pt, oracle.decode_pt) if transform == "parity" else (oracle.encode, oracle.decode)
 
 
 def rank_shard(rank, stripe_bytes, stripes):
@@ -190,11 +202,13 @@ def run_reference(args):
     # the same bytes as the GPU arm's first stripes: data blocks are contiguous in the stream
     data = [synth_bytes(BASE_SEED + 1, s * K * blk, K * blk).reshape(K, W, P) for s in range(sample)]
 
+    o_enc, o_dec = oracle_codec(args.transform)
+
     def step():
         for s in range(sample):
-            par = oracle.encode(W, K, M, G, data[s], nthreads=cores)
+            par = o_enc(W, K, M, G, data[s], nthreads=cores)
             full = np.concatenate([data[s], par])
-            oracle.decode(W, K, M, G, full, pats[s], nthreads=cores)
+            o_dec(W, K, M, G, full, pats[s], nthreads=cores)
 
     for _ in range(args.warmup):
         step()
@@ -222,14 +236,18 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--stripes", type=int, default=STRIPES,
                     help="stripes per GPU (default 256; smaller values make profiling cases)")
-    ap.add_argument("--workload", default="coding", choices=["coding", "sweep", "mixed", "served", "gf16"],
+    ap.add_argument("--workload", default="coding", choices=["coding", "sweep", "mixed", "served", "gf16", "transforms"],
                     help="coding: the default line; sweep: GF(2^12) k=16 m=4 packet sweep 4 KiB-1 MiB; mixed: "
                          "4096 uneven stripes batched vs per-stripe launches; served: Poisson arrivals; gf16: "
-                         "GF(16) k=4 m=2, one stripe, encode + every erasure pattern (L2-resident)")
+                         "GF(16) k=4 m=2, one stripe, encode + every erasure pattern (L2-resident); transforms: "
+                         "embedding vs parity transform on k >= m and k < m codes")
     ap.add_argument("--seconds", type=float, default=10.0, help="served: arrival window")
     ap.add_argument("--generator", default="cauchy", choices=["cauchy", "weighted"],
                     help="cauchy: the plain Cauchy code of the configurations; weighted: the same code "
                          "family with weight-optimised row/column scalings (generalized Cauchy)")
+    ap.add_argument("--transform", default="embedding", choices=["embedding", "parity"],
+                    help="embedding: phi_E (the configurations' transform, k >= m); parity: phi_P, the "
+                         "parity-bit transform (Sec. 2.3.1), a different code of the same parameters")
     ap.add_argument("--no-tune", action="store_true",
                     help="skip the autotuner: time the automatic shapes (profiling cases of a fixed kernel)")
     args = ap.parse_args()
@@ -237,7 +255,8 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     if args.workload != "coding":
-        return {"sweep": run_sweep, "mixed": run_mixed, "served": run_served, "gf16": run_gf16}[args.workload](args)
+        return {"sweep": run_sweep, "mixed": run_mixed, "served": run_served, "gf16": run_gf16,
+                "transforms": run_transforms}[args.workload](args)
     if args.stripes != STRIPES:
         STRIPES = max(8, args.stripes // 8 * 8)
         CONFIG["stripes"] = STRIPES
@@ -272,8 +291,9 @@ def main():
     blocks = [[base + (s * K + j) * blk for j in range(K)] + [base + par0 + (s * M + i) * blk for i in range(M)]
               for s in range(STRIPES)]
     pats = patterns(pat_seed, STRIPES, K, M)
-    plan = make_plan(pyrit, args.generator, W, K, M)
+    plan = make_plan(pyrit, args.generator, W, K, M, args.transform)
     CONFIG["generator"] = "plain Cauchy" if args.generator == "cauchy" else "weight-optimised generalized Cauchy"
+    CONFIG["transform"] = "phi_E (embedding)" if args.transform == "embedding" else "phi_P (parity bit)"
     enc = pyrit.pyrit_batch_create([(plan, pyrit.PYRIT_OP_ENCODE, 0, P, blocks[s]) for s in range(STRIPES)])
     dec = pyrit.pyrit_batch_create([(plan, pyrit.PYRIT_OP_DECODE, pats[s], P, blocks[s]) for s in range(STRIPES)])
     es, ds = pyrit.pyrit_batch_stats(enc), pyrit.pyrit_batch_stats(dec)
@@ -414,7 +434,7 @@ def main():
     }
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(buf, blocks, pats, plan, pyrit, args.generator)
+        out["cpu_baseline"] = cpu_baseline(buf, blocks, pats, plan, pyrit, args.generator, args.transform)
     if rank == 0:
         print(json.dumps(out))
     for b in [enc, dec] + cenc + cdec:
@@ -424,7 +444,7 @@ def main():
         dist.destroy_process_group()
 
 
-def cpu_baseline(buf, blocks, pats, plan, pyrit, generator="cauchy"):
+def cpu_baseline(buf, blocks, pats, plan, pyrit, generator="cauchy", transform="embedding"):
     """The oracle, as it stands, on bounded samples of the same stripes and patterns: on all host
     cores (48 stripes, about 1 s of wall time there), and single-threaded (4 stripes); its parity
     is also compared with the GPU's for the sampled stripes."""
@@ -433,6 +453,7 @@ def cpu_baseline(buf, blocks, pats, plan, pyrit, generator="cauchy"):
     cores = os.cpu_count() or 1
     blk = W * P
     G = oracle.cauchy_weighted(W, K, M)[0] if generator == "weighted" else oracle.cauchy(W, K, M)
+    o_enc, o_dec = oracle_codec(transform)
     par0 = STRIPES * K * blk
 
     def timed(sample, nthreads):
@@ -441,9 +462,9 @@ def cpu_baseline(buf, blocks, pats, plan, pyrit, generator="cauchy"):
         t0 = time.perf_counter()
         match = True
         for s in range(sample):
-            par = oracle.encode(W, K, M, G, data[s], nthreads=nthreads)
+            par = o_enc(W, K, M, G, data[s], nthreads=nthreads)
             full = np.concatenate([data[s], par])
-            rebuilt = oracle.decode(W, K, M, G, full, pats[s], nthreads=nthreads)
+            rebuilt = o_dec(W, K, M, G, full, pats[s], nthreads=nthreads)
             match = match and np.array_equal(par, gpar[s]) and np.array_equal(rebuilt, full)
         dt = time.perf_counter() - t0
         return 2 * sample * K * blk / dt / 1e9, dt, match
@@ -524,6 +545,64 @@ def run_sweep(args):
         del buf
         torch.cuda.empty_cache()
     pyrit.pyrit_plan_destroy(plan)
+
+
+def run_transforms(args):
+    """The two transforms of Sec. 2.3 on the same codes: GF(2^10) (n=11) Cauchy k=10 m=4 (k >= m,
+    where the paper prefers the embedding) and k=4 m=8, GF(2^12) (n=13) k=2 m=6 (k < m, where it
+    prefers the parity bit); 64 KiB packets, stripes filling ~2 GiB of source; encode and
+    mixed-pattern (1..m erasures) decode batches, tuned, one JSON line per (code, transform). A
+    sampled stripe of each is checked against the oracle's codec for that transform."""
+    torch, pyrit, dev = _setup_gpu()
+    from paper_1709_00178_gb300.synth import BASE_SEED
+    import numpy as np
+    import oracle
+    peak, _ = peak_hbm()
+    stream = torch.cuda.Stream(device=dev)
+    P = 65536
+    for (w, k, m) in [(10, 10, 4), (10, 4, 8), (12, 2, 6)]:
+        blk = w * P
+        S = (2 << 30) // (k * blk)
+        buf = torch.empty(S * (k + m) * blk, dtype=torch.uint8, device=dev)
+        rng = np.random.default_rng(BASE_SEED + 3 + k)
+        pats = [sum(1 << int(x) for x in rng.choice(k + m, int(rng.integers(1, m + 1)), replace=False))
+                for _ in range(S)]
+        for transform in ("embedding", "parity"):
+            pyrit.pyrit_synth_fill(buf.data_ptr(), buf.numel(), BASE_SEED + 3, 0)
+            torch.cuda.synchronize()
+            base, par0 = buf.data_ptr(), S * k * blk
+            blocks = [[base + (s * k + j) * blk for j in range(k)] + [base + par0 + (s * m + i) * blk for i in range(m)]
+                      for s in range(S)]
+            plan = make_plan(pyrit, args.generator, w, k, m, transform)
+            enc = pyrit.pyrit_batch_create([(plan, 0, 0, P, blocks[s]) for s in range(S)])
+            dec = pyrit.pyrit_batch_create([(plan, 1, pats[s], P, blocks[s]) for s in range(S)])
+            pyrit.pyrit_batch_tune(enc, stream, 2)
+            pyrit.pyrit_batch_tune(dec, stream, 2)
+            te = _time_batch(torch, pyrit, enc, stream, args.steps)
+            td = _time_batch(torch, pyrit, dec, stream, args.steps)
+            # the last runs decoded the encoded stripes in place: stripe 0 must be the oracle's codeword
+            o_enc, _ = oracle_codec(transform)
+            G = oracle.cauchy_weighted(w, k, m)[0] if args.generator == "weighted" else oracle.cauchy(w, k, m)
+            torch.cuda.synchronize()
+            data0 = buf[:k * blk].cpu().numpy().reshape(k, w, P)
+            par_ok = bool(np.array_equal(buf[par0:par0 + m * blk].cpu().numpy().reshape(m, w, P),
+                                         o_enc(w, k, m, G, data0, nthreads=os.cpu_count() or 1)))
+            es, ds = pyrit.pyrit_batch_stats(enc), pyrit.pyrit_batch_stats(dec)
+            ae, ad = es["alg_bytes"] / te / 1e6, ds["alg_bytes"] / td / 1e6
+            print(json.dumps({
+                "metric": "encode+decode GB/s of source data", "workload": "transforms",
+                "value": (es["src_bytes"] + ds["src_bytes"]) / (te + td) / 1e6, "unit": "GB/s",
+                "config": {"workload": "GF(2^%d) n=%d Cauchy k=%d m=%d, 64 KiB packets, %d stripes, 1-%d erasures"
+                           % (w, w + 1, k, m, S, m), "transform": transform, "generator": args.generator},
+                "encode_ms": te, "decode_ms": td, "encode_roofline_frac": ae / peak, "decode_roofline_frac": ad / peak,
+                "encode_kernel": kernel_name(pyrit.pyrit_batch_shape(enc, 0)),
+                "decode_kernel": kernel_name(pyrit.pyrit_batch_shape(dec, 0)),
+                "oracle_parity_stripe0": par_ok, "dtype": "u8", "data": "synthetic"}), flush=True)
+            pyrit.pyrit_batch_destroy(enc)
+            pyrit.pyrit_batch_destroy(dec)
+            pyrit.pyrit_plan_destroy(plan)
+        del buf
+        torch.cuda.empty_cache()
 
 
 def run_gf16(args):

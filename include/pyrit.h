@@ -307,6 +307,15 @@ PYRIT_API int pyrit_jit_mode(int mode);
  * PYRIT_OK (also when there is nothing to code), a planning error, or PYRIT_E_JIT. */
 PYRIT_API int pyrit_plan_specialise(pyrit_plan_t plan, int op, uint64_t erasures, const pyrit_tile_t* tile);
 
+/* Resource use of the network pyrit_plan_specialise would compile for the same arguments (it is
+ * compiled first if missing; host only). info_out[9] (host): registers per thread, stack frame,
+ * spill stores and spill loads in bytes (from the assembler's report; -1 if it gave none), compile
+ * time in ms, then the network's words, mg, nc and mode (0 direct, 1 syndrome, 2 direct under the
+ * parity transform, 3 syndrome under the parity transform). PYRIT_E_INVALID_ARG when there is
+ * nothing to code, a planning error, or PYRIT_E_JIT. */
+PYRIT_API int pyrit_plan_network_info(pyrit_plan_t plan, int op, uint64_t erasures, const pyrit_tile_t* tile,
+                                      int* info_out);
+
 /* Waits up to timeout_ms for the background compiler to finish its queue: PYRIT_OK or
  * PYRIT_E_TIMEOUT. */
 PYRIT_API int pyrit_jit_wait(int timeout_ms);

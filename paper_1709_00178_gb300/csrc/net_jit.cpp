@@ -21,6 +21,7 @@
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -50,6 +51,7 @@ struct Entry {
   cudaLibrary_t lib = nullptr;
   bool loaded = false;
   Variant v{};
+  int res[5] = {-1, -1, -1, -1, 0};  // registers, stack frame, spill stores, spill loads (bytes), compile ms
 };
 
 struct Jit {
@@ -178,8 +180,25 @@ std::string net_source(const NetSpec& s) {
   return o;
 }
 
-// Compiles one spec into a cubin. Returns PYRIT_OK or PYRIT_E_JIT (log filled).
-int compile_spec(const NetSpec& s, std::vector<char>* cubin, std::string* log, uint64_t* us) {
+// The first integer after `key` in the assembler's resource report, or -1.
+int report_value(const std::string& log, const char* key, bool before) {
+  const size_t at = log.find(key);
+  if (at == std::string::npos) return -1;
+  if (before) {  // "<value> <key>"
+    size_t e = at;
+    while (e > 0 && log[e - 1] == ' ') --e;
+    size_t b = e;
+    while (b > 0 && log[b - 1] >= '0' && log[b - 1] <= '9') --b;
+    return b < e ? std::atoi(log.substr(b, e - b).c_str()) : -1;
+  }
+  size_t b = at + std::strlen(key);
+  while (b < log.size() && log[b] == ' ') ++b;
+  return b < log.size() && log[b] >= '0' && log[b] <= '9' ? std::atoi(log.c_str() + b) : -1;
+}
+
+// Compiles one spec into a cubin. Returns PYRIT_OK or PYRIT_E_JIT (log filled). The assembler's
+// resource report (registers, stack frame, spills) is parsed into res[0..3].
+int compile_spec(const NetSpec& s, std::vector<char>* cubin, std::string* log, uint64_t* us, int* res) {
   const auto t0 = std::chrono::steady_clock::now();
   const std::string src = net_source(s);
   nvrtcProgram prog;
@@ -188,12 +207,16 @@ int compile_spec(const NetSpec& s, std::vector<char>* cubin, std::string* log, u
     *log = "nvrtcCreateProgram failed";
     return PYRIT_E_JIT;
   }
-  const char* opts[] = {kArch, "-std=c++17", "-lineinfo"};
-  const nvrtcResult r = nvrtcCompileProgram(prog, 3, opts);
+  const char* opts[] = {kArch, "-std=c++17", "-lineinfo", "--ptxas-options=-v"};
+  const nvrtcResult r = nvrtcCompileProgram(prog, 4, opts);
   size_t ls = 0;
   nvrtcGetProgramLogSize(prog, &ls);
   log->assign(ls, '\0');
   if (ls) nvrtcGetProgramLog(prog, &(*log)[0]);
+  res[0] = report_value(*log, "Used", false);
+  res[1] = report_value(*log, "bytes stack frame", true);
+  res[2] = report_value(*log, "bytes spill stores", true);
+  res[3] = report_value(*log, "bytes spill loads", true);
   int rc = PYRIT_E_JIT;
   size_t cs = 0;
   if (r == NVRTC_SUCCESS && nvrtcGetCUBINSize(prog, &cs) == NVRTC_SUCCESS && cs > 0) {
@@ -227,8 +250,11 @@ void compile_here(Jit& J, Entry* e, std::unique_lock<std::mutex>& lk) {
   std::vector<char> cubin;
   std::string log;
   uint64_t us = 0;
-  const int rc = compile_spec(e->spec, &cubin, &log, &us);
+  int res[4];
+  const int rc = compile_spec(e->spec, &cubin, &log, &us, res);
   lk.lock();
+  for (int i = 0; i < 4; ++i) e->res[i] = res[i];
+  e->res[4] = (int)(us / 1000);
   finish(J, e, rc, cubin, log, us);
   --J.busy;
   J.cv.notify_all();
@@ -489,30 +515,65 @@ int pyrit_jit_log(char* buf, int cap) {
   return len;
 }
 
-int pyrit_plan_specialise(pyrit_plan_t plan, int op, uint64_t erasures, const pyrit_tile_t* tile) {
+}  // extern "C"
+
+namespace {
+
+// The network a plan's operation uses: *s filled and 1, 0 when there is nothing to code (no
+// parity rows, no erasure), or an error status.
+int plan_network_spec(pyrit_plan_s* plan, int op, uint64_t erasures, const pyrit_tile_t* tile, NetSpec* s) {
   if (!plan) return PYRIT_E_INVALID_ARG;
   std::vector<void*> none((size_t)(plan->k + plan->m), nullptr);  // only the masks are used
   JobDesc job;
   if (op == PYRIT_OP_ENCODE) {
-    if (plan->m == 0) return PYRIT_OK;
+    if (plan->m == 0) return 0;
     make_encode_job(plan, none.data(), none.data() + plan->k, 16, &job);
   } else if (op == PYRIT_OP_DECODE_ANY) {
-    if (plan->m == 0) return PYRIT_OK;
+    if (plan->m == 0) return 0;
     if (plan->k + plan->m > kMaxIn) return PYRIT_E_INVALID_ARG;
-    return net_compile(tile ? net_spec_syndrome(plan, tile->words, tile->minb, tile->nc)
-                            : net_spec_syndrome(plan, 0, 0, 0));
+    *s = tile ? net_spec_syndrome(plan, tile->words, tile->minb, tile->nc) : net_spec_syndrome(plan, 0, 0, 0);
+    return 1;
   } else if (op == PYRIT_OP_DECODE) {
     DecodeEntry e;
     const int rc = plan_decode_entry(plan, erasures, &e);
     if (rc != PYRIT_OK) return rc;
-    if (e.ne == 0) return PYRIT_OK;
+    if (e.ne == 0) return 0;
     make_decode_job(plan, e, none.data(), 16, &job);
   } else {
     return PYRIT_E_INVALID_ARG;
   }
-  const NetSpec s = tile ? net_spec(plan->n, job, tile->words, tile->mg, tile->minb, tile->nc, plan->transform)
-                         : net_spec(plan->n, job, 0, 0, 0, 0, plan->transform);
-  return net_compile(s);
+  *s = tile ? net_spec(plan->n, job, tile->words, tile->mg, tile->minb, tile->nc, plan->transform)
+            : net_spec(plan->n, job, 0, 0, 0, 0, plan->transform);
+  return 1;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pyrit_plan_specialise(pyrit_plan_t plan, int op, uint64_t erasures, const pyrit_tile_t* tile) {
+  NetSpec s;
+  const int rc = plan_network_spec(plan, op, erasures, tile, &s);
+  return rc == 1 ? net_compile(s) : rc;
+}
+
+int pyrit_plan_network_info(pyrit_plan_t plan, int op, uint64_t erasures, const pyrit_tile_t* tile, int* info_out) {
+  if (!info_out) return PYRIT_E_INVALID_ARG;
+  NetSpec s;
+  int rc = plan_network_spec(plan, op, erasures, tile, &s);
+  if (rc == 0) return PYRIT_E_INVALID_ARG;  // nothing to code: no network
+  if (rc < 0) return rc;
+  rc = net_compile(s);
+  if (rc != PYRIT_OK) return rc;
+  Jit& J = jit();
+  std::lock_guard<std::mutex> lk(J.mu);
+  auto it = J.cache.find(key_of(s));
+  if (it == J.cache.end()) return PYRIT_E_JIT;
+  const Entry& e = *it->second;
+  const int shape[4] = {s.words, s.mg, s.nc, s.mode};
+  std::memcpy(info_out, e.res, sizeof(e.res));
+  std::memcpy(info_out + 5, shape, sizeof(shape));
+  return PYRIT_OK;
 }
 
 int pyrit_jit_source(int n, int nin, int nout, const uint16_t* masks, const pyrit_tile_t* tile, int transform,

@@ -329,6 +329,7 @@ def pyrit_tune_clear():
 _JIT_SIGS = {
     "pyrit_jit_mode": (_i, [_i]),
     "pyrit_plan_specialise": (_i, [_vp, _i, _u64, ctypes.POINTER(pyrit_tile_t)]),
+    "pyrit_plan_network_info": (_i, [_vp, _i, _u64, ctypes.POINTER(pyrit_tile_t), _vp]),
     "pyrit_jit_wait": (_i, [_i]),
     "pyrit_jit_quiesce": (_i, [_i]),
     "pyrit_jit_stats": (_i, [_vp]),
@@ -355,6 +356,17 @@ def pyrit_plan_specialise(plan, op=PYRIT_OP_ENCODE, erasures=0, tile=None):
     t = _tile(tile)
     return _check(_lib.pyrit_plan_specialise(plan, op, erasures, ctypes.byref(t) if t is not None else None),
                   "pyrit_plan_specialise")
+
+
+def pyrit_plan_network_info(plan, op=PYRIT_OP_ENCODE, erasures=0, tile=None):
+    """Resource use of a plan's generated network (compiled if missing): dict of registers,
+    stack_bytes, spill_store_bytes, spill_load_bytes, compile_ms, words, mg, nc, mode."""
+    t = _tile(tile)
+    info = np.zeros(9, np.int32)
+    _check(_lib.pyrit_plan_network_info(plan, op, erasures, ctypes.byref(t) if t is not None else None,
+                                        _np_ptr(info)), "pyrit_plan_network_info")
+    keys = ("registers", "stack_bytes", "spill_store_bytes", "spill_load_bytes", "compile_ms", "words", "mg", "nc", "mode")
+    return {k: int(v) for k, v in zip(keys, info)}
 
 
 def pyrit_jit_wait(timeout_ms=60000):

@@ -338,3 +338,23 @@ def test_runtime_compiler_builds_parity_networks_without_a_device():
         assert after["failed"] == before["failed"], pyrit.pyrit_jit_log()
     finally:
         pyrit.pyrit_plan_destroy(plan)
+
+
+def test_network_resource_report():
+    """The run-time compiler's resource report for a plan's networks: registers within the
+    hardware limit of the launch shape (65536 registers per SM shared by four schedulers, so at
+    most 16384 / (32 * ceil(warps / 4)) per thread), shape fields echo the spec."""
+    plan = pyrit.pyrit_plan_create(10, 11, 10, 4)
+    try:
+        for op in (pyrit.PYRIT_OP_ENCODE, pyrit.PYRIT_OP_DECODE_ANY):
+            info = pyrit.pyrit_plan_network_info(plan, op)
+            warps = info["nc"] + 1
+            assert 0 < info["registers"] <= 16384 // (32 * -(-warps // 4))
+            assert info["spill_store_bytes"] >= 0 and info["stack_bytes"] >= 0
+            assert info["mode"] == (0 if op == pyrit.PYRIT_OP_ENCODE else 1)
+        info = pyrit.pyrit_plan_network_info(plan, pyrit.PYRIT_OP_ENCODE, tile={"words": 1, "nc": 16})
+        assert (info["words"], info["nc"]) == (1, 16)
+        with pytest.raises(pyrit.PyritError):
+            pyrit.pyrit_plan_network_info(plan, pyrit.PYRIT_OP_DECODE, 0)  # nothing erased: no network
+    finally:
+        pyrit.pyrit_plan_destroy(plan)
