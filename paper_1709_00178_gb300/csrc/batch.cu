@@ -60,6 +60,24 @@ int make_tiling(const Group& g, const TileShape& sh, uint2** tiles_dev, uint32_t
   return PYRIT_OK;
 }
 
+// Compiles network candidates side by side (host threads), loads them and appends them to the
+// tuner's candidates, leaving out shapes whose registers spilled (more than 64 bytes of spill
+// stores) unless every one did.
+void add_networks(const NetSpec* specs, int ns, std::vector<const Variant*>* cands) {
+  std::vector<std::thread> th;
+  for (int i = 0; i < ns; ++i) th.emplace_back([specs, i] { net_compile(specs[i]); });
+  for (auto& t : th) t.join();
+  std::vector<const Variant*> lean, all;
+  for (int i = 0; i < ns; ++i) {
+    const Variant* v = net_variant(specs[i], true);
+    if (!v) continue;
+    all.push_back(v);
+    if (net_spill_bytes(specs[i]) <= 64) lean.push_back(v);
+  }
+  const std::vector<const Variant*>& use = lean.empty() ? all : lean;
+  cands->insert(cands->end(), use.begin(), use.end());
+}
+
 int log2_floor(uint64_t v) {
   int r = -1;
   while (v) {
@@ -326,19 +344,11 @@ int pyrit_batch_tune(pyrit_batch_t b, pyrit_stream_t stream, int iters) {
       const int ns = net_candidate_shapes(g.key.n, g.job0.nout, specs, 8);
       for (int i = 0; i < ns; ++i)
         specs[i] = net_spec(g.key.n, g.job0, specs[i].words, specs[i].mg, specs[i].minb, specs[i].nc, g.transform);
-      std::vector<std::thread> th;
-      for (int i = 0; i < ns; ++i) th.emplace_back([&specs, i] { net_compile(specs[i]); });
-      for (auto& t : th) t.join();
-      for (int i = 0; i < ns; ++i)
-        if (const Variant* v = net_variant(specs[i], true)) cands.push_back(v);
+      add_networks(specs, ns, &cands);
     } else if (g.syn_plan && jit_mode() != PYRIT_JIT_OFF) {
       NetSpec specs[8];
       const int ns = net_syndrome_shapes(g.syn_plan, specs, 8);
-      std::vector<std::thread> th;
-      for (int i = 0; i < ns; ++i) th.emplace_back([&specs, i] { net_compile(specs[i]); });
-      for (auto& t : th) t.join();
-      for (int i = 0; i < ns; ++i)
-        if (const Variant* v = net_variant(specs[i], true)) cands.push_back(v);
+      add_networks(specs, ns, &cands);
     }
     float best = 1e30f;
     TileShape best_shape = g.shape;

@@ -167,6 +167,8 @@ int jit_mode();
 const Variant* net_variant(const NetSpec& s, bool block);
 // Compiles a spec into the cache (host only, no device call). PYRIT_OK or PYRIT_E_JIT.
 int net_compile(const NetSpec& s);
+// Spill stores (bytes) the assembler reported for a compiled network; -1 if not compiled or unknown.
+int net_spill_bytes(const NetSpec& s);
 
 // Fills shape->grid (SMs x occupancy) if it is 0; makes the one-time per-device attribute calls.
 void resolve_grid(TileShape* shape);
