@@ -31,6 +31,11 @@ def lib():
             "oracle_poly_mul": (u64, [u64, u64]),
             "oracle_aop": (u64, [i32]),
             "oracle_aop_irreducible": (i32, [i32]),
+            "oracle_poly_irreducible": (i32, [u64]),
+            "oracle_esp": (u64, [i32, i32]),
+            "oracle_field_poly": (u64, [i32]),
+            "oracle_ring_size": (i32, [i32]),
+            "oracle_phi_P": (u32, [i32, i32, u32]),
             "oracle_gf_mul_slow": (u32, [i32, u32, u32]),
             "oracle_gf_order": (u32, [i32, u32]),
             "oracle_gf_primitive": (u32, [i32]),
@@ -84,6 +89,30 @@ def aop(w):
 
 def aop_irreducible(w):
     return bool(lib().oracle_aop_irreducible(w))
+
+
+def poly_irreducible(p):
+    return bool(lib().oracle_poly_irreducible(p))
+
+
+def esp(s, r):
+    """The s-equally spaced polynomial of degree s r: 1 + x^s + ... + x^{rs} (Sec. 2.4)."""
+    return int(lib().oracle_esp(s, r))
+
+
+def field_poly(w):
+    """The modulus of GF(2^w): the AOP if irreducible, else the irreducible ESP (0: none)."""
+    return int(lib().oracle_field_poly(w))
+
+
+def ring_size(w):
+    """n of the ring R_{2,n} carrying GF(2^w) (w + 1 for an AOP, 9 for GF(2^6)); 0 if none."""
+    return int(lib().oracle_ring_size(w))
+
+
+def phi_P(w, n, b):
+    """The parity transform of a field element (Sec. 2.3.1, Sec. 2.4.1)."""
+    return int(lib().oracle_phi_P(w, n, b))
 
 
 def gf_mul_slow(w, a, b):

@@ -3,7 +3,9 @@
  *
  * A plain, slow and deliberately literal CPU implementation of what the coding path computes:
  * systematic MDS erasure encoding and decoding over GF(2^w) = F2[x]/(p(x)), p the all-one
- * polynomial (AOP) of degree w, with log/antilog tables and a Cauchy generator matrix.
+ * polynomial (AOP) of degree w when that is irreducible (Sec. 2.3), else an irreducible equally
+ * spaced polynomial (ESP) of degree w (Sec. 2.4: GF(2^6) from x^6 + x^3 + 1), with log/antilog
+ * tables and a Cauchy generator matrix.
  * It also holds a small reference for the ring R_{2,n} = F2[x]/(x^n+1) that the tests use to
  * check the paper's algebraic claims.
  *
@@ -62,25 +64,75 @@ uint64_t oracle_poly_mul(uint64_t a, uint64_t b) {
 /* The all-one polynomial of degree w: 1 + x + ... + x^w (Sec. 2.3). */
 uint64_t oracle_aop(int w) { return (((uint64_t)1) << (w + 1)) - 1; }
 
-/* Irreducibility of the AOP of degree w, by trial division by every polynomial of degree
- * 1..w/2 (the definition of irreducible, not the paper's number-theoretic criterion, so
- * that the tests can check that criterion against it). Returns 1 if irreducible. */
-int oracle_aop_irreducible(int w) {
+/* Irreducibility of p (degree 1..30), by trial division by every polynomial of degree
+ * 1..deg(p)/2: the definition of irreducible, not the paper's number-theoretic criteria, so that
+ * the tests can check those criteria against it. Returns 1 if irreducible. */
+int oracle_poly_irreducible(uint64_t p) {
+  const int w = poly_deg(p);
   if (w < 1 || w > 30) return 0;
-  uint64_t p = oracle_aop(w);
   for (int d = 1; d <= w / 2; d++)
     for (uint64_t f = (uint64_t)1 << d; f < ((uint64_t)1 << (d + 1)); f++)
       if (oracle_poly_mod(p, f) == 0) return 0;
   return 1;
 }
 
+/* Irreducibility of the AOP of degree w. Returns 1 if irreducible. */
+int oracle_aop_irreducible(int w) { return w >= 1 && w <= 30 && oracle_poly_irreducible(oracle_aop(w)); }
+
+/* The s-equally spaced polynomial of degree s r (Sec. 2.4, its definition): p(x^s) for the AOP p
+ * of degree r, i.e. 1 + x^s + x^{2s} + ... + x^{rs}. s = 1 gives the AOP itself. */
+uint64_t oracle_esp(int s, int r) {
+  uint64_t g = 0;
+  for (int i = 0; i <= r; i++) g |= (uint64_t)1 << (s * i);
+  return g;
+}
+
+/* The modulus of GF(2^w) in this codec: the AOP of degree w when irreducible, else the
+ * irreducible ESP p(x^s) of degree w = s r with the smallest s > 1, else 0 (no such field). The
+ * ring that carries it is R_{2,n}, n = s (r + 1), since x^{s(r+1)} + 1 = g(x) (x^s + 1). */
+static int field_spacing_search(int w) {
+  if (w < 2 || w > ORACLE_MAX_W) return 0;
+  if (oracle_aop_irreducible(w)) return 1;
+  for (int s = 2; s <= w / 2; s++)
+    if (w % s == 0 && oracle_poly_irreducible(oracle_esp(s, w / s))) return s;
+  return 0;
+}
+
+/* The search above, once per w (the field product calls it for every multiplication). */
+static pthread_mutex_t spacing_mu = PTHREAD_MUTEX_INITIALIZER;
+static int spacing_of[ORACLE_MAX_W + 1];
+static int spacing_known[ORACLE_MAX_W + 1];
+
+static int field_spacing(int w) {
+  if (w < 2 || w > ORACLE_MAX_W) return 0;
+  pthread_mutex_lock(&spacing_mu);
+  if (!spacing_known[w]) {
+    spacing_of[w] = field_spacing_search(w);
+    spacing_known[w] = 1;
+  }
+  const int s = spacing_of[w];
+  pthread_mutex_unlock(&spacing_mu);
+  return s;
+}
+
+uint64_t oracle_field_poly(int w) {
+  const int s = field_spacing(w);
+  return s ? oracle_esp(s, w / s) : 0;
+}
+
+/* n of the ring R_{2,n} the field GF(2^w) is embedded in (0 if the field is not supported). */
+int oracle_ring_size(int w) {
+  const int s = field_spacing(w);
+  return s ? s * (w / s + 1) : 0;
+}
+
 /* ------------------------------------------------------------------------------------------ */
-/* The field GF(2^w) = F2[x]/(AOP) (Sec. 2.1, Sec. 2.3)                                        */
+/* The field GF(2^w) = F2[x]/(AOP or ESP) (Sec. 2.1, Sec. 2.3, Sec. 2.4)                       */
 /* ------------------------------------------------------------------------------------------ */
 
-/* Field product by the definition: carry-less product, then remainder mod the AOP. */
+/* Field product by the definition: carry-less product, then remainder mod the field's modulus. */
 uint32_t oracle_gf_mul_slow(int w, uint32_t a, uint32_t b) {
-  return (uint32_t)oracle_poly_mod(oracle_poly_mul(a, b), oracle_aop(w));
+  return (uint32_t)oracle_poly_mod(oracle_poly_mul(a, b), oracle_field_poly(w));
 }
 
 /* Multiplicative order of a nonzero element (0 if its powers reach 0 or never return to 1,
@@ -105,10 +157,11 @@ typedef struct {
 } gf_t;
 
 /* The primitive element: the smallest integer >= 2 whose order is 2^w - 1. Under an AOP the
- * element x (= 2) has order w+1 (x^{w+1} = 1), so it is not primitive unless w+1 = 2^w - 1;
- * the paper does not name a generator, hence the search. Returns 0 if none exists. */
+ * element x (= 2) has order w+1 (x^{w+1} = 1), under an ESP of degree s r order s (r + 1), so it
+ * is not primitive; the paper does not name a generator, hence the search. Returns 0 if none
+ * exists. */
 uint32_t oracle_gf_primitive(int w) {
-  if (w < 2 || w > ORACLE_MAX_W || !oracle_aop_irreducible(w)) return 0;
+  if (w < 2 || w > ORACLE_MAX_W || !oracle_field_poly(w)) return 0;
   uint32_t q1 = (1u << w) - 1;
   for (uint32_t g = 2; g <= q1; g++)
     if (oracle_gf_order(w, g) == q1) return g;
@@ -440,7 +493,7 @@ int oracle_ring_idempotents(int n, uint32_t* out, int cap) {
 /* All ring elements r with r mod p = u (the set from which the sparse transform picks), by
  * brute force over all 2^n elements. Returns the count (written up to cap). */
 int oracle_ring_representatives(int w, int n, uint32_t u, uint32_t* out, int cap) {
-  uint64_t p = oracle_aop(w);
+  uint64_t p = oracle_field_poly(w);
   int c = 0;
   for (uint32_t r = 0; r < (1u << n); r++)
     if (oracle_poly_mod(r, p) == u) {
@@ -460,9 +513,9 @@ static int popcount32(uint32_t v) {
 }
 
 /* Sparse transform phi_S (Sec. 2.2): the representative of u with the fewest ones; ties go to
- * the smallest integer (ties cannot occur for an AOP with n odd). */
+ * the smallest integer (they cannot occur for an AOP with n odd; they do for the ESP). */
 uint32_t oracle_sparse_rep(int w, int n, uint32_t u) {
-  uint64_t p = oracle_aop(w);
+  uint64_t p = oracle_field_poly(w);
   uint32_t best = 0;
   int bw = 99;
   for (uint32_t r = 0; r < (1u << n); r++)
@@ -512,7 +565,7 @@ void oracle_poly_mod_vec(uint64_t p, const uint32_t* a, uint32_t* out, size_t cn
 /* wt[u] = number of ones of phi_S(u), for every u < 2^w: the fewest ones over all ring elements
  * r with r mod p = u, in one pass over the 2^n ring elements. */
 static void sparse_weights(int w, int n, int* wt) {
-  uint64_t p = oracle_aop(w);
+  uint64_t p = oracle_field_poly(w);
   for (uint32_t u = 0; u < (1u << w); u++) wt[u] = 99;
   for (uint32_t r = 0; r < (1u << n); r++) {
     uint32_t u = (uint32_t)oracle_poly_mod(r, p);
@@ -536,7 +589,7 @@ int oracle_cauchy_weighted(int w, int k, int m, uint32_t* G, uint64_t* weights) 
     gf_free(&f);
     return -1;
   }
-  const int n = w + 1;
+  const int n = oracle_ring_size(w);
   const uint32_t q = 1u << w;
   int* wt = (int*)malloc(sizeof(int) * q);
   uint32_t* c = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(m > 0 ? m : 1) * (size_t)k);
@@ -610,13 +663,28 @@ int oracle_cauchy_weighted(int w, int k, int m, uint32_t* G, uint64_t* weights) 
 /* The parity transform (Sec. 2.3.1), written literally in the ring                            */
 /* ------------------------------------------------------------------------------------------ */
 
-/* phi_P(b) = b + par(b) x^w: the field element padded with its parity bit, an even-weight ring
- * element (an element of the ideal A_1). phi_P^{-1} drops the coefficient of x^w. */
-static uint32_t phi_P(int w, uint32_t b) { return b | ((uint32_t)(popcount32(b) & 1) << w); }
+/* phi_P pads a field element b with parity bits so that it lands in the ideal A_1. For an AOP
+ * (n = w + 1) one bit, the parity of b, at x^w (Sec. 2.3.1); for the ESP p(x^s) of degree w = s r
+ * (n = s (r + 1)) one bit per interleaved word: coefficient w + j is the parity of the
+ * coefficients j, j + s, ..., j + (r-1) s of b (Sec. 2.4.1; s = 1 is the AOP case). phi_P^{-1}
+ * drops the n - w top coefficients. */
+static uint32_t phi_P(int w, int n, uint32_t b) {
+  const int s = n - w;
+  uint32_t r = b;
+  for (int j = 0; j < s; j++) {
+    uint32_t par = 0;
+    for (int q = j; q < w; q += s) par ^= (b >> q) & 1u;
+    r |= par << (w + j);
+  }
+  return r;
+}
 static uint32_t phi_P_inv(int w, uint32_t r) { return r & ((1u << w) - 1); }
 
+/* phi_P as an export for the tests. */
+uint32_t oracle_phi_P(int w, int n, uint32_t b) { return phi_P(w, n, b); }
+
 typedef struct {
-  int w, k, nout;
+  int w, n, k, nout;
   const uint32_t* R;     /* nout x k ring masks (phi_S of the coefficients) */
   const int* src;        /* block index of source s */
   const int* dst;        /* block index of output o */
@@ -624,15 +692,15 @@ typedef struct {
   size_t P, t0, t1;
 } pt_job_t;
 
-/* out_o = phi_P^{-1}( sum_s R[o][s] * phi_P(y_s) ) in R_{2,w+1}, symbol lane by symbol lane. */
+/* out_o = phi_P^{-1}( sum_s R[o][s] * phi_P(y_s) ) in R_{2,n}, symbol lane by symbol lane. */
 static void* pt_run(void* arg) {
   pt_job_t* J = (pt_job_t*)arg;
-  const int w = J->w, n = w + 1;
+  const int w = J->w, n = J->n;
   size_t blk = (size_t)w * J->P;
   uint32_t y[ORACLE_MAX_K];
   for (size_t t = J->t0; t < J->t1; t++)
     for (int b = 0; b < 8; b++) {
-      for (int s = 0; s < J->k; s++) y[s] = phi_P(w, gather_symbol(J->blocks + (size_t)J->src[s] * blk, w, J->P, t, b));
+      for (int s = 0; s < J->k; s++) y[s] = phi_P(w, n, gather_symbol(J->blocks + (size_t)J->src[s] * blk, w, J->P, t, b));
       for (int o = 0; o < J->nout; o++) {
         uint32_t acc = 0;
         for (int s = 0; s < J->k; s++) acc ^= oracle_ring_mul(n, J->R[o * J->k + s], y[s]);
@@ -642,14 +710,14 @@ static void* pt_run(void* arg) {
   return NULL;
 }
 
-static void pt_code(int w, int k, int nout, const uint32_t* R, const int* src, const int* dst, uint8_t* blocks,
-                    size_t P, int nthreads) {
+static void pt_code(int w, int n, int k, int nout, const uint32_t* R, const int* src, const int* dst,
+                    uint8_t* blocks, size_t P, int nthreads) {
   if (nthreads < 1) nthreads = 1;
   if ((size_t)nthreads > P) nthreads = (int)P;
   if (nthreads > 256) nthreads = 256;
   pt_job_t jobs[256];
   for (int i = 0; i < nthreads; i++)
-    jobs[i] = (pt_job_t){w, k, nout, R, src, dst, blocks, P, P * (size_t)i / (size_t)nthreads,
+    jobs[i] = (pt_job_t){w, n, k, nout, R, src, dst, blocks, P, P * (size_t)i / (size_t)nthreads,
                          P * (size_t)(i + 1) / (size_t)nthreads};
   run_threads(pt_run, jobs, sizeof(pt_job_t), nthreads);
 }
@@ -659,15 +727,15 @@ static void pt_code(int w, int k, int nout, const uint32_t* R, const int* src, c
  * Returns 0, -1 unsupported field, -3 bad sizes. */
 int oracle_encode_pt(int w, int k, int m, const uint32_t* G, uint8_t* blocks, size_t P, int nthreads) {
   if (k < 1 || k > ORACLE_MAX_K || m < 0 || m > 64 || P == 0) return -3;
-  if (!oracle_aop_irreducible(w)) return -1;
-  const int n = w + 1;
+  const int n = oracle_ring_size(w);
+  if (!n) return -1;
   uint32_t* R = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(m > 0 ? m : 1) * (size_t)k);
   int src[ORACLE_MAX_K], dst[64];
   for (int i = 0; i < m; i++)
     for (int j = 0; j < k; j++) R[i * k + j] = oracle_sparse_rep(w, n, G[(k + i) * k + j]);
   for (int j = 0; j < k; j++) src[j] = j;
   for (int i = 0; i < m; i++) dst[i] = k + i;
-  pt_code(w, k, m, R, src, dst, blocks, P, nthreads);
+  pt_code(w, n, k, m, R, src, dst, blocks, P, nthreads);
   free(R);
   return 0;
 }
@@ -694,7 +762,7 @@ int oracle_decode_pt(int w, int k, int m, const uint32_t* G, uint8_t* blocks, ui
     gf_free(&f);
     return -1;
   }
-  const int n = w + 1;
+  const int n = oracle_ring_size(w);
   uint32_t* Gs = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)k * (size_t)k);
   uint32_t* Inv = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)k * (size_t)k);
   uint32_t* R = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)ne * (size_t)k);
@@ -712,7 +780,7 @@ int oracle_decode_pt(int w, int k, int m, const uint32_t* G, uint8_t* blocks, ui
         }
         R[r * k + s] = oracle_sparse_rep(w, n, v);
       }
-    pt_code(w, k, ne, R, surv, er, blocks, P, nthreads);
+    pt_code(w, n, k, ne, R, surv, er, blocks, P, nthreads);
   }
   free(Gs);
   free(Inv);

@@ -112,8 +112,13 @@ def test_table_multiply_equals_definition(w):
 
 
 def test_unsupported_fields_rejected():
-    # w = 6: x^7+1 has AOP factor x^6+...+1 = (x^3+x+1)(x^3+x^2+1), so no field.
-    with pytest.raises(ValueError):
-        oracle.gf_tables(6)
-    with pytest.raises(ValueError):
-        oracle.cauchy(6, 3, 2)
+    # w = 6: the AOP x^6+...+1 = (x^3+x+1)(x^3+x^2+1) is reducible; GF(2^6) comes from the ESP
+    # x^6+x^3+1 instead (Sec. 2.4). w = 3, 8, 9: neither an irreducible AOP nor an irreducible ESP.
+    assert oracle.poly_mod(oracle.aop(6), 0b1011) == 0 and not oracle.aop_irreducible(6)
+    assert oracle.field_poly(6) == 0b1001001
+    for w in (3, 8, 9):
+        assert oracle.field_poly(w) == 0 and oracle.ring_size(w) == 0
+        with pytest.raises(ValueError):
+            oracle.gf_tables(w)
+        with pytest.raises(ValueError):
+            oracle.cauchy(w, 3, 2)
