@@ -2,15 +2,18 @@
  * pyrit.h -- C ABI of the GB300 PYRIT erasure codec.
  *
  * PYRIT (polynomial ring transform; Detchart & Lacan, arXiv:1709.00178) computes systematic MDS
- * erasure codes over the field GF(2^w) = F2[x]/(p(x)), p the all-one polynomial (AOP) of degree w,
- * by doing every multiplication in the ring R_{2,n} = F2[x]/(x^n + 1), n = w + 1:
+ * erasure codes over the field GF(2^w) = F2[x]/(p(x)) by doing every multiplication in the ring
+ * R_{2,n} = F2[x]/(x^n + 1). p is the all-one polynomial (AOP) of degree w with n = w + 1
+ * (Sec. 2.3), or for GF(2^6) the equally spaced polynomial (ESP) x^6 + x^3 + 1 with n = 9
+ * (Sec. 2.4); in both cases p divides x^n + 1.
  *   - each generator (or decoding-matrix) coefficient u is replaced by its sparsest ring
  *     representative phi_S(u) (Sec. 2.2, "the sparse transform");
- *   - each source block is embedded in the ring by padding it with a zero packet (phi_E,
- *     Sec. 2.3.2), so multiplying it by x^s is a cyclic rotation of its packets and multiplying
- *     by phi_S(u) is an XOR of one rotation per set bit of phi_S(u) (Sec. 3);
- *   - the ring result is mapped back to the field by the remainder mod p, which for an AOP is
- *     "XOR the top packet into every other packet" (phi_E^{-1}, Sec. 2.3.2).
+ *   - each source block is embedded in the ring by padding it with n - w zero packets (phi_E,
+ *     Sec. 2.3.2, 2.4.2), so multiplying it by x^s is a cyclic rotation of its packets and
+ *     multiplying by phi_S(u) is an XOR of one rotation per set bit of phi_S(u) (Sec. 3);
+ *   - the ring result is mapped back to the field by the remainder mod p: for an AOP "XOR the top
+ *     packet into every other packet", for the ESP "XOR the top three packets into both lower
+ *     groups of three" (phi_E^{-1}).
  *
  * Data layout. A block is w packets of P bytes, contiguous, packet q at byte offset q*P. Bit b of
  * byte t of packet q is coefficient q (of x^q) of the field symbol in lane (t, b); every lane is
@@ -53,7 +56,8 @@ typedef struct CUstream_st* pyrit_stream_t;
 /* ---- status codes ------------------------------------------------------------------------ */
 #define PYRIT_OK 0
 #define PYRIT_E_INVALID_ARG -1        /* null pointer, P = 0, k/m out of range, bad mask bits  */
-#define PYRIT_E_UNSUPPORTED_FIELD -2  /* n != w+1, or the AOP of degree w is reducible         */
+#define PYRIT_E_UNSUPPORTED_FIELD -2  /* (w, n) is not an irreducible AOP with n = w+1 or the
+                                         ESP field w = 6, n = 9 (or no kernels for that n)      */
 #define PYRIT_E_TOO_LONG -3           /* k + m > 2^w: the default Cauchy code needs distinct points */
 #define PYRIT_E_NOT_MDS -4            /* generator not systematic, entry >= 2^w, or a singular
                                          k x k submatrix was found                              */
@@ -86,10 +90,12 @@ PYRIT_API const char* pyrit_strerror(int status);
 
 typedef struct pyrit_plan_s* pyrit_plan_t;
 
-/* Creates a coding plan for a systematic (k+m, k) code over GF(2^w), n = w+1.
- *   w, n : field degree and ring size. n must be w + 1 (AOP rings only) and the AOP of degree w
- *          irreducible (w+1 prime with 2 a primitive root mod w+1, Sec. 2.3); the kernels are
- *          built for w in {2, 4, 10, 12} (n in {3, 5, 11, 13}).
+/* Creates a coding plan for a systematic (k+m, k) code over GF(2^w) carried by R_{2,n}.
+ *   w, n : field degree and ring size. Either n = w + 1 with the AOP of degree w irreducible
+ *          (w+1 prime with 2 a primitive root mod w+1, Sec. 2.3), or the s-ESP of degree w = s r,
+ *          n = s (r + 1), irreducible by the criterion Sec. 2.4 quotes. The kernels are built for
+ *          (w, n) in {(2, 3), (4, 5), (6, 9), (10, 11), (12, 13)}; (6, 9) is GF(2^6) from
+ *          x^6 + x^3 + 1.
  *   k, m : 1 <= k <= PYRIT_MAX_K, 0 <= m <= PYRIT_MAX_M.
  *   G    : NULL for the default generator [I_k ; C], C[i][j] = 1/(x_i + y_j) with x_i = k+i,
  *          y_j = j (a Cauchy matrix, Sec. 3 "generalized Cauchy matrices"; requires
@@ -160,12 +166,14 @@ PYRIT_API int pyrit_plan_decode_masks(pyrit_plan_t plan, uint64_t erasures, int*
  * count *ne_out. Host only. */
 PYRIT_API int pyrit_plan_syndrome_masks(pyrit_plan_t plan, uint64_t erasures, uint16_t* syn_out, int* ne_out);
 
-/* phi_S of one field element u < 2^w: the lighter of its two ring representatives u and
- * u + p(x) (Sec. 2.2; for an AOP and odd n the weights differ, so there is no tie).
+/* phi_S of one field element u < 2^w: the lightest of its 2^(n-w) ring representatives
+ * u + h(x) p(x), deg h < n - w (Sec. 2.2; the smallest integer on ties, which an AOP with odd n
+ * never has).
  * Returns the n-bit mask, or 0xFFFFFFFF for a bad argument. */
 PYRIT_API uint32_t pyrit_sparse_transform(int w, int n, uint32_t u);
 
-/* Field product in GF(2^w) under the AOP, computed by the planner (host). */
+/* Field product in GF(2^w) under the library's modulus for w (the ESP x^6 + x^3 + 1 for w = 6, else
+ * the AOP of degree w), computed by the planner (host). */
 PYRIT_API uint32_t pyrit_gf_mul(int w, uint32_t a, uint32_t b);
 
 /* ---- single-stripe coding (device; asynchronous on `stream`) ------------------------------ */

@@ -1,10 +1,10 @@
 #!/usr/bin/env python3
 """Generates ring_network.inc: the paired multiply-accumulate networks of the staged ring kernel.
 
-For a ring R_{2,N} (w = N - 1) the generated device function ring_mac_pairs_n<N>(acc, d, r) adds
-r * d to the N ring accumulators, r an N-bit mask (phi_S of a field coefficient, paper Sec. 2.2)
-and d the W = N-1 packets of an embedded source block (its x^W coefficient is zero, phi_E,
-Sec. 2.3.2). Multiplying by x^s rotates the packets by s (Sec. 3), so r * d is the XOR of one
+For a ring R_{2,N} the generated device function ring_mac_pairs_n<N>(acc, d, r) adds r * d to the
+N ring accumulators, r an N-bit mask (phi_S of a field coefficient, paper Sec. 2.2) and d the W
+packets of an embedded source block (W = N - 1 for the all-one polynomials, 6 for N = 9; its
+coefficients at x^W and above are zero, phi_E, Sec. 2.3.2 and Sec. 2.4.2). Multiplying by x^s rotates the packets by s (Sec. 3), so r * d is the XOR of one
 rotation per set bit of r.
 
 The set bits are consumed in increasing order and fused two at a time: for consecutive set bits
@@ -18,7 +18,13 @@ Run from this directory: python gen_ring_network.py  (rewrites ring_network.inc)
 """
 import os
 
-RINGS = (3, 5, 11, 13)
+RINGS = (3, 5, 9, 11, 13)
+
+
+def ring_w(N):
+    """Field degree carried by R_{2,N}: N - 1 for the all-one polynomials, 6 for N = 9 (the ESP
+    x^6 + x^3 + 1); the source's packets at index >= w are the embedding's zeros."""
+    return 6 if N == 9 else N - 1
 
 
 def emit_ring(N):
@@ -26,7 +32,7 @@ def emit_ring(N):
     out.append("// R_{2,%d}: %d labelled states, %d fused pairs." % (N, (N + 1) + N * (N + 1) // 2, N * (N - 1) // 2))
     out.append("template <int WORDS>")
     out.append("__device__ __forceinline__ void ring_mac_pairs_n%d(uint32_t (&acc)[%d][WORDS], "
-               "const uint32_t (&d)[%d][WORDS], const uint32_t r) {" % (N, N, N - 1))
+               "const uint32_t (&d)[%d][WORDS], const uint32_t r) {" % (N, N, ring_w(N)))
     # X_s: no pending bit, about to test position s.  P_p_s: bit p pending, about to test s.
     for s in range(N):
         if s:
@@ -65,7 +71,7 @@ def main():
     body.append("")
     body.append("template <int N, int WORDS>")
     body.append("__device__ __forceinline__ void ring_mac_pairs(uint32_t (&acc)[N][WORDS], "
-                "const uint32_t (&d)[N - 1][WORDS], const uint32_t r) {")
+                "const uint32_t (&d)[RingDim<N>::W][WORDS], const uint32_t r) {")
     for N in RINGS:
         body.append("  if constexpr (N == %d) ring_mac_pairs_n%d<WORDS>(acc, d, r);" % (N, N))
     body.append("}")

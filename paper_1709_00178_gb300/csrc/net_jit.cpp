@@ -92,14 +92,14 @@ void put(std::string& o, const char* fmt, long a = 0, long b = 0, long c = 0, lo
 
 // CUDA C++ source of a network (compiled together with the embedded ring_staged.cuh).
 std::string net_source(const NetSpec& s) {
-  const int N = s.n, W = N - 1;
+  const int N = s.n, W = field_degree(N), S = N - W;
   const int groups = output_groups(s.mg, s.nout, s.nc);
   std::string o;
   o += "#include \"ring_staged.cuh\"\n"
        "namespace pyrit {\n"
        "struct NetMac : ";
   // modes: 0 direct / 1 syndrome under the embedding transform, 2 direct / 3 syndrome under the
-  // parity transform (each source enters the ring with its parity packet as packet W)
+  // parity transform (each source enters the ring with its parity packets as packets W..N-1)
   static const char* const kStore[4] = {"DirectStore", "SyndromeStore", "ParityStore", "SyndromePsiStore"};
   const bool syndrome = s.mode == 1 || s.mode == 3, parity = s.mode >= 2;
   o += kStore[s.mode];
@@ -111,14 +111,19 @@ std::string net_source(const NetSpec& s) {
     o += "  __device__ __forceinline__ void tile(const JobDesc*, int, int) {}\n";
   }
   o += "  template <int N, int WORDS, int MG>\n"
-       "  __device__ __forceinline__ void apply(uint32_t (&acc)[MG][N][WORDS], const uint32_t (&d)[N - 1][WORDS],\n"
-       "                                        int j, int g, int) {\n";
+       "  __device__ __forceinline__ void apply(uint32_t (&acc)[MG][N][WORDS],\n"
+       "                                        const uint32_t (&d)[RingDim<N>::W][WORDS], int j, int g, int) {\n";
   if (parity) {
-    // phi_P: the source's parity packet, i.e. the XOR of its W packets
-    o += "    uint32_t dp[WORDS];\n#pragma unroll\n    for (int x = 0; x < WORDS; ++x) {\n      dp[x] = d[0][x];\n";
-    int q = 1;
-    for (; q + 1 < W; q += 2) put(o, "      dp[x] = xor3(dp[x], d[%ld][x], d[%ld][x]);\n", q, q + 1);
-    if (q < W) put(o, "      dp[x] ^= d[%ld][x];\n", q);
+    // phi_P: parity packet j (ring packet W + j) is the XOR of the source's packets j, j + S, ...
+    // (one packet, the XOR of all W, for an all-one polynomial; S = 3 interleaved words for the ESP)
+    put(o, "    uint32_t dp[%ld][WORDS];\n#pragma unroll\n    for (int x = 0; x < WORDS; ++x) {\n", S);
+    for (int j = 0; j < S; ++j) {
+      put(o, "      dp[%ld][x] = d[%ld][x];\n", j, j);
+      int q = j + S;
+      for (; q + S < W; q += 2 * S)
+        put(o, "      dp[%ld][x] = xor3(dp[%ld][x], d[%ld][x], d[%ld][x]);\n", j, j, q, q + S);
+      if (q < W) put(o, "      dp[%ld][x] ^= d[%ld][x];\n", j, q);
+    }
     o += "    }\n";
   }
   // Syndrome networks guard each parity row with one warp-uniform test of the tile's needed rows
@@ -136,11 +141,12 @@ std::string net_source(const NetSpec& s) {
         const uint32_t r = s.mask[j][out];
         std::string lines;
         for (int t = 0; t < N; ++t) {
-          // under the parity transform a direct network never builds the top accumulator
-          // (phi_P^{-1} drops it)
-          if (parity && !syndrome && t == W) continue;
+          // under the parity transform a direct network never builds the top accumulators
+          // (phi_P^{-1} drops them)
+          if (parity && !syndrome && t >= W) continue;
           // accumulator t receives packet t - s for every set bit s, two terms per three-input
-          // XOR; packet W is the zero packet of phi_E (dropped) or the parity packet of phi_P
+          // XOR; packets W..N-1 are the zero packets of phi_E (dropped) or the parity packets of
+          // phi_P
           std::vector<std::string> terms;
           for (int sh = 0; sh < N; ++sh) {
             if (!((r >> sh) & 1u)) continue;
@@ -150,7 +156,9 @@ std::string net_source(const NetSpec& s) {
               std::snprintf(buf, sizeof(buf), "d[%d][x]", q);
               terms.push_back(buf);
             } else if (parity) {
-              terms.push_back("dp[x]");
+              char buf[32];
+              std::snprintf(buf, sizeof(buf), "dp[%d][x]", q - W);
+              terms.push_back(buf);
             }
           }
           char acc[32];
@@ -355,8 +363,13 @@ int shapes_for(int n, int nout, bool syndrome, NetSpec* out, int cap) {
                                    {2, 0, 1, 11}, {2, 0, 1, 16}, {4, 0, 1, 11}, {2, 0, 1, 8}};
   static const Shape4 small_s[] = {{2, 0, 1, 11}, {4, 0, 1, 8}, {4, 0, 1, 12}, {2, 0, 1, 24},
                                    {4, 0, 1, 15}, {2, 0, 1, 8}, {4, 0, 1, 11}, {2, 0, 1, 16}};
+  static const Shape4 n9_d[] = {{2, 0, 1, 11}, {2, 0, 1, 12}, {4, 0, 1, 8}, {2, 0, 1, 15},
+                                {1, 0, 1, 16}, {4, 0, 1, 11}, {2, 1, 1, 11}, {1, 0, 1, 12}};
+  static const Shape4 n9_s[] = {{2, 0, 1, 15}, {2, 0, 1, 12}, {2, 0, 1, 11}, {4, 0, 1, 8},
+                                {1, 0, 1, 16}, {2, 0, 1, 8}, {1, 0, 1, 15}, {4, 0, 1, 11}};
   const bool wide = nout > 4;
-  const Shape4* list = n == 11   ? (syndrome ? (wide ? n11_sw : n11_s) : (wide ? n11_dw : n11_d))
+  const Shape4* list = n == 9    ? (syndrome ? n9_s : n9_d)
+                       : n == 11 ? (syndrome ? (wide ? n11_sw : n11_s) : (wide ? n11_dw : n11_d))
                        : n == 13 ? (syndrome ? (wide ? n13_sw : n13_s) : (wide ? n13_dw : n13_d))
                                  : (syndrome ? small_s : small_d);
   int count = 0;
@@ -369,7 +382,7 @@ int shapes_for(int n, int nout, bool syndrome, NetSpec* out, int cap) {
     // accumulators (+ an output under construction for syndrome decoding), one staged source and
     // addressing and loop state against the register budget; the estimate runs about 20 above
     // what the compiler allocates without spilling (measured), hence the allowance
-    if ((mg + (syndrome ? 1 : 0)) * n * c.words + (n - 1) * c.words + 16 > reg_cap(c.nc, c.minb) + 20) continue;
+    if ((mg + (syndrome ? 1 : 0)) * n * c.words + field_degree(n) * c.words + 16 > reg_cap(c.nc, c.minb) + 20) continue;
     NetSpec s;
     std::memset(&s, 0, sizeof(s));
     s.n = n;
@@ -443,7 +456,7 @@ static bool spec_valid(const NetSpec& s) {
   const bool nc_ok = s.nc >= 1 && s.nc <= 31;
   if (s.mode < 0 || s.mode > 3) return false;
   if ((s.mode == 1 || s.mode == 3) && !(s.mg == s.nout && s.nout <= kSyndromeBaseRow)) return false;
-  return (s.n == 3 || s.n == 5 || s.n == 11 || s.n == 13) && s.nin >= 1 && s.nin <= kMaxIn && s.nout >= 1 &&
+  return (s.n == 3 || s.n == 5 || s.n == 9 || s.n == 11 || s.n == 13) && s.nin >= 1 && s.nin <= kMaxIn && s.nout >= 1 &&
          s.nout <= kMaxOut && words_ok && s.mg >= 1 && s.mg <= kMaxOut && s.minb >= 1 && s.minb <= 4 && nc_ok &&
          output_groups(s.mg, s.nout, s.nc) * s.mg >= s.nout && s.nc % output_groups(s.mg, s.nout, s.nc) == 0;
 }

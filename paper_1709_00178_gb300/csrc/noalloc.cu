@@ -147,7 +147,7 @@ extern "C" int pyrit_code_stripes_noalloc(const pyrit_stripe_t* stripes, int cou
     a.groups = (uint32_t)L.shape.groups;
     a.stages = (uint32_t)L.shape.stages;
     a.err = reinterpret_cast<int*>(scratch);
-    const size_t smem = staged_smem_bytes(L.shape.stages, L.shape.v->n - 1, L.shape.tw);
+    const size_t smem = staged_smem_bytes(L.shape.stages, field_degree(L.shape.v->n), L.shape.tw);
     const int grid = (int)(L.ntiles < (uint32_t)L.shape.grid ? L.ntiles : (uint32_t)L.shape.grid);
     void* args[] = {&a};
     if (cudaLaunchKernel(L.shape.v->fn, dim3(grid), dim3((L.shape.v->nc + 1) * 32), args, smem, st) != cudaSuccess)

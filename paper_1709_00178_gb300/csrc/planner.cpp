@@ -8,29 +8,71 @@
 
 namespace pyrit {
 
-// Sec. 2.3: the AOP of degree w is irreducible iff w+1 is prime and 2 generates the
-// multiplicative group of F_{w+1} (read from the text's "w generates F*_{w+1}", which its own
-// GF(16) example contradicts literally). The kernels are instantiated for n in {3, 5, 11, 13}.
-bool aop_field_supported(int w, int n) {
-  if (w < 2 || w > 15 || n != w + 1) return false;
-  const int p = w + 1;
+namespace {
+
+// Sec. 2.3: the AOP of degree r is irreducible iff r+1 is prime and 2 generates the
+// multiplicative group of F_{r+1} (read from the text's "w generates F*_{w+1}", which its own
+// GF(16) example contradicts literally).
+bool aop_irreducible(int r) {
+  const int p = r + 1;
+  if (r < 2) return false;  // the criteria below need r + 1 an odd prime (x^s + 1 is reducible)
   for (int d = 2; d * d <= p; ++d)
     if (p % d == 0) return false;
   int order = 1;
   for (int v = 2 % p; v != 1; v = (v * 2) % p) ++order;
-  if (order != w) return false;
-  return n == 3 || n == 5 || n == 11 || n == 13;
+  return order == r;
 }
 
-// Product in GF(2^w) = F2[x]/(1 + x + ... + x^w): shift-and-add, reducing each time the shifted
-// multiplicand reaches degree w with x^w = 1 + x + ... + x^{w-1}.
+uint64_t pow_mod(uint64_t b, uint64_t e, uint64_t m) {
+  uint64_t r = 1 % m;
+  b %= m;
+  while (e) {
+    if (e & 1) r = r * b % m;
+    b = b * b % m;
+    e >>= 1;
+  }
+  return r;
+}
+
+// Sec. 2.4 (citing Itoh and Tsujii): the s-ESP p(x^s) of degree s r, p the AOP of degree r, is
+// irreducible iff p is and s = (r+1)^(t-1) for some t >= 2 with 2^(r (r+1)^(t-2)) != 1 mod
+// (r+1)^t. s = 1 is the AOP itself.
+bool esp_irreducible(int s, int r) {
+  if (!aop_irreducible(r)) return false;
+  if (s == 1) return true;
+  uint64_t pw = (uint64_t)r + 1;  // (r+1)^(t-1), t = 2
+  for (int t = 2; pw <= (uint64_t)s; ++t, pw *= (uint64_t)(r + 1))
+    if (pw == (uint64_t)s) return pow_mod(2, (uint64_t)r * (pw / (uint64_t)(r + 1)), pw * (uint64_t)(r + 1)) != 1;
+  return false;
+}
+
+}  // namespace
+
+// GF(2^w) is supported on R_{2,n} when the field's modulus is the s-ESP of degree w = s r with
+// n = s (r + 1) (s = 1: the AOP, n = w + 1), irreducible by the paper's criteria, and n is one of
+// the ring sizes the kernels are instantiated for: 3, 5, 11, 13 (AOPs) and 9 (x^6 + x^3 + 1).
+bool field_supported(int w, int n) {
+  if (w < 2 || w > 15 || n <= w) return false;
+  const int s = n - w;
+  if (w % s != 0 || !esp_irreducible(s, w / s)) return false;
+  return field_degree(n) == w && (n == 3 || n == 5 || n == 9 || n == 11 || n == 13);
+}
+
+// The modulus of GF(2^w) in this library: the ESP x^6 + x^3 + 1 for w = 6, else the AOP of degree w.
+uint32_t field_modulus(int w) {
+  if (w == 6) return 0x49u;  // 1 + x^3 + x^6
+  return (1u << (w + 1)) - 1;
+}
+
+// Product in GF(2^w) = F2[x]/(modulus): shift-and-add, reducing each time the shifted
+// multiplicand reaches degree w (x^w = the modulus minus its leading term).
 uint32_t gf_mul(int w, uint32_t a, uint32_t b) {
-  const uint32_t low = (1u << w) - 1;
+  const uint32_t g = field_modulus(w);
   uint32_t r = 0;
   for (int i = 0; i < w; ++i) {
     if ((b >> i) & 1u) r ^= a;
     a <<= 1;
-    if ((a >> w) & 1u) a = (a & low) ^ low;
+    if ((a >> w) & 1u) a ^= g;
   }
   return r;
 }
@@ -46,13 +88,27 @@ uint32_t gf_inv(int w, uint32_t a) {
   return a ? r : 0;
 }
 
-// phi_S (Sec. 2.2) for an AOP: the ring elements reducing to u mod p are u and u + p(x), where
-// p(x) is the all-ones polynomial of n = w+1 coefficients, i.e. the complement of u in n bits.
-// Their weights are t and n - t; n odd means the lighter one is unique.
+// phi_S (Sec. 2.2): the ring elements of R_{2,n} reducing to u mod the modulus g are u + h g for
+// the 2^(n-w) polynomials h of degree < n - w. The lightest is taken, the smallest on ties. For an
+// AOP that is u or its complement in n bits (weights t and n - t, never tied for odd n); for the
+// ESP of GF(2^6) one of eight.
 uint32_t sparse_rep(int w, int n, uint32_t u) {
-  const uint32_t all = (1u << n) - 1;
-  const uint32_t lo = u & ((1u << w) - 1), hi = lo ^ all;
-  return __builtin_popcount(lo) <= __builtin_popcount(hi) ? lo : hi;
+  const uint32_t g = field_modulus(w);
+  u &= (1u << w) - 1;
+  uint32_t best = u;
+  int bw = __builtin_popcount(u);
+  for (uint32_t h = 1; h < (1u << (n - w)); ++h) {
+    uint32_t hg = 0;  // carry-less h * g
+    for (int i = 0; i < n - w; ++i)
+      if ((h >> i) & 1u) hg ^= g << i;
+    const uint32_t r = u ^ hg;
+    const int c = __builtin_popcount(r);
+    if (c < bw || (c == bw && r < best)) {
+      best = r;
+      bw = c;
+    }
+  }
+  return best;
 }
 
 // Inverse over GF(2^w) by elimination with row swaps (k <= 32). Returns false if singular.
@@ -281,7 +337,8 @@ const char* pyrit_strerror(int s) {
   switch (s) {
     case PYRIT_OK: return "ok";
     case PYRIT_E_INVALID_ARG: return "invalid argument";
-    case PYRIT_E_UNSUPPORTED_FIELD: return "unsupported field (n must be w+1 with an irreducible AOP)";
+    case PYRIT_E_UNSUPPORTED_FIELD:
+      return "unsupported field (n = w+1 with an irreducible AOP, or w = 6, n = 9 for x^6+x^3+1)";
     case PYRIT_E_TOO_LONG: return "code too long for the field (k+m > 2^w)";
     case PYRIT_E_NOT_MDS: return "generator is not systematic MDS";
     case PYRIT_E_TOO_MANY_ERASURES: return "more erasures than parity blocks";
@@ -301,7 +358,7 @@ int pyrit_plan_create(int w, int n, int k, int m, const uint32_t* G, pyrit_plan_
   if (!out) return PYRIT_E_INVALID_ARG;
   *out = nullptr;
   if (k < 1 || k > kMaxIn || m < 0 || m > kMaxOut) return PYRIT_E_INVALID_ARG;
-  if (!aop_field_supported(w, n)) return PYRIT_E_UNSUPPORTED_FIELD;
+  if (!field_supported(w, n)) return PYRIT_E_UNSUPPORTED_FIELD;
   if (!G && (uint64_t)k + (uint64_t)m > (1ull << w)) return PYRIT_E_TOO_LONG;
   pyrit_plan_s* p = new (std::nothrow) pyrit_plan_s;
   if (!p) return PYRIT_E_OOM;
@@ -370,16 +427,12 @@ int pyrit_plan_encode_masks(pyrit_plan_t p, uint16_t* masks_out) {
 
 int pyrit_generator_weighted(int w, int n, int k, int m, uint32_t* G_out, uint64_t* weights_out) {
   if (!G_out || k < 1 || k > kMaxIn || m < 0 || m > kMaxOut) return PYRIT_E_INVALID_ARG;
-  if (n != w + 1 || !aop_field_supported(w, n)) return PYRIT_E_UNSUPPORTED_FIELD;
+  if (!field_supported(w, n)) return PYRIT_E_UNSUPPORTED_FIELD;
   if ((uint64_t)k + (uint64_t)m > (1ull << w)) return PYRIT_E_TOO_LONG;
   const uint32_t q = 1u << w;
-  // weight of phi_S(u): an AOP element has the two representatives u and u + p (p = all n ones),
-  // so the sparse one has min(ones, n - ones) ones
+  // weight of phi_S(u), the number of ones of the sparsest representative
   std::vector<int> wt(q);
-  for (uint32_t u = 0; u < q; ++u) {
-    const int ones = __builtin_popcount(u);
-    wt[u] = ones < n - ones ? ones : n - ones;
-  }
+  for (uint32_t u = 0; u < q; ++u) wt[u] = __builtin_popcount(sparse_rep(w, n, u));
   std::vector<uint32_t> c((size_t)m * k);
   for (int i = 0; i < m; ++i)
     for (int j = 0; j < k; ++j) c[(size_t)i * k + j] = gf_inv(w, (uint32_t)(k + i) ^ (uint32_t)j);
@@ -466,7 +519,7 @@ int pyrit_plan_decode_masks(pyrit_plan_t p, uint64_t erasures, int* survivors_ou
 }
 
 uint32_t pyrit_sparse_transform(int w, int n, uint32_t u) {
-  if (!aop_field_supported(w, n) || u >= (1u << w)) return 0xFFFFFFFFu;
+  if (!field_supported(w, n) || u >= (1u << w)) return 0xFFFFFFFFu;
   return sparse_rep(w, n, u);
 }
 

@@ -16,6 +16,10 @@ namespace pyrit {
 
 static_assert(kMaxIn == PYRIT_MAX_K && kMaxOut == PYRIT_MAX_M, "job limits follow the C ABI's");
 
+// Field degree w carried by the ring R_{2,n}: RingDim<n>::W for a run-time n.
+inline int field_degree(int n) { return n == 9 ? 6 : n - 1; }
+static_assert(RingDim<9>::W == 6 && RingDim<11>::W == 10, "field_degree follows RingDim");
+
 // Dynamic shared memory of the staged kernel: S stages of W packets x tw bytes and 2 S mbarriers.
 inline size_t staged_smem_bytes(int stages, int w, int tw) {
   return (size_t)stages * w * tw + 2 * sizeof(uint64_t) * stages;
@@ -23,7 +27,7 @@ inline size_t staged_smem_bytes(int stages, int w, int tw) {
 
 // A compiled instance of the staged ring kernel.
 struct Variant {
-  int n;         // ring size N (w = N - 1)
+  int n;         // ring size N (w = field_degree(N))
   int words;     // 32-bit words per consumer thread per packet
   int mg;        // outputs accumulated per consumer warp
   int minb;      // CTAs per SM the register budget is sized for
@@ -35,11 +39,11 @@ struct Variant {
   int nout;      // generated networks: the output count they were compiled for (0: generic)
 };
 
-// Output groups of a launch: the smallest power of two g with g * mg >= nout (and g < nc); the
-// consumer warps split evenly into them. Generated networks are compiled for this same split.
 // Generated networks whose jobs are in syndrome form (modes 1 and 3).
 inline bool syndrome_mode(int mode) { return mode == 1 || mode == 3; }
 
+// Output groups of a launch: the smallest power of two g with g * mg >= nout (and g < nc); the
+// consumer warps split evenly into them. Generated networks are compiled for this same split.
 inline int output_groups(int mg, int nout, int nc) {
   int g = 1;
   while (g * mg < nout && g < nc) g *= 2;
@@ -67,7 +71,8 @@ struct ShapeHint {
 };
 
 // ---- planner (host) -------------------------------------------------------------------------
-bool aop_field_supported(int w, int n);
+bool field_supported(int w, int n);
+uint32_t field_modulus(int w);
 uint32_t gf_mul(int w, uint32_t a, uint32_t b);
 uint32_t gf_inv(int w, uint32_t a);
 uint32_t sparse_rep(int w, int n, uint32_t u);

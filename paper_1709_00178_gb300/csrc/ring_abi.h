@@ -19,6 +19,17 @@ typedef unsigned long uintptr_t;
 
 namespace pyrit {
 
+// Ring sizes and field degrees. GF(2^w) is carried by R_{2,n}: n = w + 1 for a field defined by
+// the all-one polynomial of degree w (Sec. 2.3), n = 9 for GF(2^6) defined by the equally spaced
+// polynomial x^6 + x^3 + 1 (Sec. 2.4: n = s (r + 1), w = s r, s = 3, r = 2). The S = n - w top
+// ring coefficients are the ones the embedding pads with zeros; reduction mod the field's modulus
+// folds coefficient w + j into every coefficient t < w with t = j (mod S).
+template <int N>
+struct RingDim {
+  static constexpr int W = N == 9 ? 6 : N - 1;
+  static constexpr int S = N - W;
+};
+
 constexpr int kMaxIn = 32;  // sources of one coding job (data blocks or survivors)
 constexpr int kMaxOut = 8;  // destinations of one coding job (parity or erased blocks)
 // Syndrome-form decode jobs keep, for output o, 1 + the row of their partial sum (0: none) in

@@ -13,10 +13,10 @@ namespace pyrit {
 
 // acc += x^S * d in R_{2,N}: packet q of the embedded source lands in accumulator (q + S) mod N.
 template <int N, int WORDS, int S>
-__device__ __forceinline__ void xor_rotated(uint32_t (&acc)[N][WORDS], const uint32_t (&d)[N - 1][WORDS]) {
+__device__ __forceinline__ void xor_rotated(uint32_t (&acc)[N][WORDS], const uint32_t (&d)[RingDim<N>::W][WORDS]) {
   if constexpr (S < N) {
 #pragma unroll
-    for (int q = 0; q < N - 1; ++q)
+    for (int q = 0; q < RingDim<N>::W; ++q)
 #pragma unroll
       for (int x = 0; x < WORDS; ++x) acc[(q + S) % N][x] ^= d[q][x];
   }
@@ -25,8 +25,8 @@ __device__ __forceinline__ void xor_rotated(uint32_t (&acc)[N][WORDS], const uin
 // acc += x^s * d for a run-time shift s < N. The rotation is resolved by a warp-uniform jump to
 // straight-line code with static register indices (all lanes share the job, so no divergence).
 template <int N, int WORDS>
-__device__ __forceinline__ void xor_rotated_dyn(uint32_t (&acc)[N][WORDS], const uint32_t (&d)[N - 1][WORDS],
-                                                int s) {
+__device__ __forceinline__ void xor_rotated_dyn(uint32_t (&acc)[N][WORDS],
+                                                const uint32_t (&d)[RingDim<N>::W][WORDS], int s) {
   switch (s) {
     case 0: xor_rotated<N, WORDS, 0>(acc, d); break;
     case 1: xor_rotated<N, WORDS, 1>(acc, d); break;
@@ -46,10 +46,10 @@ __device__ __forceinline__ void xor_rotated_dyn(uint32_t (&acc)[N][WORDS], const
 }
 
 // acc += (x^S1 + x^S2) * d in R_{2,N} in one pass: accumulator t receives d[t - S1] ^ d[t - S2]
-// (one three-input XOR), or a single term where the other index is the zero packet d[N-1].
+// (one three-input XOR), or a single term where the other index is a zero packet (index >= W).
 template <int N, int WORDS, int S1, int S2>
-__device__ __forceinline__ void xor_pair(uint32_t (&acc)[N][WORDS], const uint32_t (&d)[N - 1][WORDS]) {
-  constexpr int W = N - 1;
+__device__ __forceinline__ void xor_pair(uint32_t (&acc)[N][WORDS], const uint32_t (&d)[RingDim<N>::W][WORDS]) {
+  constexpr int W = RingDim<N>::W;
 #pragma unroll
   for (int t = 0; t < N; ++t) {
     const int q1 = (t - S1 + N) % N, q2 = (t - S2 + N) % N;
@@ -74,7 +74,7 @@ __device__ __forceinline__ void xor_pair(uint32_t (&acc)[N][WORDS], const uint32
 //   DISPATCH 2: the generated pairing automaton: consecutive set bits fused into one pass of
 //               three-input XORs, static forward branches only (ring_network.inc).
 template <int N, int WORDS, int MG, int DISPATCH>
-__device__ __forceinline__ void ring_mac(uint32_t (&acc)[MG][N][WORDS], const uint32_t (&d)[N - 1][WORDS],
+__device__ __forceinline__ void ring_mac(uint32_t (&acc)[MG][N][WORDS], const uint32_t (&d)[RingDim<N>::W][WORDS],
                                          const uint32_t (&mu)[(MG + 1) / 2]) {
 #pragma unroll
   for (int i = 0; i < MG; ++i) {
@@ -84,7 +84,7 @@ __device__ __forceinline__ void ring_mac(uint32_t (&acc)[MG][N][WORDS], const ui
       for (int s = 0; s < N; ++s) {
         if (m & (1u << s)) {
 #pragma unroll
-          for (int q = 0; q < N - 1; ++q)
+          for (int q = 0; q < RingDim<N>::W; ++q)
 #pragma unroll
             for (int x = 0; x < WORDS; ++x) acc[i][(q + s) % N][x] ^= d[q][x];
         }
@@ -129,8 +129,8 @@ struct MaskMac : DirectStore {
   }
 
   template <int N, int WORDS, int MG_>
-  __device__ __forceinline__ void apply(uint32_t (&acc)[MG_][N][WORDS], const uint32_t (&d)[N - 1][WORDS], int j,
-                                        int, int lane) {
+  __device__ __forceinline__ void apply(uint32_t (&acc)[MG_][N][WORDS], const uint32_t (&d)[RingDim<N>::W][WORDS],
+                                        int j, int, int lane) {
     uint32_t mu[MW];
 #pragma unroll
     for (int x = 0; x < MW; ++x) mu[x] = __reduce_or_sync(0xFFFFFFFFu, lane == j ? rw[x] : 0u);
@@ -147,7 +147,7 @@ __global__ void __launch_bounds__((NC + 1) * 32, MINB) ring_staged_kernel(const 
 // staging. The same ring arithmetic on byte-wide lanes; all outputs per thread.
 template <int N>
 __global__ void __launch_bounds__(256) ring_plain_kernel(const __grid_constant__ JobDesc job) {
-  constexpr int W = N - 1;
+  constexpr int W = RingDim<N>::W, S = RingDim<N>::S;
   const uint64_t P = job.P;
   for (uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; c < P; c += (uint64_t)gridDim.x * blockDim.x) {
     uint32_t acc[kMaxOut][N][1];
@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(256) ring_plain_kernel(const __grid_constant__
     for (int i = 0; i < kMaxOut; ++i) {
       if (i < job.nout) {
 #pragma unroll
-        for (int r = 0; r < W; ++r) job.out[i][(uint64_t)r * P + c] = (uint8_t)(acc[i][r][0] ^ acc[i][W][0]);
+        for (int r = 0; r < W; ++r) job.out[i][(uint64_t)r * P + c] = (uint8_t)(acc[i][r][0] ^ acc[i][W + r % S][0]);
       }
     }
   }

@@ -13,6 +13,7 @@
 namespace pyrit {
 
 const Variant* variants_small(int* count);
+const Variant* variants_n9(int* count);
 const Variant* variants_n11(int* count);
 const Variant* variants_n13(int* count);
 
@@ -31,7 +32,7 @@ struct Registry {
   Variant all[kMaxVariants];
   int count = 0;
   Registry() {
-    const Variant* (*srcs[])(int*) = {variants_small, variants_n11, variants_n13};
+    const Variant* (*srcs[])(int*) = {variants_small, variants_n9, variants_n11, variants_n13};
     for (auto f : srcs) {
       int c = 0;
       const Variant* t = f(&c);
@@ -57,7 +58,7 @@ void ensure_attr(const Variant* v) {
     cudaFuncSetAttribute(v->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
 }
 
-size_t smem_bytes(const TileShape& s) { return staged_smem_bytes(s.stages, s.v->n - 1, s.tw); }
+size_t smem_bytes(const TileShape& s) { return staged_smem_bytes(s.stages, field_degree(s.v->n), s.tw); }
 
 int occupancy(const TileShape& s) {
   ensure_attr(s.v);
@@ -131,7 +132,7 @@ bool shape_for_variant(const Variant* v, int max_nout, const ShapeHint& h, TileS
   const int groups = output_groups(v->mg, max_nout, v->nc);
   s.groups = groups;
   s.tw = (v->nc / groups) * 32 * 4 * v->words;
-  const int w = v->n - 1;
+  const int w = field_degree(v->n);
   const int budget = (226 * 1024) / v->minb - 1024;  // shared memory per CTA at the target occupancy
   s.stages = h.stages > 0 ? h.stages : std::max(2, std::min(8, budget / (w * s.tw)));
   s.grid = 0;
@@ -194,6 +195,7 @@ int launch_plain(int n, const JobDesc& job, cudaStream_t stream) {
   switch (n) {
     case 3: ring_plain_kernel<3><<<grid, 256, 0, stream>>>(job); break;
     case 5: ring_plain_kernel<5><<<grid, 256, 0, stream>>>(job); break;
+    case 9: ring_plain_kernel<9><<<grid, 256, 0, stream>>>(job); break;
     case 11: ring_plain_kernel<11><<<grid, 256, 0, stream>>>(job); break;
     case 13: ring_plain_kernel<13><<<grid, 256, 0, stream>>>(job); break;
     default: return PYRIT_E_UNSUPPORTED_FIELD;

@@ -2,18 +2,20 @@
 // kernels (compiled by nvcc) and the plan-specialised ones (generated at run time and compiled by
 // NVRTC). It is written for both compilers: no standard headers, only ring_abi.h and ptx.cuh.
 //
-// A coding job computes out[i] = sum_j u_ij in[j] over GF(2^w), w = N - 1, for every symbol lane
-// of bit-sliced blocks (packet q of a block holds coefficient q). Each coefficient arrives as its
-// ring representative r_ij = phi_S(u_ij) (an N-bit mask, Sec. 2.2). Per 32-bit column word the
-// pipeline:
-//   1. embeds the source block in R_{2,N} (phi_E): its W packets plus an implicit zero packet;
+// A coding job computes out[i] = sum_j u_ij in[j] over GF(2^w), w = RingDim<N>::W (N - 1 for an
+// all-one polynomial, 6 for N = 9), for every symbol lane of bit-sliced blocks (packet q of a
+// block holds coefficient q). Each coefficient arrives as its ring representative
+// r_ij = phi_S(u_ij) (an N-bit mask, Sec. 2.2). Per 32-bit column word the pipeline:
+//   1. embeds the source block in R_{2,N} (phi_E): its W packets plus S = N - W implicit zero
+//      packets;
 //   2. for every set bit s of r_ij, XORs the source rotated by s packets into the N ring
 //      accumulators of output i (x^s times a ring element is a cyclic shift of its coefficients;
-//      the zero packet contributes nothing, so each set bit costs W XORs -- Sec. 3); this step is
+//      the zero packets contribute nothing, so each set bit costs W XORs -- Sec. 3); this step is
 //      the policy `Mac`, either driven by the masks at run time or a network fixed at compile time;
-//   3. reduces each accumulator mod p (phi_E^{-1}): out[t] = acc[t] ^ acc[W] (Sec. 2.3.2), then
-//      stores the W field packets.
-// The extra ring packet is never written to memory, as in the paper's register scheme (Sec. 3).
+//   3. reduces each accumulator mod the field's modulus (phi_E^{-1}): out[t] = acc[t] ^
+//      acc[W + t mod S] (Sec. 2.3.2 for S = 1, Sec. 2.4.2 for the ESP), then stores the W field
+//      packets.
+// The extra ring packets are never written to memory, as in the paper's register scheme (Sec. 3).
 //
 // GB300 mapping (prior art: the paper's x86 SIMD register schedule). A CTA owns a column tile of
 // `tw` bytes of one job. A producer warp streams the job's source blocks, one block (W packets
@@ -27,8 +29,8 @@
 // The policy Mac provides, per consumer warp:
 //   void tile(const JobDesc* J, int g, int lane);      // once per tile (e.g. load the masks)
 //   template <int N, int WORDS, int MG>
-//   void apply(uint32_t (&acc)[MG][N][WORDS], const uint32_t (&d)[N - 1][WORDS], int j, int g,
-//              int lane);                             // acc_i += r_ij * d for the group's outputs
+//   void apply(uint32_t (&acc)[MG][N][WORDS], const uint32_t (&d)[RingDim<N>::W][WORDS], int j,
+//              int g, int lane);                      // acc_i += r_ij * d for the group's outputs
 //   template <int N, int WORDS, int MG>
 //   void store(uint32_t (&acc)[MG][N][WORDS], const JobDesc* J, int g, uint32_t col0,
 //              uint32_t off, bool valid);              // phi_E^{-1} and the stores of the tile;
@@ -101,15 +103,15 @@ __device__ __forceinline__ typename Vec<WORDS>::T vmake(const uint32_t (&w)[WORD
   }
 }
 
-// phi_E^{-1} and the stores of a direct job: output g*MG + i is acc[i] reduced mod the AOP
-// (out[t] = acc[t] ^ acc[W], Sec. 2.3.2); its W field packets are stored at column col0 + off.
+// phi_E^{-1} and the stores of a direct job: output g*MG + i is acc[i] reduced mod the field's
+// modulus (out[t] = acc[t] ^ acc[W + t mod S]); its W field packets are stored at col0 + off.
 struct DirectStore {
   static constexpr bool kSparse = false;
 
   template <int N, int WORDS, int MG>
   __device__ __forceinline__ void store(uint32_t (&acc)[MG][N][WORDS], const JobDesc* J, int g, uint32_t col0,
                                         uint32_t off, bool valid) {
-    constexpr int W = N - 1;
+    constexpr int W = RingDim<N>::W, S = RingDim<N>::S;
     using V = typename Vec<WORDS>::T;
     if (!valid) return;
     const uint64_t P = J->P;
@@ -123,7 +125,7 @@ struct DirectStore {
         for (int r = 0; r < W; ++r) {
           uint32_t o4[WORDS];
 #pragma unroll
-          for (int x = 0; x < WORDS; ++x) o4[x] = acc[i][r][x] ^ acc[i][W][x];
+          for (int x = 0; x < WORDS; ++x) o4[x] = acc[i][r][x] ^ acc[i][W + r % S][x];
           *reinterpret_cast<V*>(dst + (size_t)r * P) = vmake<WORDS>(o4);
         }
       }
@@ -147,10 +149,12 @@ struct DirectStore {
 // mask[kSyndromeBaseRow][o] is 1 + the row whose partial sum is added (0: none). Rows are first
 // reduced in place (phi_E^{-1}), products are formed in the ring with the reduced rows embedded
 // (phi_E), and each output is reduced once more before its store.
-// PSI: the jobs code under the parity transform (Sec. 2.3.1). The first phase's rows then reduce
-// to field values in the psi domain (psi(d) = phi_P(d) mod p = d + par(d) (1 + ... + x^{W-1})), the
-// second phase is the same linear algebra there, and each output finally goes through psi^{-1} =
-// psi (an involution for even W): its parity is XORed into every packet.
+// PSI: the jobs code under the parity transform (Sec. 2.3.1, Sec. 2.4.1). The first phase's rows
+// then reduce to field values in the psi domain (psi(d) = phi_P(d) mod the field's modulus:
+// coefficient t of d plus the parity of its interleaved word t mod S, i.e. for an AOP
+// d + par(d) (1 + ... + x^{W-1}), for the ESP the swap of d's two halves), the second phase is the
+// same linear algebra there, and each output finally goes through psi^{-1} = psi (an involution):
+// the parity of each interleaved word is XORed into that word's packets.
 template <bool PSI>
 struct SyndromeStoreT {
   static constexpr bool kSparse = true;  // erased columns and unused parity are absent sources
@@ -162,14 +166,14 @@ struct SyndromeStoreT {
   __device__ __forceinline__ void store(uint32_t (&acc)[MG][N][WORDS], const JobDesc* J, int, uint32_t col0,
                                         uint32_t off, bool valid) {
     // lanes past the tile's width take part in nothing here but the stores they skip
-    constexpr int W = N - 1;
+    constexpr int W = RingDim<N>::W, S = RingDim<N>::S;
     using V = typename Vec<WORDS>::T;
 #pragma unroll
     for (int r = 0; r < MG; ++r)
 #pragma unroll
       for (int t = 0; t < W; ++t)
 #pragma unroll
-        for (int x = 0; x < WORDS; ++x) acc[r][t][x] ^= acc[r][W][x];
+        for (int x = 0; x < WORDS; ++x) acc[r][t][x] ^= acc[r][W + t % S][x];
     const uint64_t P = J->P;
     const int nout = J->nout;
     for (int o = 0; o < nout; ++o) {
@@ -205,20 +209,22 @@ struct SyndromeStoreT {
       }
       if (valid) {
         uint8_t* dst = J->out[o] + col0 + off;
-        uint32_t par[WORDS];
+        uint32_t par[S][WORDS];
 #pragma unroll
-        for (int x = 0; x < WORDS; ++x) par[x] = 0u;
+        for (int j = 0; j < S; ++j)
+#pragma unroll
+          for (int x = 0; x < WORDS; ++x) par[j][x] = 0u;
         if constexpr (PSI) {
 #pragma unroll
           for (int t = 0; t < W; ++t)
 #pragma unroll
-            for (int x = 0; x < WORDS; ++x) par[x] ^= res[t][x] ^ res[W][x];
+            for (int x = 0; x < WORDS; ++x) par[t % S][x] ^= res[t][x] ^ res[W + t % S][x];
         }
 #pragma unroll
         for (int t = 0; t < W; ++t) {
           uint32_t o4[WORDS];
 #pragma unroll
-          for (int x = 0; x < WORDS; ++x) o4[x] = res[t][x] ^ res[W][x] ^ par[x];
+          for (int x = 0; x < WORDS; ++x) o4[x] = res[t][x] ^ res[W + t % S][x] ^ par[t % S][x];
           *reinterpret_cast<V*>(dst + (size_t)t * P) = vmake<WORDS>(o4);
         }
       }
@@ -228,16 +234,17 @@ struct SyndromeStoreT {
 using SyndromeStore = SyndromeStoreT<false>;
 using SyndromePsiStore = SyndromeStoreT<true>;
 
-// phi_P^{-1} and the stores of a direct job under the parity transform (Sec. 2.3.1): every source
-// entered the ring padded with its parity packet, so each ring result lies in the ideal A_1 and
-// its field packets are its first W coefficients (the top one is dropped, never computed).
+// phi_P^{-1} and the stores of a direct job under the parity transform (Sec. 2.3.1, Sec. 2.4.1):
+// every source entered the ring padded with its parity packets, so each ring result lies in the
+// ideal A_1 and its field packets are its first W coefficients (the top S are dropped, never
+// computed).
 struct ParityStore {
   static constexpr bool kSparse = false;
 
   template <int N, int WORDS, int MG>
   __device__ __forceinline__ void store(uint32_t (&acc)[MG][N][WORDS], const JobDesc* J, int g, uint32_t col0,
                                         uint32_t off, bool valid) {
-    constexpr int W = N - 1;
+    constexpr int W = RingDim<N>::W;
     using V = typename Vec<WORDS>::T;
     if (!valid) return;
     const uint64_t P = J->P;
@@ -256,7 +263,7 @@ struct ParityStore {
 
 template <int N, int WORDS, int MG, int NC, class Mac>
 __device__ __forceinline__ void ring_staged_body(const CodeArgs& a) {
-  constexpr int W = N - 1;
+  constexpr int W = RingDim<N>::W;
   using V = typename Vec<WORDS>::T;
   extern __shared__ __align__(128) uint8_t smem[];
   const uint32_t S = a.stages, TW = a.tw;

@@ -15,7 +15,7 @@ import oracle
 from paper_1709_00178_gb300 import pyrit
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-RINGS = [(2, 3), (4, 5), (10, 11), (12, 13)]
+RINGS = [(2, 3), (4, 5), (6, 9), (10, 11), (12, 13)]
 
 
 def test_library_exports_every_declared_symbol():
@@ -31,7 +31,7 @@ def test_library_exports_every_declared_symbol():
 
 def _brute_sparse(w, n):
     """phi_S for every u by brute force over all 2^n ring elements (oracle reduction)."""
-    p = oracle.aop(w)
+    p = oracle.field_poly(w)
     reds = oracle.poly_mod_vec(p, np.arange(1 << n, dtype=np.uint32))
     best = {}
     for r, u in enumerate(reds.tolist()):
@@ -48,7 +48,7 @@ def test_sparse_transform_matches_brute_force(w, n):
     assert np.array_equal(got, ref)
 
 
-@pytest.mark.parametrize("w", [2, 4, 10, 12])
+@pytest.mark.parametrize("w", [2, 4, 6, 10, 12])
 def test_planner_field_product(w):
     q = 1 << w
     rng = np.random.default_rng(w)
@@ -67,25 +67,31 @@ def test_planner_field_product(w):
 
 
 def test_field_support_matches_oracle_irreducibility():
+    # The planner accepts (w, n) by the paper's number-theoretic criteria (Sec. 2.3 for AOPs,
+    # Sec. 2.4 for ESPs); the oracle finds each field's modulus by trial division. They must agree
+    # on every pair, restricted to the ring sizes the kernels are built for.
     for w in range(2, 16):
-        supported = True
-        try:
-            h = pyrit.pyrit_plan_create(w, w + 1, 1, 1)
-            pyrit.pyrit_plan_destroy(h)
-        except pyrit.PyritError as e:
-            assert e.status == pyrit.PYRIT_E_UNSUPPORTED_FIELD
-            supported = False
-        assert supported == (oracle.aop_irreducible(w) and w + 1 in (3, 5, 11, 13)), w
+        for n in range(w + 1, 17):
+            supported = True
+            try:
+                h = pyrit.pyrit_plan_create(w, n, 1, 1)
+                pyrit.pyrit_plan_destroy(h)
+            except pyrit.PyritError as e:
+                assert e.status == pyrit.PYRIT_E_UNSUPPORTED_FIELD
+                supported = False
+            assert supported == (oracle.ring_size(w) == n and n in (3, 5, 9, 11, 13)), (w, n)
+    assert oracle.ring_size(6) == 9
 
 
-@pytest.mark.parametrize("w,k,m", [(2, 2, 2), (4, 4, 2), (10, 10, 4), (12, 16, 4), (4, 12, 4), (12, 32, 8)])
+@pytest.mark.parametrize("w,k,m", [(2, 2, 2), (4, 4, 2), (10, 10, 4), (12, 16, 4), (4, 12, 4), (12, 32, 8),
+                                   (6, 8, 4), (6, 32, 8)])
 def test_default_generator_and_encode_masks(w, k, m):
-    plan = pyrit.pyrit_plan_create(w, w + 1, k, m)
+    plan = pyrit.pyrit_plan_create(w, oracle.ring_size(w), k, m)
     try:
-        assert pyrit.pyrit_plan_info(plan) == (w, w + 1, k, m)
+        assert pyrit.pyrit_plan_info(plan) == (w, oracle.ring_size(w), k, m)
         G = pyrit.pyrit_plan_generator(plan)
         assert np.array_equal(G, oracle.cauchy(w, k, m))
-        sp = _brute_sparse(w, w + 1)
+        sp = _brute_sparse(w, oracle.ring_size(w))
         assert np.array_equal(pyrit.pyrit_plan_encode_masks(plan), sp[G[k:]].astype(np.uint16))
     finally:
         pyrit.pyrit_plan_destroy(plan)
@@ -110,10 +116,11 @@ def _oracle_decode_matrix(w, k, m, G, erasures):
     return np.array(surv), np.array(erased), np.array(rows, np.uint32).reshape(len(erased), k)
 
 
-@pytest.mark.parametrize("w,k,m,exhaustive", [(4, 4, 2, True), (10, 10, 4, False), (12, 16, 4, False)])
+@pytest.mark.parametrize("w,k,m,exhaustive", [(4, 4, 2, True), (10, 10, 4, False), (12, 16, 4, False),
+                                             (6, 8, 4, False)])
 def test_decode_masks_match_oracle(w, k, m, exhaustive):
-    plan = pyrit.pyrit_plan_create(w, w + 1, k, m)
-    sp = _brute_sparse(w, w + 1)
+    plan = pyrit.pyrit_plan_create(w, oracle.ring_size(w), k, m)
+    sp = _brute_sparse(w, oracle.ring_size(w))
     try:
         G = oracle.cauchy(w, k, m)  # the oracle's own generator (the library's is pinned equal above)
         if exhaustive:
@@ -134,7 +141,7 @@ def test_decode_masks_match_oracle(w, k, m, exhaustive):
 def test_error_codes():
     E = pyrit
     cases = [
-        (lambda: E.pyrit_plan_create(6, 7, 3, 2), E.PYRIT_E_UNSUPPORTED_FIELD),   # AOP reducible
+        (lambda: E.pyrit_plan_create(6, 7, 3, 2), E.PYRIT_E_UNSUPPORTED_FIELD),   # AOP reducible (ESP ring: n=9)
         (lambda: E.pyrit_plan_create(4, 6, 3, 2), E.PYRIT_E_UNSUPPORTED_FIELD),   # n != w+1
         (lambda: E.pyrit_plan_create(4, 5, 12, 5), E.PYRIT_E_TOO_LONG),           # k+m > 16
         (lambda: E.pyrit_plan_create(4, 5, 0, 2), E.PYRIT_E_INVALID_ARG),
@@ -150,22 +157,22 @@ def test_error_codes():
 def test_user_generator_validation():
     w, k, m = 4, 3, 2
     G = oracle.cauchy(w, k, m)
-    h = pyrit.pyrit_plan_create(w, w + 1, k, m, G)
+    h = pyrit.pyrit_plan_create(w, oracle.ring_size(w), k, m, G)
     pyrit.pyrit_plan_destroy(h)
     bad = G.copy()
     bad[0, 1] = 1  # not systematic
     with pytest.raises(pyrit.PyritError) as ei:
-        pyrit.pyrit_plan_create(w, w + 1, k, m, bad)
+        pyrit.pyrit_plan_create(w, oracle.ring_size(w), k, m, bad)
     assert ei.value.status == pyrit.PYRIT_E_NOT_MDS
     sing = G.copy()
     sing[k + 1] = sing[k]  # two equal parity rows: a singular 3x3 subset
     with pytest.raises(pyrit.PyritError) as ei:
-        pyrit.pyrit_plan_create(w, w + 1, k, m, sing)
+        pyrit.pyrit_plan_create(w, oracle.ring_size(w), k, m, sing)
     assert ei.value.status == pyrit.PYRIT_E_NOT_MDS
     big = G.copy()
     big[k, 0] = 16
     with pytest.raises(pyrit.PyritError) as ei:
-        pyrit.pyrit_plan_create(w, w + 1, k, m, big)
+        pyrit.pyrit_plan_create(w, oracle.ring_size(w), k, m, big)
     assert ei.value.status == pyrit.PYRIT_E_NOT_MDS
 
 

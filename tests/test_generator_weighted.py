@@ -23,7 +23,7 @@ def _mul(w, a, b):
 
 
 def _weight(w, u):
-    return bin(oracle.sparse_rep(w, w + 1, int(u))).count("1")
+    return bin(oracle.sparse_rep(w, oracle.ring_size(w), int(u))).count("1")
 
 
 @pytest.mark.parametrize("w,k,m", CODES)
@@ -83,7 +83,7 @@ def test_oracle_generator_decodes_every_pattern():
 
 @pytest.mark.parametrize("w,k,m", CODES)
 def test_library_generator_equals_the_oracle(w, k, m):
-    G, wts = pyrit.pyrit_generator_weighted(w, w + 1, k, m)
+    G, wts = pyrit.pyrit_generator_weighted(w, oracle.ring_size(w), k, m)
     Go, wo = oracle.cauchy_weighted(w, k, m)
     np.testing.assert_array_equal(G, Go)
     assert wts == wo

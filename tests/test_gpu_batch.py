@@ -53,14 +53,15 @@ class Pool:
 
 
 MIXED = [(4, 4, 2, 4096), (10, 10, 4, 8192), (12, 16, 4, 2048 + 16), (10, 20, 6, 1024), (12, 32, 8, 512),
-         (4, 12, 4, 1000), (2, 2, 2, 64), (12, 8, 3, 3000 + 16), (10, 4, 8, 4096 + 32), (4, 8, 8, 17)]
+         (4, 12, 4, 1000), (2, 2, 2, 64), (12, 8, 3, 3000 + 16), (10, 4, 8, 4096 + 32), (4, 8, 8, 17),
+         (6, 12, 4, 2048 + 16), (6, 20, 8, 1000)]
 
 
 def _plans(pyrit, specs):
     plans = {}
     for (w, k, m, P) in specs:
         if (w, k, m) not in plans:
-            plans[(w, k, m)] = pyrit.pyrit_plan_create(w, w + 1, k, m)
+            plans[(w, k, m)] = pyrit.pyrit_plan_create(w, oracle.ring_size(w), k, m)
     return plans
 
 
@@ -117,11 +118,12 @@ def _all_tiles(pyrit, n):
 
 
 @pytest.mark.parametrize("w,k,m,P,S", [(10, 10, 4, 4096 + 48, 6), (12, 16, 4, 2048, 5), (4, 4, 2, 8192, 4),
-                                       (2, 2, 2, 4096 + 16, 3), (12, 32, 8, 2048, 3)])
+                                       (2, 2, 2, 4096 + 16, 3), (12, 32, 8, 2048, 3), (6, 8, 4, 4096 + 48, 4),
+                                       (6, 24, 8, 2048, 3)])
 def test_every_variant_is_bit_exact(pyrit, w, k, m, P, S):
     specs = [(w, k, m, P)] * S
     pool = Pool(specs, 3)
-    plan = pyrit.pyrit_plan_create(w, w + 1, k, m)
+    plan = pyrit.pyrit_plan_create(w, oracle.ring_size(w), k, m)
     try:
         G = oracle.cauchy(w, k, m)
         full = []
@@ -130,7 +132,7 @@ def test_every_variant_is_bit_exact(pyrit, w, k, m, P, S):
             full.append(np.concatenate([data, oracle.encode(w, k, m, G, data, nthreads=NCPU)]))
         rng = np.random.default_rng(w)
         pats = [sum(1 << int(x) for x in rng.choice(k + m, m, replace=False)) for _ in range(S)]
-        for t in _all_tiles(pyrit, w + 1):
+        for t in _all_tiles(pyrit, oracle.ring_size(w)):
             for i in range(S):
                 arr = full[i].copy()
                 arr[k:] = 0
@@ -183,7 +185,7 @@ def test_autotune_keeps_results_and_records_choice(pyrit, tmp_path):
     w, k, m, P, S = 10, 10, 4, 8192, 8
     specs = [(w, k, m, P)] * S
     pool = Pool(specs, 11)
-    plan = pyrit.pyrit_plan_create(w, w + 1, k, m)
+    plan = pyrit.pyrit_plan_create(w, oracle.ring_size(w), k, m)
     try:
         G = oracle.cauchy(w, k, m)
         full = []

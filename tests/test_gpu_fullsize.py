@@ -38,7 +38,7 @@ def _full_size(pyrit, w, k, m, P, S, seed, pats_fn, sample, tune):
               for s in range(S)]
     rng = np.random.default_rng(seed)
     pats = pats_fn(rng, S)
-    plan = pyrit.pyrit_plan_create(w, w + 1, k, m)
+    plan = pyrit.pyrit_plan_create(w, oracle.ring_size(w), k, m)
     G = oracle.cauchy(w, k, m)
     stream = torch.cuda.Stream()
     try:

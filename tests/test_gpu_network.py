@@ -42,7 +42,7 @@ class Stripes:
         self.buf = torch.zeros(count * self.stride, dtype=torch.uint8, device="cuda")
         # the oracle's own generator; the library plan is built from the same matrix
         self.G = oracle.cauchy_weighted(w, k, m)[0] if weighted else oracle.cauchy(w, k, m)
-        self.plan = pyrit.pyrit_plan_create(w, w + 1, k, m, self.G if weighted else None)
+        self.plan = pyrit.pyrit_plan_create(w, oracle.ring_size(w), k, m, self.G if weighted else None)
         self.data = [synth_bytes(seed + s, 0, k * w * P).reshape(k, w, P) for s in range(count)]
         for s in range(count):
             self.view(s)[:k * w * P].copy_(torch.from_numpy(self.data[s].reshape(-1)).cuda())
@@ -83,7 +83,8 @@ def _encode_batch_matches(pyrit, st, tile=None, graph=False, expect_network=True
 
 # P values: several tiles per stripe with a ragged last tile (tile widths are 1-6 KiB)
 @pytest.mark.parametrize("w,k,m,P,count", [(10, 10, 4, 8192 + 16, 5), (12, 16, 4, 4096 + 48, 3), (4, 8, 8, 6000 + 16, 3),
-                                           (2, 2, 2, 2048 + 32, 4), (10, 32, 8, 1024 + 16, 2), (12, 5, 1, 4096, 3)])
+                                           (2, 2, 2, 2048 + 32, 4), (10, 32, 8, 1024 + 16, 2), (12, 5, 1, 4096, 3),
+                                           (6, 8, 4, 8192 + 16, 4), (6, 32, 8, 1024 + 16, 2)])
 def test_network_batch_encode_all_fields(pyrit, jit_mode, w, k, m, P, count):
     st = Stripes(pyrit, w, k, m, P, count, 0x4E00 + w * 100 + k)
     try:
@@ -275,7 +276,8 @@ def _random_patterns(rng, count, k, m):
 
 
 @pytest.mark.parametrize("w,k,m,P,count", [(10, 10, 4, 8192 + 16, 24), (12, 16, 4, 4096 + 32, 12), (4, 4, 2, 2048, 16),
-                                           (10, 24, 8, 1024 + 16, 10), (2, 2, 2, 512, 8)])
+                                           (10, 24, 8, 1024 + 16, 10), (2, 2, 2, 512, 8), (6, 12, 4, 4096 + 16, 12),
+                                           (6, 24, 8, 1024 + 16, 8)])
 def test_syndrome_network_mixed_patterns(pyrit, jit_mode, w, k, m, P, count):
     """Every stripe has its own random erasure pattern: the batch runs the plan's syndrome network."""
     rng = np.random.default_rng(0x5E + w + k)

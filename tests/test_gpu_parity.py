@@ -68,7 +68,7 @@ class Stripe:
 
 
 def _encode_case(pyrit, w, k, m, P, seed, misalign=0):
-    plan = pyrit.pyrit_plan_create(w, w + 1, k, m)
+    plan = pyrit.pyrit_plan_create(w, oracle.ring_size(w), k, m)
     try:
         G = oracle.cauchy(w, k, m)
         data = synth_bytes(seed, 0, k * w * P).reshape(k, w, P)
@@ -90,7 +90,7 @@ def _encode_case(pyrit, w, k, m, P, seed, misalign=0):
 # The three single-stripe workloads (GF(16) k=4 m=2 P=256 KiB; GF(2^10) k=10 m=4 P=64 KiB;
 # GF(2^12) k=16 m=4 P=32 KiB) plus GF(4), at their packet sizes (every tile full).
 @pytest.mark.parametrize("w,k,m,P", [(4, 4, 2, 256 * 1024), (10, 10, 4, 64 * 1024), (12, 16, 4, 32 * 1024),
-                                     (2, 2, 2, 8192)])
+                                     (2, 2, 2, 8192), (6, 8, 4, 64 * 1024)])
 def test_encode_workload_shapes(pyrit, w, k, m, P):
     _encode_case(pyrit, w, k, m, P, BASE_SEED + w)
 
@@ -98,13 +98,13 @@ def test_encode_workload_shapes(pyrit, w, k, m, P):
 # Ragged tails of the staged kernel (multiples of 16 that leave a partial last tile) and odd packet
 # sizes of the plain-load kernel.
 @pytest.mark.parametrize("P", [16, 48, 1040, 2064, 4096 + 1024 + 16, 65536 + 16])
-@pytest.mark.parametrize("w,k,m", [(4, 4, 2), (10, 10, 4), (12, 16, 4)])
+@pytest.mark.parametrize("w,k,m", [(4, 4, 2), (10, 10, 4), (12, 16, 4), (6, 8, 4)])
 def test_encode_ragged_tiles(pyrit, w, k, m, P):
     _encode_case(pyrit, w, k, m, P, 1000 + P + w)
 
 
 @pytest.mark.parametrize("P", [1, 3, 15, 17, 1000, 4097])
-@pytest.mark.parametrize("w,k,m", [(4, 4, 2), (10, 10, 4), (12, 16, 4)])
+@pytest.mark.parametrize("w,k,m", [(4, 4, 2), (10, 10, 4), (12, 16, 4), (6, 8, 4)])
 def test_encode_odd_packet_sizes(pyrit, w, k, m, P):
     _encode_case(pyrit, w, k, m, P, 2000 + P + w)
 
@@ -114,14 +114,14 @@ def test_encode_unaligned_pointers(pyrit, misalign):
     _encode_case(pyrit, 10, 10, 4, 4096, 77, misalign=misalign)
 
 
-@pytest.mark.parametrize("w,k,m", [(4, 4, 1), (4, 1, 2), (12, 32, 8), (10, 20, 6), (4, 8, 8)])
+@pytest.mark.parametrize("w,k,m", [(4, 4, 1), (4, 1, 2), (12, 32, 8), (10, 20, 6), (4, 8, 8), (6, 32, 8), (6, 1, 2)])
 def test_encode_extreme_shapes(pyrit, w, k, m):
     _encode_case(pyrit, w, k, m, 2048 + 32, 3000 + k * 10 + m)
 
 
 def test_encode_zero_and_ones(pyrit):
     w, k, m, P = 10, 10, 4, 4096
-    plan = pyrit.pyrit_plan_create(w, w + 1, k, m)
+    plan = pyrit.pyrit_plan_create(w, oracle.ring_size(w), k, m)
     try:
         G = oracle.cauchy(w, k, m)
         for fill in (0x00, 0xFF):
@@ -149,7 +149,7 @@ def test_decode_all_patterns_gf16_full_size(pyrit):
     # GF(16), k=4, m=2, P = 256 KiB: every pattern of <= 2 erasures (22 patterns).
     w, k, m, P = 4, 4, 2, 256 * 1024
     _, full = _encode_case(pyrit, w, k, m, P, BASE_SEED)
-    plan = pyrit.pyrit_plan_create(w, w + 1, k, m)
+    plan = pyrit.pyrit_plan_create(w, oracle.ring_size(w), k, m)
     try:
         n = 0
         for e in range(1, m + 1):
@@ -165,7 +165,7 @@ def test_decode_all_patterns_gf1024_small(pyrit):
     # k=10, m=4: all 1470 patterns of 1..4 erasures on a two-tile stripe with a ragged tail.
     w, k, m, P = 10, 10, 4, 2048 + 48
     _, full = _encode_case(pyrit, w, k, m, P, 99)
-    plan = pyrit.pyrit_plan_create(w, w + 1, k, m)
+    plan = pyrit.pyrit_plan_create(w, oracle.ring_size(w), k, m)
     try:
         for e in range(1, m + 1):
             for c in itertools.combinations(range(k + m), e):
@@ -174,11 +174,29 @@ def test_decode_all_patterns_gf1024_small(pyrit):
         pyrit.pyrit_plan_destroy(plan)
 
 
+def test_decode_all_patterns_gf64_small(pyrit):
+    # GF(2^6) from x^6 + x^3 + 1 on R_{2,9} (Sec. 2.4), k=8, m=4: all 793 patterns of 1..4 erasures
+    # on a two-tile stripe with a ragged tail.
+    w, k, m, P = 6, 8, 4, 2048 + 48
+    _, full = _encode_case(pyrit, w, k, m, P, 98)
+    plan = pyrit.pyrit_plan_create(w, oracle.ring_size(w), k, m)
+    try:
+        n = 0
+        for e in range(1, m + 1):
+            for c in itertools.combinations(range(k + m), e):
+                _decode_check(pyrit, plan, full, sum(1 << x for x in c), w, k, m, P)
+                n += 1
+        assert n == 793
+    finally:
+        pyrit.pyrit_plan_destroy(plan)
+
+
 @pytest.mark.parametrize("w,k,m,P,npat", [(10, 10, 4, 64 * 1024, 12), (12, 16, 4, 32 * 1024, 12),
-                                          (12, 32, 8, 4096, 8), (4, 12, 4, 1000, 6)])
+                                          (12, 32, 8, 4096, 8), (4, 12, 4, 1000, 6), (6, 20, 8, 4096, 10),
+                                          (6, 8, 4, 64 * 1024, 8)])
 def test_decode_random_patterns(pyrit, w, k, m, P, npat):
     _, full = _encode_case(pyrit, w, k, m, P, 500 + w + k)
-    plan = pyrit.pyrit_plan_create(w, w + 1, k, m)
+    plan = pyrit.pyrit_plan_create(w, oracle.ring_size(w), k, m)
     rng = np.random.default_rng(P + k)
     try:
         for _ in range(npat):
@@ -194,7 +212,7 @@ def test_decode_random_patterns(pyrit, w, k, m, P, npat):
 def test_decode_unaligned(pyrit):
     w, k, m, P = 10, 10, 4, 1000
     _, full = _encode_case(pyrit, w, k, m, P, 7)
-    plan = pyrit.pyrit_plan_create(w, w + 1, k, m)
+    plan = pyrit.pyrit_plan_create(w, oracle.ring_size(w), k, m)
     try:
         _decode_check(pyrit, plan, full, 0b1011, w, k, m, P, misalign=3)
     finally:

@@ -44,7 +44,7 @@ class PtStripes:
         self.stride = ((k + m) * w * P + 255) // 256 * 256
         self.buf = torch.zeros(count * self.stride, dtype=torch.uint8, device="cuda")
         self.G = oracle.cauchy_weighted(w, k, m)[0] if weighted else oracle.cauchy(w, k, m)
-        self.plan = pyrit.pyrit_plan_create(w, w + 1, k, m, self.G if weighted else None)
+        self.plan = pyrit.pyrit_plan_create(w, oracle.ring_size(w), k, m, self.G if weighted else None)
         assert pyrit.pyrit_plan_set_transform(self.plan, pyrit.PYRIT_TRANSFORM_PARITY) == pyrit.PYRIT_TRANSFORM_PARITY
         self.data = [synth_bytes(seed + s, 0, k * w * P).reshape(k, w, P) for s in range(count)]
         self._full = [None] * count
@@ -82,7 +82,8 @@ def _random_patterns(rng, count, k, m):
 
 
 @pytest.mark.parametrize("w,k,m,P,count", [(10, 10, 4, 8192 + 16, 4), (12, 16, 4, 4096 + 48, 3), (4, 8, 8, 6000 + 16, 3),
-                                           (2, 2, 2, 2048 + 32, 4), (10, 32, 8, 1024 + 16, 2), (4, 2, 6, 3072, 3)])
+                                           (2, 2, 2, 2048 + 32, 4), (10, 32, 8, 1024 + 16, 2), (4, 2, 6, 3072, 3),
+                                           (6, 8, 4, 4096 + 16, 3), (6, 2, 6, 2048, 3)])
 def test_parity_transform_batch_encode(pyrit, jit_mode, w, k, m, P, count):
     st = PtStripes(pyrit, w, k, m, P, count, 0x9700 + w * 100 + k)
     try:
@@ -124,7 +125,8 @@ def _decode_batch(pyrit, st, pats, expect_mode, graph=False, tune=False):
 
 
 @pytest.mark.parametrize("w,k,m,P,count", [(10, 10, 4, 8192 + 16, 16), (12, 16, 4, 4096 + 32, 10), (4, 4, 2, 2048, 12),
-                                           (10, 24, 8, 1024 + 16, 8), (2, 2, 2, 512, 8), (4, 2, 6, 1024 + 16, 8)])
+                                           (10, 24, 8, 1024 + 16, 8), (2, 2, 2, 512, 8), (4, 2, 6, 1024 + 16, 8),
+                                           (6, 12, 4, 2048 + 16, 10), (6, 4, 8, 1024, 8)])
 def test_parity_transform_mixed_pattern_decode(pyrit, jit_mode, w, k, m, P, count):
     """Every stripe has its own pattern: the plan's syndrome network under the parity transform."""
     rng = np.random.default_rng(0x97DE + w + k)

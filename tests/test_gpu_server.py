@@ -103,7 +103,7 @@ def test_alone_equals_mix(pyrit):
 def test_admission_respects_budget(pyrit):
     w, k, m, P = 12, 16, 4, 64 * 1024
     one = (k + m) * w * P
-    plan = pyrit.pyrit_plan_create(w, w + 1, k, m)
+    plan = pyrit.pyrit_plan_create(w, oracle.ring_size(w), k, m)
     buf = torch.zeros(12 * one, dtype=torch.uint8, device="cuda")
     srv = pyrit.pyrit_server_create(3 * one, max_batch=8, slots=4)
     try:
@@ -122,7 +122,7 @@ def test_admission_respects_budget(pyrit):
 def test_invalid_requests_refused_before_work(pyrit):
     w, k, m, P = 4, 4, 2, 4096
     one = (k + m) * w * P
-    plan = pyrit.pyrit_plan_create(w, w + 1, k, m)
+    plan = pyrit.pyrit_plan_create(w, oracle.ring_size(w), k, m)
     buf = torch.zeros(2 * one, dtype=torch.uint8, device="cuda")
     srv = pyrit.pyrit_server_create(one, max_batch=4, slots=2)
     try:
@@ -146,7 +146,7 @@ def test_drain_wait_is_bounded(pyrit):
     # PYRIT_E_TIMEOUT (the work continues and a later drain completes it).
     w, k, m, P = 12, 16, 4, 1 << 20
     one = (k + m) * w * P
-    plan = pyrit.pyrit_plan_create(w, w + 1, k, m)
+    plan = pyrit.pyrit_plan_create(w, oracle.ring_size(w), k, m)
     buf = torch.zeros(one, dtype=torch.uint8, device="cuda")
     srv = pyrit.pyrit_server_create(2 * one, max_batch=4, slots=1)
     try:

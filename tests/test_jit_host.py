@@ -36,13 +36,19 @@ def _parse(src):
             a = b
         if a:
             assert cur is not None
-            # d[q][x] is packet q of the source; dp[x] (the parity transform's padding packet, the
-            # XOR of the source's packets) is recorded as q = -1
-            qs = [int(q) if q else -1 for q in re.findall(r"d(?:\[(\d+)\]|p)\[x\]", a.groups()[-1])]
+            # d[q][x] is packet q of the source; dp[j][x] (the parity transform's padding packet j,
+            # the parity of the source's interleaved word j) is recorded as q = -1 - j
+            qs = [int(q) if q else -1 - int(p) for q, p in
+                  re.findall(r"d(?:\[(\d+)\]|p\[(\d+)\])\[x\]", a.groups()[-1])]
             cases[cur].append((int(a.group(1)), int(a.group(2)), qs))
         if "} break;" in line:
             cur = None
     return dict(nin=nin, n=n, words=words, mg=mg, nc=nc, cases=cases)
+
+
+def _w_of(n):
+    """The field degree the oracle carries on R_{2,n} (n - 1 for an AOP, 6 for n = 9)."""
+    return next(w for w in range(2, 16) if oracle.ring_size(w) == n)
 
 
 def _ring_columns(entries, ii, n, w):
@@ -63,7 +69,7 @@ def _ring_columns(entries, ii, n, w):
 def _check_network(src, masks, n):
     """masks[o][j]: the table the source was generated for. Every (j, o) must be covered once."""
     net = _parse(src)
-    w = n - 1
+    w = _w_of(n)
     nout, nin = masks.shape
     assert net["n"] == n and net["nin"] == nin
     mg = net["mg"]
@@ -86,13 +92,13 @@ def _check_network(src, masks, n):
 def _oracle_parity_masks(w, k, m):
     G = oracle.cauchy(w, k, m)
     C = G[k:]
-    masks = np.array([[oracle.sparse_rep(w, w + 1, int(C[o][j])) for j in range(k)] for o in range(m)], np.uint16)
+    masks = np.array([[oracle.sparse_rep(w, oracle.ring_size(w), int(C[o][j])) for j in range(k)] for o in range(m)], np.uint16)
     return C, masks
 
 
-@pytest.mark.parametrize("w,k,m", [(10, 10, 4), (12, 16, 4), (4, 8, 8), (2, 1, 2), (10, 32, 8)])
+@pytest.mark.parametrize("w,k,m", [(10, 10, 4), (12, 16, 4), (4, 8, 8), (2, 1, 2), (10, 32, 8), (6, 8, 4), (6, 32, 8)])
 def test_generated_network_is_the_field_product(w, k, m):
-    n = w + 1
+    n = oracle.ring_size(w)
     C, masks = _oracle_parity_masks(w, k, m)
     net = _check_network(pyrit.pyrit_jit_source(n, masks), masks, n)
     # phi_E^{-1} of the ring columns gives the field product by the Cauchy coefficient
@@ -103,12 +109,11 @@ def test_generated_network_is_the_field_product(w, k, m):
             if o >= m:
                 continue
             for q, col in enumerate(_ring_columns(entries, ii, n, w)):
-                top = (col >> w) & 1
-                field = (col ^ (((1 << n) - 1) if top else 0)) & ((1 << w) - 1)
+                field = oracle.poly_mod(col, oracle.field_poly(w))
                 assert field == oracle.gf_mul_slow(w, int(C[o][j]), 1 << q)
 
 
-@pytest.mark.parametrize("n", [3, 5, 11, 13])
+@pytest.mark.parametrize("n", [3, 5, 9, 11, 13])
 def test_generated_network_random_masks_and_shapes(n):
     rng = np.random.default_rng(1000 + n)
     shapes = [None, {"mg": 0, "nc": 16}, {"words": 2, "nc": 8}]
@@ -153,7 +158,7 @@ def test_jit_mode_roundtrip():
 
 @pytest.mark.parametrize("w,k,m", [(2, 1, 2), (4, 8, 4), (10, 10, 4), (12, 16, 4)])
 def test_runtime_compiler_builds_networks_without_a_device(w, k, m):
-    plan = pyrit.pyrit_plan_create(w, w + 1, k, m)
+    plan = pyrit.pyrit_plan_create(w, oracle.ring_size(w), k, m)
     try:
         before = pyrit.pyrit_jit_stats()
         pyrit.pyrit_plan_specialise(plan)
@@ -193,7 +198,7 @@ def test_syndrome_tables_rebuild_every_erasure_pattern(w, k, m):
     rng = np.random.default_rng(77 + w * k + m)
     G = oracle.cauchy(w, k, m)
     C = G[k:]
-    plan = pyrit.pyrit_plan_create(w, w + 1, k, m)
+    plan = pyrit.pyrit_plan_create(w, oracle.ring_size(w), k, m)
     try:
         patterns = []
         for e in range(1, m + 1):
@@ -237,34 +242,36 @@ def test_syndrome_tables_rebuild_every_erasure_pattern(w, k, m):
 
 
 def _psi(w, d):
-    """phi_P(d) mod p (Sec. 2.3.1): every coefficient of d flipped by its parity bit."""
-    return d ^ ((1 << w) - 1 if bin(d).count("1") & 1 else 0)
+    """phi_P(d) mod the field's modulus (Sec. 2.3.1, Sec. 2.4.1), from the oracle."""
+    return oracle.poly_mod(oracle.phi_P(w, oracle.ring_size(w), d), oracle.field_poly(w))
 
 
 def _parity_columns(entries, ii, n, w):
-    """Ring rows of output slot ii for each basis source x^q under the parity transform: the
-    source's padding packet (its parity) is 1 for every basis vector."""
+    """Ring rows of output slot ii for each basis source x^q under the parity transform: padding
+    packet j (the parity of the source's interleaved word j, coefficients j, j + S, ...) is 1 for
+    the basis vector x^q exactly when q = j mod S, S = n - w."""
+    S = n - w
     cols = []
     for q in range(w):
         acc = 0
         for (i, t, qs) in entries:
             if i != ii:
                 continue
-            assert t < w, "the parity transform drops the top ring row: it must not be accumulated"
+            assert t < w, "the parity transform drops the top ring rows: they must not be accumulated"
             for qq in qs:
-                assert -1 <= qq < w
-                if qq == q or qq == -1:
+                assert -S <= qq < w
+                if qq == q or qq == -1 - q % S:
                     acc ^= 1 << t
         cols.append(acc)
     return cols
 
 
-@pytest.mark.parametrize("w,k,m", [(10, 10, 4), (12, 16, 4), (4, 8, 8), (2, 1, 2), (10, 32, 8)])
+@pytest.mark.parametrize("w,k,m", [(10, 10, 4), (12, 16, 4), (4, 8, 8), (2, 1, 2), (10, 32, 8), (6, 8, 4), (6, 20, 8)])
 def test_generated_parity_network_is_the_conjugated_field_product(w, k, m):
     """Under the parity transform the network of mask r maps a source d to the low w coefficients
     of r * phi_P(d) in R_{2,n} (phi_P pads d with its parity bit, phi_P^{-1} drops the top one);
     that is psi(u * psi(d)) for the field coefficient u, psi(d) = phi_P(d) mod p."""
-    n = w + 1
+    n = oracle.ring_size(w)
     C, masks = _oracle_parity_masks(w, k, m)
     net = _parse(pyrit.pyrit_jit_source(n, masks, None, pyrit.PYRIT_TRANSFORM_PARITY))
     assert net["n"] == n and net["nin"] == k
@@ -278,16 +285,16 @@ def test_generated_parity_network_is_the_conjugated_field_product(w, k, m):
                 continue
             seen.add((j, o))
             for q, col in enumerate(_parity_columns(entries, ii, n, w)):
-                ring = oracle.ring_mul(n, int(masks[o][j]), (1 << q) | (1 << w)) & ((1 << w) - 1)
+                ring = oracle.ring_mul(n, int(masks[o][j]), oracle.phi_P(w, n, 1 << q)) & ((1 << w) - 1)
                 assert col == ring, (case, ii, q)
                 assert col == _psi(w, oracle.gf_mul_slow(w, int(C[o][j]), _psi(w, 1 << q)))
     assert seen == {(j, o) for j in range(k) for o in range(m)}
 
 
-@pytest.mark.parametrize("n", [3, 5, 11, 13])
+@pytest.mark.parametrize("n", [3, 5, 9, 11, 13])
 def test_generated_parity_network_random_masks(n):
     rng = np.random.default_rng(2000 + n)
-    w = n - 1
+    w = _w_of(n)
     for trial in range(4):
         nin = int(rng.integers(1, 33))
         nout = int(rng.integers(1, 9))
@@ -302,7 +309,7 @@ def test_generated_parity_network_random_masks(n):
                 if o >= nout:
                     continue
                 for q, col in enumerate(_parity_columns(entries, ii, n, w)):
-                    assert col == oracle.ring_mul(n, int(masks[o][j]), (1 << q) | (1 << w)) & ((1 << w) - 1)
+                    assert col == oracle.ring_mul(n, int(masks[o][j]), oracle.phi_P(w, n, 1 << q)) & ((1 << w) - 1)
 
 
 def test_plan_transform_setting():
