@@ -72,11 +72,18 @@ typedef struct CUstream_st* pyrit_stream_t;
 #define PYRIT_E_JIT -12               /* run-time compilation or loading of a plan-specialised
                                          network failed (pyrit_jit_log has the compiler's log)  */
 #define PYRIT_E_UNSUPPORTED -13       /* the request needs a path this build does not provide for
-                                         it (the parity transform outside generated networks)   */
+                                         it: the parity transform outside generated networks, or
+                                         a stripe of several jobs (more than PYRIT_JOB_OUTPUTS
+                                         parity or erased blocks) in the server or the
+                                         allocation-free entry point                             */
 
 /* Limits of this build. */
-#define PYRIT_MAX_K 32 /* data blocks per stripe                   */
-#define PYRIT_MAX_M 8  /* parity blocks per stripe                 */
+#define PYRIT_MAX_K 64      /* data blocks per stripe                                     */
+#define PYRIT_MAX_M 63      /* parity blocks per stripe                                   */
+#define PYRIT_MAX_BLOCKS 64 /* k + m (erasure patterns are 64-bit masks)                  */
+#define PYRIT_JOB_OUTPUTS 8 /* outputs one coding job writes: a stripe with more parity (or
+                               erased) blocks is coded as ceil(count / 8) jobs that read the
+                               same sources                                               */
 
 /* Operations. */
 #define PYRIT_OP_ENCODE 0
@@ -96,7 +103,7 @@ typedef struct pyrit_plan_s* pyrit_plan_t;
  *          n = s (r + 1), irreducible by the criterion Sec. 2.4 quotes. The kernels are built for
  *          (w, n) in {(2, 3), (4, 5), (6, 9), (10, 11), (12, 13)}; (6, 9) is GF(2^6) from
  *          x^6 + x^3 + 1.
- *   k, m : 1 <= k <= PYRIT_MAX_K, 0 <= m <= PYRIT_MAX_M.
+ *   k, m : 1 <= k <= PYRIT_MAX_K, 0 <= m <= PYRIT_MAX_M, k + m <= PYRIT_MAX_BLOCKS.
  *   G    : NULL for the default generator [I_k ; C], C[i][j] = 1/(x_i + y_j) with x_i = k+i,
  *          y_j = j (a Cauchy matrix, Sec. 3 "generalized Cauchy matrices"; requires
  *          k + m <= 2^w), or a host array of (k+m)*k uint32 entries, row-major, whose top k rows
@@ -157,7 +164,7 @@ PYRIT_API int pyrit_plan_decode_masks(pyrit_plan_t plan, uint64_t erasures, int*
                             int* erased_out, uint16_t* masks_out, int* ne_out);
 
 /* The syndrome form of the decoding for an erasure pattern (used by the plan's syndrome-decode
- * network; requires k + m <= PYRIT_MAX_K). With U the first a surviving parity rows (a = erased
+ * network; requires m <= PYRIT_JOB_OUTPUTS). With U the first a surviving parity rows (a = erased
  * data blocks) and, for parity row r, acc_r = (sum of C[r][j] d_j over surviving data j) + p_r
  * when r is in U, every erased block (ascending, as in pyrit_plan_decode_masks) is a sum of the
  * rows' values: output o = acc_{base-1} (when base = syn_out[8*8 + o] > 0: an erased parity block
@@ -309,7 +316,7 @@ PYRIT_API int pyrit_jit_mode(int mode);
 
 /* Compiles (host only, no device call) the network of a plan's encode (op PYRIT_OP_ENCODE), of
  * its decode for one erasure pattern (PYRIT_OP_DECODE), or its syndrome-decode network, which
- * serves every erasure pattern (PYRIT_OP_DECODE_ANY; requires k + m <= PYRIT_MAX_K), into the
+ * serves every erasure pattern (PYRIT_OP_DECODE_ANY; requires m <= PYRIT_JOB_OUTPUTS), into the
  * cache, so that later calls find it.
  * tile: NULL for the default shape, else its words, mg, minb and nc (0 = default) select one.
  * PYRIT_OK (also when there is nothing to code), a planning error, or PYRIT_E_JIT. */
@@ -414,7 +421,7 @@ PYRIT_API void pyrit_server_destroy(pyrit_server_t server);
  * or a latency-bound path that cannot take cudaMalloc's implicit device synchronisation.
  *
  * Scratch. The job descriptors, the tile list and two status words live in one fixed file-scope
- * device array of 340 KiB (256 + PYRIT_NOALLOC_MAX_STRIPES * 848 + PYRIT_NOALLOC_MAX_TILES * 8
+ * device array of 532 KiB (256 + PYRIT_NOALLOC_MAX_STRIPES * 1616 + PYRIT_NOALLOC_MAX_TILES * 8
  * bytes) inside the library's module image: every GPU that loads the library holds it until the
  * process exits. The caller passes every input and output buffer; no cudaMalloc, cudaFree or other
  * allocating routine is called (on the host, a decoding matrix for an erasure pattern that a plan has

@@ -23,8 +23,8 @@ struct Group {
   uint32_t njobs = 0, ntiles = 0, tiles_per_job = 0;
   int max_nout = 0;
   TuneKey key;
-  bool netable = false;  // every job has the same nin, nout and masks: a generated network applies
-  JobDesc job0{};        // host copy of the group's first job (its mask table)
+  bool netable = false;         // the jobs share nin and use at most kMaxJobs tables: a network applies
+  std::vector<JobDesc> tables;  // one job per distinct (nout, mask table), in the order jobs use them
   const pyrit_plan_s* syn_plan = nullptr;  // all jobs decode this plan: its syndrome network applies
   size_t syn_off = 0;                      // the syndrome-form jobs in the device allocation
   int transform = PYRIT_TRANSFORM_EMBEDDING;  // the group's stripes all use this transform
@@ -140,26 +140,32 @@ int pyrit_batch_create(const pyrit_stripe_t* stripes, int count, const pyrit_til
   std::vector<std::vector<JobDesc>> by_n(32);
   std::vector<std::vector<int>> src_of(32);
   for (int i = 0; i < count; ++i) {
-    JobDesc job;
+    JobDesc jobs[kMaxJobs];
+    int nj = 0;
     uint64_t alg = 0, src = 0;
-    const int rc = stripe_job(stripes[i], &job, &alg, &src);
+    const int rc = stripe_jobs(stripes[i], jobs, &nj, &alg, &src);
     if (rc != PYRIT_OK) {
       delete b;
       return rc;
     }
     b->src_bytes += src;
-    if (job.nout == 0) continue;
+    if (nj == 0) continue;
     b->alg_bytes += alg;
     const int n = stripes[i].plan->n;
     const bool parity = stripes[i].plan->transform == PYRIT_TRANSFORM_PARITY;
-    if (job_is_staged(job)) {
-      by_n[n + (parity ? 16 : 0)].push_back(job);
-      src_of[n + (parity ? 16 : 0)].push_back(i);
-    } else if (parity) {  // the plain-load kernel has no parity transform
-      delete b;
-      return PYRIT_E_UNSUPPORTED;
-    } else
-      b->plain.emplace_back(n, job);
+    // a stripe's jobs (one per group of up to kMaxOut outputs) stay adjacent in the group, so
+    // that their tiles, which read the same source columns, run close together and share L2
+    for (int q = 0; q < nj; ++q) {
+      if (job_is_staged(jobs[q])) {
+        by_n[n + (parity ? 16 : 0)].push_back(jobs[q]);
+        src_of[n + (parity ? 16 : 0)].push_back(i);
+      } else if (parity) {  // the plain-load kernel has no parity transform
+        delete b;
+        return PYRIT_E_UNSUPPORTED;
+      } else {
+        b->plain.emplace_back(n, jobs[q]);
+      }
+    }
   }
 
   // Shapes, tile lists and the device image.
@@ -184,15 +190,29 @@ int pyrit_batch_create(const pyrit_stripe_t* stripes, int count, const pyrit_til
       same_p = same_p && j.P == jobs[0].P;
       shared = shared && std::memcmp(j.mask, jobs[0].mask, sizeof(j.mask)) == 0;
     }
-    bool same_io = true;
-    for (const JobDesc& j : jobs) same_io = same_io && j.nin == jobs[0].nin && j.nout == jobs[0].nout;
+    // Distinct tables (nout and masks): a generated network holds up to kMaxJobs of them (the
+    // output groups of wide stripes), and each job carries its table's index.
+    bool same_in = true;
+    for (JobDesc& j : jobs) {
+      same_in = same_in && j.nin == jobs[0].nin;
+      int t = 0;
+      while (t < (int)g.tables.size() &&
+             !(g.tables[t].nout == j.nout && std::memcmp(g.tables[t].mask, j.mask, sizeof(j.mask)) == 0))
+        ++t;
+      if (t == (int)g.tables.size() && (int)g.tables.size() <= kMaxJobs) g.tables.push_back(j);
+      j.table = t < kMaxJobs ? t : 0;
+    }
     g.max_nout = max_nout;
     g.key = TuneKey{n, shared ? 1 : 0, max_nout, same_p ? log2_floor(jobs[0].P) : -1};
-    g.netable = shared && same_io;
-    g.job0 = jobs[0];
+    g.netable = same_in && (int)g.tables.size() <= kMaxJobs;
+    std::vector<const JobDesc*> tptr;
+    for (const JobDesc& t : g.tables) tptr.push_back(&t);
+    auto table_spec = [&](int words, int mg, int minb, int nc) {
+      return net_spec_tables(n, tptr.data(), (int)tptr.size(), words, mg, minb, nc, g.transform);
+    };
     // Syndrome decoding: every job decodes a stripe of one plan whose columns fit a job.
     const pyrit_plan_s* plan0 = stripes[src_of[slot][0]].plan;
-    bool syn = plan0->k + plan0->m <= kMaxIn;
+    bool syn = plan0->k + plan0->m <= kMaxIn && plan0->m <= kMaxOut;  // one decode job per stripe
     for (int si : src_of[slot]) syn = syn && stripes[si].op == PYRIT_OP_DECODE && stripes[si].plan == plan0;
     std::vector<JobDesc> syn_jobs;
     if (syn) {
@@ -208,6 +228,9 @@ int pyrit_batch_create(const pyrit_stripe_t* stripes, int count, const pyrit_til
       }
     }
     if (syn) g.syn_plan = plan0;
+    // Decodes of several patterns of one plan take its syndrome network, compiled once per plan; a
+    // multi-table direct network would be compiled again for every new set of patterns.
+    if (g.syn_plan && g.tables.size() > 1) g.netable = false;
     const bool jit_on = jit_mode() != PYRIT_JIT_OFF;
     const Variant* v = nullptr;
     ShapeHint sh_hint = hint;
@@ -223,7 +246,7 @@ int pyrit_batch_create(const pyrit_stripe_t* stripes, int count, const pyrit_til
       if (tv.dispatch != PYRIT_DISPATCH_NETWORK) {
         if (!parity) v = find_variant(n, tv.words, tv.dispatch, tv.mg, tv.minb, tv.nc);
       } else if (g.netable && jit_on)
-        v = net_variant(net_spec(n, jobs[0], tv.words, tv.mg, tv.minb, tv.nc, g.transform), true);
+        v = net_variant(table_spec(tv.words, tv.mg, tv.minb, tv.nc), true);
       else if (g.syn_plan && jit_on)
         v = net_variant(net_spec_syndrome(g.syn_plan, tv.words, tv.minb, tv.nc), true);
     }
@@ -235,7 +258,7 @@ int pyrit_batch_create(const pyrit_stripe_t* stripes, int count, const pyrit_til
         return PYRIT_E_INVALID_ARG;
       }
       if (jit_on)
-        v = g.netable ? net_variant(net_spec(n, jobs[0], hint.words, hint.mg, hint.minb, hint.nc, g.transform), true)
+        v = g.netable ? net_variant(table_spec(hint.words, hint.mg, hint.minb, hint.nc), true)
                       : net_variant(net_spec_syndrome(g.syn_plan, hint.words, hint.minb, hint.nc), true);
       if (!v) {
         delete b;
@@ -246,7 +269,7 @@ int pyrit_batch_create(const pyrit_stripe_t* stripes, int count, const pyrit_til
       sh_hint = ShapeHint();
       // a failure leaves the generic kernel (under the parity transform: an error)
       if (g.netable)
-        v = net_variant(net_spec(n, jobs[0], 0, 0, 0, 0, g.transform), true);
+        v = net_variant(table_spec(0, 0, 0, 0), true);
       else if (g.syn_plan)
         v = net_variant(net_spec_syndrome(g.syn_plan, 0, 0, 0), true);
     }
@@ -341,9 +364,12 @@ int pyrit_batch_tune(pyrit_batch_t b, pyrit_stream_t stream, int iters) {
     if (g.netable && jit_mode() != PYRIT_JIT_OFF) {
       // the network shapes, compiled side by side (host threads) before they are loaded and timed
       NetSpec specs[8];
-      const int ns = net_candidate_shapes(g.key.n, g.job0.nout, specs, 8);
+      const int ns = net_candidate_shapes(g.key.n, g.max_nout, specs, 8);
+      std::vector<const JobDesc*> tptr;
+      for (const JobDesc& t : g.tables) tptr.push_back(&t);
       for (int i = 0; i < ns; ++i)
-        specs[i] = net_spec(g.key.n, g.job0, specs[i].words, specs[i].mg, specs[i].minb, specs[i].nc, g.transform);
+        specs[i] = net_spec_tables(g.key.n, tptr.data(), (int)tptr.size(), specs[i].words, specs[i].mg,
+                                   specs[i].minb, specs[i].nc, g.transform);
       add_networks(specs, ns, &cands);
     } else if (g.syn_plan && jit_mode() != PYRIT_JIT_OFF) {
       NetSpec specs[8];

@@ -33,6 +33,20 @@ int run_job(const pyrit_plan_s* plan, const JobDesc& job, cudaStream_t stream) {
   return launch_plain(n, job, stream);
 }
 
+// Codes a stripe's jobs in order on the stream (one per group of up to kMaxOut outputs; they read
+// the same sources). Under the parity transform every job must be able to run on a network
+// before the first is launched.
+int run_jobs(const pyrit_plan_s* plan, const JobDesc* jobs, int nj, cudaStream_t stream) {
+  if (plan->transform == PYRIT_TRANSFORM_PARITY)
+    for (int i = 0; i < nj; ++i)
+      if (!job_is_staged(jobs[i])) return PYRIT_E_UNSUPPORTED;
+  for (int i = 0; i < nj; ++i) {
+    const int rc = run_job(plan, jobs[i], stream);
+    if (rc != PYRIT_OK) return rc;
+  }
+  return PYRIT_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -44,9 +58,9 @@ int pyrit_encode(pyrit_plan_t plan, const void* const* data, void* const* parity
   for (int i = 0; i < plan->m; ++i)
     if (!parity[i]) return PYRIT_E_INVALID_ARG;
   if (plan->m == 0) return PYRIT_OK;
-  JobDesc job;
-  make_encode_job(plan, data, parity, P, &job);
-  return run_job(plan, job, reinterpret_cast<cudaStream_t>(stream));
+  JobDesc jobs[kMaxJobs];
+  const int nj = make_encode_jobs(plan, data, parity, P, jobs);
+  return run_jobs(plan, jobs, nj, reinterpret_cast<cudaStream_t>(stream));
 }
 
 int pyrit_decode(pyrit_plan_t plan, void* const* blocks, uint64_t erasures, size_t P, pyrit_stream_t stream) {
@@ -58,12 +72,13 @@ int pyrit_decode(pyrit_plan_t plan, void* const* blocks, uint64_t erasures, size
   const int rc = plan_decode_entry(plan, erasures, &e);
   if (rc != PYRIT_OK) return rc;
   if (e.ne == 0) return PYRIT_OK;
-  JobDesc job;
-  make_decode_job(plan, e, blocks, P, &job);
+  JobDesc jobs[kMaxJobs];
+  const int nj = make_decode_jobs(plan, e, blocks, P, jobs);
   const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   // The plan's syndrome-decode network serves every erasure pattern: used once compiled (compiled
-  // in the call under the parity transform, which has no generic kernel).
-  if (e.syn_ok && job_is_staged(job)) {
+  // in the call under the parity transform, which has no generic kernel). It exists for m <= 8,
+  // where the decode is one job.
+  if (e.syn_ok && nj == 1 && job_is_staged(jobs[0])) {
     const bool block = plan->transform == PYRIT_TRANSFORM_PARITY;
     if (const Variant* net = net_variant(net_spec_syndrome(plan, 0, 0, 0), block)) {
       JobDesc sj;
@@ -74,7 +89,7 @@ int pyrit_decode(pyrit_plan_t plan, void* const* blocks, uint64_t erasures, size
       return launch_staged(sh, &sj, nullptr, nullptr, tpj, tpj, st);
     }
   }
-  return run_job(plan, job, st);
+  return run_jobs(plan, jobs, nj, st);
 }
 
 int pyrit_device_status(int* code_out, int* where_out) {

@@ -104,9 +104,13 @@ std::string net_source(const NetSpec& s) {
   const bool syndrome = s.mode == 1 || s.mode == 3, parity = s.mode >= 2;
   o += kStore[s.mode];
   o += " {\n";
+  const bool multi = s.ntables > 1;
   if (syndrome) {
     // syndrome decode: only the rows a tile's erasure pattern uses are accumulated
     o += "  __device__ __forceinline__ void tile(const JobDesc* J, int, int) { load_rows(J); }\n";
+  } else if (multi) {
+    // several tables (the output groups of wide stripes): the tile's job names its table
+    o += "  int tbl;\n  __device__ __forceinline__ void tile(const JobDesc* J, int, int) { tbl = J->table; }\n";
   } else {
     o += "  __device__ __forceinline__ void tile(const JobDesc*, int, int) {}\n";
   }
@@ -130,15 +134,19 @@ std::string net_source(const NetSpec& s) {
   // (a switch on the needed-row set with one block per set measured no faster and compiled
   // several times longer).
   const bool guard = syndrome;
-  put(o, "    switch (g * %ld + j) {\n", s.nin);
-  for (int g = 0; g < groups; ++g) {
+  if (multi)
+    put(o, "    switch ((tbl * %ld + g) * %ld + j) {\n", groups, s.nin);
+  else
+    put(o, "    switch (g * %ld + j) {\n", s.nin);
+  for (int cs = 0; cs < s.ntables * groups; ++cs) {
+    const int tb = cs / groups, g = cs % groups;
     for (int j = 0; j < s.nin; ++j) {
-      put(o, "      case %ld: {\n", g * s.nin + j);
+      put(o, "      case %ld: {\n", ((long)tb * groups + g) * s.nin + j);
       if (!guard) o += "#pragma unroll\n        for (int x = 0; x < WORDS; ++x) {\n";
       for (int ii = 0; ii < s.mg; ++ii) {
         const int out = g * s.mg + ii;
-        if (out >= s.nout) break;
-        const uint32_t r = s.mask[j][out];
+        if (out >= s.tnout[tb]) break;
+        const uint32_t r = s.mask[tb][j][out];
         std::string lines;
         for (int t = 0; t < N; ++t) {
           // under the parity transform a direct network never builds the top accumulators
@@ -396,26 +404,40 @@ int shapes_for(int n, int nout, bool syndrome, NetSpec* out, int cap) {
   return count;
 }
 
-NetSpec net_spec(int n, const JobDesc& job, int words, int mg, int minb, int nc, int transform) {
+NetSpec net_spec_tables(int n, const JobDesc* const* tables, int ntables, int words, int mg, int minb, int nc,
+                        int transform) {
   NetSpec s;
   std::memset(&s, 0, sizeof(s));
+  int nout = 0;
+  for (int t = 0; t < ntables; ++t) nout = std::max(nout, (int)tables[t]->nout);
   NetSpec def[1];
-  if (net_candidate_shapes(n, job.nout, def, 1) == 1) s = def[0];
+  if (net_candidate_shapes(n, nout, def, 1) == 1) s = def[0];
   s.n = n;
-  s.nin = job.nin;
-  s.nout = job.nout;
+  s.nin = tables[0]->nin;
+  s.nout = nout;
   if (words) s.words = words;
   if (mg) s.mg = mg;
   if (minb) s.minb = minb;
   if (nc) s.nc = nc;
   if (!s.words) s.words = 1;
-  if (!s.mg) s.mg = job.nout;
+  if (!s.mg) s.mg = nout;
   if (!s.minb) s.minb = 1;
   if (!s.nc) s.nc = 16;
   s.mode = transform == PYRIT_TRANSFORM_PARITY ? 2 : 0;
-  for (int j = 0; j < job.nin; ++j)
-    for (int o = 0; o < job.nout; ++o) s.mask[j][o] = job.mask[j][o];
+  s.ntables = ntables < kMaxJobs ? ntables : kMaxJobs;
+  for (int t = 0; t < s.ntables; ++t) {
+    const JobDesc& job = *tables[t];
+    s.tnout[t] = job.nout;
+    for (int j = 0; j < job.nin && j < kMaxIn; ++j)
+      for (int o = 0; o < job.nout && o < kMaxOut; ++o) s.mask[t][j][o] = job.mask[j][o];
+  }
+  if (ntables > kMaxJobs) s.ntables = 0;  // rejected by spec_valid
   return s;
+}
+
+NetSpec net_spec(int n, const JobDesc& job, int words, int mg, int minb, int nc, int transform) {
+  const JobDesc* t = &job;
+  return net_spec_tables(n, &t, 1, words, mg, minb, nc, transform);
 }
 
 NetSpec net_spec_syndrome(const pyrit_plan_s* p, int words, int minb, int nc) {
@@ -428,18 +450,20 @@ NetSpec net_spec_syndrome(const pyrit_plan_s* p, int words, int minb, int nc) {
   s.nin = p->k + p->m;
   s.nout = p->m;
   s.mg = p->m;
+  s.ntables = 1;
+  s.tnout[0] = p->m;
   if (words) s.words = words;
   if (minb) s.minb = minb;
   if (nc) s.nc = nc;
   if (!s.words) s.words = 1;
   if (!s.minb) s.minb = 1;
   if (!s.nc) s.nc = 8;
-  if (s.nin > kMaxIn) return s;  // rejected by spec_valid
+  if (s.nin > kMaxIn || p->m > kMaxOut) return s;  // rejected by spec_valid
   // H = [C | I_m]: data column j carries the parity rows' coefficients, parity column k + r only
   // its own row with coefficient 1 (mask x^0)
   for (int r = 0; r < p->m; ++r) {
-    for (int j = 0; j < p->k; ++j) s.mask[j][r] = p->enc_mask[r * p->k + j];
-    s.mask[p->k + r][r] = 1;
+    for (int j = 0; j < p->k; ++j) s.mask[0][j][r] = p->enc_mask[r * p->k + j];
+    s.mask[0][p->k + r][r] = 1;
   }
   return s;
 }
@@ -455,7 +479,10 @@ static bool spec_valid(const NetSpec& s) {
   const bool words_ok = s.words == 1 || s.words == 2 || s.words == 4;
   const bool nc_ok = s.nc >= 1 && s.nc <= 31;
   if (s.mode < 0 || s.mode > 3) return false;
-  if ((s.mode == 1 || s.mode == 3) && !(s.mg == s.nout && s.nout <= kSyndromeBaseRow)) return false;
+  if ((s.mode == 1 || s.mode == 3) && !(s.mg == s.nout && s.nout <= kSyndromeBaseRow && s.ntables == 1)) return false;
+  if (s.ntables < 1 || s.ntables > kMaxJobs) return false;
+  for (int t = 0; t < s.ntables; ++t)
+    if (s.tnout[t] < 1 || s.tnout[t] > s.nout) return false;
   return (s.n == 3 || s.n == 5 || s.n == 9 || s.n == 11 || s.n == 13) && s.nin >= 1 && s.nin <= kMaxIn && s.nout >= 1 &&
          s.nout <= kMaxOut && words_ok && s.mg >= 1 && s.mg <= kMaxOut && s.minb >= 1 && s.minb <= 4 && nc_ok &&
          output_groups(s.mg, s.nout, s.nc) * s.mg >= s.nout && s.nc % output_groups(s.mg, s.nout, s.nc) == 0;
@@ -565,32 +592,34 @@ int pyrit_jit_log(char* buf, int cap) {
 
 namespace {
 
-// The network a plan's operation uses: *s filled and 1, 0 when there is nothing to code (no
-// parity rows, no erasure), or an error status.
-int plan_network_spec(pyrit_plan_s* plan, int op, uint64_t erasures, const pyrit_tile_t* tile, NetSpec* s) {
+// The networks a plan's operation uses, one per job (a stripe with more than kMaxOut parity or
+// erased blocks is several jobs): fills s[0..count) and returns count, 0 when there is nothing to
+// code (no parity rows, no erasure), or an error status.
+int plan_network_specs(pyrit_plan_s* plan, int op, uint64_t erasures, const pyrit_tile_t* tile,
+                       NetSpec* s /* [kMaxJobs] */) {
   if (!plan) return PYRIT_E_INVALID_ARG;
   std::vector<void*> none((size_t)(plan->k + plan->m), nullptr);  // only the masks are used
-  JobDesc job;
+  JobDesc jobs[kMaxJobs];
+  int nj = 0;
   if (op == PYRIT_OP_ENCODE) {
-    if (plan->m == 0) return 0;
-    make_encode_job(plan, none.data(), none.data() + plan->k, 16, &job);
+    nj = make_encode_jobs(plan, none.data(), none.data() + plan->k, 16, jobs);
   } else if (op == PYRIT_OP_DECODE_ANY) {
     if (plan->m == 0) return 0;
-    if (plan->k + plan->m > kMaxIn) return PYRIT_E_INVALID_ARG;
-    *s = tile ? net_spec_syndrome(plan, tile->words, tile->minb, tile->nc) : net_spec_syndrome(plan, 0, 0, 0);
+    if (plan->k + plan->m > kMaxIn || plan->m > kMaxOut) return PYRIT_E_INVALID_ARG;
+    s[0] = tile ? net_spec_syndrome(plan, tile->words, tile->minb, tile->nc) : net_spec_syndrome(plan, 0, 0, 0);
     return 1;
   } else if (op == PYRIT_OP_DECODE) {
     DecodeEntry e;
     const int rc = plan_decode_entry(plan, erasures, &e);
     if (rc != PYRIT_OK) return rc;
-    if (e.ne == 0) return 0;
-    make_decode_job(plan, e, none.data(), 16, &job);
+    nj = make_decode_jobs(plan, e, none.data(), 16, jobs);
   } else {
     return PYRIT_E_INVALID_ARG;
   }
-  *s = tile ? net_spec(plan->n, job, tile->words, tile->mg, tile->minb, tile->nc, plan->transform)
-            : net_spec(plan->n, job, 0, 0, 0, 0, plan->transform);
-  return 1;
+  for (int i = 0; i < nj; ++i)
+    s[i] = tile ? net_spec(plan->n, jobs[i], tile->words, tile->mg, tile->minb, tile->nc, plan->transform)
+                : net_spec(plan->n, jobs[i], 0, 0, 0, 0, plan->transform);
+  return nj;
 }
 
 }  // namespace
@@ -598,17 +627,23 @@ int plan_network_spec(pyrit_plan_s* plan, int op, uint64_t erasures, const pyrit
 extern "C" {
 
 int pyrit_plan_specialise(pyrit_plan_t plan, int op, uint64_t erasures, const pyrit_tile_t* tile) {
-  NetSpec s;
-  const int rc = plan_network_spec(plan, op, erasures, tile, &s);
-  return rc == 1 ? net_compile(s) : rc;
+  NetSpec s[kMaxJobs];
+  const int ns = plan_network_specs(plan, op, erasures, tile, s);
+  if (ns < 0) return ns;
+  for (int i = 0; i < ns; ++i) {
+    const int rc = net_compile(s[i]);
+    if (rc != PYRIT_OK) return rc;
+  }
+  return PYRIT_OK;
 }
 
 int pyrit_plan_network_info(pyrit_plan_t plan, int op, uint64_t erasures, const pyrit_tile_t* tile, int* info_out) {
   if (!info_out) return PYRIT_E_INVALID_ARG;
-  NetSpec s;
-  int rc = plan_network_spec(plan, op, erasures, tile, &s);
+  NetSpec specs[kMaxJobs];
+  int rc = plan_network_specs(plan, op, erasures, tile, specs);
   if (rc == 0) return PYRIT_E_INVALID_ARG;  // nothing to code: no network
   if (rc < 0) return rc;
+  const NetSpec& s = specs[0];  // the first job's network (all jobs of a stripe share its shape)
   rc = net_compile(s);
   if (rc != PYRIT_OK) return rc;
   Jit& J = jit();

@@ -51,22 +51,20 @@ int scratch_address(uint8_t** out) {
   return PYRIT_OK;
 }
 
+// The one job of a stripe. The fixed kernels have no parity transform (it runs only on generated
+// networks), and a stripe with more than kMaxOut parity (or erased) blocks is several jobs, which
+// the fixed scratch does not hold: both are PYRIT_E_UNSUPPORTED here.
 int stripe_job(const pyrit_stripe_t& s, JobDesc* job) {
-  pyrit_plan_s* p = s.plan;
-  if (!p || !s.blocks || s.packet_bytes == 0 || s.packet_bytes > (1ull << 40)) return PYRIT_E_INVALID_ARG;
-  if (s.op != PYRIT_OP_ENCODE && s.op != PYRIT_OP_DECODE) return PYRIT_E_INVALID_ARG;
-  for (int b = 0; b < p->k + p->m; ++b)
-    if (!s.blocks[b]) return PYRIT_E_INVALID_ARG;
-  // the fixed kernels have no parity transform (it runs only on generated networks)
-  if (p->transform == PYRIT_TRANSFORM_PARITY) return PYRIT_E_UNSUPPORTED;
-  if (s.op == PYRIT_OP_ENCODE) {
-    make_encode_job(p, s.blocks, s.blocks + p->k, s.packet_bytes, job);
-    return PYRIT_OK;
-  }
-  DecodeEntry e;
-  const int rc = plan_decode_entry(p, s.erasures, &e);
+  JobDesc jobs[kMaxJobs];
+  int nj = 0;
+  uint64_t alg = 0, src = 0;
+  const int rc = stripe_jobs(s, jobs, &nj, &alg, &src);
   if (rc != PYRIT_OK) return rc;
-  make_decode_job(p, e, s.blocks, s.packet_bytes, job);
+  if (s.plan->transform == PYRIT_TRANSFORM_PARITY || nj > 1) return PYRIT_E_UNSUPPORTED;
+  if (nj == 1)
+    *job = jobs[0];
+  else
+    std::memset(job, 0, sizeof(*job));
   return PYRIT_OK;
 }
 

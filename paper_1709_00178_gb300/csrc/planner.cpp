@@ -111,7 +111,7 @@ uint32_t sparse_rep(int w, int n, uint32_t u) {
   return best;
 }
 
-// Inverse over GF(2^w) by elimination with row swaps (k <= 32). Returns false if singular.
+// Inverse over GF(2^w) by elimination with row swaps (k <= 64). Returns false if singular.
 static bool invert(int w, int k, const uint32_t* A, uint32_t* out) {
   uint32_t a[kMaxIn][kMaxIn], b[kMaxIn][kMaxIn];
   for (int r = 0; r < k; ++r)
@@ -149,7 +149,7 @@ static bool invert(int w, int k, const uint32_t* A, uint32_t* out) {
 
 // Every k x k row subset of G invertible (the MDS property, Sec. 2.2), by enumeration.
 static bool all_subsets_invertible(int w, int k, int m, const uint32_t* G) {
-  int idx[kMaxIn + kMaxOut];
+  int idx[kMaxBlocks];
   for (int i = 0; i < k; ++i) idx[i] = i;
   uint32_t sub[kMaxIn * kMaxIn], inv[kMaxIn * kMaxIn];
   const int nrow = k + m;
@@ -180,7 +180,7 @@ static void syndrome_entry(const pyrit_plan_s* p, DecodeEntry* e) {
   const int k = p->k, m = p->m, w = p->w, n = p->n;
   e->syn_ok = false;
   std::memset(e->syn, 0, sizeof(e->syn));
-  if (k + m > kMaxIn) return;
+  if (k + m > kMaxIn || m > kMaxOut) return;
   int D[kMaxOut], U[kMaxOut], a = 0, nu = 0;
   for (int r = 0; r < e->ne; ++r)
     if (e->erased[r] < k) D[a++] = e->erased[r];
@@ -261,28 +261,42 @@ int plan_decode_entry(pyrit_plan_s* p, uint64_t erasures, DecodeEntry* out) {
   return e.status;
 }
 
-void make_encode_job(const pyrit_plan_s* p, const void* const* data, void* const* parity, size_t P,
-                     JobDesc* job) {
-  std::memset(job, 0, sizeof(*job));
-  job->nin = p->k;
-  job->nout = p->m;
-  job->P = P;
-  for (int j = 0; j < p->k; ++j) job->in[j] = static_cast<const uint8_t*>(data[j]);
-  for (int i = 0; i < p->m; ++i) job->out[i] = static_cast<uint8_t*>(parity[i]);
-  for (int i = 0; i < p->m; ++i)
-    for (int j = 0; j < p->k; ++j) job->mask[j][i] = p->enc_mask[i * p->k + j];
+int make_encode_jobs(const pyrit_plan_s* p, const void* const* data, void* const* parity, size_t P,
+                     JobDesc* jobs) {
+  const int nj = (p->m + kMaxOut - 1) / kMaxOut;
+  for (int g = 0; g < nj; ++g) {
+    JobDesc* job = &jobs[g];
+    std::memset(job, 0, sizeof(*job));
+    const int o0 = g * kMaxOut, no = std::min(kMaxOut, p->m - o0);
+    job->nin = p->k;
+    job->nout = no;
+    job->P = P;
+    job->table = g;
+    for (int j = 0; j < p->k; ++j) job->in[j] = static_cast<const uint8_t*>(data[j]);
+    for (int i = 0; i < no; ++i) job->out[i] = static_cast<uint8_t*>(parity[o0 + i]);
+    for (int i = 0; i < no; ++i)
+      for (int j = 0; j < p->k; ++j) job->mask[j][i] = p->enc_mask[(o0 + i) * p->k + j];
+  }
+  return nj;
 }
 
-void make_decode_job(const pyrit_plan_s* p, const DecodeEntry& e, void* const* blocks, size_t P,
-                     JobDesc* job) {
-  std::memset(job, 0, sizeof(*job));
-  job->nin = p->k;
-  job->nout = e.ne;
-  job->P = P;
-  for (int s = 0; s < p->k; ++s) job->in[s] = static_cast<const uint8_t*>(blocks[e.surv[s]]);
-  for (int r = 0; r < e.ne; ++r) job->out[r] = static_cast<uint8_t*>(blocks[e.erased[r]]);
-  for (int r = 0; r < e.ne; ++r)
-    for (int s = 0; s < p->k; ++s) job->mask[s][r] = e.mask[r][s];
+int make_decode_jobs(const pyrit_plan_s* p, const DecodeEntry& e, void* const* blocks, size_t P,
+                     JobDesc* jobs) {
+  const int nj = (e.ne + kMaxOut - 1) / kMaxOut;
+  for (int g = 0; g < nj; ++g) {
+    JobDesc* job = &jobs[g];
+    std::memset(job, 0, sizeof(*job));
+    const int o0 = g * kMaxOut, no = std::min(kMaxOut, e.ne - o0);
+    job->nin = p->k;
+    job->nout = no;
+    job->P = P;
+    job->table = g;
+    for (int s = 0; s < p->k; ++s) job->in[s] = static_cast<const uint8_t*>(blocks[e.surv[s]]);
+    for (int r = 0; r < no; ++r) job->out[r] = static_cast<uint8_t*>(blocks[e.erased[o0 + r]]);
+    for (int r = 0; r < no; ++r)
+      for (int s = 0; s < p->k; ++s) job->mask[s][r] = e.mask[o0 + r][s];
+  }
+  return nj;
 }
 
 void make_syndrome_job(const pyrit_plan_s* p, const DecodeEntry& e, void* const* blocks, size_t P, JobDesc* job) {
@@ -304,9 +318,9 @@ void make_syndrome_job(const pyrit_plan_s* p, const DecodeEntry& e, void* const*
   job->mask[kSyndromeNeedRow][0] = (uint16_t)need;
 }
 
-// Validates a stripe request and builds its coding job; alg / src receive its algorithmic and
+// Validates a stripe request and builds its coding jobs; alg / src receive its algorithmic and
 // source bytes.
-int stripe_job(const pyrit_stripe_t& s, JobDesc* job, uint64_t* alg, uint64_t* src) {
+int stripe_jobs(const pyrit_stripe_t& s, JobDesc* jobs, int* njobs, uint64_t* alg, uint64_t* src) {
   pyrit_plan_s* p = s.plan;
   if (!p || !s.blocks || s.packet_bytes == 0 || s.packet_bytes > (1ull << 40)) return PYRIT_E_INVALID_ARG;
   if (s.op != PYRIT_OP_ENCODE && s.op != PYRIT_OP_DECODE) return PYRIT_E_INVALID_ARG;
@@ -315,14 +329,14 @@ int stripe_job(const pyrit_stripe_t& s, JobDesc* job, uint64_t* alg, uint64_t* s
   const uint64_t blk = (uint64_t)p->w * s.packet_bytes;
   *src = (uint64_t)p->k * blk;
   if (s.op == PYRIT_OP_ENCODE) {
-    make_encode_job(p, s.blocks, s.blocks + p->k, s.packet_bytes, job);
+    *njobs = make_encode_jobs(p, s.blocks, s.blocks + p->k, s.packet_bytes, jobs);
     *alg = (uint64_t)(p->k + p->m) * blk;
     return PYRIT_OK;
   }
   DecodeEntry e;
   const int rc = plan_decode_entry(p, s.erasures, &e);
   if (rc != PYRIT_OK) return rc;
-  make_decode_job(p, e, s.blocks, s.packet_bytes, job);
+  *njobs = make_decode_jobs(p, e, s.blocks, s.packet_bytes, jobs);
   *alg = (uint64_t)(p->k + e.ne) * blk;
   return PYRIT_OK;
 }
@@ -357,7 +371,7 @@ const char* pyrit_strerror(int s) {
 int pyrit_plan_create(int w, int n, int k, int m, const uint32_t* G, pyrit_plan_t* out) {
   if (!out) return PYRIT_E_INVALID_ARG;
   *out = nullptr;
-  if (k < 1 || k > kMaxIn || m < 0 || m > kMaxOut) return PYRIT_E_INVALID_ARG;
+  if (k < 1 || k > PYRIT_MAX_K || m < 0 || m > PYRIT_MAX_M || k + m > kMaxBlocks) return PYRIT_E_INVALID_ARG;
   if (!field_supported(w, n)) return PYRIT_E_UNSUPPORTED_FIELD;
   if (!G && (uint64_t)k + (uint64_t)m > (1ull << w)) return PYRIT_E_TOO_LONG;
   pyrit_plan_s* p = new (std::nothrow) pyrit_plan_s;
@@ -426,7 +440,7 @@ int pyrit_plan_encode_masks(pyrit_plan_t p, uint16_t* masks_out) {
 }
 
 int pyrit_generator_weighted(int w, int n, int k, int m, uint32_t* G_out, uint64_t* weights_out) {
-  if (!G_out || k < 1 || k > kMaxIn || m < 0 || m > kMaxOut) return PYRIT_E_INVALID_ARG;
+  if (!G_out || k < 1 || k > PYRIT_MAX_K || m < 0 || m > PYRIT_MAX_M || k + m > kMaxBlocks) return PYRIT_E_INVALID_ARG;
   if (!field_supported(w, n)) return PYRIT_E_UNSUPPORTED_FIELD;
   if ((uint64_t)k + (uint64_t)m > (1ull << w)) return PYRIT_E_TOO_LONG;
   const uint32_t q = 1u << w;

@@ -14,7 +14,9 @@
 
 namespace pyrit {
 
-static_assert(kMaxIn == PYRIT_MAX_K && kMaxOut == PYRIT_MAX_M, "job limits follow the C ABI's");
+static_assert(kMaxIn == PYRIT_MAX_K && kMaxOut == PYRIT_JOB_OUTPUTS, "job limits follow the C ABI's");
+constexpr int kMaxBlocks = PYRIT_MAX_BLOCKS;                      // k + m of a stripe
+constexpr int kMaxJobs = (PYRIT_MAX_M + kMaxOut - 1) / kMaxOut;  // jobs of one stripe
 
 // Field degree w carried by the ring R_{2,n}: RingDim<n>::W for a run-time n.
 inline int field_degree(int n) { return n == 9 ? 6 : n - 1; }
@@ -81,9 +83,9 @@ struct DecodeEntry {
   int status = PYRIT_OK;
   int ne = 0;
   int surv[kMaxIn];
-  int erased[kMaxOut];
-  uint16_t mask[kMaxOut][kMaxIn];  // row r = erased block erased[r], column s = survivor surv[s]
-  // Syndrome form (k + m <= kMaxIn): syn[r][o] = phi_S of the coefficient of parity row r's
+  int erased[kMaxBlocks];
+  uint16_t mask[kMaxBlocks][kMaxIn];  // row r = erased block erased[r], column s = survivor surv[s]
+  // Syndrome form (k + m <= kMaxIn, m <= kMaxOut): syn[r][o] = phi_S of the coefficient of row r's
   // accumulator for output o; syn[kSyndromeBaseRow][o] = 1 + the row whose partial sum output o
   // adds (an erased parity block), 0 for an erased data block.
   bool syn_ok = false;
@@ -104,14 +106,17 @@ struct pyrit_plan_s {
 namespace pyrit {
 // Looks up or computes the decoding matrix of `erasures` (thread-safe). Returns a status.
 int plan_decode_entry(pyrit_plan_s* p, uint64_t erasures, DecodeEntry* out);
-// Fills a job for encoding one stripe.
-void make_encode_job(const pyrit_plan_s* p, const void* const* data, void* const* parity, size_t P,
-                     JobDesc* job);
-// Validates a stripe request and builds its coding job (alg / src: algorithmic and source bytes).
-int stripe_job(const pyrit_stripe_t& s, JobDesc* job, uint64_t* alg, uint64_t* src);
-// Fills a job for decoding one stripe with a decode entry.
-void make_decode_job(const pyrit_plan_s* p, const DecodeEntry& e, void* const* blocks, size_t P,
-                     JobDesc* job);
+// Fills the jobs that encode one stripe: output group g (parity blocks 8g..8g+7) is jobs[g], each
+// reading all k data blocks. Returns the job count, ceil(m / 8) (0 when m = 0).
+int make_encode_jobs(const pyrit_plan_s* p, const void* const* data, void* const* parity, size_t P,
+                     JobDesc* jobs /* [kMaxJobs] */);
+// Validates a stripe request and builds its coding jobs (alg / src: algorithmic and source bytes);
+// *njobs = how many (0 when there is nothing to code).
+int stripe_jobs(const pyrit_stripe_t& s, JobDesc* jobs /* [kMaxJobs] */, int* njobs, uint64_t* alg, uint64_t* src);
+// Fills the jobs that decode one stripe with a decode entry (erased blocks 8g..8g+7 in jobs[g]).
+// Returns the job count, ceil(ne / 8).
+int make_decode_jobs(const pyrit_plan_s* p, const DecodeEntry& e, void* const* blocks, size_t P,
+                     JobDesc* jobs /* [kMaxJobs] */);
 // Fills the syndrome-form decode job (requires e.syn_ok): sources are the k + m block columns in
 // index order, absent (null) unless they are survivors; outputs are the erased blocks.
 void make_syndrome_job(const pyrit_plan_s* p, const DecodeEntry& e, void* const* blocks, size_t P, JobDesc* job);
@@ -149,16 +154,22 @@ void tune_record(const TuneKey& k, const TuneVal& v);
 // out as straight-line code, so no mask bit is tested at run time. Generated, compiled (NVRTC) and
 // cached per NetSpec; `mask` holds the table for j < nin, o < nout and zeros elsewhere.
 struct NetSpec {
-  int32_t n, nin, nout, words, mg, minb, nc;
-  int32_t mode;  // 0 / 2: direct (the job's own table), 1 / 3: syndrome decode of a plan (table
+  int32_t n, nin, nout, words, mg, minb, nc;  // nout: the largest output count of its tables
+  int32_t mode;  // 0 / 2: direct (the jobs' own tables), 1 / 3: syndrome decode of a plan (table
                  // [C | I]); 0 and 1 under the embedding transform, 2 and 3 under the parity one
-  uint16_t mask[kMaxIn][kMaxOut];
+  int32_t ntables;           // direct modes: tables; a job's JobDesc::table picks one (syndrome: 1)
+  int32_t tnout[kMaxJobs];   // output count of each table
+  uint16_t mask[kMaxJobs][kMaxIn][kMaxOut];
 };
-// The network spec of a job under a shape (zero fields: the default shape for (n, nout)) and a
-// transform (PYRIT_TRANSFORM_EMBEDDING or _PARITY).
+// The network spec of one job under a shape (zero fields: the default shape for (n, nout)) and a
+// transform (PYRIT_TRANSFORM_EMBEDDING or _PARITY): one table, which the job must select as 0.
 NetSpec net_spec(int n, const JobDesc& job, int words, int mg, int minb, int nc, int transform);
-// The syndrome-decode network spec of a plan, under its transform (requires k + m <= kMaxIn;
-// zero fields: default).
+// The network spec of several tables (each given by one job that uses it, all with the same nin):
+// the jobs of a launch then carry their table's index in JobDesc::table.
+NetSpec net_spec_tables(int n, const JobDesc* const* tables, int ntables, int words, int mg, int minb, int nc,
+                        int transform);
+// The syndrome-decode network spec of a plan, under its transform (requires k + m <= kMaxIn and
+// m <= kMaxOut; zero fields: default).
 NetSpec net_spec_syndrome(const pyrit_plan_s* p, int words, int minb, int nc);
 // Candidate shapes of a plan's syndrome network, the default first.
 int net_syndrome_shapes(const pyrit_plan_s* p, NetSpec* out, int cap);

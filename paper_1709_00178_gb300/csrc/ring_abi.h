@@ -30,8 +30,8 @@ struct RingDim {
   static constexpr int S = N - W;
 };
 
-constexpr int kMaxIn = 32;  // sources of one coding job (data blocks or survivors)
-constexpr int kMaxOut = 8;  // destinations of one coding job (parity or erased blocks)
+constexpr int kMaxIn = 64;  // sources of one coding job (data blocks or survivors)
+constexpr int kMaxOut = 8;  // destinations of one coding job (a stripe's outputs split into jobs of 8)
 // Syndrome-form decode jobs keep, for output o, 1 + the row of their partial sum (0: none) in
 // mask[kSyndromeBaseRow][o]; rows 0..kMaxOut-1 hold the per-row coefficients.
 constexpr int kSyndromeBaseRow = kMaxOut;
@@ -48,6 +48,8 @@ struct alignas(16) JobDesc {
   uint16_t mask[kMaxIn][kMaxOut];  // source-major so one 16-byte load gives every output's mask
   uint64_t P;                      // packet bytes
   int32_t nin, nout;
+  int32_t table;                   // which table of a multi-table generated network codes this job
+  int32_t reserved;
 };
 
 // Launch arguments of the staged ring kernel. Tiles are (job, column range [col0, col0 + tw)).

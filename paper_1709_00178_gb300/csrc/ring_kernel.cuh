@@ -103,37 +103,46 @@ __device__ __forceinline__ void ring_mac(uint32_t (&acc)[MG][N][WORDS], const ui
 }
 
 // Multiply-accumulate driven by the job's masks at run time (the generic kernels). Lane l holds
-// the mask words of source l for its group's outputs (one 16-byte row per source: the masks of
-// outputs 0..7); each source's masks are broadcast from lane j by a warp OR-reduction, uniform
-// across the warp by construction, which keeps the dispatch on uniform branches.
+// the mask words of sources l and l + 32 for its group's outputs (one 16-byte row per source: the
+// masks of outputs 0..7); each source's masks are broadcast from its lane by a warp OR-reduction,
+// uniform across the warp by construction, which keeps the dispatch on uniform branches.
 template <int MG, int DISPATCH>
 struct MaskMac : DirectStore {
   static constexpr int MW = (MG + 1) / 2;  // 32-bit mask words per source for MG outputs
-  uint32_t rw[MW];
+  uint32_t rw[2][MW];                      // [0]: source lane, [1]: source lane + 32
 
-  __device__ __forceinline__ void tile(const JobDesc* J, int g, int lane) {
-    uint4 row = make_uint4(0u, 0u, 0u, 0u);
-    if (lane < J->nin) row = *reinterpret_cast<const uint4*>(&J->mask[lane][0]);
+  // The group's mask words out of one source row.
+  __device__ __forceinline__ static void group_words(const uint4& row, int g, uint32_t (&out)[MW]) {
     if constexpr (MG == 1) {
       // one output per warp: output g's mask is half (g & 1) of word g / 2
       const int wi = g >> 1;
       const uint32_t wv = wi == 0 ? row.x : wi == 1 ? row.y : wi == 2 ? row.z : row.w;
-      rw[0] = (wv >> (16 * (g & 1))) & 0xFFFFu;
+      out[0] = (wv >> (16 * (g & 1))) & 0xFFFFu;
     } else {
 #pragma unroll
       for (int x = 0; x < MW; ++x) {
         const int idx = g * MW + x;
-        rw[x] = idx == 0 ? row.x : idx == 1 ? row.y : idx == 2 ? row.z : idx == 3 ? row.w : 0u;
+        out[x] = idx == 0 ? row.x : idx == 1 ? row.y : idx == 2 ? row.z : idx == 3 ? row.w : 0u;
       }
+    }
+  }
+
+  __device__ __forceinline__ void tile(const JobDesc* J, int g, int lane) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      uint4 row = make_uint4(0u, 0u, 0u, 0u);
+      if (lane + 32 * h < J->nin) row = *reinterpret_cast<const uint4*>(&J->mask[lane + 32 * h][0]);
+      group_words(row, g, rw[h]);
     }
   }
 
   template <int N, int WORDS, int MG_>
   __device__ __forceinline__ void apply(uint32_t (&acc)[MG_][N][WORDS], const uint32_t (&d)[RingDim<N>::W][WORDS],
                                         int j, int, int lane) {
+    const int h = j >> 5, jl = j & 31;  // warp-uniform
     uint32_t mu[MW];
 #pragma unroll
-    for (int x = 0; x < MW; ++x) mu[x] = __reduce_or_sync(0xFFFFFFFFu, lane == j ? rw[x] : 0u);
+    for (int x = 0; x < MW; ++x) mu[x] = __reduce_or_sync(0xFFFFFFFFu, lane == jl ? (h ? rw[1][x] : rw[0][x]) : 0u);
     ring_mac<N, WORDS, MG, DISPATCH>(acc, d, mu);
   }
 };

@@ -358,10 +358,17 @@ int pyrit_server_submit(pyrit_server_t s, const pyrit_request_t* reqs, int count
   for (int i = 0; i < count; ++i) {
     Pending p;
     uint64_t alg = 0, src = 0;
-    const int rc = stripe_job(reqs[i].stripe, &p.job, &alg, &src);
+    JobDesc jobs[kMaxJobs];
+    int nj = 0;
+    const int rc = stripe_jobs(reqs[i].stripe, jobs, &nj, &alg, &src);
     if (rc != PYRIT_OK) return rc;
-    // requests wait for no compilation, and only a generated network has the parity transform
-    if (reqs[i].stripe.plan->transform == PYRIT_TRANSFORM_PARITY) return PYRIT_E_UNSUPPORTED;
+    // requests wait for no compilation, and only a generated network has the parity transform;
+    // a request is one job (at most kMaxOut parity or erased blocks)
+    if (reqs[i].stripe.plan->transform == PYRIT_TRANSFORM_PARITY || nj > 1) return PYRIT_E_UNSUPPORTED;
+    if (nj == 1)
+      p.job = jobs[0];
+    else
+      std::memset(&p.job, 0, sizeof(p.job));
     p.n = reqs[i].stripe.plan->n;
     p.plan = reqs[i].stripe.plan;
     p.op = reqs[i].stripe.op;

@@ -42,8 +42,10 @@ PYRIT_JIT_SYNC = 1
 PYRIT_JIT_ASYNC = 2
 PYRIT_NOALLOC_MAX_STRIPES = 256
 PYRIT_NOALLOC_MAX_TILES = 16384
-PYRIT_MAX_K = 32
-PYRIT_MAX_M = 8
+PYRIT_MAX_K = 64
+PYRIT_MAX_M = 63
+PYRIT_MAX_BLOCKS = 64
+PYRIT_JOB_OUTPUTS = 8
 PYRIT_OP_ENCODE = 0
 PYRIT_OP_DECODE = 1
 PYRIT_OP_DECODE_ANY = 2

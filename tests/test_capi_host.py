@@ -145,8 +145,10 @@ def test_error_codes():
         (lambda: E.pyrit_plan_create(4, 6, 3, 2), E.PYRIT_E_UNSUPPORTED_FIELD),   # n != w+1
         (lambda: E.pyrit_plan_create(4, 5, 12, 5), E.PYRIT_E_TOO_LONG),           # k+m > 16
         (lambda: E.pyrit_plan_create(4, 5, 0, 2), E.PYRIT_E_INVALID_ARG),
-        (lambda: E.pyrit_plan_create(4, 5, 33, 2), E.PYRIT_E_INVALID_ARG),
-        (lambda: E.pyrit_plan_create(4, 5, 4, 9), E.PYRIT_E_INVALID_ARG),
+        (lambda: E.pyrit_plan_create(4, 5, 65, 2), E.PYRIT_E_INVALID_ARG),           # k > 64
+        (lambda: E.pyrit_plan_create(6, 9, 40, 25), E.PYRIT_E_INVALID_ARG),          # k + m > 64
+        (lambda: E.pyrit_plan_create(4, 5, 33, 2), E.PYRIT_E_TOO_LONG),              # k + m > 16
+        (lambda: E.pyrit_plan_create(4, 5, 4, 64), E.PYRIT_E_INVALID_ARG),           # m > 63
     ]
     for f, code in cases:
         with pytest.raises(E.PyritError) as ei:

@@ -154,9 +154,11 @@ def test_jit_off_uses_the_generic_kernel(pyrit, jit_mode):
         pyrit.pyrit_plan_destroy(st.plan)
 
 
-def test_network_request_for_mixed_masks_is_refused(pyrit, jit_mode):
+def test_network_request_without_a_network_is_refused(pyrit, jit_mode):
+    """Codes with different source counts share no network: an explicit network request is refused
+    before any device work; without it the group runs on a generic kernel."""
     a = Stripes(pyrit, 10, 10, 4, 4096, 1, 0x111)
-    c = Stripes(pyrit, 10, 10, 2, 4096, 1, 0x222)
+    c = Stripes(pyrit, 10, 12, 2, 4096, 1, 0x222)
     try:
         before = [a.host(0).copy(), c.host(0).copy()]
         mixed = a.stripes(pyrit.PYRIT_OP_ENCODE) + c.stripes(pyrit.PYRIT_OP_ENCODE)
@@ -165,13 +167,33 @@ def test_network_request_for_mixed_masks_is_refused(pyrit, jit_mode):
         assert ei.value.status == pyrit.PYRIT_E_INVALID_ARG
         np.testing.assert_array_equal(a.host(0), before[0])
         np.testing.assert_array_equal(c.host(0), before[1])
-        # without the override the group has mixed masks and runs on a generic kernel
         b = pyrit.pyrit_batch_create(mixed)
         try:
             assert pyrit.pyrit_batch_shape(b, 0)["dispatch"] != pyrit.PYRIT_DISPATCH_NETWORK
             pyrit.pyrit_batch_run(b)
             np.testing.assert_array_equal(a.host(0), a.full(0))
             np.testing.assert_array_equal(c.host(0), c.full(0))
+        finally:
+            pyrit.pyrit_batch_destroy(b)
+    finally:
+        pyrit.pyrit_plan_destroy(a.plan)
+        pyrit.pyrit_plan_destroy(c.plan)
+
+
+def test_codes_with_equal_source_counts_share_a_multi_table_network(pyrit, jit_mode):
+    """Two codes with the same k and different parity rows: one network holds both tables and each
+    job selects its own."""
+    a = Stripes(pyrit, 10, 10, 4, 4096 + 16, 2, 0x333)
+    c = Stripes(pyrit, 10, 10, 2, 4096 + 16, 2, 0x444)
+    try:
+        b = pyrit.pyrit_batch_create(a.stripes(pyrit.PYRIT_OP_ENCODE) + c.stripes(pyrit.PYRIT_OP_ENCODE))
+        try:
+            shape = pyrit.pyrit_batch_shape(b, 0)
+            assert shape["dispatch"] == pyrit.PYRIT_DISPATCH_NETWORK and pyrit.pyrit_batch_stats(b)["launches"] == 1
+            pyrit.pyrit_batch_run(b, graph=True)
+            for s in range(2):
+                np.testing.assert_array_equal(a.host(s), a.full(s))
+                np.testing.assert_array_equal(c.host(s), c.full(s))
         finally:
             pyrit.pyrit_batch_destroy(b)
     finally:
@@ -314,13 +336,12 @@ def test_every_syndrome_shape(pyrit, jit_mode, shape):
         pyrit.pyrit_plan_destroy(st.plan)
 
 
-def test_wide_code_decodes_on_the_generic_kernel(pyrit, jit_mode):
-    # k + m = 36 columns do not fit a job: the generic kernel decodes, still bit-exact
+def test_wide_code_decodes_on_the_syndrome_network(pyrit, jit_mode):
+    # k + m = 36 block columns (beyond 32): the syndrome network's first phase reads up to 64
     rng = np.random.default_rng(0x36)
     st = Stripes(pyrit, 12, 30, 6, 2048, 4, 0x360)
     try:
-        shape = _decode_batch_matches(pyrit, st, _random_patterns(rng, 4, 30, 6), expect_mode=None)
-        assert shape["dispatch"] != pyrit.PYRIT_DISPATCH_NETWORK
+        _decode_batch_matches(pyrit, st, _random_patterns(rng, 4, 30, 6), expect_mode=1)
     finally:
         pyrit.pyrit_plan_destroy(st.plan)
 

@@ -226,10 +226,11 @@ def test_parity_transform_single_calls(pyrit, jit_mode, policy):
 def test_parity_transform_refusals(pyrit, jit_mode):
     """Paths without a generated network refuse the parity transform instead of coding the field
     code: the generic kernels (run-time compiler off, an explicit generic shape), unaligned stripes
-    (the plain-load kernel), codes too wide for the syndrome network with mixed patterns, the server
-    and the allocation-free entry point."""
+    (the plain-load kernel), the server and the allocation-free entry point. (Mixed patterns of codes
+    with more parity blocks than the syndrome network holds run on multi-table direct networks while
+    their tables fit one; more tables are refused, see test_gpu_wide.py.)"""
     st = PtStripes(pyrit, 10, 10, 4, 4096, 2, 0x97F8)
-    wide = PtStripes(pyrit, 10, 30, 6, 1024, 2, 0x97F9)
+    wide = PtStripes(pyrit, 10, 20, 12, 1024, 2, 0x97F9)
     try:
         enc = [(st.plan, pyrit.PYRIT_OP_ENCODE, 0, st.P, st.blocks(s)) for s in range(2)]
 
@@ -246,8 +247,7 @@ def test_parity_transform_refusals(pyrit, jit_mode):
         odd = [(st.plan, pyrit.PYRIT_OP_ENCODE, 0, st.P - 8, st.blocks(0))]
         refused(pyrit.pyrit_batch_create, odd)
         refused(pyrit.pyrit_encode, st.plan, st.blocks(0)[:10], st.blocks(0)[10:], st.P - 8)
-        pats = [0b11 | (1 << 31), 0b101 | (1 << 33)]
-        refused(pyrit.pyrit_batch_create, [(wide.plan, pyrit.PYRIT_OP_DECODE, pats[s], wide.P, wide.blocks(s)) for s in range(2)])
+        pats = [0b11 | (1 << 21), 0b101 | (1 << 23)]
         refused(pyrit.pyrit_code_stripes_noalloc, enc)
         srv = pyrit.pyrit_server_create(1 << 30)
         try:
@@ -257,7 +257,18 @@ def test_parity_transform_refusals(pyrit, jit_mode):
         # nothing was written by any refused call
         for s in range(2):
             assert not st.host(s)[10:].any()
-        # a wide code still decodes one pattern per batch (its direct network)
+        # two patterns of a code with 12 parity blocks: one network with both decoding tables
+        for s_ in range(2):
+            wide.write_erased(s_, pats[s_])
+        b = pyrit.pyrit_batch_create([(wide.plan, pyrit.PYRIT_OP_DECODE, pats[s_], wide.P, wide.blocks(s_)) for s_ in range(2)])
+        try:
+            assert pyrit.pyrit_batch_shape(b, 0)["mode"] == MODE_DIRECT_PARITY
+            pyrit.pyrit_batch_run(b)
+            for s_ in range(2):
+                np.testing.assert_array_equal(wide.host(s_), wide.full(s_))
+        finally:
+            pyrit.pyrit_batch_destroy(b)
+        # and one pattern per batch (its direct network)
         wide.write_erased(0, pats[0])
         wide.write_erased(1, pats[0])
         b = pyrit.pyrit_batch_create([(wide.plan, pyrit.PYRIT_OP_DECODE, pats[0], wide.P, wide.blocks(s)) for s in range(2)])

@@ -118,7 +118,7 @@ def test_generated_network_random_masks_and_shapes(n):
     rng = np.random.default_rng(1000 + n)
     shapes = [None, {"mg": 0, "nc": 16}, {"words": 2, "nc": 8}]
     for trial in range(6):
-        nin = int(rng.integers(1, 33))
+        nin = int(rng.integers(1, 65))
         nout = int(rng.integers(1, 9))
         masks = rng.integers(0, 1 << n, size=(nout, nin)).astype(np.uint16)
         masks[0][0] = 0                 # a zero coefficient writes nothing
@@ -137,7 +137,7 @@ def test_output_groups_split_the_outputs():
 
 def test_jit_source_rejects_bad_tables():
     masks = np.zeros((4, 10), np.uint16)
-    for bad in [(7, masks, None), (11, np.zeros((9, 10), np.uint16), None), (11, np.zeros((4, 33), np.uint16), None),
+    for bad in [(7, masks, None), (11, np.zeros((9, 10), np.uint16), None), (11, np.zeros((4, 65), np.uint16), None),
                 (11, masks, {"words": 3}), (11, masks, {"nc": 40})]:
         with pytest.raises(pyrit.PyritError) as ei:
             pyrit.pyrit_jit_source(*bad)
@@ -296,7 +296,7 @@ def test_generated_parity_network_random_masks(n):
     rng = np.random.default_rng(2000 + n)
     w = _w_of(n)
     for trial in range(4):
-        nin = int(rng.integers(1, 33))
+        nin = int(rng.integers(1, 65))
         nout = int(rng.integers(1, 9))
         masks = rng.integers(0, 1 << n, size=(nout, nin)).astype(np.uint16)
         masks[-1][-1] = (1 << n) - 1
