@@ -87,11 +87,12 @@ def make_plan(pyrit, generator, w, k, m, transform="embedding"):
     """The library plan of a code: the plain Cauchy generator, or the weight-optimised generalized
     Cauchy one (the oracle legs compute their own copy; a CPU test pins the two equal), under the
     embedding or the parity transform (Sec. 2.3)."""
+    n = 9 if w == 6 else w + 1  # GF(2^6) from x^6 + x^3 + 1 lives in R_{2,9}; the others in R_{2,w+1}
     if generator == "weighted":
-        G, _ = pyrit.pyrit_generator_weighted(w, w + 1, k, m)
-        plan = pyrit.pyrit_plan_create(w, w + 1, k, m, G)
+        G, _ = pyrit.pyrit_generator_weighted(w, n, k, m)
+        plan = pyrit.pyrit_plan_create(w, n, k, m, G)
     else:
-        plan = pyrit.pyrit_plan_create(w, w + 1, k, m)
+        plan = pyrit.pyrit_plan_create(w, n, k, m)
     if transform == "parity":
         pyrit.pyrit_plan_set_transform(plan, pyrit.PYRIT_TRANSFORM_PARITY)
     return plan
@@ -236,11 +237,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--stripes", type=int, default=STRIPES,
                     help="stripes per GPU (default 256; smaller values make profiling cases)")
-    ap.add_argument("--workload", default="coding", choices=["coding", "sweep", "mixed", "served", "gf16", "transforms"],
+    ap.add_argument("--workload", default="coding", choices=["coding", "sweep", "mixed", "served", "gf16", "transforms", "paper"],
                     help="coding: the default line; sweep: GF(2^12) k=16 m=4 packet sweep 4 KiB-1 MiB; mixed: "
                          "4096 uneven stripes batched vs per-stripe launches; served: Poisson arrivals; gf16: "
                          "GF(16) k=4 m=2, one stripe, encode + every erasure pattern (L2-resident); transforms: "
-                         "embedding vs parity transform on k >= m and k < m codes")
+                         "embedding vs parity transform on k >= m and k < m codes; paper: the paper's (12,8), (60,40) and "
+                         "(60,20) use cases across block sizes")
     ap.add_argument("--seconds", type=float, default=10.0, help="served: arrival window")
     ap.add_argument("--generator", default="cauchy", choices=["cauchy", "weighted"],
                     help="cauchy: the plain Cauchy code of the configurations; weighted: the same code "
@@ -256,7 +258,7 @@ def main():
         return run_reference(args)
     if args.workload != "coding":
         return {"sweep": run_sweep, "mixed": run_mixed, "served": run_served, "gf16": run_gf16,
-                "transforms": run_transforms}[args.workload](args)
+                "transforms": run_transforms, "paper": run_paper}[args.workload](args)
     if args.stripes != STRIPES:
         STRIPES = max(8, args.stripes // 8 * 8)
         CONFIG["stripes"] = STRIPES
@@ -603,6 +605,72 @@ def run_transforms(args):
             pyrit.pyrit_plan_destroy(plan)
         del buf
         torch.cuda.empty_cache()
+
+
+def run_paper(args):
+    """The paper's three use cases (Sec. 5): (n, k) = (12, 8) over GF(2^4) with the embedding,
+    (60, 40) over GF(2^6) with the embedding and (60, 20) over GF(2^6) with the parity transform
+    (GF(2^6) from x^6 + x^3 + 1, Sec. 2.4), encode and decode across block sizes. Decoding rebuilds
+    n - k lost blocks, the same ones in every stripe (failed devices). Stripes fill ~2 GiB of
+    source per point (larger than L2); batches are tuned; a sampled stripe of each point is checked
+    against the oracle's codec for its transform."""
+    torch, pyrit, dev = _setup_gpu()
+    from paper_1709_00178_gb300.synth import BASE_SEED
+    import numpy as np
+    import oracle
+    peak, _ = peak_hbm()
+    stream = torch.cuda.Stream(device=dev)
+    cases = [("(12,8) GF(2^4) embedding", 4, 8, 4, "embedding"),
+             ("(60,40) GF(2^6) embedding", 6, 40, 20, "embedding"),
+             ("(60,20) GF(2^6) parity transform", 6, 20, 40, "parity")]
+    for name, w, k, m, transform in cases:
+        n = 9 if w == 6 else w + 1
+        plan = make_plan(pyrit, args.generator, w, k, m, transform)
+        G = oracle.cauchy_weighted(w, k, m)[0] if args.generator == "weighted" else oracle.cauchy(w, k, m)
+        o_enc, o_dec = oracle_codec(transform)
+        rng = np.random.default_rng(BASE_SEED + 5 + k)
+        lost = sum(1 << int(x) for x in rng.choice(k + m, m, replace=False))
+        for block_kib in (64, 256, 1024, 4096):
+            P = block_kib * 1024 // w // 16 * 16
+            blk = w * P
+            S = max(8, (2 << 30) // (k * blk))
+            buf = torch.empty(S * (k + m) * blk, dtype=torch.uint8, device=dev)
+            pyrit.pyrit_synth_fill(buf.data_ptr(), buf.numel(), BASE_SEED + 5, 0)
+            torch.cuda.synchronize()
+            base, par0 = buf.data_ptr(), S * k * blk
+            blocks = [[base + (s * k + j) * blk for j in range(k)] + [base + par0 + (s * m + i) * blk for i in range(m)]
+                      for s in range(S)]
+            enc = pyrit.pyrit_batch_create([(plan, 0, 0, P, blocks[s]) for s in range(S)])
+            dec = pyrit.pyrit_batch_create([(plan, 1, lost, P, blocks[s]) for s in range(S)])
+            pyrit.pyrit_batch_tune(enc, stream, 2)
+            pyrit.pyrit_batch_tune(dec, stream, 2)
+            te = _time_batch(torch, pyrit, enc, stream, args.steps)
+            td = _time_batch(torch, pyrit, dec, stream, args.steps)
+            torch.cuda.synchronize()
+            # the last runs decoded the encoded stripes in place: stripe 0 must be the oracle's codeword
+            # (checked on its first 2 KiB columns: every byte column is an independent codeword)
+            cw = min(P, 2048)
+            data0 = np.ascontiguousarray(buf[:k * blk].cpu().numpy().reshape(k, w, P)[:, :, :cw])
+            want = o_enc(w, k, m, G, data0, nthreads=os.cpu_count() or 1)
+            got = buf[par0:par0 + m * blk].cpu().numpy().reshape(m, w, P)[:, :, :cw]
+            ok = bool(np.array_equal(got, want))
+            es, ds = pyrit.pyrit_batch_stats(enc), pyrit.pyrit_batch_stats(dec)
+            ae, ad = es["alg_bytes"] / te / 1e6, ds["alg_bytes"] / td / 1e6
+            print(json.dumps({
+                "metric": "encode / decode GB/s of source data", "workload": "paper",
+                "config": {"workload": name, "w": w, "n": n, "k": k, "m": m, "block_bytes": blk, "packet_bytes": P,
+                           "stripes": S, "lost_blocks": m, "transform": transform, "generator": args.generator},
+                "encode_gbs": es["src_bytes"] / te / 1e6, "decode_gbs": ds["src_bytes"] / td / 1e6,
+                "encode_ms": te, "decode_ms": td, "encode_roofline_frac": ae / peak, "decode_roofline_frac": ad / peak,
+                "encode_kernel": kernel_name(pyrit.pyrit_batch_shape(enc, 0)),
+                "decode_kernel": kernel_name(pyrit.pyrit_batch_shape(dec, 0)),
+                "launches": [es["launches"], ds["launches"]], "oracle_parity_stripe0": ok,
+                "dtype": "u8", "data": "synthetic"}), flush=True)
+            pyrit.pyrit_batch_destroy(enc)
+            pyrit.pyrit_batch_destroy(dec)
+            del buf
+            torch.cuda.empty_cache()
+        pyrit.pyrit_plan_destroy(plan)
 
 
 def run_gf16(args):

@@ -375,8 +375,12 @@ int shapes_for(int n, int nout, bool syndrome, NetSpec* out, int cap) {
                                 {1, 0, 1, 16}, {4, 0, 1, 11}, {2, 1, 1, 11}, {1, 0, 1, 12}};
   static const Shape4 n9_s[] = {{2, 0, 1, 15}, {2, 0, 1, 12}, {2, 0, 1, 11}, {4, 0, 1, 8},
                                 {1, 0, 1, 16}, {2, 0, 1, 8}, {1, 0, 1, 15}, {4, 0, 1, 11}};
+  // GF(2^6) with 5-8 outputs per job (the paper's (60, 40) and (60, 20) codes): one word per thread
+  // and 15 warps measured best, two words spill at 8 outputs
+  static const Shape4 n9_w[] = {{1, 0, 1, 15}, {1, 0, 1, 11}, {1, 0, 1, 12}, {1, 0, 1, 16},
+                                {2, 0, 1, 11}, {2, 0, 1, 15}, {1, 0, 1, 8}, {2, 0, 1, 8}};
   const bool wide = nout > 4;
-  const Shape4* list = n == 9    ? (syndrome ? n9_s : n9_d)
+  const Shape4* list = n == 9    ? (wide ? n9_w : (syndrome ? n9_s : n9_d))
                        : n == 11 ? (syndrome ? (wide ? n11_sw : n11_s) : (wide ? n11_dw : n11_d))
                        : n == 13 ? (syndrome ? (wide ? n13_sw : n13_s) : (wide ? n13_dw : n13_d))
                                  : (syndrome ? small_s : small_d);
