@@ -421,7 +421,7 @@ PYRIT_API void pyrit_server_destroy(pyrit_server_t server);
  * or a latency-bound path that cannot take cudaMalloc's implicit device synchronisation.
  *
  * Scratch. The job descriptors, the tile list and two status words live in one fixed file-scope
- * device array of 532 KiB (256 + PYRIT_NOALLOC_MAX_STRIPES * 1616 + PYRIT_NOALLOC_MAX_TILES * 8
+ * device array of 536 KiB (256 + PYRIT_NOALLOC_MAX_STRIPES * 1632 + PYRIT_NOALLOC_MAX_TILES * 8
  * bytes) inside the library's module image: every GPU that loads the library holds it until the
  * process exits. The caller passes every input and output buffer; no cudaMalloc, cudaFree or other
  * allocating routine is called (on the host, a decoding matrix for an erasure pattern that a plan has

@@ -17,6 +17,7 @@ namespace pyrit {
 static_assert(kMaxIn == PYRIT_MAX_K && kMaxOut == PYRIT_JOB_OUTPUTS, "job limits follow the C ABI's");
 constexpr int kMaxBlocks = PYRIT_MAX_BLOCKS;                      // k + m of a stripe
 constexpr int kMaxJobs = (PYRIT_MAX_M + kMaxOut - 1) / kMaxOut;  // jobs of one stripe
+static_assert(sizeof(JobDesc) == 1632, "the job descriptor size is documented in pyrit.h (no-alloc scratch)");
 
 // Field degree w carried by the ring R_{2,n}: RingDim<n>::W for a run-time n.
 inline int field_degree(int n) { return n == 9 ? 6 : n - 1; }
