@@ -36,6 +36,13 @@ def lib():
             "oracle_field_poly": (u64, [i32]),
             "oracle_ring_size": (i32, [i32]),
             "oracle_phi_P": (u32, [i32, i32, u32]),
+            "oracle_ring_factor": (u64, [i32, i32]),
+            "oracle_gf_mul_mod": (u32, [i32, u64, u32, u32]),
+            "oracle_cauchy_mod": (i32, [i32, u64, i32, i32, vp]),
+            "oracle_gf_invert_mod": (i32, [i32, u64, i32, vp, vp]),
+            "oracle_encode_mod": (i32, [i32, u64, i32, i32, vp, vp, vp, sz, i32]),
+            "oracle_decode_mod": (i32, [i32, u64, i32, i32, vp, vp, u64, sz, i32]),
+            "oracle_sparse_rep_mod": (u32, [i32, i32, u64, u32]),
             "oracle_gf_mul_slow": (u32, [i32, u32, u32]),
             "oracle_gf_order": (u32, [i32, u32]),
             "oracle_gf_primitive": (u32, [i32]),
@@ -108,6 +115,62 @@ def field_poly(w):
 def ring_size(w):
     """n of the ring R_{2,n} carrying GF(2^w) (w + 1 for an AOP, 9 for GF(2^6)); 0 if none."""
     return int(lib().oracle_ring_size(w))
+
+
+def ring_factor(w, n):
+    """The smallest irreducible factor of degree w of x^n + 1 (n odd; Props. 1-2), 0 if none."""
+    return int(lib().oracle_ring_factor(w, n))
+
+
+def gf_mul_mod(w, poly, a, b):
+    """Product in F2[x]/(poly) by the definition (carry-less product, remainder)."""
+    return int(lib().oracle_gf_mul_mod(w, poly, a, b))
+
+
+def cauchy_mod(w, poly, k, m):
+    G = np.zeros((k + m, k), np.uint32)
+    rc = lib().oracle_cauchy_mod(w, poly, k, m, _p(G))
+    if rc:
+        raise ValueError("oracle_cauchy_mod(w=%d,poly=%#x,k=%d,m=%d) -> %d" % (w, poly, k, m, rc))
+    return G
+
+
+def gf_invert_mod(w, poly, A):
+    A = _u32(A)
+    k = A.shape[0]
+    inv = np.zeros_like(A)
+    rc = lib().oracle_gf_invert_mod(w, poly, k, _p(A), _p(inv))
+    if rc:
+        raise ValueError("singular")
+    return inv
+
+
+def encode_mod(w, poly, k, m, G, data, nthreads=1):
+    """encode() over F2[x]/(poly)."""
+    G = _u32(G)
+    data = np.ascontiguousarray(data, dtype=np.uint8)
+    P = data.size // (k * w)
+    parity = np.zeros((m, w, P), np.uint8)
+    rc = lib().oracle_encode_mod(w, poly, k, m, _p(G), _p(data), _p(parity), P, nthreads)
+    if rc:
+        raise ValueError("oracle_encode_mod -> %d" % rc)
+    return parity
+
+
+def decode_mod(w, poly, k, m, G, blocks, erased, nthreads=1):
+    """decode() over F2[x]/(poly)."""
+    G = _u32(G)
+    out = np.array(blocks, dtype=np.uint8, copy=True, order="C")
+    P = out.size // ((k + m) * w)
+    rc = lib().oracle_decode_mod(w, poly, k, m, _p(G), _p(out), erased, P, nthreads)
+    if rc:
+        raise ValueError("oracle_decode_mod -> %d" % rc)
+    return out.reshape(k + m, w, P)
+
+
+def sparse_rep_mod(w, n, poly, u):
+    """phi_S over the representatives of u mod poly in R_{2,n}."""
+    return int(lib().oracle_sparse_rep_mod(w, n, poly, u))
 
 
 def phi_P(w, n, b):

@@ -130,21 +130,39 @@ int oracle_ring_size(int w) {
 /* The field GF(2^w) = F2[x]/(AOP or ESP) (Sec. 2.1, Sec. 2.3, Sec. 2.4)                       */
 /* ------------------------------------------------------------------------------------------ */
 
-/* Field product by the definition: carry-less product, then remainder mod the field's modulus. */
-uint32_t oracle_gf_mul_slow(int w, uint32_t a, uint32_t b) {
-  return (uint32_t)oracle_poly_mod(oracle_poly_mul(a, b), oracle_field_poly(w));
+/* Field product by the definition: carry-less product, then remainder mod the modulus `poly`
+ * (any irreducible polynomial of degree w: the AOP, an ESP, or another factor of x^n + 1). */
+uint32_t oracle_gf_mul_mod(int w, uint64_t poly, uint32_t a, uint32_t b) {
+  (void)w;
+  return (uint32_t)oracle_poly_mod(oracle_poly_mul(a, b), poly);
 }
+
+/* The same under the library's default modulus for w. */
+uint32_t oracle_gf_mul_slow(int w, uint32_t a, uint32_t b) { return oracle_gf_mul_mod(w, oracle_field_poly(w), a, b); }
 
 /* Multiplicative order of a nonzero element (0 if its powers reach 0 or never return to 1,
  * which only happens when the modulus is reducible). */
-uint32_t oracle_gf_order(int w, uint32_t g) {
+static uint32_t gf_order_mod(int w, uint64_t poly, uint32_t g) {
   uint32_t q = (1u << w);
   uint32_t v = g;
   for (uint32_t e = 1; e <= q; e++) {
     if (v == 1) return e;
     if (v == 0) return 0;
-    v = oracle_gf_mul_slow(w, v, g);
+    v = oracle_gf_mul_mod(w, poly, v, g);
   }
+  return 0;
+}
+
+uint32_t oracle_gf_order(int w, uint32_t g) { return gf_order_mod(w, oracle_field_poly(w), g); }
+
+/* The smallest irreducible factor of degree w of x^n + 1 (n odd, Props. 1-2: x^n + 1 is then a
+ * product of distinct irreducible polynomials), by trial over the degree-w polynomials in
+ * increasing order; 0 if there is none. */
+uint64_t oracle_ring_factor(int w, int n) {
+  if (w < 1 || w > ORACLE_MAX_W || n < 3 || n > 31 || (n & 1) == 0) return 0;
+  const uint64_t xn1 = ((uint64_t)1 << n) | 1;
+  for (uint64_t p = (uint64_t)1 << w; p < ((uint64_t)1 << (w + 1)); p++)
+    if (oracle_poly_mod(xn1, p) == 0 && oracle_poly_irreducible(p)) return p;
   return 0;
 }
 
@@ -160,18 +178,21 @@ typedef struct {
  * element x (= 2) has order w+1 (x^{w+1} = 1), under an ESP of degree s r order s (r + 1), so it
  * is not primitive; the paper does not name a generator, hence the search. Returns 0 if none
  * exists. */
-uint32_t oracle_gf_primitive(int w) {
-  if (w < 2 || w > ORACLE_MAX_W || !oracle_field_poly(w)) return 0;
+static uint32_t gf_primitive_mod(int w, uint64_t poly) {
+  if (w < 2 || w > ORACLE_MAX_W || !poly || poly_deg(poly) != w || !oracle_poly_irreducible(poly)) return 0;
   uint32_t q1 = (1u << w) - 1;
   for (uint32_t g = 2; g <= q1; g++)
-    if (oracle_gf_order(w, g) == q1) return g;
+    if (gf_order_mod(w, poly, g) == q1) return g;
   return 0;
 }
 
-static int gf_init(gf_t* f, int w) {
+uint32_t oracle_gf_primitive(int w) { return gf_primitive_mod(w, oracle_field_poly(w)); }
+
+/* Log/antilog tables of GF(2^w) = F2[x]/(poly) over its smallest primitive element. */
+static int gf_init_mod(gf_t* f, int w, uint64_t poly) {
   f->w = w;
   f->q1 = (1u << w) - 1;
-  f->g = oracle_gf_primitive(w);
+  f->g = gf_primitive_mod(w, poly);
   f->log = NULL;
   f->alog = NULL;
   if (!f->g) return -1;
@@ -182,10 +203,12 @@ static int gf_init(gf_t* f, int w) {
   for (uint32_t e = 0; e < f->q1; e++) {
     f->alog[e] = v;
     f->log[v] = e;
-    v = oracle_gf_mul_slow(w, v, f->g);
+    v = oracle_gf_mul_mod(w, poly, v, f->g);
   }
   return 0;
 }
+
+static int gf_init(gf_t* f, int w) { return gf_init_mod(f, w, oracle_field_poly(w)); }
 
 static void gf_free(gf_t* f) {
   free(f->log);
@@ -235,11 +258,11 @@ uint32_t oracle_gf_mul(int w, uint32_t a, uint32_t b) {
  * The paper names generalized Cauchy matrices without their parameters; this is the plain
  * Cauchy matrix on those points. It needs k + m <= 2^w so that all points are distinct.
  * Returns 0, or -1 for an unsupported field, -2 for k + m > 2^w. */
-int oracle_cauchy(int w, int k, int m, uint32_t* G) {
+int oracle_cauchy_mod(int w, uint64_t poly, int k, int m, uint32_t* G) {
   if (k < 1 || m < 0 || k > ORACLE_MAX_K) return -2;
   if ((uint64_t)k + (uint64_t)m > ((uint64_t)1 << w)) return -2;
   gf_t f;
-  if (gf_init(&f, w)) {
+  if (gf_init_mod(&f, w, poly)) {
     gf_free(&f);
     return -1;
   }
@@ -250,6 +273,8 @@ int oracle_cauchy(int w, int k, int m, uint32_t* G) {
   gf_free(&f);
   return 0;
 }
+
+int oracle_cauchy(int w, int k, int m, uint32_t* G) { return oracle_cauchy_mod(w, oracle_field_poly(w), k, m, G); }
 
 /* Gauss-Jordan inverse of a k x k matrix over GF(2^w). The pivot of column c is the first row
  * at or below row c with a nonzero entry in column c. Returns 0, or -1 if singular. */
@@ -289,15 +314,19 @@ static int gf_invert(const gf_t* f, int k, const uint32_t* A, uint32_t* Inv) {
   return 0;
 }
 
-int oracle_gf_invert(int w, int k, const uint32_t* A, uint32_t* Inv) {
+int oracle_gf_invert_mod(int w, uint64_t poly, int k, const uint32_t* A, uint32_t* Inv) {
   gf_t f;
-  if (gf_init(&f, w)) {
+  if (gf_init_mod(&f, w, poly)) {
     gf_free(&f);
     return -2;
   }
   int rc = gf_invert(&f, k, A, Inv);
   gf_free(&f);
   return rc;
+}
+
+int oracle_gf_invert(int w, int k, const uint32_t* A, uint32_t* Inv) {
+  return oracle_gf_invert_mod(w, oracle_field_poly(w), k, A, Inv);
 }
 
 /* ------------------------------------------------------------------------------------------ */
@@ -357,13 +386,13 @@ static void run_threads(void* (*fn)(void*), void* jobs, size_t job_size, int nth
 
 /* Encodes one stripe. data: k blocks of w*P bytes, contiguous; parity: m blocks, written.
  * Returns 0, -1 for an unsupported field, -3 for bad sizes. */
-int oracle_encode(int w, int k, int m, const uint32_t* G, const uint8_t* data, uint8_t* parity,
-                  size_t P, int nthreads) {
+int oracle_encode_mod(int w, uint64_t poly, int k, int m, const uint32_t* G, const uint8_t* data,
+                      uint8_t* parity, size_t P, int nthreads) {
   if (k < 1 || k > ORACLE_MAX_K || m < 0 || P == 0) return -3;
   if (nthreads < 1) nthreads = 1;
   if ((size_t)nthreads > P) nthreads = (int)P;
   gf_t f;
-  if (gf_init(&f, w)) {
+  if (gf_init_mod(&f, w, poly)) {
     gf_free(&f);
     return -1;
   }
@@ -376,6 +405,11 @@ int oracle_encode(int w, int k, int m, const uint32_t* G, const uint8_t* data, u
   run_threads(enc_run, jobs, sizeof(enc_job_t), nthreads);
   gf_free(&f);
   return 0;
+}
+
+int oracle_encode(int w, int k, int m, const uint32_t* G, const uint8_t* data, uint8_t* parity, size_t P,
+                  int nthreads) {
+  return oracle_encode_mod(w, oracle_field_poly(w), k, m, G, data, parity, P, nthreads);
 }
 
 typedef struct {
@@ -424,8 +458,8 @@ static void* dec_run(void* arg) {
  * first k non-erased blocks in index order (the paper does not say which to use; the result
  * is the same for any choice because the code is MDS).
  * Returns 0, -1 unsupported field, -3 bad sizes, -4 more than m erasures, -5 singular. */
-int oracle_decode(int w, int k, int m, const uint32_t* G, uint8_t* blocks, uint64_t erased,
-                  size_t P, int nthreads) {
+int oracle_decode_mod(int w, uint64_t poly, int k, int m, const uint32_t* G, uint8_t* blocks,
+                      uint64_t erased, size_t P, int nthreads) {
   if (k < 1 || k > ORACLE_MAX_K || m < 0 || k + m > 64 || P == 0) return -3;
   int ne = 0;
   for (int e = 0; e < k + m; e++) ne += (int)((erased >> e) & 1);
@@ -433,7 +467,7 @@ int oracle_decode(int w, int k, int m, const uint32_t* G, uint8_t* blocks, uint6
   if (ne > m) return -4;
   if (ne == 0) return 0;
   gf_t f;
-  if (gf_init(&f, w)) {
+  if (gf_init_mod(&f, w, poly)) {
     gf_free(&f);
     return -1;
   }
@@ -462,6 +496,11 @@ int oracle_decode(int w, int k, int m, const uint32_t* G, uint8_t* blocks, uint6
   free(Inv);
   gf_free(&f);
   return rc;
+}
+
+int oracle_decode(int w, int k, int m, const uint32_t* G, uint8_t* blocks, uint64_t erased, size_t P,
+                  int nthreads) {
+  return oracle_decode_mod(w, oracle_field_poly(w), k, m, G, blocks, erased, P, nthreads);
 }
 
 /* ------------------------------------------------------------------------------------------ */
@@ -514,8 +553,8 @@ static int popcount32(uint32_t v) {
 
 /* Sparse transform phi_S (Sec. 2.2): the representative of u with the fewest ones; ties go to
  * the smallest integer (they cannot occur for an AOP with n odd; they do for the ESP). */
-uint32_t oracle_sparse_rep(int w, int n, uint32_t u) {
-  uint64_t p = oracle_field_poly(w);
+uint32_t oracle_sparse_rep_mod(int w, int n, uint64_t p, uint32_t u) {
+  (void)w;
   uint32_t best = 0;
   int bw = 99;
   for (uint32_t r = 0; r < (1u << n); r++)
@@ -528,6 +567,8 @@ uint32_t oracle_sparse_rep(int w, int n, uint32_t u) {
     }
   return best;
 }
+
+uint32_t oracle_sparse_rep(int w, int n, uint32_t u) { return oracle_sparse_rep_mod(w, n, oracle_field_poly(w), u); }
 
 /* ------------------------------------------------------------------------------------------ */
 /* Element-wise batch forms of the above, so that exhaustive tests do not pay one foreign call */
