@@ -56,8 +56,8 @@ typedef struct CUstream_st* pyrit_stream_t;
 /* ---- status codes ------------------------------------------------------------------------ */
 #define PYRIT_OK 0
 #define PYRIT_E_INVALID_ARG -1        /* null pointer, P = 0, k/m out of range, bad mask bits  */
-#define PYRIT_E_UNSUPPORTED_FIELD -2  /* (w, n) is not an irreducible AOP with n = w+1 or the
-                                         ESP field w = 6, n = 9 (or no kernels for that n)      */
+#define PYRIT_E_UNSUPPORTED_FIELD -2  /* x^n + 1 (n odd, 3 <= n <= 15) has no irreducible
+                                         factor of degree w                                     */
 #define PYRIT_E_TOO_LONG -3           /* k + m > 2^w: the default Cauchy code needs distinct points */
 #define PYRIT_E_NOT_MDS -4            /* generator not systematic, entry >= 2^w, or a singular
                                          k x k submatrix was found                              */
@@ -100,9 +100,13 @@ typedef struct pyrit_plan_s* pyrit_plan_t;
 /* Creates a coding plan for a systematic (k+m, k) code over GF(2^w) carried by R_{2,n}.
  *   w, n : field degree and ring size. Either n = w + 1 with the AOP of degree w irreducible
  *          (w+1 prime with 2 a primitive root mod w+1, Sec. 2.3), or the s-ESP of degree w = s r,
- *          n = s (r + 1), irreducible by the criterion Sec. 2.4 quotes. The kernels are built for
- *          (w, n) in {(2, 3), (4, 5), (6, 9), (10, 11), (12, 13)}; (6, 9) is GF(2^6) from
- *          x^6 + x^3 + 1.
+ *          n = s (r + 1), irreducible by the criterion Sec. 2.4 quotes. The generic kernels are
+ *          built for (w, n) in {(2, 3), (4, 5), (6, 9), (10, 11), (12, 13)}; (6, 9) is GF(2^6)
+ *          from x^6 + x^3 + 1. Any other odd n <= 15 with an irreducible factor of degree w of
+ *          x^n + 1 (Props. 1-2; e.g. GF(8) on n = 7, GF(16) from x^4 + x + 1 on n = 15) gives a
+ *          field whose modulus is the smallest such factor: the embedding only, coded by generated
+ *          networks only (single calls and batches; the server and the allocation-free entry point
+ *          return PYRIT_E_UNSUPPORTED).
  *   k, m : 1 <= k <= PYRIT_MAX_K, 0 <= m <= PYRIT_MAX_M, k + m <= PYRIT_MAX_BLOCKS.
  *   G    : NULL for the default generator [I_k ; C], C[i][j] = 1/(x_i + y_j) with x_i = k+i,
  *          y_j = j (a Cauchy matrix, Sec. 3 "generalized Cauchy matrices"; requires
@@ -145,6 +149,11 @@ PYRIT_API int pyrit_plan_set_transform(pyrit_plan_t plan, int transform);
 
 /* Plan parameters (any pointer may be NULL). */
 PYRIT_API int pyrit_plan_info(pyrit_plan_t plan, int* w, int* n, int* k, int* m);
+
+/* The plan's field: its modulus g (bit i = coefficient of x^i) and whether the generic kernels are
+ * built for it (*native_out = 1 for the AOP rings and GF(2^6) on n = 9; 0 for a field from another
+ * factor of x^n + 1, which only generated networks code). Any pointer may be NULL. */
+PYRIT_API int pyrit_plan_modulus(pyrit_plan_t plan, uint32_t* g_out, int* native_out);
 
 /* Copies the (k+m) x k generator, row-major, into G_out. */
 PYRIT_API int pyrit_plan_generator(pyrit_plan_t plan, uint32_t* G_out);
@@ -330,6 +339,13 @@ PYRIT_API int pyrit_plan_specialise(pyrit_plan_t plan, int op, uint64_t erasures
  * nothing to code, a planning error, or PYRIT_E_JIT. */
 PYRIT_API int pyrit_plan_network_info(pyrit_plan_t plan, int op, uint64_t erasures, const pyrit_tile_t* tile,
                                       int* info_out);
+
+/* The CUDA C++ source of the network pyrit_plan_specialise would compile for the same arguments
+ * (the first job's, for a stripe of several jobs), NUL-terminated (truncated to cap - 1) into buf;
+ * returns its length, PYRIT_E_INVALID_ARG when there is nothing to code, or a planning error.
+ * For inspection and tests; host only. */
+PYRIT_API int pyrit_plan_network_source(pyrit_plan_t plan, int op, uint64_t erasures, const pyrit_tile_t* tile,
+                                        char* buf, int cap);
 
 /* Waits up to timeout_ms for the background compiler to finish its queue: PYRIT_OK or
  * PYRIT_E_TIMEOUT. */

@@ -28,6 +28,8 @@ struct Group {
   const pyrit_plan_s* syn_plan = nullptr;  // all jobs decode this plan: its syndrome network applies
   size_t syn_off = 0;                      // the syndrome-form jobs in the device allocation
   int transform = PYRIT_TRANSFORM_EMBEDDING;  // the group's stripes all use this transform
+  uint32_t net_g = 0;     // the field's modulus for generated networks (0: the ring's native field)
+  bool net_only = false;  // only generated networks code the group (parity transform, other field)
 };
 
 // The group's device job array for a variant (syndrome networks take syndrome-form jobs).
@@ -135,10 +137,25 @@ int pyrit_batch_create(const pyrit_stripe_t* stripes, int count, const pyrit_til
   if (!b) return PYRIT_E_OOM;
   cudaGetDevice(&b->device);
 
-  // Jobs per (ring size, transform), in stripe order (with the stripe each came from): slot n for
-  // the embedding transform, 16 + n for the parity transform.
-  std::vector<std::vector<JobDesc>> by_n(32);
-  std::vector<std::vector<int>> src_of(32);
+  // Jobs per (ring size, transform, field), in stripe order (with the stripe each came from): one
+  // launch group each.
+  struct SlotKey {
+    int n, transform;
+    uint32_t g;
+  };
+  std::vector<SlotKey> keys;
+  std::vector<std::vector<JobDesc>> by_n;
+  std::vector<std::vector<int>> src_of;
+  auto slot_of = [&](const pyrit_plan_s* p) {
+    const SlotKey k{p->n, p->transform == PYRIT_TRANSFORM_PARITY ? PYRIT_TRANSFORM_PARITY : PYRIT_TRANSFORM_EMBEDDING,
+                    plan_net_g(p)};
+    for (size_t i = 0; i < keys.size(); ++i)
+      if (keys[i].n == k.n && keys[i].transform == k.transform && keys[i].g == k.g) return i;
+    keys.push_back(k);
+    by_n.emplace_back();
+    src_of.emplace_back();
+    return keys.size() - 1;
+  };
   for (int i = 0; i < count; ++i) {
     JobDesc jobs[kMaxJobs];
     int nj = 0;
@@ -152,14 +169,15 @@ int pyrit_batch_create(const pyrit_stripe_t* stripes, int count, const pyrit_til
     if (nj == 0) continue;
     b->alg_bytes += alg;
     const int n = stripes[i].plan->n;
-    const bool parity = stripes[i].plan->transform == PYRIT_TRANSFORM_PARITY;
+    const bool net_only = network_only(stripes[i].plan);
     // a stripe's jobs (one per group of up to kMaxOut outputs) stay adjacent in the group, so
     // that their tiles, which read the same source columns, run close together and share L2
     for (int q = 0; q < nj; ++q) {
       if (job_is_staged(jobs[q])) {
-        by_n[n + (parity ? 16 : 0)].push_back(jobs[q]);
-        src_of[n + (parity ? 16 : 0)].push_back(i);
-      } else if (parity) {  // the plain-load kernel has no parity transform
+        const size_t slot = slot_of(stripes[i].plan);
+        by_n[slot].push_back(jobs[q]);
+        src_of[slot].push_back(i);
+      } else if (net_only) {  // the plain-load kernel has neither the parity transform nor other fields
         delete b;
         return PYRIT_E_UNSUPPORTED;
       } else {
@@ -176,13 +194,15 @@ int pyrit_batch_create(const pyrit_stripe_t* stripes, int count, const pyrit_til
     std::memcpy(image.data() + off, src, bytes);
     return off;
   };
-  for (int slot = 0; slot < 32; ++slot) {
+  for (size_t slot = 0; slot < keys.size(); ++slot) {
     std::vector<JobDesc>& jobs = by_n[slot];
     if (jobs.empty()) continue;
-    const int n = slot & 15;
+    const int n = keys[slot].n;
     Group g;
-    g.transform = slot >= 16 ? PYRIT_TRANSFORM_PARITY : PYRIT_TRANSFORM_EMBEDDING;
-    const bool parity = slot >= 16;
+    g.transform = keys[slot].transform;
+    g.net_g = keys[slot].g;
+    g.net_only = g.transform == PYRIT_TRANSFORM_PARITY || g.net_g != 0;
+    const bool parity = g.net_only;  // generated networks only
     int max_nout = 0;
     bool same_p = true, shared = true;
     for (const JobDesc& j : jobs) {
@@ -208,11 +228,12 @@ int pyrit_batch_create(const pyrit_stripe_t* stripes, int count, const pyrit_til
     std::vector<const JobDesc*> tptr;
     for (const JobDesc& t : g.tables) tptr.push_back(&t);
     auto table_spec = [&](int words, int mg, int minb, int nc) {
-      return net_spec_tables(n, tptr.data(), (int)tptr.size(), words, mg, minb, nc, g.transform);
+      return net_spec_tables(n, tptr.data(), (int)tptr.size(), words, mg, minb, nc, g.transform, g.net_g);
     };
     // Syndrome decoding: every job decodes a stripe of one plan whose columns fit a job.
     const pyrit_plan_s* plan0 = stripes[src_of[slot][0]].plan;
-    bool syn = plan0->k + plan0->m <= kMaxIn && plan0->m <= kMaxOut;  // one decode job per stripe
+    // one decode job per stripe; the syndrome store reduces in the native fields only
+    bool syn = plan0->k + plan0->m <= kMaxIn && plan0->m <= kMaxOut && plan0->native;
     for (int si : src_of[slot]) syn = syn && stripes[si].op == PYRIT_OP_DECODE && stripes[si].plan == plan0;
     std::vector<JobDesc> syn_jobs;
     if (syn) {
@@ -358,7 +379,7 @@ int pyrit_batch_tune(pyrit_batch_t b, pyrit_stream_t stream, int iters) {
   const Variant* all = variants(&nv);
   for (Group& g : b->groups) {
     std::vector<const Variant*> cands;
-    const bool parity = g.transform == PYRIT_TRANSFORM_PARITY;  // generated networks only
+    const bool parity = g.net_only;  // generated networks only
     for (int i = 0; i < nv && !parity; ++i)
       if (all[i].n == g.key.n) cands.push_back(&all[i]);
     if (g.netable && jit_mode() != PYRIT_JIT_OFF) {
@@ -369,7 +390,7 @@ int pyrit_batch_tune(pyrit_batch_t b, pyrit_stream_t stream, int iters) {
       for (const JobDesc& t : g.tables) tptr.push_back(&t);
       for (int i = 0; i < ns; ++i)
         specs[i] = net_spec_tables(g.key.n, tptr.data(), (int)tptr.size(), specs[i].words, specs[i].mg,
-                                   specs[i].minb, specs[i].nc, g.transform);
+                                   specs[i].minb, specs[i].nc, g.transform, g.net_g);
       add_networks(specs, ns, &cands);
     } else if (g.syn_plan && jit_mode() != PYRIT_JIT_OFF) {
       NetSpec specs[8];

@@ -10,16 +10,16 @@ namespace {
 // Codes one job: the staged kernel when P and every pointer allow 16-byte bulk copies, else the
 // plain-load kernel. The staged kernel is the generated network of the job's mask table when one
 // is compiled (a missing one is queued under PYRIT_JIT_ASYNC), else the generic one. Under the
-// parity transform only a generated network codes the job: it is compiled in the call if
-// missing, and anything else is PYRIT_E_UNSUPPORTED. The job travels in the kernel's parameters:
-// no coding state is allocated.
+// parity transform, or for a field the generic kernels are not built for, only a generated
+// network codes the job: it is compiled in the call if missing, and anything else is
+// PYRIT_E_UNSUPPORTED. The job travels in the kernel's parameters: no coding state is allocated.
 int run_job(const pyrit_plan_s* plan, const JobDesc& job, cudaStream_t stream) {
   if (job.nout == 0) return PYRIT_OK;
   const int n = plan->n;
-  const bool parity = plan->transform == PYRIT_TRANSFORM_PARITY;
+  const bool parity = network_only(plan);
   if (job_is_staged(job)) {
     TileShape sh;
-    const Variant* net = net_variant(net_spec(n, job, 0, 0, 0, 0, plan->transform), parity);
+    const Variant* net = net_variant(net_spec(n, job, 0, 0, 0, 0, plan->transform, plan_net_g(plan)), parity);
     if (net)
       shape_for_variant(net, job.nout, ShapeHint(), &sh);
     else if (parity)
@@ -37,7 +37,7 @@ int run_job(const pyrit_plan_s* plan, const JobDesc& job, cudaStream_t stream) {
 // the same sources). Under the parity transform every job must be able to run on a network
 // before the first is launched.
 int run_jobs(const pyrit_plan_s* plan, const JobDesc* jobs, int nj, cudaStream_t stream) {
-  if (plan->transform == PYRIT_TRANSFORM_PARITY)
+  if (network_only(plan))
     for (int i = 0; i < nj; ++i)
       if (!job_is_staged(jobs[i])) return PYRIT_E_UNSUPPORTED;
   for (int i = 0; i < nj; ++i) {
@@ -79,7 +79,7 @@ int pyrit_decode(pyrit_plan_t plan, void* const* blocks, uint64_t erasures, size
   // in the call under the parity transform, which has no generic kernel). It exists for m <= 8,
   // where the decode is one job.
   if (e.syn_ok && nj == 1 && job_is_staged(jobs[0])) {
-    const bool block = plan->transform == PYRIT_TRANSFORM_PARITY;
+    const bool block = network_only(plan);
     if (const Variant* net = net_variant(net_spec_syndrome(plan, 0, 0, 0), block)) {
       JobDesc sj;
       make_syndrome_job(plan, e, blocks, P, &sj);

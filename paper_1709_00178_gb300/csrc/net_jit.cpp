@@ -92,7 +92,7 @@ void put(std::string& o, const char* fmt, long a = 0, long b = 0, long c = 0, lo
 
 // CUDA C++ source of a network (compiled together with the embedded ring_staged.cuh).
 std::string net_source(const NetSpec& s) {
-  const int N = s.n, W = field_degree(N), S = N - W;
+  const int N = s.n, W = s.w, S = N - W;
   const int groups = output_groups(s.mg, s.nout, s.nc);
   std::string o;
   o += "#include \"ring_staged.cuh\"\n"
@@ -114,9 +114,42 @@ std::string net_source(const NetSpec& s) {
   } else {
     o += "  __device__ __forceinline__ void tile(const JobDesc*, int, int) {}\n";
   }
-  o += "  template <int N, int WORDS, int MG>\n"
-       "  __device__ __forceinline__ void apply(uint32_t (&acc)[MG][N][WORDS],\n"
-       "                                        const uint32_t (&d)[RingDim<N>::W][WORDS], int j, int g, int) {\n";
+  if (s.g) {
+    // A field from another factor g of x^n + 1 (Props. 1-2): phi_E^{-1} is the remainder mod g,
+    // out_t = acc_t + the accumulators q >= W whose x^q mod g has coefficient t, written out here.
+    o += "  template <int N, int WORDS, int MG>\n"
+         "  __device__ __forceinline__ void store(uint32_t (&acc)[MG][N][WORDS], const JobDesc* J, int g,\n"
+         "                                        uint32_t col0, uint32_t off, bool valid) {\n"
+         "    using V = typename Vec<WORDS>::T;\n"
+         "    if (!valid) return;\n"
+         "    const uint64_t P = J->P;\n"
+         "    const int nout = J->nout;\n"
+         "#pragma unroll\n"
+         "    for (int i = 0; i < MG; ++i) {\n"
+         "      const int o = g * MG + i;\n"
+         "      if (o >= nout) continue;\n"
+         "      uint8_t* dst = J->out[o] + col0 + off;\n";
+    for (int t = 0; t < W; ++t) {
+      std::vector<int> qs;
+      for (int q = W; q < N; ++q) {
+        uint32_t r = 1u << q;  // x^q mod g
+        for (int d = q; d >= W; --d)
+          if ((r >> d) & 1u) r ^= s.g << (d - W);
+        if ((r >> t) & 1u) qs.push_back(q);
+      }
+      put(o, "      {\n        uint32_t r[WORDS];\n#pragma unroll\n        for (int x = 0; x < WORDS; ++x) {\n"
+             "          r[x] = acc[i][%ld][x];\n", t);
+      size_t i = 0;
+      for (; i + 1 < qs.size(); i += 2)
+        put(o, "          r[x] = xor3(r[x], acc[i][%ld][x], acc[i][%ld][x]);\n", qs[i], qs[i + 1]);
+      if (i < qs.size()) put(o, "          r[x] ^= acc[i][%ld][x];\n", qs[i]);
+      put(o, "        }\n        *reinterpret_cast<V*>(dst + (size_t)%ld * P) = vmake<WORDS>(r);\n      }\n", t);
+    }
+    o += "    }\n  }\n";
+  }
+  put(o, "  template <int N, int WORDS, int MG>\n"
+         "  __device__ __forceinline__ void apply(uint32_t (&acc)[MG][N][WORDS],\n"
+         "                                        const uint32_t (&d)[%ld][WORDS], int j, int g, int) {\n", W);
   if (parity) {
     // phi_P: parity packet j (ring packet W + j) is the XOR of the source's packets j, j + S, ...
     // (one packet, the XOR of all W, for an all-one polynomial; S = 3 interleaved words for the ESP)
@@ -192,7 +225,7 @@ std::string net_source(const NetSpec& s) {
   put(o, "extern \"C\" __global__ void __launch_bounds__(%ld, %ld)\n", (s.nc + 1) * 32, s.minb);
   o += kKernelName;
   o += "(const __grid_constant__ pyrit::CodeArgs a) {\n";
-  put(o, "  pyrit::ring_staged_body<%ld, %ld, %ld, %ld, pyrit::NetMac>(a);\n}\n", N, s.words, s.mg, s.nc);
+  put(o, "  pyrit::ring_staged_body<%ld, %ld, %ld, %ld, pyrit::NetMac, %ld>(a);\n}\n", N, s.words, s.mg, s.nc, W);
   return o;
 }
 
@@ -394,7 +427,7 @@ int shapes_for(int n, int nout, bool syndrome, NetSpec* out, int cap) {
     // accumulators (+ an output under construction for syndrome decoding), one staged source and
     // addressing and loop state against the register budget; the estimate runs about 20 above
     // what the compiler allocates without spilling (measured), hence the allowance
-    if ((mg + (syndrome ? 1 : 0)) * n * c.words + field_degree(n) * c.words + 16 > reg_cap(c.nc, c.minb) + 20) continue;
+    if ((mg + (syndrome ? 1 : 0)) * n * c.words + (n - 1) * c.words + 16 > reg_cap(c.nc, c.minb) + 20) continue;
     NetSpec s;
     std::memset(&s, 0, sizeof(s));
     s.n = n;
@@ -409,7 +442,7 @@ int shapes_for(int n, int nout, bool syndrome, NetSpec* out, int cap) {
 }
 
 NetSpec net_spec_tables(int n, const JobDesc* const* tables, int ntables, int words, int mg, int minb, int nc,
-                        int transform) {
+                        int transform, uint32_t g) {
   NetSpec s;
   std::memset(&s, 0, sizeof(s));
   int nout = 0;
@@ -428,6 +461,8 @@ NetSpec net_spec_tables(int n, const JobDesc* const* tables, int ntables, int wo
   if (!s.minb) s.minb = 1;
   if (!s.nc) s.nc = 16;
   s.mode = transform == PYRIT_TRANSFORM_PARITY ? 2 : 0;
+  s.g = g;
+  s.w = g ? 31 - __builtin_clz(g) : field_degree(n);
   s.ntables = ntables < kMaxJobs ? ntables : kMaxJobs;
   for (int t = 0; t < s.ntables; ++t) {
     const JobDesc& job = *tables[t];
@@ -439,9 +474,9 @@ NetSpec net_spec_tables(int n, const JobDesc* const* tables, int ntables, int wo
   return s;
 }
 
-NetSpec net_spec(int n, const JobDesc& job, int words, int mg, int minb, int nc, int transform) {
+NetSpec net_spec(int n, const JobDesc& job, int words, int mg, int minb, int nc, int transform, uint32_t g) {
   const JobDesc* t = &job;
-  return net_spec_tables(n, &t, 1, words, mg, minb, nc, transform);
+  return net_spec_tables(n, &t, 1, words, mg, minb, nc, transform, g);
 }
 
 NetSpec net_spec_syndrome(const pyrit_plan_s* p, int words, int minb, int nc) {
@@ -456,6 +491,8 @@ NetSpec net_spec_syndrome(const pyrit_plan_s* p, int words, int minb, int nc) {
   s.mg = p->m;
   s.ntables = 1;
   s.tnout[0] = p->m;
+  s.w = p->w;
+  s.g = plan_net_g(p);  // rejected by spec_valid unless native: the syndrome store folds natively
   if (words) s.words = words;
   if (minb) s.minb = minb;
   if (nc) s.nc = nc;
@@ -485,9 +522,21 @@ static bool spec_valid(const NetSpec& s) {
   if (s.mode < 0 || s.mode > 3) return false;
   if ((s.mode == 1 || s.mode == 3) && !(s.mg == s.nout && s.nout <= kSyndromeBaseRow && s.ntables == 1)) return false;
   if (s.ntables < 1 || s.ntables > kMaxJobs) return false;
+  // a native field of its ring, or (direct embedding networks only) a factor g of x^n + 1 of degree w
+  if (s.g == 0) {
+    if (!(s.n == 3 || s.n == 5 || s.n == 9 || s.n == 11 || s.n == 13) || s.w != field_degree(s.n)) return false;
+  } else {
+    if (s.mode != 0 || (s.n & 1) == 0 || s.n < 3 || s.n > 15 || s.w < 2 || s.w >= s.n ||
+        s.w != 31 - __builtin_clz(s.g))
+      return false;
+    uint32_t r = (1u << s.n) | 1u;  // x^n + 1 mod g must vanish
+    for (int d = s.n; d >= s.w; --d)
+      if ((r >> d) & 1u) r ^= s.g << (d - s.w);
+    if (r != 0) return false;
+  }
   for (int t = 0; t < s.ntables; ++t)
     if (s.tnout[t] < 1 || s.tnout[t] > s.nout) return false;
-  return (s.n == 3 || s.n == 5 || s.n == 9 || s.n == 11 || s.n == 13) && s.nin >= 1 && s.nin <= kMaxIn && s.nout >= 1 &&
+  return s.nin >= 1 && s.nin <= kMaxIn && s.nout >= 1 &&
          s.nout <= kMaxOut && words_ok && s.mg >= 1 && s.mg <= kMaxOut && s.minb >= 1 && s.minb <= 4 && nc_ok &&
          output_groups(s.mg, s.nout, s.nc) * s.mg >= s.nout && s.nc % output_groups(s.mg, s.nout, s.nc) == 0;
 }
@@ -526,7 +575,8 @@ const Variant* net_variant(const NetSpec& s, bool block) {
       ++J.failed;
       return nullptr;
     }
-    e->v = Variant{s.n, s.words, s.mg, s.minb, PYRIT_DISPATCH_NETWORK, s.nc, reinterpret_cast<const void*>(k), s.mode, s.nout};
+    e->v = Variant{s.n,    s.words, s.mg,   s.minb, PYRIT_DISPATCH_NETWORK, s.nc, reinterpret_cast<const void*>(k),
+                   s.mode, s.nout,  s.w};
     e->loaded = true;
     ++J.loaded;
   }
@@ -621,8 +671,9 @@ int plan_network_specs(pyrit_plan_s* plan, int op, uint64_t erasures, const pyri
     return PYRIT_E_INVALID_ARG;
   }
   for (int i = 0; i < nj; ++i)
-    s[i] = tile ? net_spec(plan->n, jobs[i], tile->words, tile->mg, tile->minb, tile->nc, plan->transform)
-                : net_spec(plan->n, jobs[i], 0, 0, 0, 0, plan->transform);
+    s[i] = tile ? net_spec(plan->n, jobs[i], tile->words, tile->mg, tile->minb, tile->nc, plan->transform,
+                           plan_net_g(plan))
+                : net_spec(plan->n, jobs[i], 0, 0, 0, 0, plan->transform, plan_net_g(plan));
   return nj;
 }
 
@@ -639,6 +690,22 @@ int pyrit_plan_specialise(pyrit_plan_t plan, int op, uint64_t erasures, const py
     if (rc != PYRIT_OK) return rc;
   }
   return PYRIT_OK;
+}
+
+int pyrit_plan_network_source(pyrit_plan_t plan, int op, uint64_t erasures, const pyrit_tile_t* tile, char* buf,
+                              int cap) {
+  NetSpec specs[kMaxJobs];
+  const int rc = plan_network_specs(plan, op, erasures, tile, specs);
+  if (rc == 0) return PYRIT_E_INVALID_ARG;
+  if (rc < 0) return rc;
+  if (!spec_valid(specs[0])) return PYRIT_E_INVALID_ARG;
+  const std::string src = net_source(specs[0]);
+  if (buf && cap > 0) {
+    const int c = std::min((int)src.size(), cap - 1);
+    std::memcpy(buf, src.data(), (size_t)c);
+    buf[c] = '\0';
+  }
+  return (int)src.size();
 }
 
 int pyrit_plan_network_info(pyrit_plan_t plan, int op, uint64_t erasures, const pyrit_tile_t* tile, int* info_out) {

@@ -51,8 +51,8 @@ int scratch_address(uint8_t** out) {
   return PYRIT_OK;
 }
 
-// The one job of a stripe. The fixed kernels have no parity transform (it runs only on generated
-// networks), and a stripe with more than kMaxOut parity (or erased) blocks is several jobs, which
+// The one job of a stripe. The fixed kernels have no parity transform and only the native fields
+// (those run only on generated networks), and a stripe with more than kMaxOut parity (or erased) blocks is several jobs, which
 // the fixed scratch does not hold: both are PYRIT_E_UNSUPPORTED here.
 int stripe_job(const pyrit_stripe_t& s, JobDesc* job) {
   JobDesc jobs[kMaxJobs];
@@ -60,7 +60,7 @@ int stripe_job(const pyrit_stripe_t& s, JobDesc* job) {
   uint64_t alg = 0, src = 0;
   const int rc = stripe_jobs(s, jobs, &nj, &alg, &src);
   if (rc != PYRIT_OK) return rc;
-  if (s.plan->transform == PYRIT_TRANSFORM_PARITY || nj > 1) return PYRIT_E_UNSUPPORTED;
+  if (network_only(s.plan) || nj > 1) return PYRIT_E_UNSUPPORTED;
   if (nj == 1)
     *job = jobs[0];
   else
@@ -145,7 +145,7 @@ extern "C" int pyrit_code_stripes_noalloc(const pyrit_stripe_t* stripes, int cou
     a.groups = (uint32_t)L.shape.groups;
     a.stages = (uint32_t)L.shape.stages;
     a.err = reinterpret_cast<int*>(scratch);
-    const size_t smem = staged_smem_bytes(L.shape.stages, field_degree(L.shape.v->n), L.shape.tw);
+    const size_t smem = staged_smem_bytes(L.shape.stages, L.shape.v->w, L.shape.tw);
     const int grid = (int)(L.ntiles < (uint32_t)L.shape.grid ? L.ntiles : (uint32_t)L.shape.grid);
     void* args[] = {&a};
     if (cudaLaunchKernel(L.shape.v->fn, dim3(grid), dim3((L.shape.v->nc + 1) * 32), args, smem, st) != cudaSuccess)

@@ -48,26 +48,54 @@ bool esp_irreducible(int s, int r) {
 
 }  // namespace
 
-// GF(2^w) is supported on R_{2,n} when the field's modulus is the s-ESP of degree w = s r with
-// n = s (r + 1) (s = 1: the AOP, n = w + 1), irreducible by the paper's criteria, and n is one of
-// the ring sizes the kernels are instantiated for: 3, 5, 11, 13 (AOPs) and 9 (x^6 + x^3 + 1).
-bool field_supported(int w, int n) {
+// The native fields, which the generic kernels are built for: the s-ESP of degree w = s r with
+// n = s (r + 1) (s = 1: the AOP, n = w + 1), irreducible by the paper's criteria, on the ring
+// sizes 3, 5, 11, 13 (AOPs) and 9 (x^6 + x^3 + 1).
+bool field_native(int w, int n) {
   if (w < 2 || w > 15 || n <= w) return false;
   const int s = n - w;
   if (w % s != 0 || !esp_irreducible(s, w / s)) return false;
   return field_degree(n) == w && (n == 3 || n == 5 || n == 9 || n == 11 || n == 13);
 }
 
-// The modulus of GF(2^w) in this library: the ESP x^6 + x^3 + 1 for w = 6, else the AOP of degree w.
-uint32_t field_modulus(int w) {
-  if (w == 6) return 0x49u;  // 1 + x^3 + x^6
-  return (1u << (w + 1)) - 1;
+namespace {
+
+int poly_degree(uint32_t p) { return 31 - __builtin_clz(p); }
+
+// Remainder of a by p over F2.
+uint32_t poly_rem(uint32_t a, uint32_t p) {
+  const int dp = poly_degree(p);
+  for (int d = 31; d >= dp; --d)
+    if ((a >> d) & 1u) a ^= p << (d - dp);
+  return a;
 }
 
-// Product in GF(2^w) = F2[x]/(modulus): shift-and-add, reducing each time the shifted
-// multiplicand reaches degree w (x^w = the modulus minus its leading term).
-uint32_t gf_mul(int w, uint32_t a, uint32_t b) {
-  const uint32_t g = field_modulus(w);
+bool poly_irreducible(uint32_t p) {
+  const int w = poly_degree(p);
+  for (int d = 1; d <= w / 2; ++d)
+    for (uint32_t f = 1u << d; f < (2u << d); ++f)
+      if (poly_rem(p, f) == 0) return false;
+  return true;
+}
+
+}  // namespace
+
+// The modulus of GF(2^w) on R_{2,n}: for a native field its AOP or ESP; otherwise (Props. 1-2:
+// any irreducible factor p of x^n + 1, n odd, makes mod p a homomorphism R_{2,n} -> F2[x]/(p))
+// the smallest irreducible factor of degree w of x^n + 1, for odd n <= 15 (masks are 16-bit).
+// 0: no such field.
+uint32_t field_modulus(int w, int n) {
+  if (field_native(w, n)) return n == 9 ? 0x49u /* 1 + x^3 + x^6 */ : (1u << (w + 1)) - 1;
+  if (w < 2 || w >= n || n < 3 || n > 15 || (n & 1) == 0) return 0;
+  const uint32_t xn1 = (1u << n) | 1u;
+  for (uint32_t p = 1u << w; p < (2u << w); ++p)
+    if (poly_rem(xn1, p) == 0 && poly_irreducible(p)) return p;
+  return 0;
+}
+
+// Product in GF(2^w) = F2[x]/(g): shift-and-add, reducing each time the shifted multiplicand
+// reaches degree w (x^w = g minus its leading term).
+uint32_t gf_mul(uint32_t g, int w, uint32_t a, uint32_t b) {
   uint32_t r = 0;
   for (int i = 0; i < w; ++i) {
     if ((b >> i) & 1u) r ^= a;
@@ -78,11 +106,11 @@ uint32_t gf_mul(int w, uint32_t a, uint32_t b) {
 }
 
 // a^{-1} = a^{2^w - 2} (Fermat), by square-and-multiply. gf_inv(0) = 0.
-uint32_t gf_inv(int w, uint32_t a) {
+uint32_t gf_inv(uint32_t g, int w, uint32_t a) {
   uint32_t e = (1u << w) - 2, r = 1, s = a;
   while (e) {
-    if (e & 1u) r = gf_mul(w, r, s);
-    s = gf_mul(w, s, s);
+    if (e & 1u) r = gf_mul(g, w, r, s);
+    s = gf_mul(g, w, s, s);
     e >>= 1;
   }
   return a ? r : 0;
@@ -92,8 +120,7 @@ uint32_t gf_inv(int w, uint32_t a) {
 // the 2^(n-w) polynomials h of degree < n - w. The lightest is taken, the smallest on ties. For an
 // AOP that is u or its complement in n bits (weights t and n - t, never tied for odd n); for the
 // ESP of GF(2^6) one of eight.
-uint32_t sparse_rep(int w, int n, uint32_t u) {
-  const uint32_t g = field_modulus(w);
+uint32_t sparse_rep(uint32_t g, int w, int n, uint32_t u) {
   u &= (1u << w) - 1;
   uint32_t best = u;
   int bw = __builtin_popcount(u);
@@ -112,7 +139,7 @@ uint32_t sparse_rep(int w, int n, uint32_t u) {
 }
 
 // Inverse over GF(2^w) by elimination with row swaps (k <= 64). Returns false if singular.
-static bool invert(int w, int k, const uint32_t* A, uint32_t* out) {
+static bool invert(uint32_t g, int w, int k, const uint32_t* A, uint32_t* out) {
   uint32_t a[kMaxIn][kMaxIn], b[kMaxIn][kMaxIn];
   for (int r = 0; r < k; ++r)
     for (int c = 0; c < k; ++c) {
@@ -128,17 +155,17 @@ static bool invert(int w, int k, const uint32_t* A, uint32_t* out) {
         std::swap(a[c][x], a[piv][x]);
         std::swap(b[c][x], b[piv][x]);
       }
-    const uint32_t s = gf_inv(w, a[c][c]);
+    const uint32_t s = gf_inv(g, w, a[c][c]);
     for (int x = 0; x < k; ++x) {
-      a[c][x] = gf_mul(w, a[c][x], s);
-      b[c][x] = gf_mul(w, b[c][x], s);
+      a[c][x] = gf_mul(g, w, a[c][x], s);
+      b[c][x] = gf_mul(g, w, b[c][x], s);
     }
     for (int r = 0; r < k; ++r) {
       if (r == c || a[r][c] == 0) continue;
       const uint32_t f = a[r][c];
       for (int x = 0; x < k; ++x) {
-        a[r][x] ^= gf_mul(w, f, a[c][x]);
-        b[r][x] ^= gf_mul(w, f, b[c][x]);
+        a[r][x] ^= gf_mul(g, w, f, a[c][x]);
+        b[r][x] ^= gf_mul(g, w, f, b[c][x]);
       }
     }
   }
@@ -148,7 +175,7 @@ static bool invert(int w, int k, const uint32_t* A, uint32_t* out) {
 }
 
 // Every k x k row subset of G invertible (the MDS property, Sec. 2.2), by enumeration.
-static bool all_subsets_invertible(int w, int k, int m, const uint32_t* G) {
+static bool all_subsets_invertible(uint32_t g, int w, int k, int m, const uint32_t* G) {
   int idx[kMaxBlocks];
   for (int i = 0; i < k; ++i) idx[i] = i;
   uint32_t sub[kMaxIn * kMaxIn], inv[kMaxIn * kMaxIn];
@@ -156,7 +183,7 @@ static bool all_subsets_invertible(int w, int k, int m, const uint32_t* G) {
   while (true) {
     for (int r = 0; r < k; ++r)
       for (int c = 0; c < k; ++c) sub[r * k + c] = G[idx[r] * k + c];
-    if (!invert(w, k, sub, inv)) return false;
+    if (!invert(g, w, k, sub, inv)) return false;
     int i = k - 1;
     while (i >= 0 && idx[i] == nrow - k + i) --i;
     if (i < 0) return true;
@@ -190,7 +217,7 @@ static void syndrome_entry(const pyrit_plan_s* p, DecodeEntry* e) {
   uint32_t A[kMaxOut * kMaxOut], X[kMaxOut * kMaxOut];
   for (int i = 0; i < a; ++i)
     for (int j = 0; j < a; ++j) A[i * a + j] = p->G[(k + U[i]) * k + D[j]];
-  if (a > 0 && !invert(w, a, A, X)) return;
+  if (a > 0 && !invert(p->g, w, a, A, X)) return;
   for (int o = 0; o < e->ne; ++o) {
     const int b = e->erased[o];
     for (int s = 0; s < a; ++s) {
@@ -200,9 +227,9 @@ static void syndrome_entry(const pyrit_plan_s* p, DecodeEntry* e) {
         while (D[i] != b) ++i;
         v = X[i * a + s];
       } else {
-        for (int i = 0; i < a; ++i) v ^= gf_mul(w, p->G[b * k + D[i]], X[i * a + s]);
+        for (int i = 0; i < a; ++i) v ^= gf_mul(p->g, w, p->G[b * k + D[i]], X[i * a + s]);
       }
-      e->syn[U[s]][o] = (uint16_t)sparse_rep(w, n, v);
+      e->syn[U[s]][o] = (uint16_t)sparse_rep(p->g, w, n, v);
     }
     e->syn[kSyndromeBaseRow][o] = (uint16_t)(b < k ? 0 : b - k + 1);
   }
@@ -234,7 +261,7 @@ int plan_decode_entry(pyrit_plan_s* p, uint64_t erasures, DecodeEntry* out) {
     uint32_t Gs[kMaxIn * kMaxIn], Inv[kMaxIn * kMaxIn];
     for (int s = 0; s < k; ++s)
       for (int c = 0; c < k; ++c) Gs[s * k + c] = p->G[e.surv[s] * k + c];
-    if (!invert(w, k, Gs, Inv)) {
+    if (!invert(p->g, w, k, Gs, Inv)) {
       e.status = PYRIT_E_NOT_MDS;
     } else {
       for (int r = 0; r < e.ne; ++r) {
@@ -245,9 +272,9 @@ int plan_decode_entry(pyrit_plan_s* p, uint64_t erasures, DecodeEntry* out) {
             v = Inv[b * k + s];
           } else {  // an erased parity block: G[b] times Inv
             v = 0;
-            for (int j = 0; j < k; ++j) v ^= gf_mul(w, p->G[b * k + j], Inv[j * k + s]);
+            for (int j = 0; j < k; ++j) v ^= gf_mul(p->g, w, p->G[b * k + j], Inv[j * k + s]);
           }
-          e.mask[r][s] = (uint16_t)sparse_rep(w, n, v);
+          e.mask[r][s] = (uint16_t)sparse_rep(p->g, w, n, v);
         }
       }
       syndrome_entry(p, &e);
@@ -372,12 +399,15 @@ int pyrit_plan_create(int w, int n, int k, int m, const uint32_t* G, pyrit_plan_
   if (!out) return PYRIT_E_INVALID_ARG;
   *out = nullptr;
   if (k < 1 || k > PYRIT_MAX_K || m < 0 || m > PYRIT_MAX_M || k + m > kMaxBlocks) return PYRIT_E_INVALID_ARG;
-  if (!field_supported(w, n)) return PYRIT_E_UNSUPPORTED_FIELD;
+  const uint32_t g = field_modulus(w, n);
+  if (!g) return PYRIT_E_UNSUPPORTED_FIELD;
   if (!G && (uint64_t)k + (uint64_t)m > (1ull << w)) return PYRIT_E_TOO_LONG;
   pyrit_plan_s* p = new (std::nothrow) pyrit_plan_s;
   if (!p) return PYRIT_E_OOM;
   p->w = w;
   p->n = n;
+  p->g = g;
+  p->native = field_native(w, n);
   p->k = k;
   p->m = m;
   p->G.assign((size_t)(k + m) * k, 0);
@@ -391,7 +421,7 @@ int pyrit_plan_create(int w, int n, int k, int m, const uint32_t* G, pyrit_plan_
         }
         p->G[r * k + c] = v;
       }
-    if (binom(k + m, k) <= 20000.0 && !all_subsets_invertible(w, k, m, p->G.data())) {
+    if (binom(k + m, k) <= 20000.0 && !all_subsets_invertible(g, w, k, m, p->G.data())) {
       delete p;
       return PYRIT_E_NOT_MDS;
     }
@@ -399,11 +429,11 @@ int pyrit_plan_create(int w, int n, int k, int m, const uint32_t* G, pyrit_plan_
     // Cauchy: C[i][j] = 1 / (x_i + y_j), x_i = k + i, y_j = j (all points distinct).
     for (int r = 0; r < k; ++r) p->G[r * k + r] = 1;
     for (int i = 0; i < m; ++i)
-      for (int j = 0; j < k; ++j) p->G[(k + i) * k + j] = gf_inv(w, (uint32_t)(k + i) ^ (uint32_t)j);
+      for (int j = 0; j < k; ++j) p->G[(k + i) * k + j] = gf_inv(g, w, (uint32_t)(k + i) ^ (uint32_t)j);
   }
   p->enc_mask.resize((size_t)m * k);
   for (int i = 0; i < m; ++i)
-    for (int j = 0; j < k; ++j) p->enc_mask[i * k + j] = (uint16_t)sparse_rep(w, n, p->G[(k + i) * k + j]);
+    for (int j = 0; j < k; ++j) p->enc_mask[i * k + j] = (uint16_t)sparse_rep(g, w, n, p->G[(k + i) * k + j]);
   *out = p;
   return PYRIT_OK;
 }
@@ -412,10 +442,21 @@ void pyrit_plan_destroy(pyrit_plan_t p) { delete p; }
 
 int pyrit_plan_set_transform(pyrit_plan_t p, int transform) {
   if (!p) return PYRIT_E_INVALID_ARG;
-  if (transform == PYRIT_TRANSFORM_AUTO) transform = p->k < p->m ? PYRIT_TRANSFORM_PARITY : PYRIT_TRANSFORM_EMBEDDING;
+  // the parity transform is defined for the all-one and equally spaced polynomials (Sec. 2.3.1,
+  // Sec. 2.4.1), whose ideals are characterised by parities; other factors take the embedding
+  if (transform == PYRIT_TRANSFORM_AUTO)
+    transform = p->k < p->m && p->native ? PYRIT_TRANSFORM_PARITY : PYRIT_TRANSFORM_EMBEDDING;
   if (transform != PYRIT_TRANSFORM_EMBEDDING && transform != PYRIT_TRANSFORM_PARITY) return PYRIT_E_INVALID_ARG;
+  if (transform == PYRIT_TRANSFORM_PARITY && !p->native) return PYRIT_E_UNSUPPORTED;
   p->transform = transform;
   return transform;
+}
+
+int pyrit_plan_modulus(pyrit_plan_t p, uint32_t* g_out, int* native_out) {
+  if (!p) return PYRIT_E_INVALID_ARG;
+  if (g_out) *g_out = p->g;
+  if (native_out) *native_out = p->native ? 1 : 0;
+  return PYRIT_OK;
 }
 
 int pyrit_plan_info(pyrit_plan_t p, int* w, int* n, int* k, int* m) {
@@ -441,17 +482,20 @@ int pyrit_plan_encode_masks(pyrit_plan_t p, uint16_t* masks_out) {
 
 int pyrit_generator_weighted(int w, int n, int k, int m, uint32_t* G_out, uint64_t* weights_out) {
   if (!G_out || k < 1 || k > PYRIT_MAX_K || m < 0 || m > PYRIT_MAX_M || k + m > kMaxBlocks) return PYRIT_E_INVALID_ARG;
-  if (!field_supported(w, n)) return PYRIT_E_UNSUPPORTED_FIELD;
+  const uint32_t g = field_modulus(w, n);
+  if (!g) return PYRIT_E_UNSUPPORTED_FIELD;
   if ((uint64_t)k + (uint64_t)m > (1ull << w)) return PYRIT_E_TOO_LONG;
   const uint32_t q = 1u << w;
   // weight of phi_S(u), the number of ones of the sparsest representative
   std::vector<int> wt(q);
-  for (uint32_t u = 0; u < q; ++u) wt[u] = __builtin_popcount(sparse_rep(w, n, u));
+  for (uint32_t u = 0; u < q; ++u) wt[u] = __builtin_popcount(sparse_rep(g, w, n, u));
   std::vector<uint32_t> c((size_t)m * k);
   for (int i = 0; i < m; ++i)
-    for (int j = 0; j < k; ++j) c[(size_t)i * k + j] = gf_inv(w, (uint32_t)(k + i) ^ (uint32_t)j);
+    for (int j = 0; j < k; ++j) c[(size_t)i * k + j] = gf_inv(g, w, (uint32_t)(k + i) ^ (uint32_t)j);
   std::vector<uint32_t> a(m, 1u), b(k, 1u);
-  auto entry = [&](int i, int j, uint32_t ai, uint32_t bj) { return gf_mul(w, gf_mul(w, ai, bj), c[(size_t)i * k + j]); };
+  auto entry = [&](int i, int j, uint32_t ai, uint32_t bj) {
+    return gf_mul(g, w, gf_mul(g, w, ai, bj), c[(size_t)i * k + j]);
+  };
   uint64_t before = 0;
   for (int i = 0; i < m; ++i)
     for (int j = 0; j < k; ++j) before += (uint64_t)wt[c[(size_t)i * k + j]];
@@ -533,13 +577,15 @@ int pyrit_plan_decode_masks(pyrit_plan_t p, uint64_t erasures, int* survivors_ou
 }
 
 uint32_t pyrit_sparse_transform(int w, int n, uint32_t u) {
-  if (!field_supported(w, n) || u >= (1u << w)) return 0xFFFFFFFFu;
-  return sparse_rep(w, n, u);
+  const uint32_t g = field_modulus(w, n);
+  if (!g || u >= (1u << w)) return 0xFFFFFFFFu;
+  return sparse_rep(g, w, n, u);
 }
 
 uint32_t pyrit_gf_mul(int w, uint32_t a, uint32_t b) {
   if (w < 2 || w > 15) return 0;
-  return gf_mul(w, a & ((1u << w) - 1), b & ((1u << w) - 1));
+  const uint32_t g = w == 6 ? 0x49u : (1u << (w + 1)) - 1;  // the field of w on its native ring
+  return gf_mul(g, w, a & ((1u << w) - 1), b & ((1u << w) - 1));
 }
 
 }  // extern "C"

@@ -40,6 +40,7 @@ struct Variant {
   const void* fn;
   int mode;      // generated networks: NetSpec mode (syndrome modes take syndrome-form jobs)
   int nout;      // generated networks: the output count they were compiled for (0: generic)
+  int w;         // field degree: packets per block
 };
 
 // Generated networks whose jobs are in syndrome form (modes 1 and 3).
@@ -74,11 +75,15 @@ struct ShapeHint {
 };
 
 // ---- planner (host) -------------------------------------------------------------------------
-bool field_supported(int w, int n);
-uint32_t field_modulus(int w);
-uint32_t gf_mul(int w, uint32_t a, uint32_t b);
-uint32_t gf_inv(int w, uint32_t a);
-uint32_t sparse_rep(int w, int n, uint32_t u);
+// Native fields (generic kernels built for them): the AOP rings n = w + 1 in {3, 5, 11, 13} and
+// GF(2^6) from x^6 + x^3 + 1 on n = 9.
+bool field_native(int w, int n);
+// The modulus of GF(2^w) on R_{2,n}: the native AOP / ESP, else the smallest irreducible factor of
+// degree w of x^n + 1 (n odd <= 15); 0 if none.
+uint32_t field_modulus(int w, int n);
+uint32_t gf_mul(uint32_t g, int w, uint32_t a, uint32_t b);
+uint32_t gf_inv(uint32_t g, int w, uint32_t a);
+uint32_t sparse_rep(uint32_t g, int w, int n, uint32_t u);
 
 struct DecodeEntry {
   int status = PYRIT_OK;
@@ -97,6 +102,8 @@ struct DecodeEntry {
 
 struct pyrit_plan_s {
   int w, n, k, m;
+  uint32_t g = 0;       // the field's modulus
+  bool native = true;   // the generic kernels serve this field (else generated networks only)
   int transform = PYRIT_TRANSFORM_EMBEDDING;
   std::vector<uint32_t> G;         // (k+m) x k
   std::vector<uint16_t> enc_mask;  // m x k
@@ -160,15 +167,23 @@ struct NetSpec {
                  // [C | I]); 0 and 1 under the embedding transform, 2 and 3 under the parity one
   int32_t ntables;           // direct modes: tables; a job's JobDesc::table picks one (syndrome: 1)
   int32_t tnout[kMaxJobs];   // output count of each table
+  int32_t w;                 // field degree (packets per block)
+  uint32_t g;                // 0: the native field of R_{2,n}; else the modulus, a factor of x^n + 1
+                             // whose reduction the network emits (direct mode 0 only)
   uint16_t mask[kMaxJobs][kMaxIn][kMaxOut];
 };
 // The network spec of one job under a shape (zero fields: the default shape for (n, nout)) and a
 // transform (PYRIT_TRANSFORM_EMBEDDING or _PARITY): one table, which the job must select as 0.
-NetSpec net_spec(int n, const JobDesc& job, int words, int mg, int minb, int nc, int transform);
+NetSpec net_spec(int n, const JobDesc& job, int words, int mg, int minb, int nc, int transform, uint32_t g = 0);
 // The network spec of several tables (each given by one job that uses it, all with the same nin):
 // the jobs of a launch then carry their table's index in JobDesc::table.
 NetSpec net_spec_tables(int n, const JobDesc* const* tables, int ntables, int words, int mg, int minb, int nc,
-                        int transform);
+                        int transform, uint32_t g = 0);
+// The `g` a plan's network specs take: 0 for a native field, else the plan's modulus.
+inline uint32_t plan_net_g(const pyrit_plan_s* p) { return p->native ? 0u : p->g; }
+// Plans that only generated networks code: the parity transform, or a field that the generic
+// kernels are not built for.
+inline bool network_only(const pyrit_plan_s* p) { return p->transform == PYRIT_TRANSFORM_PARITY || !p->native; }
 // The syndrome-decode network spec of a plan, under its transform (requires k + m <= kMaxIn and
 // m <= kMaxOut; zero fields: default).
 NetSpec net_spec_syndrome(const pyrit_plan_s* p, int words, int minb, int nc);

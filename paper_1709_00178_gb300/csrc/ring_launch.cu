@@ -58,7 +58,7 @@ void ensure_attr(const Variant* v) {
     cudaFuncSetAttribute(v->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
 }
 
-size_t smem_bytes(const TileShape& s) { return staged_smem_bytes(s.stages, field_degree(s.v->n), s.tw); }
+size_t smem_bytes(const TileShape& s) { return staged_smem_bytes(s.stages, s.v->w, s.tw); }
 
 int occupancy(const TileShape& s) {
   ensure_attr(s.v);
@@ -132,7 +132,7 @@ bool shape_for_variant(const Variant* v, int max_nout, const ShapeHint& h, TileS
   const int groups = output_groups(v->mg, max_nout, v->nc);
   s.groups = groups;
   s.tw = (v->nc / groups) * 32 * 4 * v->words;
-  const int w = field_degree(v->n);
+  const int w = v->w;
   const int budget = (226 * 1024) / v->minb - 1024;  // shared memory per CTA at the target occupancy
   s.stages = h.stages > 0 ? h.stages : std::max(2, std::min(8, budget / (w * s.tw)));
   s.grid = 0;

@@ -261,9 +261,10 @@ struct ParityStore {
   }
 };
 
-template <int N, int WORDS, int MG, int NC, class Mac>
+// W: the field's degree, the packets of a block (the native field of R_{2,N} by default; a
+// generated network for another factor of x^N + 1 passes its own, with its own reduction).
+template <int N, int WORDS, int MG, int NC, class Mac, int W = RingDim<N>::W>
 __device__ __forceinline__ void ring_staged_body(const CodeArgs& a) {
-  constexpr int W = RingDim<N>::W;
   using V = typename Vec<WORDS>::T;
   extern __shared__ __align__(128) uint8_t smem[];
   const uint32_t S = a.stages, TW = a.tw;

@@ -364,7 +364,7 @@ int pyrit_server_submit(pyrit_server_t s, const pyrit_request_t* reqs, int count
     if (rc != PYRIT_OK) return rc;
     // requests wait for no compilation, and only a generated network has the parity transform;
     // a request is one job (at most kMaxOut parity or erased blocks)
-    if (reqs[i].stripe.plan->transform == PYRIT_TRANSFORM_PARITY || nj > 1) return PYRIT_E_UNSUPPORTED;
+    if (network_only(reqs[i].stripe.plan) || nj > 1) return PYRIT_E_UNSUPPORTED;
     if (nj == 1)
       p.job = jobs[0];
     else

@@ -61,6 +61,7 @@ _SIGS = {
     "pyrit_plan_destroy": (None, [_vp]),
     "pyrit_plan_info": (_i, [_vp, _vp, _vp, _vp, _vp]),
     "pyrit_plan_set_transform": (_i, [_vp, _i]),
+    "pyrit_plan_modulus": (_i, [_vp, _vp, _vp]),
     "pyrit_plan_generator": (_i, [_vp, _vp]),
     "pyrit_plan_encode_masks": (_i, [_vp, _vp]),
     "pyrit_plan_decode_masks": (_i, [_vp, _u64, _vp, _vp, _vp, _vp]),
@@ -185,6 +186,13 @@ def pyrit_plan_syndrome_masks(plan, erasures):
     _check(_lib.pyrit_plan_syndrome_masks(plan, erasures, _np_ptr(syn), ctypes.byref(ne)),
            "pyrit_plan_syndrome_masks")
     return syn, ne.value
+
+
+def pyrit_plan_modulus(plan):
+    """(g, native): the plan's field modulus and whether the generic kernels serve it."""
+    g, nat = ctypes.c_uint32(), ctypes.c_int()
+    _check(_lib.pyrit_plan_modulus(plan, ctypes.byref(g), ctypes.byref(nat)), "pyrit_plan_modulus")
+    return g.value, bool(nat.value)
 
 
 def pyrit_plan_set_transform(plan, transform):
@@ -332,6 +340,7 @@ _JIT_SIGS = {
     "pyrit_jit_mode": (_i, [_i]),
     "pyrit_plan_specialise": (_i, [_vp, _i, _u64, ctypes.POINTER(pyrit_tile_t)]),
     "pyrit_plan_network_info": (_i, [_vp, _i, _u64, ctypes.POINTER(pyrit_tile_t), _vp]),
+    "pyrit_plan_network_source": (_i, [_vp, _i, _u64, ctypes.POINTER(pyrit_tile_t), ctypes.c_char_p, _i]),
     "pyrit_jit_wait": (_i, [_i]),
     "pyrit_jit_quiesce": (_i, [_i]),
     "pyrit_jit_stats": (_i, [_vp]),
@@ -358,6 +367,16 @@ def pyrit_plan_specialise(plan, op=PYRIT_OP_ENCODE, erasures=0, tile=None):
     t = _tile(tile)
     return _check(_lib.pyrit_plan_specialise(plan, op, erasures, ctypes.byref(t) if t is not None else None),
                   "pyrit_plan_specialise")
+
+
+def pyrit_plan_network_source(plan, op=PYRIT_OP_ENCODE, erasures=0, tile=None):
+    """CUDA source of a plan's generated network (the first job's)."""
+    t = _tile(tile)
+    tp = ctypes.byref(t) if t is not None else None
+    size = _check(_lib.pyrit_plan_network_source(plan, op, erasures, tp, None, 0), "pyrit_plan_network_source")
+    buf = ctypes.create_string_buffer(size + 1)
+    _lib.pyrit_plan_network_source(plan, op, erasures, tp, buf, size + 1)
+    return buf.value.decode()
 
 
 def pyrit_plan_network_info(plan, op=PYRIT_OP_ENCODE, erasures=0, tile=None):

@@ -67,19 +67,26 @@ def test_planner_field_product(w):
 
 
 def test_field_support_matches_oracle_irreducibility():
-    # The planner accepts (w, n) by the paper's number-theoretic criteria (Sec. 2.3 for AOPs,
-    # Sec. 2.4 for ESPs); the oracle finds each field's modulus by trial division. They must agree
-    # on every pair, restricted to the ring sizes the kernels are built for.
+    # The planner accepts (w, n) by the paper's number-theoretic criteria for its native fields
+    # (Sec. 2.3 for AOPs, Sec. 2.4 for ESPs) and, for any other odd n <= 15, by the factors of
+    # x^n + 1 (Props. 1-2); the oracle finds each modulus by trial division. They must agree on
+    # every pair: which (w, n) exist, which modulus is used, which are native.
     for w in range(2, 16):
         for n in range(w + 1, 17):
-            supported = True
+            native = oracle.ring_size(w) == n and n in (3, 5, 9, 11, 13)
+            general = n % 2 == 1 and n <= 15 and oracle.ring_factor(w, n) != 0
             try:
                 h = pyrit.pyrit_plan_create(w, n, 1, 1)
-                pyrit.pyrit_plan_destroy(h)
             except pyrit.PyritError as e:
                 assert e.status == pyrit.PYRIT_E_UNSUPPORTED_FIELD
-                supported = False
-            assert supported == (oracle.ring_size(w) == n and n in (3, 5, 9, 11, 13)), (w, n)
+                assert not native and not general, (w, n)
+                continue
+            try:
+                g, nat = pyrit.pyrit_plan_modulus(h)
+                assert nat == native, (w, n)
+                assert g == (oracle.field_poly(w) if native else oracle.ring_factor(w, n)), (w, n)
+            finally:
+                pyrit.pyrit_plan_destroy(h)
     assert oracle.ring_size(6) == 9
 
 

@@ -365,3 +365,111 @@ def test_network_resource_report():
             pyrit.pyrit_plan_network_info(plan, pyrit.PYRIT_OP_DECODE, 0)  # nothing erased: no network
     finally:
         pyrit.pyrit_plan_destroy(plan)
+
+
+# ---- fields from other factors of x^n + 1 (Props. 1-2) ----------------------------------------
+
+GENERAL = [(3, 7, 4, 3), (4, 15, 8, 4), (2, 9, 2, 2), (2, 15, 1, 3)]
+
+
+def _parse_general_store(src, w):
+    """The reduction a general-field network writes out: for each field coefficient t, the ring
+    accumulators XORed into it."""
+    rows, cur = {}, None
+    for line in src.splitlines():
+        a = re.match(r"\s*r\[x\] = acc\[i\]\[(\d+)\]\[x\];", line)
+        if a:
+            cur = [int(a.group(1))]
+            continue
+        b = re.match(r"\s*r\[x\] = xor3\(r\[x\], acc\[i\]\[(\d+)\]\[x\], acc\[i\]\[(\d+)\]\[x\]\);", line)
+        if b:
+            cur += [int(b.group(1)), int(b.group(2))]
+            continue
+        c = re.match(r"\s*r\[x\] \^= acc\[i\]\[(\d+)\]\[x\];", line)
+        if c:
+            cur.append(int(c.group(1)))
+            continue
+        d = re.match(r".*dst \+ \(size_t\)(\d+) \* P\) = vmake<WORDS>\(r\);", line)
+        if d:
+            rows[int(d.group(1))] = cur
+            cur = None
+    assert sorted(rows) == list(range(w))
+    return rows
+
+
+@pytest.mark.parametrize("w,n,k,m", GENERAL)
+def test_general_field_planner_equals_oracle(w, n, k, m):
+    g = oracle.ring_factor(w, n)
+    plan = pyrit.pyrit_plan_create(w, n, k, m)
+    try:
+        assert pyrit.pyrit_plan_modulus(plan) == (g, False)
+        for u in range(1 << w):
+            assert pyrit.pyrit_sparse_transform(w, n, u) == oracle.sparse_rep_mod(w, n, g, u)
+        G = oracle.cauchy_mod(w, g, k, m)
+        np.testing.assert_array_equal(pyrit.pyrit_plan_generator(plan), G)
+        sp = np.array([oracle.sparse_rep_mod(w, n, g, u) for u in range(1 << w)], np.uint32)
+        np.testing.assert_array_equal(pyrit.pyrit_plan_encode_masks(plan), sp[G[k:]].astype(np.uint16))
+        # decoding masks of every pattern: phi_S of the oracle's decoding matrix in this field
+        from itertools import combinations
+        for e in range(1, m + 1):
+            for pat in combinations(range(k + m), e):
+                er = sum(1 << b for b in pat)
+                surv = [b for b in range(k + m) if b not in pat][:k]
+                Inv = oracle.gf_invert_mod(w, g, G[surv])
+                surv2, erased, M = pyrit.pyrit_plan_decode_masks(plan, er)
+                assert list(surv2) == surv and list(erased) == sorted(pat)
+                for r, b in enumerate(sorted(pat)):
+                    for s in range(k):
+                        if b < k:
+                            v = int(Inv[b][s])
+                        else:
+                            v = 0
+                            for j in range(k):
+                                v ^= oracle.gf_mul_mod(w, g, int(G[b][j]), int(Inv[j][s]))
+                        assert M[r][s] == sp[v], (pat, r, s)
+        # the parity transform is not defined for other factors
+        with pytest.raises(pyrit.PyritError) as ei:
+            pyrit.pyrit_plan_set_transform(plan, pyrit.PYRIT_TRANSFORM_PARITY)
+        assert ei.value.status == pyrit.PYRIT_E_UNSUPPORTED
+        assert pyrit.pyrit_plan_set_transform(plan, pyrit.PYRIT_TRANSFORM_AUTO) == pyrit.PYRIT_TRANSFORM_EMBEDDING
+    finally:
+        pyrit.pyrit_plan_destroy(plan)
+
+
+@pytest.mark.parametrize("w,n,k,m", GENERAL)
+def test_general_field_network_is_the_field_product(w, n, k, m):
+    """The generated network of a general-field plan, read back: its XOR lists give the ring
+    product by each coefficient's representative, and the reduction it writes out (the remainder
+    mod g) maps that to the field product in F2[x]/(g)."""
+    g = oracle.ring_factor(w, n)
+    plan = pyrit.pyrit_plan_create(w, n, k, m)
+    try:
+        src = pyrit.pyrit_plan_network_source(plan)
+        net = _parse(src)
+        assert net["n"] == n and net["nin"] == k
+        red = _parse_general_store(src, w)
+        for t, rows in red.items():  # the reduction is the remainder mod g
+            assert rows[0] == t
+            for q in range(n):
+                if q >= w:
+                    assert (q in rows[1:]) == bool((oracle.poly_mod(1 << q, g) >> t) & 1), (t, q)
+        G = oracle.cauchy_mod(w, g, k, m)
+        for case, entries in net["cases"].items():
+            gr, j = divmod(case, k)
+            for ii in range(net["mg"]):
+                o = gr * net["mg"] + ii
+                if o >= m:
+                    continue
+                for q, col in enumerate(_ring_columns(entries, ii, n, w)):
+                    field = 0
+                    for t, rows in red.items():
+                        if sum((col >> r) & 1 for r in rows) & 1:
+                            field |= 1 << t
+                    assert field == oracle.gf_mul_mod(w, g, int(G[k + o][j]), 1 << q), (case, ii, q)
+        # the run-time compiler builds it for sm_103a without a device
+        before = pyrit.pyrit_jit_stats()["failed"]
+        pyrit.pyrit_plan_specialise(plan)
+        pyrit.pyrit_plan_specialise(plan, pyrit.PYRIT_OP_DECODE, 0b1)
+        assert pyrit.pyrit_jit_stats()["failed"] == before, pyrit.pyrit_jit_log()
+    finally:
+        pyrit.pyrit_plan_destroy(plan)
