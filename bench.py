@@ -237,12 +237,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--stripes", type=int, default=STRIPES,
                     help="stripes per GPU (default 256; smaller values make profiling cases)")
-    ap.add_argument("--workload", default="coding", choices=["coding", "sweep", "mixed", "served", "gf16", "transforms", "paper"],
+    ap.add_argument("--workload", default="coding", choices=["coding", "sweep", "mixed", "served", "gf16", "transforms", "paper", "fields"],
                     help="coding: the default line; sweep: GF(2^12) k=16 m=4 packet sweep 4 KiB-1 MiB; mixed: "
                          "4096 uneven stripes batched vs per-stripe launches; served: Poisson arrivals; gf16: "
                          "GF(16) k=4 m=2, one stripe, encode + every erasure pattern (L2-resident); transforms: "
                          "embedding vs parity transform on k >= m and k < m codes; paper: the paper's (12,8), (60,40) and "
-                         "(60,20) use cases across block sizes")
+                         "(60,20) use cases across block sizes; fields: GF(16) and GF(8) from other factors of x^n+1")
     ap.add_argument("--seconds", type=float, default=10.0, help="served: arrival window")
     ap.add_argument("--generator", default="cauchy", choices=["cauchy", "weighted"],
                     help="cauchy: the plain Cauchy code of the configurations; weighted: the same code "
@@ -258,7 +258,7 @@ def main():
         return run_reference(args)
     if args.workload != "coding":
         return {"sweep": run_sweep, "mixed": run_mixed, "served": run_served, "gf16": run_gf16,
-                "transforms": run_transforms, "paper": run_paper}[args.workload](args)
+                "transforms": run_transforms, "paper": run_paper, "fields": run_fields}[args.workload](args)
     if args.stripes != STRIPES:
         STRIPES = max(8, args.stripes // 8 * 8)
         CONFIG["stripes"] = STRIPES
@@ -671,6 +671,62 @@ def run_paper(args):
             del buf
             torch.cuda.empty_cache()
         pyrit.pyrit_plan_destroy(plan)
+
+
+def run_fields(args):
+    """Fields from other factors of x^n + 1 (Props. 1-2) beside a native one, same code shape:
+    GF(16) from the AOP on R_{2,5} (native), GF(16) from x^4 + x + 1 on R_{2,15} (k=8 m=4), GF(8)
+    from x^3 + x + 1 on R_{2,7} (k=5 m=3: k + m <= 8); 64 KiB packets, stripes filling ~2 GiB of
+    source; encode and an m-erasure decode (one pattern for all stripes), tuned; a stripe checked
+    against the oracle's codec over the plan's modulus."""
+    torch, pyrit, dev = _setup_gpu()
+    from paper_1709_00178_gb300.synth import BASE_SEED
+    import numpy as np
+    import oracle
+    peak, _ = peak_hbm()
+    stream = torch.cuda.Stream(device=dev)
+    P = 65536
+    for (w, n, k, m, name) in [(4, 5, 8, 4, "GF(2^4) from the AOP on R_{2,5} (native)"),
+                               (4, 15, 8, 4, "GF(2^4) from x^4+x+1 on R_{2,15}"),
+                               (3, 7, 5, 3, "GF(2^3) from x^3+x+1 on R_{2,7}")]:
+        blk = w * P
+        S = (2 << 30) // (k * blk)
+        buf = torch.empty(S * (k + m) * blk, dtype=torch.uint8, device=dev)
+        pyrit.pyrit_synth_fill(buf.data_ptr(), buf.numel(), BASE_SEED + 6, 0)
+        torch.cuda.synchronize()
+        base, par0 = buf.data_ptr(), S * k * blk
+        blocks = [[base + (s * k + j) * blk for j in range(k)] + [base + par0 + (s * m + i) * blk for i in range(m)]
+                  for s in range(S)]
+        plan = pyrit.pyrit_plan_create(w, n, k, m)
+        g, native = pyrit.pyrit_plan_modulus(plan)
+        lost = (0b1011 | (1 << (k + 1))) if m == 4 else (0b101 | (1 << k))
+        enc = pyrit.pyrit_batch_create([(plan, 0, 0, P, blocks[s]) for s in range(S)])
+        dec = pyrit.pyrit_batch_create([(plan, 1, lost, P, blocks[s]) for s in range(S)])
+        pyrit.pyrit_batch_tune(enc, stream, 2)
+        pyrit.pyrit_batch_tune(dec, stream, 2)
+        te = _time_batch(torch, pyrit, enc, stream, args.steps)
+        td = _time_batch(torch, pyrit, dec, stream, args.steps)
+        torch.cuda.synchronize()
+        cw = 4096
+        data0 = np.ascontiguousarray(buf[:k * blk].cpu().numpy().reshape(k, w, P)[:, :, :cw])
+        want = oracle.encode_mod(w, g, k, m, oracle.cauchy_mod(w, g, k, m), data0, nthreads=os.cpu_count() or 1)
+        got = buf[par0:par0 + m * blk].cpu().numpy().reshape(m, w, P)[:, :, :cw]
+        es, ds = pyrit.pyrit_batch_stats(enc), pyrit.pyrit_batch_stats(dec)
+        ae, ad = es["alg_bytes"] / te / 1e6, ds["alg_bytes"] / td / 1e6
+        print(json.dumps({
+            "metric": "encode / decode GB/s of source data", "workload": "fields",
+            "config": {"workload": name + ", k=%d m=%d, 64 KiB packets, %d stripes" % (k, m, S), "w": w, "n": n,
+                       "modulus": hex(g), "native": native},
+            "encode_gbs": es["src_bytes"] / te / 1e6, "decode_gbs": ds["src_bytes"] / td / 1e6,
+            "encode_roofline_frac": ae / peak, "decode_roofline_frac": ad / peak,
+            "encode_kernel": kernel_name(pyrit.pyrit_batch_shape(enc, 0)),
+            "decode_kernel": kernel_name(pyrit.pyrit_batch_shape(dec, 0)),
+            "oracle_parity_stripe0": bool(np.array_equal(got, want)), "dtype": "u8", "data": "synthetic"}), flush=True)
+        pyrit.pyrit_batch_destroy(enc)
+        pyrit.pyrit_batch_destroy(dec)
+        pyrit.pyrit_plan_destroy(plan)
+        del buf
+        torch.cuda.empty_cache()
 
 
 def run_gf16(args):
