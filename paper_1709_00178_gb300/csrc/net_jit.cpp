@@ -24,6 +24,8 @@
 #include <cstdlib>
 #include <cstring>
 #include <deque>
+#include <functional>
+#include <iterator>
 #include <map>
 #include <memory>
 #include <string>
@@ -88,6 +90,99 @@ void put(std::string& o, const char* fmt, long a = 0, long b = 0, long c = 0, lo
   char buf[256];
   std::snprintf(buf, sizeof(buf), fmt, a, b, c, d, e, f);
   o += buf;
+}
+
+// One accumulator a case body updates: acc[out][t] ^= the XOR of its columns. Columns 0..W-1 are
+// the staged source packets d[q], W..N-1 the parity transform's padding packets dp[q - W], and
+// N.. the temporaries share_terms introduces.
+struct XorRow {
+  int out, t;
+  std::vector<int> cols;  // sorted
+};
+struct XorTemp {
+  int id;
+  std::vector<int> cols;  // 2 or 3 columns (earlier temporaries allowed)
+};
+
+// Common subexpressions of one case body. Accumulating c columns into a row costs ceil(c / 2)
+// three-input XORs; a temporary (one XOR of two or three columns) that replaces those columns in
+// several rows lowers that sum. The same ring coefficient puts the same pair of source packets,
+// d[q] and d[q - s + s'] for two set bits s, s', into many accumulators t (every rotation), and
+// the coefficients of one source in different outputs share pairs too. Greedy: take the pair or
+// triple with the largest saving (the triple: one step in every row holding it; the pair: one
+// step in every row of odd length holding it), minus the temporary's own step, ties to the
+// smallest column tuple, until nothing saves. The XOR each row receives is unchanged.
+void share_terms(std::vector<XorRow>& rows, int first_id, std::vector<XorTemp>* temps) {
+  int next = first_id;
+  for (;;) {
+    std::map<std::vector<int>, int> gain;  // candidate -> rows where it saves a step
+    for (const XorRow& r : rows) {
+      const std::vector<int>& c = r.cols;
+      const size_t len = c.size();
+      for (size_t a = 0; a < len; ++a)
+        for (size_t b = a + 1; b < len; ++b) {
+          if (len & 1u) ++gain[{c[a], c[b]}];
+          for (size_t e = b + 1; e < len; ++e) ++gain[{c[a], c[b], c[e]}];
+        }
+    }
+    const std::vector<int>* best = nullptr;
+    int best_gain = 1;  // a temporary costs one step: it must save at least two
+    for (const auto& kv : gain)
+      if (kv.second > best_gain) {
+        best_gain = kv.second;
+        best = &kv.first;
+      }
+    if (!best) return;
+    const std::vector<int> take = *best;
+    const int id = next++;
+    temps->push_back({id, take});
+    for (XorRow& r : rows) {
+      if (!std::includes(r.cols.begin(), r.cols.end(), take.begin(), take.end())) continue;
+      std::vector<int> rest;
+      std::set_difference(r.cols.begin(), r.cols.end(), take.begin(), take.end(), std::back_inserter(rest));
+      rest.push_back(id);  // ids grow, so the row stays sorted
+      r.cols.swap(rest);
+    }
+  }
+}
+
+// Writes rows (after share_terms) as statements inside a `for (x ...)` loop: each temporary just
+// before the first row that needs it (recursively), then each row's accumulation.
+void emit_rows(std::string& o, const std::vector<XorRow>& rows, const std::vector<XorTemp>& temps, int W, int N) {
+  auto name = [&](int c) {
+    char buf[32];
+    if (c < W)
+      std::snprintf(buf, sizeof(buf), "d[%d][x]", c);
+    else if (c < N)
+      std::snprintf(buf, sizeof(buf), "dp[%d][x]", c - W);
+    else
+      std::snprintf(buf, sizeof(buf), "e%d", c);
+    return std::string(buf);
+  };
+  std::vector<char> done(temps.size(), 0);
+  std::map<int, size_t> index;
+  for (size_t i = 0; i < temps.size(); ++i) index[temps[i].id] = i;
+  std::function<void(int)> need = [&](int c) {
+    auto it = index.find(c);
+    if (it == index.end() || done[it->second]) return;
+    const XorTemp& tp = temps[it->second];
+    for (int x : tp.cols) need(x);
+    done[it->second] = 1;
+    o += "          const uint32_t " + name(c) + " = ";
+    if (tp.cols.size() == 3)
+      o += "xor3(" + name(tp.cols[0]) + ", " + name(tp.cols[1]) + ", " + name(tp.cols[2]) + ");\n";
+    else
+      o += name(tp.cols[0]) + " ^ " + name(tp.cols[1]) + ";\n";
+  };
+  for (const XorRow& r : rows) {
+    for (int c : r.cols) need(c);
+    char acc[32];
+    std::snprintf(acc, sizeof(acc), "acc[%d][%d][x]", r.out, r.t);
+    size_t i = 0;
+    for (; i + 1 < r.cols.size(); i += 2)
+      o += std::string("          ") + acc + " = xor3(" + acc + ", " + name(r.cols[i]) + ", " + name(r.cols[i + 1]) + ");\n";
+    if (i < r.cols.size()) o += std::string("          ") + acc + " ^= " + name(r.cols[i]) + ";\n";
+  }
 }
 
 // CUDA C++ source of a network (compiled together with the embedded ring_staged.cuh).
@@ -175,49 +270,52 @@ std::string net_source(const NetSpec& s) {
     const int tb = cs / groups, g = cs % groups;
     for (int j = 0; j < s.nin; ++j) {
       put(o, "      case %ld: {\n", ((long)tb * groups + g) * s.nin + j);
-      if (!guard) o += "#pragma unroll\n        for (int x = 0; x < WORDS; ++x) {\n";
+      // the accumulators this source updates in each output slot of the group
+      std::vector<std::vector<XorRow>> slot(s.mg);
       for (int ii = 0; ii < s.mg; ++ii) {
         const int out = g * s.mg + ii;
         if (out >= s.tnout[tb]) break;
         const uint32_t r = s.mask[tb][j][out];
-        std::string lines;
         for (int t = 0; t < N; ++t) {
           // under the parity transform a direct network never builds the top accumulators
           // (phi_P^{-1} drops them)
           if (parity && !syndrome && t >= W) continue;
-          // accumulator t receives packet t - s for every set bit s, two terms per three-input
-          // XOR; packets W..N-1 are the zero packets of phi_E (dropped) or the parity packets of
-          // phi_P
-          std::vector<std::string> terms;
+          // accumulator t receives packet t - s for every set bit s; packets W..N-1 are the zero
+          // packets of phi_E (dropped) or the parity packets of phi_P
+          XorRow row{ii, t, {}};
           for (int sh = 0; sh < N; ++sh) {
             if (!((r >> sh) & 1u)) continue;
             const int q = (t - sh + N) % N;
-            if (q < W) {
-              char buf[32];
-              std::snprintf(buf, sizeof(buf), "d[%d][x]", q);
-              terms.push_back(buf);
-            } else if (parity) {
-              char buf[32];
-              std::snprintf(buf, sizeof(buf), "dp[%d][x]", q - W);
-              terms.push_back(buf);
-            }
+            if (q < W || parity) row.cols.push_back(q);
           }
-          char acc[32];
-          std::snprintf(acc, sizeof(acc), "acc[%d][%d][x]", ii, t);
-          for (size_t i = 0; i + 1 < terms.size(); i += 2)
-            lines += std::string("          ") + acc + " = xor3(" + acc + ", " + terms[i] + ", " + terms[i + 1] + ");\n";
-          if (terms.size() & 1) lines += std::string("          ") + acc + " ^= " + terms.back() + ";\n";
-        }
-        if (lines.empty()) continue;
-        if (guard) {
-          put(o, "        if (need & %ldu) {\n#pragma unroll\n        for (int x = 0; x < WORDS; ++x) {\n", 1L << ii);
-          o += lines;
-          o += "        }\n        }\n";
-        } else {
-          o += lines;
+          if (row.cols.empty()) continue;
+          std::sort(row.cols.begin(), row.cols.end());
+          slot[ii].push_back(std::move(row));
         }
       }
-      if (!guard) o += "        }\n";
+      if (!guard) {
+        // one body for every output of the group: terms shared across outputs are formed once
+        std::vector<XorRow> rows;
+        for (auto& v : slot) rows.insert(rows.end(), v.begin(), v.end());
+        std::vector<XorTemp> temps;
+        share_terms(rows, N, &temps);
+        o += "#pragma unroll\n        for (int x = 0; x < WORDS; ++x) {\n";
+        emit_rows(o, rows, temps, W, N);
+        o += "        }\n";
+      } else {
+        // syndrome networks guard each parity row with one warp-uniform test of the tile's
+        // needed rows, so terms are shared within a row only
+        int next_id = N;  // temporaries are numbered across the case's blocks
+        for (int ii = 0; ii < s.mg; ++ii) {
+          if (slot[ii].empty()) continue;
+          std::vector<XorTemp> temps;
+          share_terms(slot[ii], next_id, &temps);
+          next_id += (int)temps.size();
+          put(o, "        if (need & %ldu) {\n#pragma unroll\n        for (int x = 0; x < WORDS; ++x) {\n", 1L << ii);
+          emit_rows(o, slot[ii], temps, W, N);
+          o += "        }\n        }\n";
+        }
+      }
       o += "      } break;\n";
     }
   }

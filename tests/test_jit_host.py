@@ -18,17 +18,42 @@ import oracle
 from paper_1709_00178_gb300 import pyrit
 
 
+def _terms(text, temps):
+    """Source columns of an XOR expression: d[q][x] is packet q of the source; dp[j][x] (the parity
+    transform's padding packet j, the parity of the source's interleaved word j) is recorded as
+    q = -1 - j; a temporary e<id> stands for the columns it was formed from."""
+    qs = []
+    for q, p, e in re.findall(r"d(?:\[(\d+)\]|p\[(\d+)\])\[x\]|\be(\d+)\b", text):
+        if e:
+            qs += temps[int(e)]
+        else:
+            qs.append(int(q) if q else -1 - int(p))
+    return qs
+
+
 def _parse(src):
     nin = int(re.search(r"switch \(g \* (\d+) \+ j\)", src).group(1))
     n, words, mg, nc = map(int, re.search(r"ring_staged_body<(\d+), (\d+), (\d+), (\d+),", src).groups())
-    cases, cur = {}, None
+    cases, cur, temps, guard, guards = {}, None, {}, None, []
     for line in src.splitlines():
         c = re.match(r"\s*case (\d+): \{", line)
         if c:
             cur = int(c.group(1))
             cases[cur] = []
+            temps, guard = {}, None
             continue
-        # acc[i][t][x] ^= d[q][x];   or   acc[i][t][x] = xor3(acc[i][t][x], d[a][x], d[b][x]);
+        # syndrome networks: the accumulations of one parity row under a test of the needed rows
+        gd = re.match(r"\s*if \(need & (\d+)u\) \{", line)
+        if gd:
+            guard = int(gd.group(1))
+            continue
+        # a shared term: const uint32_t e<id> = a ^ b;   or   = xor3(a, b, c);
+        t = re.match(r"\s*const uint32_t e(\d+) = (.*);", line)
+        if t:
+            assert cur is not None and int(t.group(1)) not in temps, "a temporary is defined once per case"
+            temps[int(t.group(1))] = _terms(t.group(2), temps)
+            continue
+        # acc[i][t][x] ^= term;   or   acc[i][t][x] = xor3(acc[i][t][x], term, term);
         a = re.match(r"\s*acc\[(\d+)\]\[(\d+)\]\[x\] \^= (.*);", line)
         b = re.match(r"\s*acc\[(\d+)\]\[(\d+)\]\[x\] = xor3\(acc\[(\d+)\]\[(\d+)\]\[x\], (.*)\);", line)
         if b:
@@ -36,14 +61,11 @@ def _parse(src):
             a = b
         if a:
             assert cur is not None
-            # d[q][x] is packet q of the source; dp[j][x] (the parity transform's padding packet j,
-            # the parity of the source's interleaved word j) is recorded as q = -1 - j
-            qs = [int(q) if q else -1 - int(p) for q, p in
-                  re.findall(r"d(?:\[(\d+)\]|p\[(\d+)\])\[x\]", a.groups()[-1])]
-            cases[cur].append((int(a.group(1)), int(a.group(2)), qs))
+            cases[cur].append((int(a.group(1)), int(a.group(2)), _terms(a.groups()[-1], temps)))
+            guards.append((int(a.group(1)), guard))
         if "} break;" in line:
             cur = None
-    return dict(nin=nin, n=n, words=words, mg=mg, nc=nc, cases=cases)
+    return dict(nin=nin, n=n, words=words, mg=mg, nc=nc, cases=cases, guards=guards)
 
 
 def _w_of(n):
@@ -181,6 +203,33 @@ def test_runtime_compiler_builds_networks_without_a_device(w, k, m):
         assert ei.value.status == pyrit.PYRIT_E_INVALID_ARG
     finally:
         pyrit.pyrit_plan_destroy(plan)
+
+
+@pytest.mark.parametrize("w,k,m", [(4, 4, 2), (10, 10, 4), (12, 16, 4), (6, 8, 4)])
+def test_syndrome_network_is_the_parity_check_product(w, k, m):
+    """The first phase of a plan's syndrome-decode network, read back: for block column j of
+    [C | I_m], parity row i accumulates the ring product of column j's packets by phi_S(C[i][j])
+    (by 1 for its own parity block, by 0 for another's), every accumulation of row i sits under
+    the tile's test of row i, and the field value after phi_E^{-1} is the oracle's product."""
+    n = oracle.ring_size(w)
+    C, masks = _oracle_parity_masks(w, k, m)
+    plan = pyrit.pyrit_plan_create(w, n, k, m)
+    try:
+        net = _parse(pyrit.pyrit_plan_network_source(plan, pyrit.PYRIT_OP_DECODE_ANY))
+    finally:
+        pyrit.pyrit_plan_destroy(plan)
+    assert net["nin"] == k + m and net["mg"] >= m
+    assert net["guards"] and all(g == 1 << i for i, g in net["guards"])
+    for j in range(k + m):
+        entries = net["cases"][j]
+        for i in range(net["mg"]):
+            r = int(masks[i][j]) if (i < m and j < k) else int(j - k == i)
+            cols = _ring_columns(entries, i, n, w)
+            for q in range(w):
+                assert cols[q] == oracle.ring_mul(n, r, 1 << q), (j, i, q)
+                if i < m:
+                    u = int(C[i][j]) if j < k else r
+                    assert oracle.poly_mod(cols[q], oracle.field_poly(w)) == oracle.gf_mul_slow(w, u, 1 << q)
 
 
 def _field_of_mask(w, mask):
