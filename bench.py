@@ -244,6 +244,8 @@ def main():
                          "embedding vs parity transform on k >= m and k < m codes; paper: the paper's (12,8), (60,40) and "
                          "(60,20) use cases across block sizes; fields: GF(16) and GF(8) from other factors of x^n+1")
     ap.add_argument("--seconds", type=float, default=10.0, help="served: arrival window")
+    ap.add_argument("--rate", type=float, default=20000.0, help="served: Poisson arrival rate (requests/s)")
+    ap.add_argument("--slots", type=int, default=16, help="served: stream slots of the batching server")
     ap.add_argument("--generator", default="cauchy", choices=["cauchy", "weighted"],
                     help="cauchy: the plain Cauchy code of the configurations; weighted: the same code "
                          "family with weight-optimised row/column scalings (generalized Cauchy)")
@@ -878,7 +880,7 @@ def run_served(args):
     from paper_1709_00178_gb300.synth import BASE_SEED
     import numpy as np
     w, k, m = 12, 16, 4
-    rate = 20000.0
+    rate = args.rate
     rng = np.random.default_rng(BASE_SEED + 4)
     POOL = 512
     pool_P = [1 << int(e) for e in rng.integers(12, 21, POOL)]
@@ -910,60 +912,78 @@ def run_served(args):
         reqs.append((plan, int(ops[i]), pool_pat[s] if ops[i] else 0, P, blocks, i, 0))
         src_bytes += k * w * P
     arr, keep = pyrit.pyrit_requests_array(reqs)
-    srv = pyrit.pyrit_server_create(16 << 30, max_batch=64, slots=4)
-    # The clock sampler starts before anything is timed: its startup queries the driver, which
-    # stalled the server's stream calls for tens of milliseconds when it coincided with the first
-    # arrivals. Then a short unmeasured burst warms the launch shapes and the device.
-    clocks = Clocks(0)
-    clocks.start()
-    pyrit.pyrit_server_submit_slice(srv, arr, 0, min(64, nreq))
-    pyrit.pyrit_server_drain(srv, 60000)
-    pyrit.pyrit_server_poll(srv, 1 << 20)
-    time.sleep(0.5)
-    # The load generator must not pause: a full collection over the request tables (millions of
-    # objects) would hold submissions back for tens of milliseconds and count as service latency.
-    import gc
-    gc.collect()
-    gc.freeze()
-    gc.disable()
-    # The arrival times are written first (200k ctypes fields take tens of milliseconds), with the
-    # first arrival far enough ahead that submission starts before it: arrivals must not pile up
-    # into a burst the load generator itself created.
-    t0 = pyrit.pyrit_server_now_ns(srv) + 1000000000
-    for i in range(nreq):
-        arr[i].arrival_ns = int(t0 + arrivals[i])
-    if pyrit.pyrit_server_now_ns(srv) >= t0:
-        raise RuntimeError("load generator set-up ran past the first arrival")
-    i = 0
-    while i < nreq:
-        now = pyrit.pyrit_server_now_ns(srv)
-        j = i
-        while j < nreq and arr[j].arrival_ns <= now:
-            j += 1
-        if j > i:
-            pyrit.pyrit_server_submit_slice(srv, arr, i, j - i)
-            i = j
-    pyrit.pyrit_server_drain(srv, 600000)
-    gc.enable()
-    clk = clocks.stop()
-    done = pyrit.pyrit_server_poll(srv, nreq + 64)
-    st = pyrit.pyrit_server_stats(srv)
-    pyrit.pyrit_server_destroy(srv)
-    lat = np.array([d[4] - d[2] for d in done if d[0] < nreq], dtype=np.float64) / 1e3  # us
-    t_first = min(d[2] for d in done)
-    t_last = max(d[4] for d in done)
-    ok = all(d[1] == 0 for d in done)
-    print(json.dumps({
-        "metric": "served p50/p99 latency", "workload": "served", "unit": "us",
-        "value": float(np.percentile(lat, 99)), "p50_us": float(np.percentile(lat, 50)),
-        "p99_us": float(np.percentile(lat, 99)), "p999_us": float(np.percentile(lat, 99.9)),
-        "max_us": float(lat.max()), "requests": len(lat), "all_ok": ok,
-        "sustained_gbs": src_bytes / ((t_last - t_first) * 1e-9) / 1e9,
+
+    def serve(max_batch, slots):
+        """One pass of the arrival stream through a server; latency and throughput statistics."""
+        srv = pyrit.pyrit_server_create(16 << 30, max_batch=max_batch, slots=slots)
+        # The clock sampler starts before anything is timed: its startup queries the driver, which
+        # stalled the server's stream calls for tens of milliseconds when it coincided with the
+        # first arrivals. Then a short unmeasured burst warms the launch shapes and the device.
+        clocks = Clocks(0)
+        clocks.start()
+        pyrit.pyrit_server_submit_slice(srv, arr, 0, min(64, nreq))
+        pyrit.pyrit_server_drain(srv, 60000)
+        pyrit.pyrit_server_poll(srv, 1 << 20)
+        time.sleep(0.5)
+        # The load generator must not pause: a full collection over the request tables (millions
+        # of objects) would hold submissions back for tens of milliseconds and count as service
+        # latency.
+        import gc
+        gc.collect()
+        gc.freeze()
+        gc.disable()
+        # The arrival times are written first (200k ctypes fields take tens of milliseconds), with
+        # the first arrival far enough ahead that submission starts before it: arrivals must not
+        # pile up into a burst the load generator itself created.
+        t0 = pyrit.pyrit_server_now_ns(srv) + 1000000000
+        for i in range(nreq):
+            arr[i].arrival_ns = int(t0 + arrivals[i])
+        if pyrit.pyrit_server_now_ns(srv) >= t0:
+            raise RuntimeError("load generator set-up ran past the first arrival")
+        i = 0
+        while i < nreq:
+            now = pyrit.pyrit_server_now_ns(srv)
+            j = i
+            while j < nreq and arr[j].arrival_ns <= now:
+                j += 1
+            if j > i:
+                pyrit.pyrit_server_submit_slice(srv, arr, i, j - i)
+                i = j
+        pyrit.pyrit_server_drain(srv, 600000)
+        gc.enable()
+        clk = clocks.stop()
+        done = pyrit.pyrit_server_poll(srv, nreq + 64)
+        st = pyrit.pyrit_server_stats(srv)
+        pyrit.pyrit_server_destroy(srv)
+        lat = np.array([d[4] - d[2] for d in done if d[0] < nreq], dtype=np.float64) / 1e3  # us
+        t_first = min(d[2] for d in done)
+        t_last = max(d[4] for d in done)
+        return {"p50_us": float(np.percentile(lat, 50)), "p99_us": float(np.percentile(lat, 99)),
+                "p999_us": float(np.percentile(lat, 99.9)), "max_us": float(lat.max()), "requests": len(lat),
+                "all_ok": all(d[1] == 0 for d in done),
+                "sustained_gbs": src_bytes / ((t_last - t_first) * 1e-9) / 1e9,
+                "batches": st["batches"], "launches": st["launches"], "max_inflight_bytes": st["max_inflight"],
+                "clocks": clk}
+
+    # Continuous batching (up to 64 admitted requests per launch group, 16 stream slots whose
+    # launches overlap: a request that finds a slot free starts alone, requests that arrive while
+    # every slot is busy share the next free one), then the same arrivals through the same server
+    # and kernels with one request per launch: per-stripe launches as requests arrive, up to 16 in
+    # flight on their own streams.
+    batched = serve(64, args.slots)
+    single = serve(1, 16)
+    clk = batched.pop("clocks")
+    single.pop("clocks")
+    out = {"metric": "served p50/p99 latency", "workload": "served", "unit": "us", "value": batched["p99_us"]}
+    out.update(batched)
+    out.update({
         "offered_gbs": src_bytes / (arrivals[-1] * 1e-9) / 1e9,
-        "batches": st["batches"], "launches": st["launches"], "max_inflight_bytes": st["max_inflight"],
-        "config": {"workload": "Poisson 20k req/s, GF(2^12) k=16 m=4, P 4 KiB-1 MiB, half 4-erasure decode, "
-                               "16 GiB budget, 4 stream slots, batches up to 64", "seconds": args.seconds},
-        "clocks": clk, "higher_is_better": False, "dtype": "u8", "data": "synthetic"}), flush=True)
+        "per_request_launches": single,
+        "config": {"workload": "Poisson %gk req/s, GF(2^12) k=16 m=4, P 4 KiB-1 MiB, half 4-erasure decode, "
+                               "16 GiB budget, %d stream slots, batches up to 64; per_request_launches: the same "
+                               "arrivals one request per launch, 16 stream slots" % (rate / 1000, args.slots), "seconds": args.seconds},
+        "clocks": clk, "higher_is_better": False, "dtype": "u8", "data": "synthetic"})
+    print(json.dumps(out), flush=True)
     pyrit.pyrit_plan_destroy(plan)
 
 

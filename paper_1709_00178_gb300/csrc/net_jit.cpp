@@ -7,7 +7,8 @@
 // erasure pattern) those tests are known before the launch. The generated step writes them out:
 // for source j and output i, ring accumulator t receives the XOR of the source packets
 // q = t - s (mod N) over the set bits s of r_ij, where q = W (the zero packet that phi_E pads,
-// Sec. 2.3.2) drops out -- one XOR expression per accumulator, no bit tested. Per source the
+// Sec. 2.3.2) drops out -- one XOR expression per accumulator, no bit tested, with pairs and
+// triples of packets that several accumulators receive formed once (share_terms). Per source the
 // kernel takes one warp-uniform branch (a switch on the source index) into that straight-line
 // code. Staging, phi_E^{-1} and the stores are the generic kernels' own text (ring_staged.cuh).
 //

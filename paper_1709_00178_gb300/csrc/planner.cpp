@@ -1,6 +1,7 @@
 // Host planner: field checks, the sparse transform phi_S, generator validation and the decoding
 // matrices (paper Secs. 2.2, 2.3, 3 and 4.3). Host memory only; no CUDA call.
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <new>
 
@@ -404,6 +405,8 @@ int pyrit_plan_create(int w, int n, int k, int m, const uint32_t* G, pyrit_plan_
   if (!G && (uint64_t)k + (uint64_t)m > (1ull << w)) return PYRIT_E_TOO_LONG;
   pyrit_plan_s* p = new (std::nothrow) pyrit_plan_s;
   if (!p) return PYRIT_E_OOM;
+  static std::atomic<uint64_t> next_serial{1};
+  p->serial = next_serial.fetch_add(1);
   p->w = w;
   p->n = n;
   p->g = g;

@@ -102,6 +102,8 @@ struct DecodeEntry {
 
 struct pyrit_plan_s {
   int w, n, k, m;
+  uint64_t serial = 0;  // unique in the process (keys caches that must not confuse a new plan
+                        // allocated at a destroyed plan's address with the old one)
   uint32_t g = 0;       // the field's modulus
   bool native = true;   // the generic kernels serve this field (else generated networks only)
   int transform = PYRIT_TRANSFORM_EMBEDDING;

@@ -45,6 +45,7 @@ struct Pending {
   bool syn = false;
   int n;
   uint64_t bytes;    // device bytes of the stripe ((k+m) w P): what the admission budget counts
+  uint64_t tiles;    // column tiles of the stripe at the narrowest tile width that could code it
   uint64_t tag;
   int64_t arrival;   // server clock, ns
 };
@@ -58,6 +59,7 @@ struct Slot {
   uint2* host_tiles = nullptr;
   std::vector<Pending> reqs;
   uint64_t bytes = 0;
+  uint64_t tiles = 0;  // sum of the admitted requests' tile bounds
   int64_t launch_ns = 0;
   bool busy = false;
 };
@@ -68,6 +70,11 @@ struct pyrit_server_s {
   TileShape shapes[16][kMaxOut + 1];  // launch shape per (ring size, largest output count), lazily
   bool shape_set[16][kMaxOut + 1] = {};
   std::map<const Variant*, TileShape> net_shapes;  // launch shapes of the generated networks used
+  // Per (plan serial, syndrome form, output count): the compiled network that codes such requests
+  // (only ready networks are kept), and the tile width of the network shape that would serve them.
+  std::map<uint64_t, const Variant*> nets;
+  std::map<uint64_t, uint32_t> net_tw;
+  uint32_t generic_tw[16] = {};  // narrowest generic tile width per ring size (0: not computed)
   size_t budget = 0;
   int max_batch = 0;
   uint32_t max_tiles = 0;
@@ -121,6 +128,7 @@ void reap(pyrit_server_s* s) {
     s->inflight -= sl.bytes;
     sl.reqs.clear();
     sl.bytes = 0;
+    sl.tiles = 0;
     sl.busy = false;
   }
 }
@@ -149,13 +157,23 @@ int slot_shape(pyrit_server_s* s, int n, int max_nout, TileShape* out) {
   return PYRIT_OK;
 }
 
+// Cache key of the requests of one plan, form (syndrome decode or not) and output count.
+uint64_t request_key(const Pending& p) { return p.plan->serial << 5 | (p.syn ? 16u : 0u) | (uint64_t)p.job.nout; }
+
 // The generated network that would code request p now (nullptr: the generic kernel), queued for
-// the background compiler if it is missing.
-const Variant* request_network(const Pending& p) {
+// the background compiler if it is missing. A ready network is remembered per request key, so
+// later requests of the same plan and form skip building its spec. Called with the lock held.
+const Variant* request_network(pyrit_server_s* s, const Pending& p) {
   if (p.job.nout == 0 || jit_mode() == PYRIT_JIT_OFF) return nullptr;
-  if (p.op == PYRIT_OP_ENCODE) return net_variant(net_spec(p.n, p.job, 0, 0, 0, 0, PYRIT_TRANSFORM_EMBEDDING), false);
-  if (p.syn) return net_variant(net_spec_syndrome(p.plan, 0, 0, 0), false);
-  return nullptr;
+  if (p.op != PYRIT_OP_ENCODE && !p.syn) return nullptr;
+  const uint64_t key = request_key(p);
+  auto it = s->nets.find(key);
+  if (it != s->nets.end()) return it->second;
+  const Variant* v = p.op == PYRIT_OP_ENCODE
+                         ? net_variant(net_spec(p.n, p.job, 0, 0, 0, 0, PYRIT_TRANSFORM_EMBEDDING), false)
+                         : net_variant(net_spec_syndrome(p.plan, 0, 0, 0), false);
+  if (v) s->nets.emplace(key, v);
+  return v;
 }
 
 // Launch shape of a generated network (cached).
@@ -170,47 +188,74 @@ const TileShape& network_shape(pyrit_server_s* s, const Variant* v) {
   return it->second;
 }
 
-// Column tiles the slot's requests need: an upper bound whichever kernel codes each of them (the
-// narrowest tile width among its ring size's generic shape and the default network shapes), so
-// that a network finishing its compilation between admission and launch cannot overflow the table.
-uint64_t slot_tiles(pyrit_server_s* s, const std::vector<Pending>& reqs) {
-  int max_nout[16] = {0};
-  for (const Pending& p : reqs) max_nout[p.n] = std::max(max_nout[p.n], (int)p.job.nout);
-  uint64_t t = 0;
-  for (const Pending& p : reqs) {
-    if (p.job.nout == 0) continue;
-    TileShape sh;
-    if (slot_shape(s, p.n, max_nout[p.n], &sh) != PYRIT_OK) return ~0ull;
-    uint64_t tw = (uint64_t)sh.tw;
-    NetSpec cand[8];
-    const int nc = p.syn ? net_syndrome_shapes(p.plan, cand, 8) : net_candidate_shapes(p.n, p.job.nout, cand, 8);
-    for (int i = 0; i < nc && i < 1; ++i) {  // the default network shape is the one served
-      const int groups = output_groups(cand[i].mg, cand[i].nout, cand[i].nc);
-      tw = std::min<uint64_t>(tw, (uint64_t)(cand[i].nc / groups) * 32u * 4u * (uint64_t)cand[i].words);
+// Column tiles request p needs, an upper bound whichever kernel codes it: its packet size over the
+// narrowest tile width among its ring size's generic shapes (for any output count of the batch it
+// joins) and the default shape of the network that would code it, so that neither the batch's
+// composition nor a network finishing its compilation between admission and launch can overflow
+// a slot's tile table. Widths are cached. Called with the lock held.
+uint64_t request_tiles(pyrit_server_s* s, const Pending& p) {
+  if (p.job.nout == 0) return 0;
+  if (p.n < 0 || p.n >= 16) return ~0ull;
+  uint32_t& gtw = s->generic_tw[p.n];
+  if (gtw == 0) {
+    uint32_t tw = ~0u;
+    for (int mo = 1; mo <= kMaxOut; ++mo) {
+      TileShape sh;
+      if (slot_shape(s, p.n, mo, &sh) != PYRIT_OK) return ~0ull;
+      tw = std::min<uint32_t>(tw, (uint32_t)sh.tw);
     }
-    t += (p.job.P + tw - 1) / tw;
+    gtw = tw;
   }
-  return t;
+  uint64_t tw = gtw;
+  const uint64_t key = request_key(p);
+  auto it = s->net_tw.find(key);
+  if (it == s->net_tw.end()) {
+    uint32_t ntw = ~0u;
+    NetSpec cand[1];  // the default network shape is the one served
+    const int nc = p.syn ? net_syndrome_shapes(p.plan, cand, 1) : net_candidate_shapes(p.n, p.job.nout, cand, 1);
+    if (nc == 1) {
+      const int groups = output_groups(cand[0].mg, cand[0].nout, cand[0].nc);
+      ntw = (uint32_t)(cand[0].nc / groups) * 32u * 4u * (uint32_t)cand[0].words;
+    }
+    it = s->net_tw.emplace(key, ntw).first;
+  }
+  tw = std::min<uint64_t>(tw, it->second);
+  return tw ? (p.job.P + tw - 1) / tw : ~0ull;
 }
 
 // Packs the slot's admitted requests into launches: requests with a compiled network grouped by
 // that network (encode table or plan's syndrome decode), the rest by ring size on the generic
-// kernel; an explicit tile list per group; all staged in pinned memory and copied on the slot's
-// stream.
+// kernel. A group of one request carries its job in the kernel parameters with implicit tiles
+// (nothing to copy first); larger groups get an explicit tile list, staged with their jobs in
+// pinned memory and copied on the slot's stream.
 int launch_slot(pyrit_server_s* s, Slot& sl) {
   uint32_t nj = 0, nt = 0;
   struct G {
     TileShape shape;
     uint32_t job0, njobs, tile0, ntiles;
+    bool single;     // one job, passed by value
+    JobDesc job;     // that job
   };
   std::vector<G> groups;
   std::vector<const Variant*> net(sl.reqs.size());
-  for (size_t i = 0; i < sl.reqs.size(); ++i) net[i] = request_network(sl.reqs[i]);
+  for (size_t i = 0; i < sl.reqs.size(); ++i) net[i] = request_network(s, sl.reqs[i]);
   auto add_group = [&](const TileShape& shape, auto member, bool syn_form) -> int {
     G g{};
     g.shape = shape;
     g.job0 = nj;
     g.tile0 = nt;
+    size_t members = 0, first = 0;
+    for (size_t i = 0; i < sl.reqs.size(); ++i)
+      if (sl.reqs[i].job.nout != 0 && member(i) && members++ == 0) first = i;
+    if (members == 1) {
+      const Pending& p = sl.reqs[first];
+      g.single = true;
+      g.job = syn_form ? p.syn_job : p.job;
+      g.njobs = 1;
+      g.ntiles = (uint32_t)((p.job.P + (uint64_t)g.shape.tw - 1) / (uint64_t)g.shape.tw);
+      groups.push_back(g);
+      return PYRIT_OK;
+    }
     for (size_t i = 0; i < sl.reqs.size(); ++i) {
       const Pending& p = sl.reqs[i];
       if (p.job.nout == 0 || !member(i)) continue;
@@ -252,7 +297,9 @@ int launch_slot(pyrit_server_s* s, Slot& sl) {
   if (nt && cudaMemcpyAsync(sl.dev_tiles, sl.host_tiles, nt * sizeof(uint2), cudaMemcpyHostToDevice, sl.st) != cudaSuccess)
     return PYRIT_E_CUDA;
   for (const G& g : groups) {
-    const int rc = launch_staged(g.shape, nullptr, sl.dev_jobs + g.job0, sl.dev_tiles + g.tile0, g.ntiles, 0, sl.st);
+    const int rc = g.single ? launch_staged(g.shape, &g.job, nullptr, nullptr, g.ntiles, g.ntiles, sl.st)
+                            : launch_staged(g.shape, nullptr, sl.dev_jobs + g.job0, sl.dev_tiles + g.tile0, g.ntiles,
+                                            0, sl.st);
     if (rc != PYRIT_OK) return rc;
     ++s->launches;
   }
@@ -282,12 +329,10 @@ void run(pyrit_server_s* s) {
       while (!s->arrivals.empty() && (int)free_slot->reqs.size() < s->max_batch) {
         const Pending& p = s->arrivals.front();
         if (s->inflight + free_slot->bytes + p.bytes > s->budget) break;
+        if (free_slot->tiles + p.tiles > s->max_tiles) break;
         free_slot->reqs.push_back(p);
-        if (slot_tiles(s, free_slot->reqs) > s->max_tiles) {
-          free_slot->reqs.pop_back();
-          break;
-        }
         free_slot->bytes += p.bytes;
+        free_slot->tiles += p.tiles;
         s->arrivals.pop_front();
       }
       if (!free_slot->reqs.empty()) {
@@ -386,9 +431,8 @@ int pyrit_server_submit(pyrit_server_t s, const pyrit_request_t* reqs, int count
     {
       // one request must fit a slot's tile table even at the narrowest tiles of its ring size
       std::lock_guard<std::mutex> lk(s->mu);
-      std::vector<Pending> one(1, p);
-      one[0].job.nout = kMaxOut;
-      if (slot_tiles(s, one) > s->max_tiles) return PYRIT_E_INVALID_ARG;
+      p.tiles = request_tiles(s, p);
+      if (p.tiles > s->max_tiles) return PYRIT_E_INVALID_ARG;
     }
     p.tag = reqs[i].tag;
     batch.push_back(p);

@@ -160,3 +160,44 @@ def test_drain_wait_is_bounded(pyrit):
     finally:
         pyrit.pyrit_server_destroy(srv)
         pyrit.pyrit_plan_destroy(plan)
+
+
+def test_plans_replaced_between_requests(pyrit):
+    """The server remembers which compiled network codes a plan's requests. Plans destroyed and
+    created again (possibly at the same address) with a different generator must be coded with
+    their own tables: every encode equals the oracle's under that plan's generator, and every
+    decode rebuilds the erased blocks."""
+    w, k, m, P = 10, 10, 4, 4096
+    n = oracle.ring_size(w)
+    one = (k + m) * w * P
+    buf = torch.empty(2 * one, dtype=torch.uint8, device="cuda")
+    srv = pyrit.pyrit_server_create(64 << 20, max_batch=8, slots=2)
+    try:
+        for rnd in range(6):
+            G = pyrit.pyrit_generator_weighted(w, n, k, m)[0] if rnd % 2 else oracle.cauchy(w, k, m)
+            plan = pyrit.pyrit_plan_create(w, n, k, m, G)
+            try:
+                pyrit.pyrit_plan_specialise(plan, pyrit.PYRIT_OP_ENCODE)
+                pyrit.pyrit_plan_specialise(plan, pyrit.PYRIT_OP_DECODE_ANY)
+                pyrit.pyrit_synth_fill(buf.data_ptr(), buf.numel(), 500 + rnd)
+                torch.cuda.synchronize()
+                base = buf.data_ptr()
+                enc = [base + e * w * P for e in range(k + m)]
+                pyrit.pyrit_server_submit(srv, [(plan, 0, 0, P, enc, 2 * rnd, 0)])
+                assert pyrit.pyrit_server_drain(srv, 20000) == 0
+                h = buf[:one].cpu().numpy().reshape(k + m, w, P)
+                assert np.array_equal(h[k:], oracle.encode(w, k, m, np.asarray(G).reshape(k + m, k), h[:k], nthreads=NCPU)), rnd
+                # a copy of the stripe with three blocks lost, rebuilt by a syndrome-form decode
+                buf[one:] = buf[:one]
+                lost = (1 << 1) | (1 << 7) | (1 << (k + 2))
+                for b in (1, 7, k + 2):
+                    buf[one + b * w * P:one + (b + 1) * w * P] = 0
+                dec = [base + one + e * w * P for e in range(k + m)]
+                pyrit.pyrit_server_submit(srv, [(plan, 1, lost, P, dec, 2 * rnd + 1, 0)])
+                assert pyrit.pyrit_server_drain(srv, 20000) == 0
+                assert torch.equal(buf[one:], buf[:one]), rnd
+                assert all(d[1] == 0 for d in pyrit.pyrit_server_poll(srv))
+            finally:
+                pyrit.pyrit_plan_destroy(plan)
+    finally:
+        pyrit.pyrit_server_destroy(srv)
