@@ -395,10 +395,12 @@ typedef struct {
 /* Starts a server on the current device. A scheduler thread admits submitted requests in arrival
  * order while the device bytes of the requests in flight ((k+m) w P each) stay within hbm_budget,
  * and whenever one of `slots` stream slots is free it packs the admitted requests (at most
- * max_batch) into one batch: their jobs are copied into the slot's device descriptor table and
- * coded by one persistent launch of the staged ring kernel per ring size on the slot's stream.
- * Batches on different slots overlap on the device; new arrivals join the next free slot
- * (continuous batching). Decoding matrices come from the plans' caches; launch shapes from the
+ * max_batch) into one batch, coded on the slot's stream by one persistent launch per kernel: the
+ * plan's compiled network (encode table or syndrome decode) where it has one, else the staged
+ * ring kernel per ring size. A launch of one request passes its job in the kernel parameters;
+ * larger launches copy their jobs into the slot's device descriptor table first. Batches on
+ * different slots overlap on the device; new arrivals join the next free slot (continuous
+ * batching). Decoding matrices come from the plans' caches; launch shapes from the
  * autotuner's table when it has the key. queue_cap bounds the requests waiting for admission.
  * Allocates its slots' device tables and pinned staging. */
 PYRIT_API int pyrit_server_create(size_t hbm_budget, int max_batch, int slots, int queue_cap, pyrit_server_t* out);
