@@ -246,6 +246,8 @@ def main():
     ap.add_argument("--seconds", type=float, default=10.0, help="served: arrival window")
     ap.add_argument("--rate", type=float, default=20000.0, help="served: Poisson arrival rate (requests/s)")
     ap.add_argument("--slots", type=int, default=16, help="served: stream slots of the batching server")
+    ap.add_argument("--packet", type=int, default=0,
+                    help="sweep: one packet size in bytes instead of 4 KiB..1 MiB (with --stripes: a profiling case)")
     ap.add_argument("--generator", default="cauchy", choices=["cauchy", "weighted"],
                     help="cauchy: the plain Cauchy code of the configurations; weighted: the same code "
                          "family with weight-optimised row/column scalings (generalized Cauchy)")
@@ -517,9 +519,14 @@ def run_sweep(args):
     peak, _ = peak_hbm()
     plan = make_plan(pyrit, args.generator, w, k, m)
     stream = torch.cuda.Stream(device=dev)
+    nvtx = torch.cuda.nvtx
     for e in range(12, 21):
         P = 1 << e
+        if args.packet and P != args.packet:
+            continue
         S = (8 << 30) // (k * w * P)
+        if args.packet and args.stripes != STRIPES:
+            S = max(1, args.stripes)
         blk = w * P
         buf = torch.empty(S * (k + m) * blk, dtype=torch.uint8, device=dev)
         pyrit.pyrit_synth_fill(buf.data_ptr(), buf.numel(), BASE_SEED + 2, 0)
@@ -531,10 +538,13 @@ def run_sweep(args):
         pats = [sum(1 << int(x) for x in rng.choice(k + m, m, replace=False)) for _ in range(S)]
         enc = pyrit.pyrit_batch_create([(plan, 0, 0, P, blocks[s]) for s in range(S)])
         dec = pyrit.pyrit_batch_create([(plan, 1, pats[s], P, blocks[s]) for s in range(S)])
-        pyrit.pyrit_batch_tune(enc, stream, 2)
-        pyrit.pyrit_batch_tune(dec, stream, 2)
+        if not args.no_tune:
+            pyrit.pyrit_batch_tune(enc, stream, 2)
+            pyrit.pyrit_batch_tune(dec, stream, 2)
+        nvtx.range_push("timed")
         te = _time_batch(torch, pyrit, enc, stream, args.steps)
         td = _time_batch(torch, pyrit, dec, stream, args.steps)
+        nvtx.range_pop()
         es, ds = pyrit.pyrit_batch_stats(enc), pyrit.pyrit_batch_stats(dec)
         ae, ad = es["alg_bytes"] / te / 1e6, ds["alg_bytes"] / td / 1e6
         print(json.dumps({
@@ -704,10 +714,13 @@ def run_fields(args):
         lost = (0b1011 | (1 << (k + 1))) if m == 4 else (0b101 | (1 << k))
         enc = pyrit.pyrit_batch_create([(plan, 0, 0, P, blocks[s]) for s in range(S)])
         dec = pyrit.pyrit_batch_create([(plan, 1, lost, P, blocks[s]) for s in range(S)])
-        pyrit.pyrit_batch_tune(enc, stream, 2)
-        pyrit.pyrit_batch_tune(dec, stream, 2)
+        if not args.no_tune:
+            pyrit.pyrit_batch_tune(enc, stream, 2)
+            pyrit.pyrit_batch_tune(dec, stream, 2)
+        nvtx.range_push("timed")
         te = _time_batch(torch, pyrit, enc, stream, args.steps)
         td = _time_batch(torch, pyrit, dec, stream, args.steps)
+        nvtx.range_pop()
         torch.cuda.synchronize()
         cw = 4096
         data0 = np.ascontiguousarray(buf[:k * blk].cpu().numpy().reshape(k, w, P)[:, :, :cw])
