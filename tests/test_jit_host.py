@@ -522,3 +522,33 @@ def test_general_field_network_is_the_field_product(w, n, k, m):
         assert pyrit.pyrit_jit_stats()["failed"] == before, pyrit.pyrit_jit_log()
     finally:
         pyrit.pyrit_plan_destroy(plan)
+
+
+def _xor_statements(src):
+    body = src[src.index("switch ("):]
+    return sum(1 for line in body.splitlines() if re.search(r"xor3\(| \^= | \^ ", line))
+
+
+@pytest.mark.parametrize("w,k,m,enc_max,syn_max", [(10, 10, 4, 620, 735), (12, 16, 4, 1500, 1680)])
+def test_shared_terms_reduce_the_xor_count(w, k, m, enc_max, syn_max):
+    """The generated networks form shared pairs and triples of source packets once: each XOR
+    statement is one 32-bit three-input operation per column word, so their count per network is
+    the coding work. Without sharing the plain Cauchy codes take sum(ceil(terms / 2)) statements:
+    868 (encode) and 908 (syndrome first phase) for GF(2^10) k=10 m=4, 2200 and 2248 for GF(2^12)
+    k=16 m=4; with it at most the bounds here (614 / 728 and 1492 / 1672 when written)."""
+    n = oracle.ring_size(w)
+    C, masks = _oracle_parity_masks(w, k, m)
+    unshared = 0
+    for j in range(k):
+        for o in range(m):
+            for t in range(n):
+                terms = sum(1 for s in range(n) if (int(masks[o][j]) >> s) & 1 and (t - s) % n < w)
+                unshared += (terms + 1) // 2
+    plan = pyrit.pyrit_plan_create(w, n, k, m)
+    try:
+        enc = _xor_statements(pyrit.pyrit_plan_network_source(plan, pyrit.PYRIT_OP_ENCODE))
+        syn = _xor_statements(pyrit.pyrit_plan_network_source(plan, pyrit.PYRIT_OP_DECODE_ANY))
+    finally:
+        pyrit.pyrit_plan_destroy(plan)
+    assert enc <= enc_max and enc < 0.75 * unshared, (enc, unshared)
+    assert syn <= syn_max, syn
