@@ -20,56 +20,81 @@ _lib = None
 
 
 def lib():
+    """The oracle library built from ``pyrit_oracle.c`` (built on first use)."""
     global _lib
     if _lib is None:
-        # ORACLE_LIB lets the mutation tests load a deliberately broken copy of the oracle.
-        L = ctypes.CDLL(os.environ.get("ORACLE_LIB") or build_oracle())
-        u32, u64, i32, sz = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int, ctypes.c_size_t
-        vp = ctypes.c_void_p
-        sig = {
-            "oracle_poly_mod": (u64, [u64, u64]),
-            "oracle_poly_mul": (u64, [u64, u64]),
-            "oracle_aop": (u64, [i32]),
-            "oracle_aop_irreducible": (i32, [i32]),
-            "oracle_poly_irreducible": (i32, [u64]),
-            "oracle_esp": (u64, [i32, i32]),
-            "oracle_field_poly": (u64, [i32]),
-            "oracle_ring_size": (i32, [i32]),
-            "oracle_phi_P": (u32, [i32, i32, u32]),
-            "oracle_ring_factor": (u64, [i32, i32]),
-            "oracle_gf_mul_mod": (u32, [i32, u64, u32, u32]),
-            "oracle_cauchy_mod": (i32, [i32, u64, i32, i32, vp]),
-            "oracle_gf_invert_mod": (i32, [i32, u64, i32, vp, vp]),
-            "oracle_encode_mod": (i32, [i32, u64, i32, i32, vp, vp, vp, sz, i32]),
-            "oracle_decode_mod": (i32, [i32, u64, i32, i32, vp, vp, u64, sz, i32]),
-            "oracle_sparse_rep_mod": (u32, [i32, i32, u64, u32]),
-            "oracle_gf_mul_slow": (u32, [i32, u32, u32]),
-            "oracle_gf_order": (u32, [i32, u32]),
-            "oracle_gf_primitive": (u32, [i32]),
-            "oracle_gf_tables": (i32, [i32, vp, vp, vp]),
-            "oracle_gf_mul": (u32, [i32, u32, u32]),
-            "oracle_cauchy": (i32, [i32, i32, i32, vp]),
-            "oracle_cauchy_weighted": (i32, [i32, i32, i32, vp, vp]),
-            "oracle_encode_pt": (i32, [i32, i32, i32, vp, vp, sz, i32]),
-            "oracle_decode_pt": (i32, [i32, i32, i32, vp, vp, u64, sz, i32]),
-            "oracle_gf_invert": (i32, [i32, i32, vp, vp]),
-            "oracle_encode": (i32, [i32, i32, i32, vp, vp, vp, sz, i32]),
-            "oracle_decode": (i32, [i32, i32, i32, vp, vp, u64, sz, i32]),
-            "oracle_ring_mul": (u32, [i32, u32, u32]),
-            "oracle_ring_idempotents": (i32, [i32, vp, i32]),
-            "oracle_ring_representatives": (i32, [i32, i32, u32, vp, i32]),
-            "oracle_sparse_rep": (u32, [i32, i32, u32]),
-            "oracle_gf_mul_vec": (i32, [i32, vp, vp, vp, sz]),
-            "oracle_gf_mul_slow_vec": (None, [i32, vp, vp, vp, sz]),
-            "oracle_ring_mul_vec": (None, [i32, vp, vp, vp, sz]),
-            "oracle_poly_mod_vec": (None, [u64, vp, vp, sz]),
-        }
-        for name, (res, args) in sig.items():
-            f = getattr(L, name)
-            f.restype = res
-            f.argtypes = args
-        _lib = L
+        _lib = _load(build_oracle())
     return _lib
+
+
+def bind(path):
+    """An independent copy of these bindings over the C library at ``path``.
+
+    The mutation test (``tests/test_oracle_mutants.py``) compiles deliberately broken copies of
+    ``pyrit_oracle.c`` and checks that the pins reject each one; it passes their paths here. The
+    copy is a separate module object: this module's own functions keep using the library built
+    from ``pyrit_oracle.c``, and nothing in the environment can redirect them."""
+    import importlib.util
+    global _bound
+    _bound += 1
+    spec = importlib.util.spec_from_file_location("oracle._bound%d" % _bound, __file__)
+    mod = importlib.util.module_from_spec(spec)
+    mod.__package__ = __name__
+    spec.loader.exec_module(mod)
+    mod._lib = mod._load(os.path.abspath(path))
+    return mod
+
+
+_bound = 0
+
+
+def _load(path):
+    L = ctypes.CDLL(path)
+    u32, u64, i32, sz = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int, ctypes.c_size_t
+    vp = ctypes.c_void_p
+    sig = {
+        "oracle_poly_mod": (u64, [u64, u64]),
+        "oracle_poly_mul": (u64, [u64, u64]),
+        "oracle_aop": (u64, [i32]),
+        "oracle_aop_irreducible": (i32, [i32]),
+        "oracle_poly_irreducible": (i32, [u64]),
+        "oracle_esp": (u64, [i32, i32]),
+        "oracle_field_poly": (u64, [i32]),
+        "oracle_ring_size": (i32, [i32]),
+        "oracle_phi_P": (u32, [i32, i32, u32]),
+        "oracle_ring_factor": (u64, [i32, i32]),
+        "oracle_gf_mul_mod": (u32, [i32, u64, u32, u32]),
+        "oracle_cauchy_mod": (i32, [i32, u64, i32, i32, vp]),
+        "oracle_gf_invert_mod": (i32, [i32, u64, i32, vp, vp]),
+        "oracle_encode_mod": (i32, [i32, u64, i32, i32, vp, vp, vp, sz, i32]),
+        "oracle_decode_mod": (i32, [i32, u64, i32, i32, vp, vp, u64, sz, i32]),
+        "oracle_sparse_rep_mod": (u32, [i32, i32, u64, u32]),
+        "oracle_gf_mul_slow": (u32, [i32, u32, u32]),
+        "oracle_gf_order": (u32, [i32, u32]),
+        "oracle_gf_primitive": (u32, [i32]),
+        "oracle_gf_tables": (i32, [i32, vp, vp, vp]),
+        "oracle_gf_mul": (u32, [i32, u32, u32]),
+        "oracle_cauchy": (i32, [i32, i32, i32, vp]),
+        "oracle_cauchy_weighted": (i32, [i32, i32, i32, vp, vp]),
+        "oracle_encode_pt": (i32, [i32, i32, i32, vp, vp, sz, i32]),
+        "oracle_decode_pt": (i32, [i32, i32, i32, vp, vp, u64, sz, i32]),
+        "oracle_gf_invert": (i32, [i32, i32, vp, vp]),
+        "oracle_encode": (i32, [i32, i32, i32, vp, vp, vp, sz, i32]),
+        "oracle_decode": (i32, [i32, i32, i32, vp, vp, u64, sz, i32]),
+        "oracle_ring_mul": (u32, [i32, u32, u32]),
+        "oracle_ring_idempotents": (i32, [i32, vp, i32]),
+        "oracle_ring_representatives": (i32, [i32, i32, u32, vp, i32]),
+        "oracle_sparse_rep": (u32, [i32, i32, u32]),
+        "oracle_gf_mul_vec": (i32, [i32, vp, vp, vp, sz]),
+        "oracle_gf_mul_slow_vec": (None, [i32, vp, vp, vp, sz]),
+        "oracle_ring_mul_vec": (None, [i32, vp, vp, vp, sz]),
+        "oracle_poly_mod_vec": (None, [u64, vp, vp, sz]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    return L
 
 
 def _p(a):

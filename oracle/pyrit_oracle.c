@@ -552,7 +552,8 @@ static int popcount32(uint32_t v) {
 }
 
 /* Sparse transform phi_S (Sec. 2.2): the representative of u with the fewest ones; ties go to
- * the smallest integer (they cannot occur for an AOP with n odd; they do for the ESP). */
+ * the smallest integer. Ties cannot occur for an AOP with n odd (weights t and n - t) and do not for
+ * GF(2^6) on n = 9; they do for GF(4) from x^2 + x + 1 in R_{2,9} and R_{2,15}. */
 uint32_t oracle_sparse_rep_mod(int w, int n, uint64_t p, uint32_t u) {
   (void)w;
   uint32_t best = 0;
