@@ -117,6 +117,10 @@ typedef struct pyrit_plan_s* pyrit_plan_t;
  * Computes phi_S of every parity coefficient (Sec. 2.2). Host memory only: no device call.
  * On success *out owns the plan; release it with pyrit_plan_destroy. */
 PYRIT_API int pyrit_plan_create(int w, int n, int k, int m, const uint32_t* G, pyrit_plan_t* out);
+
+/* pyrit_plan_create with 16-bit generator entries (every field this build codes has w <= 15, so
+ * an entry fits; G NULL: the default generator). Same checks, codes and ownership. */
+PYRIT_API int pyrit_plan(int w, int n, int k, int m, const uint16_t* G, pyrit_plan_t* out);
 PYRIT_API void pyrit_plan_destroy(pyrit_plan_t plan);
 
 /* A weight-optimised generalized Cauchy generator to pass to pyrit_plan_create (Sec. 3 codes with
@@ -451,10 +455,19 @@ PYRIT_API void pyrit_server_destroy(pyrit_server_t server);
  * overlaps on the GPU (for example on two streams at once) race on the array: order them on one
  * stream or wait between them. Host callers are serialised by a lock.
  * Errors. More than PYRIT_NOALLOC_MAX_STRIPES stripes or PYRIT_NOALLOC_MAX_TILES tiles returns
- * PYRIT_E_SCRATCH_LIMIT before any device work; invalid stripes return the codes of
- * pyrit_batch_create. A device-side bounded wait that gives up is recorded in the array's status
- * words and is not reported by this call. Asynchronous on `stream` otherwise. */
+ * PYRIT_E_SCRATCH_LIMIT before any device work; invalid stripes (and a ring size no kernel is built
+ * for) return the codes of pyrit_batch_create, also before any device work. A device-side bounded
+ * wait that gives up (its outputs are then incomplete) is recorded in the array's status words,
+ * not in the word pyrit_device_status reads: read it with pyrit_noalloc_status after the call's work
+ * and before the next call, which clears the words. Asynchronous on `stream` otherwise. */
 PYRIT_API int pyrit_code_stripes_noalloc(const pyrit_stripe_t* stripes, int count, pyrit_stream_t stream);
+
+/* Reads and clears the status words of pyrit_code_stripes_noalloc's fixed array on the current
+ * device, after the work already queued on `stream` (synchronises `stream`). *code_out receives 0 or
+ * PYRIT_E_TIMEOUT (a bounded device wait gave up); *where_out (may be NULL) the kernel site id. Like
+ * the entry point it serves (the paper has no counterpart), it allocates nothing: one copy into the
+ * caller's stack and one memset of the array. */
+PYRIT_API int pyrit_noalloc_status(int* code_out, int* where_out, pyrit_stream_t stream);
 
 /* ---- device status ----------------------------------------------------------------------- */
 
@@ -462,6 +475,14 @@ PYRIT_API int pyrit_code_stripes_noalloc(const pyrit_stripe_t* stripes, int coun
  * Kernels set it when a bounded wait gives up (PYRIT_E_TIMEOUT) instead of spinning forever.
  * *code_out receives 0 or a PYRIT_E_* code; *where_out (may be NULL) a kernel-specific site id. */
 PYRIT_API int pyrit_device_status(int* code_out, int* where_out);
+
+/* Self-test of the bounded waits (no counterpart in the paper): enqueues on `stream` one thread that
+ * waits, with the same bounded mbarrier wait every pipeline stage uses, on a barrier that nothing
+ * completes, for limit_ns (1 ns .. 1 s). The wait gives up, records PYRIT_E_TIMEOUT and site 100,
+ * and the kernel returns normally: the context stays usable. channel 0 records into the word
+ * pyrit_device_status reads, channel 1 into the status words pyrit_noalloc_status reads. For
+ * callers that want to check, on their own device, that a wait that runs out is reported. */
+PYRIT_API int pyrit_selftest_bounded_wait(int channel, uint64_t limit_ns, pyrit_stream_t stream);
 
 /* ---- synthetic inputs (device) ------------------------------------------------------------ */
 

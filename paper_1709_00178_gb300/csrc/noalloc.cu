@@ -51,6 +51,9 @@ int scratch_address(uint8_t** out) {
   return PYRIT_OK;
 }
 
+// Rings the plain-load kernel is instantiated for (launch_plain).
+bool plain_ring(int n) { return n == 3 || n == 5 || n == 9 || n == 11 || n == 13; }
+
 // The one job of a stripe. The fixed kernels have no parity transform and only the native fields
 // (those run only on generated networks), and a stripe with more than kMaxOut parity (or erased) blocks is several jobs, which
 // the fixed scratch does not hold: both are PYRIT_E_UNSUPPORTED here.
@@ -90,6 +93,7 @@ extern "C" int pyrit_code_stripes_noalloc(const pyrit_stripe_t* stripes, int cou
     if (rc != PYRIT_OK) return rc;
     ring_of[i] = stripes[i].plan->n;
     staged[i] = g_host_jobs[i].nout > 0 && job_is_staged(g_host_jobs[i]);
+    if (g_host_jobs[i].nout > 0 && !staged[i] && !plain_ring(ring_of[i])) return PYRIT_E_UNSUPPORTED_FIELD;
   }
   struct Launch {
     TileShape shape;
@@ -157,4 +161,59 @@ extern "C" int pyrit_code_stripes_noalloc(const pyrit_stripe_t* stripes, int cou
       if (rc != PYRIT_OK) return rc;
     }
   return PYRIT_OK;
+}
+
+namespace {
+
+// Bounded-wait self-test: thread 0 waits on an mbarrier that nothing arrives at, with the given
+// limit, exactly as a pipeline wait does; it gives up and records PYRIT_E_TIMEOUT and kSelftestSite
+// in `err`. The wait always ends (after limit_ns) and touches no memory but `err`.
+constexpr int kSelftestSite = 100;
+
+__global__ void bounded_wait_selftest_kernel(int* err, uint64_t limit_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_fence_init();
+    mbar_wait_for(&bar, 0u, err, kSelftestSite, limit_ns);
+  }
+}
+
+}  // namespace
+
+extern "C" int pyrit_noalloc_status(int* code_out, int* where_out, pyrit_stream_t stream) {
+  if (!code_out) return PYRIT_E_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  std::lock_guard<std::mutex> lk(g_mu);
+  uint8_t* scratch = nullptr;
+  const int rc = scratch_address(&scratch);
+  if (rc != PYRIT_OK) return rc;
+  int h[2] = {0, 0};
+  // Ordered after the calls queued on `stream`; the copy into pageable host memory completes
+  // before it returns, and the stream is synchronised once more before the words are cleared.
+  if (cudaMemcpyAsync(h, scratch, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess) return PYRIT_E_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return PYRIT_E_CUDA;
+  if (cudaMemsetAsync(scratch, 0, sizeof(h), st) != cudaSuccess) return PYRIT_E_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return PYRIT_E_CUDA;
+  *code_out = h[0];
+  if (where_out) *where_out = h[1];
+  return PYRIT_OK;
+}
+
+extern "C" int pyrit_selftest_bounded_wait(int channel, uint64_t limit_ns, pyrit_stream_t stream) {
+  if ((channel != 0 && channel != 1) || limit_ns == 0 || limit_ns > 1000000000ull) return PYRIT_E_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  int* err = nullptr;
+  if (channel == 0) {
+    err = device_error_word();
+    if (!err) return PYRIT_E_CUDA;
+  } else {
+    std::lock_guard<std::mutex> lk(g_mu);
+    uint8_t* scratch = nullptr;
+    const int rc = scratch_address(&scratch);
+    if (rc != PYRIT_OK) return rc;
+    err = reinterpret_cast<int*>(scratch);
+  }
+  bounded_wait_selftest_kernel<<<1, 32, 0, st>>>(err, limit_ns);
+  return cudaGetLastError() == cudaSuccess ? PYRIT_OK : PYRIT_E_CUDA;
 }

@@ -443,6 +443,13 @@ int pyrit_plan_create(int w, int n, int k, int m, const uint32_t* G, pyrit_plan_
 
 void pyrit_plan_destroy(pyrit_plan_t p) { delete p; }
 
+int pyrit_plan(int w, int n, int k, int m, const uint16_t* G, pyrit_plan_t* out) {
+  if (!G) return pyrit_plan_create(w, n, k, m, nullptr, out);
+  if (k < 1 || m < 0 || k > PYRIT_MAX_K || m > PYRIT_MAX_M || k + m > PYRIT_MAX_BLOCKS) return PYRIT_E_INVALID_ARG;
+  std::vector<uint32_t> g32(G, G + (size_t)(k + m) * (size_t)k);
+  return pyrit_plan_create(w, n, k, m, g32.data(), out);
+}
+
 int pyrit_plan_set_transform(pyrit_plan_t p, int transform) {
   if (!p) return PYRIT_E_INVALID_ARG;
   // the parity transform is defined for the all-one and equally spaced polynomials (Sec. 2.3.1,

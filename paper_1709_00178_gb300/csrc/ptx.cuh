@@ -50,19 +50,24 @@ __device__ __forceinline__ uint64_t global_timer_ns() {
 // records PYRIT_E_TIMEOUT in the error word and returns instead of spinning.
 constexpr uint64_t kWaitLimitNs = 4000000000ull;
 
-// Waits until the phase of `bar` with parity `parity` has completed, for at most kWaitLimitNs.
+// Waits until the phase of `bar` with parity `parity` has completed, for at most limit_ns.
 // Returns false (after recording `site` in err[1] and PYRIT_E_TIMEOUT in err[0]) on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int site) {
+__device__ __forceinline__ bool mbar_wait_for(uint64_t* bar, uint32_t parity, int* err, int site, uint64_t limit_ns) {
   for (int i = 0; i < 32; ++i)
     if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_timer_ns();
   while (true) {
     if (mbar_try_wait(bar, parity)) return true;
-    if (global_timer_ns() - t0 > kWaitLimitNs) {
+    if (global_timer_ns() - t0 > limit_ns) {
       if (err && atomicCAS(err, 0, -9 /* PYRIT_E_TIMEOUT */) == 0) err[1] = site;
       return false;
     }
   }
+}
+
+// The pipeline's waits: bounded by kWaitLimitNs.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int site) {
+  return mbar_wait_for(bar, parity, err, site, kWaitLimitNs);
 }
 
 // Bulk asynchronous copy global -> shared of `bytes` (multiple of 16, both addresses 16-byte

@@ -58,6 +58,7 @@ _i, _u32, _u64, _sz, _vp = ctypes.c_int, ctypes.c_uint32, ctypes.c_uint64, ctype
 _SIGS = {
     "pyrit_strerror": (ctypes.c_char_p, [_i]),
     "pyrit_plan_create": (_i, [_i, _i, _i, _i, _vp, ctypes.POINTER(_vp)]),
+    "pyrit_plan": (_i, [_i, _i, _i, _i, _vp, ctypes.POINTER(_vp)]),
     "pyrit_plan_destroy": (None, [_vp]),
     "pyrit_plan_info": (_i, [_vp, _vp, _vp, _vp, _vp]),
     "pyrit_plan_set_transform": (_i, [_vp, _i]),
@@ -140,6 +141,18 @@ def pyrit_plan_create(w, n, k, m, G=None):
             raise ValueError("G must be (k+m) x k")
     _check(_lib.pyrit_plan_create(w, n, k, m, _np_ptr(g) if g is not None else None, ctypes.byref(h)),
            "pyrit_plan_create")
+    return h.value
+
+
+def pyrit_plan(w, n, k, m, G=None):
+    """pyrit_plan_create with 16-bit generator entries."""
+    h = ctypes.c_void_p()
+    g = None
+    if G is not None:
+        g = np.ascontiguousarray(np.asarray(G, dtype=np.uint16))
+        if g.shape != (k + m, k):
+            raise ValueError("G must be (k+m) x k")
+    _check(_lib.pyrit_plan(w, n, k, m, _np_ptr(g) if g is not None else None, ctypes.byref(h)), "pyrit_plan")
     return h.value
 
 
@@ -434,7 +447,9 @@ def pyrit_jit_source(n, masks, tile=None, transform=PYRIT_TRANSFORM_EMBEDDING):
 
 # ---- coding without device allocation ---------------------------------------------------------
 
-_NOALLOC_SIGS = {"pyrit_code_stripes_noalloc": (_i, [ctypes.POINTER(pyrit_stripe_t), _i, _vp])}
+_NOALLOC_SIGS = {"pyrit_code_stripes_noalloc": (_i, [ctypes.POINTER(pyrit_stripe_t), _i, _vp]),
+                 "pyrit_noalloc_status": (_i, [_vp, _vp, _vp]),
+                 "pyrit_selftest_bounded_wait": (_i, [_i, _u64, _vp])}
 _bind(_NOALLOC_SIGS)
 EXPORTS = EXPORTS + tuple(_NOALLOC_SIGS)
 
@@ -449,6 +464,22 @@ def pyrit_code_stripes_noalloc(stripes, stream=None):
         keep.append(ba)
         arr[i] = pyrit_stripe_t(plan, op, er, P, ctypes.cast(ba, ctypes.POINTER(ctypes.c_void_p)))
     return _check(_lib.pyrit_code_stripes_noalloc(arr, len(stripes), _stream(stream)), "pyrit_code_stripes_noalloc")
+
+
+def pyrit_noalloc_status(stream=None):
+    """(code, site) of the no-allocation entry point's status words, read and cleared after the
+    work queued on `stream`."""
+    code, where = ctypes.c_int(), ctypes.c_int()
+    _check(_lib.pyrit_noalloc_status(ctypes.byref(code), ctypes.byref(where), _stream(stream)),
+           "pyrit_noalloc_status")
+    return code.value, where.value
+
+
+def pyrit_selftest_bounded_wait(channel, limit_ns, stream=None):
+    """Enqueues a bounded wait that runs out after limit_ns and records PYRIT_E_TIMEOUT in the
+    library's error word (channel 0) or the no-allocation status words (channel 1)."""
+    return _check(_lib.pyrit_selftest_bounded_wait(channel, limit_ns, _stream(stream)),
+                  "pyrit_selftest_bounded_wait")
 
 
 # ---- served coding -----------------------------------------------------------------------------

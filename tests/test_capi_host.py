@@ -104,6 +104,25 @@ def test_default_generator_and_encode_masks(w, k, m):
         pyrit.pyrit_plan_destroy(plan)
 
 
+@pytest.mark.parametrize("w,k,m", [(10, 10, 4), (12, 16, 4)])
+def test_plan_with_16_bit_generator(w, k, m):
+    # pyrit_plan takes the generator as 16-bit entries: the oracle's Cauchy matrix given that way,
+    # and the default (NULL), make the same plan as pyrit_plan_create; a non-systematic G is refused.
+    n = oracle.ring_size(w)
+    G = oracle.cauchy(w, k, m)
+    for g in (G.astype(np.uint16), None):
+        plan = pyrit.pyrit_plan(w, n, k, m, g)
+        try:
+            assert np.array_equal(pyrit.pyrit_plan_generator(plan), G)
+        finally:
+            pyrit.pyrit_plan_destroy(plan)
+    bad = G.astype(np.uint16)
+    bad[0, 1] = 1
+    with pytest.raises(pyrit.PyritError) as ei:
+        pyrit.pyrit_plan(w, n, k, m, bad)
+    assert ei.value.status == pyrit.PYRIT_E_NOT_MDS
+
+
 def _oracle_decode_matrix(w, k, m, G, erasures):
     surv = [e for e in range(k + m) if not (erasures >> e) & 1][:k]
     erased = [e for e in range(k + m) if (erasures >> e) & 1]

@@ -102,3 +102,52 @@ def test_noalloc_rejects_more_than_its_scratch(pyrit):
     finally:
         pyrit.pyrit_plan_destroy(plan)
         del buf
+
+
+def test_noalloc_second_call_allocates_nothing(pyrit):
+    # After a warm-up call (which loads the kernels it uses), an identical call must leave the
+    # device's free memory unchanged and load no generated network: nothing was allocated.
+    codes = [(10, 10, 4), (12, 16, 4)]
+    plans = {c: pyrit.pyrit_plan_create(c[0], c[0] + 1, c[1], c[2]) for c in codes}
+    try:
+        specs = [(10, 10, 4, 8192, pyrit.PYRIT_OP_ENCODE, 0), (12, 16, 4, 4096, pyrit.PYRIT_OP_DECODE, 0b1011),
+                 (10, 10, 4, 1000, pyrit.PYRIT_OP_ENCODE, 0)]
+        offs, total = _layout(specs)
+        buf = torch.empty(total, dtype=torch.uint8, device="cuda")
+        pyrit.pyrit_synth_fill(buf.data_ptr(), total, 0xC33E)
+        stripes = _stripes(pyrit, plans, specs, buf.data_ptr(), offs)
+        pyrit.pyrit_code_stripes_noalloc(stripes)
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        loaded0 = pyrit.pyrit_jit_stats()["loaded"]
+        pyrit.pyrit_code_stripes_noalloc(stripes)
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
+        assert pyrit.pyrit_jit_stats()["loaded"] == loaded0
+        assert pyrit.pyrit_noalloc_status() == (0, 0)
+    finally:
+        for p in plans.values():
+            pyrit.pyrit_plan_destroy(p)
+
+
+def test_noalloc_status_reports_a_wait_that_ran_out(pyrit):
+    # A bounded wait that runs out (2 ms, on a barrier nothing completes) must come back through
+    # pyrit_noalloc_status for the no-allocation scratch and through pyrit_device_status for the
+    # library's error word, once, and leave the context usable.
+    pyrit.pyrit_selftest_bounded_wait(1, 2_000_000)
+    assert pyrit.pyrit_noalloc_status() == (pyrit.PYRIT_E_TIMEOUT, 100)
+    assert pyrit.pyrit_noalloc_status() == (0, 0)  # read and cleared
+    pyrit.pyrit_selftest_bounded_wait(0, 2_000_000)
+    assert pyrit.pyrit_device_status() == (pyrit.PYRIT_E_TIMEOUT, 100)
+    assert pyrit.pyrit_device_status() == (0, 0)
+    with pytest.raises(pyrit.PyritError):
+        pyrit.pyrit_selftest_bounded_wait(2, 1000)
+    # the context still codes
+    plans = {(4, 4, 2): pyrit.pyrit_plan_create(4, 5, 4, 2)}
+    try:
+        ref, got = _run_both(pyrit, plans, [(4, 4, 2, 4096, pyrit.PYRIT_OP_ENCODE, 0)], 0xD44E)
+        assert torch.equal(ref, got)
+        assert pyrit.pyrit_noalloc_status() == (0, 0)
+    finally:
+        for p in plans.values():
+            pyrit.pyrit_plan_destroy(p)
