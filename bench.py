@@ -14,6 +14,13 @@ blocks (rebuilt in place), each as one persistent batched launch replayed from a
            ((k+m)wP per encoded stripe, (k+e)wP per decoded stripe with e erasures) per launch over
            its event-timed duration, against the measured HBM copy bandwidth; the headline object
            is the kernel with the larger share of the step.
+  served   (sub-object) a 2.5 s Poisson window at 20k requests/s of GF(2^12) k=16 m=4 requests
+           (packets 4 KiB-1 MiB, half 4-erasure decodes): p50/p99/p99.9 latency and sustained GB/s
+           with continuous batching, and the same arrivals served one request per launch.
+  mixed    (sub-object) 4096 uneven stripes in one batched launch per ring size against 4096
+           per-stripe launches of the same kernel: GB/s, roofline fraction, speed-up.
+  sweep32k (sub-object) the 32 KiB point of the GF(2^12) k=16 m=4 packet-size sweep (~8 GiB of
+           source): encode and 4-erasure decode roofline fractions.
 
 `--impl reference` times the CPU oracle (the plain log/antilog coder) on a bounded sample of the
 same workload. Multi-GPU (torchrun): every rank codes its own 256 stripes (weak scaling, no
@@ -204,6 +211,8 @@ def run_reference(args):
     data = [synth_bytes(BASE_SEED + 1, s * K * blk, K * blk).reshape(K, W, P) for s in range(sample)]
 
     o_enc, o_dec = oracle_codec(args.transform)
+    CONFIG["generator"] = "plain Cauchy" if args.generator == "cauchy" else "weight-optimised generalized Cauchy"
+    CONFIG["transform"] = "phi_E (embedding)" if args.transform == "embedding" else "phi_P (parity bit)"
 
     def step():
         for s in range(sample):
@@ -256,6 +265,8 @@ def main():
                          "parity-bit transform (Sec. 2.3.1), a different code of the same parameters")
     ap.add_argument("--no-tune", action="store_true",
                     help="skip the autotuner: time the automatic shapes (profiling cases of a fixed kernel)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default line without its served / mixed / sweep32k sub-objects (profiling runs)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -386,6 +397,13 @@ def main():
     cdec = [pyrit.pyrit_batch_create([(plan, 1, pats[s], P, blocks[s]) for s in range(c * per, (c + 1) * per)])
             for c in range(CH)]
     streams = [torch.cuda.Stream(device=dev) for _ in range(4)]
+    # The blocks each decode rebuilt (its erased ones), read back to pinned memory every step.
+    lost = [(s, e) for s in range(STRIPES) for e in range(K + M) if (pats[s] >> e) & 1]
+    host_rebuilt = torch.empty(len(lost) * blk, dtype=torch.uint8, pin_memory=True)
+    dev_block = lambda s, e: buf[s * K * blk + e * blk:s * K * blk + (e + 1) * blk] if e < K else \
+        buf[par0 + (s * M + e - K) * blk:par0 + (s * M + e - K + 1) * blk]
+    rebuilt_of_chunk = [[(i, dev_block(s, e)) for i, (s, e) in enumerate(lost) if c * per <= s < (c + 1) * per]
+                        for c in range(CH)]
 
     def e2e_step():
         for c in range(CH):
@@ -397,6 +415,8 @@ def main():
                 pyrit.pyrit_batch_run(cenc[c], st, graph=True)
                 pyrit.pyrit_batch_run(cdec[c], st, graph=True)
                 host_par[p0:p1].copy_(buf[par0 + p0:par0 + p1], non_blocking=True)
+                for i, src in rebuilt_of_chunk[c]:
+                    host_rebuilt[i * blk:(i + 1) * blk].copy_(src, non_blocking=True)
 
     def e2e_timed(steps):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -419,15 +439,20 @@ def main():
     nvtx.range_pop()
     e2e_ms = max_over_ranks(e2e_ms, world, dist, dev)
     e2e_val = whole_job_gbs(world, src_per_step, e2e_ms / args.steps)
-    # every parity read back must equal the device-resident result
+    # every parity block and rebuilt block read back must equal the device-resident result
     e2e_ok = bool(torch.equal(buf[par0:].cpu(), host_par))
+    e2e_rebuilt_ok = all(bool(torch.equal(host_rebuilt[i * blk:(i + 1) * blk], dev_block(s, e).cpu()))
+                         for i, (s, e) in enumerate(lost[:64]))
 
     out = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u8", "data": "synthetic (seeded SplitMix64 bytes)", "config": CONFIG,
         "e2e": {"value": e2e_val, "unit": "GB/s", "h2d_bytes_per_step": STRIPES * K * blk,
-                "d2h_bytes_per_step": STRIPES * M * blk, "parity_readback_matches": e2e_ok},
+                "d2h_bytes_per_step": STRIPES * M * blk + len(lost) * blk, "parity_readback_matches": e2e_ok,
+                "rebuilt_readback_matches": e2e_rebuilt_ok,
+                "what": "per step: the data blocks uploaded from pinned host memory, encode, decode, the parity "
+                        "blocks and every rebuilt (erased) block read back to pinned host memory"},
         "gpu_launches": launches_per_step * args.steps,
         "roofline": {"bound": "hbm", "achieved": dominant["achieved"], "peak": peak, "unit": "GB/s",
                      "frac": dominant["frac"], "traffic": dominant["traffic"],
@@ -441,10 +466,21 @@ def main():
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(buf, blocks, pats, plan, pyrit, args.generator, args.transform)
-    if rank == 0:
-        print(json.dumps(out))
     for b in [enc, dec] + cenc + cdec:
         pyrit.pyrit_batch_destroy(b)
+    del buf, host, host_par, host_rebuilt
+    torch.cuda.empty_cache()
+    if world == 1 and not args.no_extras:
+        # The other configurations, compact: the served loop (a short Poisson window, both server
+        # policies), the 4096-stripe mixed batch against per-stripe launches, and the 32 KiB point of
+        # the GF(2^12) sweep.
+        out["served"] = served_measure(torch, pyrit, dev, 20000.0, 2.5, args.slots)
+        out["mixed"] = mixed_measure(torch, pyrit, dev, 5)
+        plan12 = make_plan(pyrit, args.generator, 12, 16, 4)
+        out["sweep32k"] = sweep_point(torch, pyrit, dev, plan12, 32768, 5, generator=args.generator)
+        pyrit.pyrit_plan_destroy(plan12)
+    if rank == 0:
+        print(json.dumps(out))
     pyrit.pyrit_plan_destroy(plan)
     if world > 1:
         dist.destroy_process_group()
@@ -509,55 +545,77 @@ def _time_batch(torch, pyrit, batch, stream, steps):
     return a.elapsed_time(b) / steps
 
 
-def run_sweep(args):
-    """GF(2^12) (n=13), Cauchy k=16 m=4: packet sizes 4 KiB..1 MiB, stripes filling ~8 GiB of
-    source data; encode and 4-erasure decode per point, batched and autotuned."""
-    torch, pyrit, dev = _setup_gpu()
+def sweep_point(torch, pyrit, dev, plan, P, steps, tune=True, stripes=0, generator="cauchy"):
+    """One point of the GF(2^12) (n=13) Cauchy k=16 m=4 packet-size sweep: stripes filling ~8 GiB of
+    source at packet size P (or `stripes` of them), an encode batch and a 4-erasure decode batch,
+    tuned and timed (graph replay). A sampled stripe is checked against the oracle."""
     from paper_1709_00178_gb300.synth import BASE_SEED
     import numpy as np
     w, k, m = 12, 16, 4
     peak, _ = peak_hbm()
-    plan = make_plan(pyrit, args.generator, w, k, m)
+    e = P.bit_length() - 1
+    S = stripes if stripes else (8 << 30) // (k * w * P)
+    blk = w * P
+    buf = torch.empty(S * (k + m) * blk, dtype=torch.uint8, device=dev)
+    pyrit.pyrit_synth_fill(buf.data_ptr(), buf.numel(), BASE_SEED + 2, 0)
+    torch.cuda.synchronize()
+    base, par0 = buf.data_ptr(), S * k * blk
+    blocks = [[base + (s * k + j) * blk for j in range(k)] + [base + par0 + (s * m + i) * blk for i in range(m)]
+              for s in range(S)]
+    rng = np.random.default_rng(BASE_SEED + 2 + e)
+    pats = [sum(1 << int(x) for x in rng.choice(k + m, m, replace=False)) for _ in range(S)]
+    enc = pyrit.pyrit_batch_create([(plan, 0, 0, P, blocks[s]) for s in range(S)])
+    dec = pyrit.pyrit_batch_create([(plan, 1, pats[s], P, blocks[s]) for s in range(S)])
     stream = torch.cuda.Stream(device=dev)
+    if tune:
+        pyrit.pyrit_batch_tune(enc, stream, 2)
+        pyrit.pyrit_batch_tune(dec, stream, 2)
     nvtx = torch.cuda.nvtx
+    nvtx.range_push("timed")
+    te = _time_batch(torch, pyrit, enc, stream, steps)
+    td = _time_batch(torch, pyrit, dec, stream, steps)
+    nvtx.range_pop()
+    torch.cuda.synchronize()
+    # the last runs encoded every stripe and then decoded it in place: stripe 0 is the oracle's codeword
+    import oracle
+    G = oracle.cauchy_weighted(w, k, m)[0] if generator == "weighted" else oracle.cauchy(w, k, m)
+    cw = min(P, 4096)
+    data0 = np.ascontiguousarray(buf[:k * blk].cpu().numpy().reshape(k, w, P)[:, :, :cw])
+    par_got = buf[par0:par0 + m * blk].cpu().numpy().reshape(m, w, P)[:, :, :cw]
+    ok = bool(np.array_equal(par_got, oracle.encode(w, k, m, G, data0, nthreads=os.cpu_count() or 1)))
+    es, ds = pyrit.pyrit_batch_stats(enc), pyrit.pyrit_batch_stats(dec)
+    ae, ad = es["alg_bytes"] / te / 1e6, ds["alg_bytes"] / td / 1e6
+    out = {"workload": "GF(2^12) n=13 Cauchy k=16 m=4, %d KiB packets, %d stripes, 4-erasure decode" % (P // 1024, S),
+           "packet_bytes": P, "stripes": S,
+           "value": (es["src_bytes"] + ds["src_bytes"]) / (te + td) / 1e6, "unit": "GB/s",
+           "encode_ms": te, "decode_ms": td, "encode_roofline_frac": ae / peak, "decode_roofline_frac": ad / peak,
+           "encode_alg_gbs": ae, "decode_alg_gbs": ad,
+           "encode_kernel": kernel_name(pyrit.pyrit_batch_shape(enc, 0)),
+           "decode_kernel": kernel_name(pyrit.pyrit_batch_shape(dec, 0)), "oracle_parity_stripe0": ok}
+    pyrit.pyrit_batch_destroy(enc)
+    pyrit.pyrit_batch_destroy(dec)
+    del buf
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_sweep(args):
+    """GF(2^12) (n=13), Cauchy k=16 m=4: packet sizes 4 KiB..1 MiB, stripes filling ~8 GiB of
+    source data; encode and 4-erasure decode per point, batched and autotuned (sweep_point)."""
+    torch, pyrit, dev = _setup_gpu()
+    plan = make_plan(pyrit, args.generator, 12, 16, 4)
     for e in range(12, 21):
         P = 1 << e
         if args.packet and P != args.packet:
             continue
-        S = (8 << 30) // (k * w * P)
-        if args.packet and args.stripes != STRIPES:
-            S = max(1, args.stripes)
-        blk = w * P
-        buf = torch.empty(S * (k + m) * blk, dtype=torch.uint8, device=dev)
-        pyrit.pyrit_synth_fill(buf.data_ptr(), buf.numel(), BASE_SEED + 2, 0)
-        torch.cuda.synchronize()
-        base, par0 = buf.data_ptr(), S * k * blk
-        blocks = [[base + (s * k + j) * blk for j in range(k)] + [base + par0 + (s * m + i) * blk for i in range(m)]
-                  for s in range(S)]
-        rng = np.random.default_rng(BASE_SEED + 2 + e)
-        pats = [sum(1 << int(x) for x in rng.choice(k + m, m, replace=False)) for _ in range(S)]
-        enc = pyrit.pyrit_batch_create([(plan, 0, 0, P, blocks[s]) for s in range(S)])
-        dec = pyrit.pyrit_batch_create([(plan, 1, pats[s], P, blocks[s]) for s in range(S)])
-        if not args.no_tune:
-            pyrit.pyrit_batch_tune(enc, stream, 2)
-            pyrit.pyrit_batch_tune(dec, stream, 2)
-        nvtx.range_push("timed")
-        te = _time_batch(torch, pyrit, enc, stream, args.steps)
-        td = _time_batch(torch, pyrit, dec, stream, args.steps)
-        nvtx.range_pop()
-        es, ds = pyrit.pyrit_batch_stats(enc), pyrit.pyrit_batch_stats(dec)
-        ae, ad = es["alg_bytes"] / te / 1e6, ds["alg_bytes"] / td / 1e6
-        print(json.dumps({
-            "metric": "encode+decode GB/s of source data", "workload": "sweep",
-            "value": (es["src_bytes"] + ds["src_bytes"]) / (te + td) / 1e6, "unit": "GB/s",
-            "config": {"workload": "GF(2^12) n=13 Cauchy k=16 m=4, 4-erasure decode", "packet_bytes": P, "stripes": S,
-                       "generator": args.generator},
-            "encode_ms": te, "decode_ms": td, "encode_roofline_frac": ae / peak, "decode_roofline_frac": ad / peak,
-            "encode_alg_gbs": ae, "decode_alg_gbs": ad, "dtype": "u8", "data": "synthetic"}), flush=True)
-        pyrit.pyrit_batch_destroy(enc)
-        pyrit.pyrit_batch_destroy(dec)
-        del buf
-        torch.cuda.empty_cache()
+        S = max(1, args.stripes) if (args.packet and args.stripes != STRIPES) else 0
+        r = sweep_point(torch, pyrit, dev, plan, P, args.steps, tune=not args.no_tune, stripes=S,
+                        generator=args.generator)
+        out = {"metric": "encode+decode GB/s of source data", "workload": "sweep", "value": r.pop("value"),
+               "unit": r.pop("unit"), "config": {"workload": r.pop("workload"), "packet_bytes": P, "stripes": r["stripes"],
+                                                 "generator": args.generator}, "dtype": "u8", "data": "synthetic"}
+        out.update(r)
+        print(json.dumps(out), flush=True)
     pyrit.pyrit_plan_destroy(plan)
 
 
@@ -803,37 +861,16 @@ def run_gf16(args):
     pyrit.pyrit_plan_destroy(plan)
 
 
-def run_mixed(args):
-    """4096 uneven stripes: ring n uniform in {5, 11, 13}, k in 4..32, m in 2..8 (redrawn until
-    k+m <= 2^w), P log-uniform 512 B..256 KiB (multiple of 16), half encode, half decode with 1..m
-    erasures. The batched persistent launch (autotuned) against 4096 per-stripe launches of the
-    same kernel; both must write the same bytes. The stripes' mask tables differ, so both arms run
-    the generic kernels (run-time compiled networks are switched off for the comparison)."""
-    torch, pyrit, dev = _setup_gpu()
-    pyrit.pyrit_jit_mode(pyrit.PYRIT_JIT_OFF)
-    from paper_1709_00178_gb300.synth import BASE_SEED
+def mixed_measure(torch, pyrit, dev, steps, tune=True, per_stripe_reps=3, oracle_sample=6):
+    """4096 uneven stripes (the mixed-batch workload of synth.mixed_batch_specs) coded by one
+    batched persistent launch per ring size (default compilation policy, autotuned, replayed from
+    a CUDA graph) against 4096 per-stripe launches of the same generic kernel (run-time compilation
+    off for that arm only). Both must write the same bytes, and a seeded sample of stripes is
+    compared with the oracle. Returns the measurement as a dict."""
+    from paper_1709_00178_gb300.synth import BASE_SEED, mixed_batch_specs, stripe_offsets
     import numpy as np
-    rng = np.random.default_rng(BASE_SEED + 3)
-    S = 4096
-    specs = []
-    for _ in range(S):
-        n = int(rng.choice([5, 11, 13]))
-        w = n - 1
-        while True:
-            k, m = int(rng.integers(4, 33)), int(rng.integers(2, 9))
-            if k + m <= (1 << w):
-                break
-        P = max(16, int(2 ** rng.uniform(9, 18)) // 16 * 16)
-        op = int(rng.integers(0, 2))
-        er = 0
-        if op:
-            e = int(rng.integers(1, m + 1))
-            er = sum(1 << int(x) for x in rng.choice(k + m, e, replace=False))
-        specs.append((w, k, m, P, op, er))
-    offs, total = [], 0
-    for (w, k, m, P, op, er) in specs:
-        offs.append(total)
-        total += ((k + m) * w * P + 255) // 256 * 256
+    specs = mixed_batch_specs(BASE_SEED + 3, 4096)
+    offs, total = stripe_offsets(specs)
     buf = torch.empty(total, dtype=torch.uint8, device=dev)
     pyrit.pyrit_synth_fill(buf.data_ptr(), total, BASE_SEED + 3, 0)
     torch.cuda.synchronize()
@@ -847,10 +884,16 @@ def run_mixed(args):
     stream = torch.cuda.Stream(device=dev)
     batch = pyrit.pyrit_batch_create(stripes)
     st = pyrit.pyrit_batch_stats(batch)
-    pyrit.pyrit_batch_tune(batch, stream, 2)
-    t_batch = _time_batch(torch, pyrit, batch, stream, args.steps)
+    if tune:
+        pyrit.pyrit_batch_tune(batch, stream, 2)
+    t_batch = _time_batch(torch, pyrit, batch, stream, steps)
+    shapes = []
+    for g in range(st["launches"]):
+        try:
+            shapes.append(kernel_name(pyrit.pyrit_batch_shape(batch, g)))
+        except Exception:
+            break
     after_batch = buf.clone()
-
     ks = [spec[1] for spec in specs]
 
     def per_stripe():
@@ -860,42 +903,71 @@ def run_mixed(args):
             else:
                 pyrit.pyrit_decode(plan, blocks, er, P, stream)
 
-    per_stripe()
-    torch.cuda.synchronize()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    reps = max(1, min(5, args.steps))
-    a.record(stream)
-    for _ in range(reps):
+    mode = pyrit.pyrit_jit_mode(pyrit.PYRIT_JIT_OFF)
+    try:
         per_stripe()
-    b.record(stream)
-    torch.cuda.synchronize()
-    t_per = a.elapsed_time(b) / reps
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(per_stripe_reps):
+            per_stripe()
+        b.record(stream)
+        torch.cuda.synchronize()
+    finally:
+        pyrit.pyrit_jit_mode(mode)
+    t_per = a.elapsed_time(b) / per_stripe_reps
     same = bool(torch.equal(after_batch, buf))
+    del after_batch
+    oracle_ok = None
+    if oracle_sample:
+        import oracle
+        rng = np.random.default_rng(BASE_SEED + 33)
+        small = [i for i, sp in enumerate(specs) if sp[3] <= 16384]
+        ok = True
+        for i in rng.choice(small, oracle_sample, replace=False):
+            w, k, m, P, op, er = specs[i]
+            h = buf[offs[i]:offs[i] + (k + m) * w * P].cpu().numpy().reshape(k + m, w, P)
+            G = oracle.cauchy(w, k, m)
+            if op == 0:
+                ok = ok and np.array_equal(h[k:], oracle.encode(w, k, m, G, h[:k], nthreads=os.cpu_count() or 1))
+            else:
+                ok = ok and np.array_equal(h, oracle.decode(w, k, m, G, h, er, nthreads=os.cpu_count() or 1))
+        oracle_ok = bool(ok)
     peak, _ = peak_hbm()
-    print(json.dumps({
-        "metric": "encode+decode GB/s of source data", "workload": "mixed", "unit": "GB/s",
-        "value": st["src_bytes"] / t_batch / 1e6,
-        "config": {"workload": "4096 uneven stripes, n in {5,11,13}, k 4-32, m 2-8, P 512 B-256 KiB, half decode",
-                   "stripes": S, "alg_bytes": st["alg_bytes"], "launches": st["launches"], "tiles": st["tiles"]},
-        "batched_ms": t_batch, "per_stripe_ms": t_per, "speedup_vs_per_stripe": t_per / t_batch,
-        "batched_roofline_frac": st["alg_bytes"] / t_batch / 1e6 / peak, "same_bytes": same,
-        "dtype": "u8", "data": "synthetic"}), flush=True)
+    out = {"workload": "4096 uneven stripes, n in {5,11,13}, k 4-32, m 2-8, P 512 B-256 KiB, half decode",
+           "value": st["src_bytes"] / t_batch / 1e6, "unit": "GB/s", "stripes": len(specs),
+           "alg_bytes": st["alg_bytes"], "src_bytes": st["src_bytes"], "launches": st["launches"], "tiles": st["tiles"],
+           "kernels": shapes, "batched_ms": t_batch, "per_stripe_ms": t_per, "speedup_vs_per_stripe": t_per / t_batch,
+           "roofline_frac": st["alg_bytes"] / t_batch / 1e6 / peak, "same_bytes_as_per_stripe": same,
+           "oracle_sample_ok": oracle_ok, "oracle_sample": oracle_sample}
     pyrit.pyrit_batch_destroy(batch)
     for p in plans.values():
         pyrit.pyrit_plan_destroy(p)
+    del buf
+    torch.cuda.empty_cache()
+    return out
 
 
-def run_served(args):
-    """Poisson arrivals (seeded, 20 000 requests/s) of GF(2^12) k=16 m=4 requests, P one of
-    4 KiB..1 MiB (powers of two, uniform), half encode and half 4-erasure decode, served with
-    continuous batching under a 16 GiB budget; payloads pre-generated in device memory."""
+def run_mixed(args):
+    """The mixed-batch workload as its own JSON line (mixed_measure)."""
     torch, pyrit, dev = _setup_gpu()
+    r = mixed_measure(torch, pyrit, dev, args.steps, tune=not args.no_tune, per_stripe_reps=max(1, min(5, args.steps)))
+    out = {"metric": "encode+decode GB/s of source data", "workload": "mixed", "unit": "GB/s", "value": r.pop("value"),
+           "config": {"workload": r.pop("workload"), "stripes": r["stripes"]}, "dtype": "u8", "data": "synthetic"}
+    out.update(r)
+    print(json.dumps(out), flush=True)
+
+
+def served_measure(torch, pyrit, dev, rate, seconds, slots, pool=512):
+    """Poisson arrivals (seeded, `rate` requests/s for `seconds`) of GF(2^12) k=16 m=4 requests, P
+    one of 4 KiB..1 MiB (powers of two, uniform), half encode and half 4-erasure decode, served with
+    continuous batching under a 16 GiB budget; payloads pre-generated in device memory. Then the same
+    arrivals through the same server with one request per launch. Returns the measurement."""
     from paper_1709_00178_gb300.synth import BASE_SEED
     import numpy as np
     w, k, m = 12, 16, 4
-    rate = args.rate
     rng = np.random.default_rng(BASE_SEED + 4)
-    POOL = 512
+    POOL = pool
     pool_P = [1 << int(e) for e in rng.integers(12, 21, POOL)]
     pool_pat = [sum(1 << int(x) for x in rng.choice(k + m, m, replace=False)) for _ in range(POOL)]
     offs, total = [], 0
@@ -913,7 +985,7 @@ def run_served(args):
     pyrit.pyrit_plan_specialise(plan, pyrit.PYRIT_OP_ENCODE)
     pyrit.pyrit_plan_specialise(plan, pyrit.PYRIT_OP_DECODE_ANY)
     base = buf.data_ptr()
-    nreq = int(rate * args.seconds)
+    nreq = int(rate * seconds)
     gaps = rng.exponential(1e9 / rate, nreq)
     arrivals = np.cumsum(gaps).astype(np.int64)
     ops = rng.integers(0, 2, nreq)
@@ -925,7 +997,6 @@ def run_served(args):
         reqs.append((plan, int(ops[i]), pool_pat[s] if ops[i] else 0, P, blocks, i, 0))
         src_bytes += k * w * P
     arr, keep = pyrit.pyrit_requests_array(reqs)
-
     def serve(max_batch, slots):
         """One pass of the arrival stream through a server; latency and throughput statistics."""
         srv = pyrit.pyrit_server_create(16 << 30, max_batch=max_batch, slots=slots)
@@ -978,26 +1049,39 @@ def run_served(args):
                 "batches": st["batches"], "launches": st["launches"], "max_inflight_bytes": st["max_inflight"],
                 "clocks": clk}
 
-    # Continuous batching (up to 64 admitted requests per launch group, 16 stream slots whose
+    # Continuous batching (up to 64 admitted requests per launch group, `slots` stream slots whose
     # launches overlap: a request that finds a slot free starts alone, requests that arrive while
     # every slot is busy share the next free one), then the same arrivals through the same server
     # and kernels with one request per launch: per-stripe launches as requests arrive, up to 16 in
     # flight on their own streams.
-    batched = serve(64, args.slots)
+    batched = serve(64, slots)
     single = serve(1, 16)
     clk = batched.pop("clocks")
     single.pop("clocks")
-    out = {"metric": "served p50/p99 latency", "workload": "served", "unit": "us", "value": batched["p99_us"]}
-    out.update(batched)
+    out = dict(batched)
     out.update({
         "offered_gbs": src_bytes / (arrivals[-1] * 1e-9) / 1e9,
         "per_request_launches": single,
-        "config": {"workload": "Poisson %gk req/s, GF(2^12) k=16 m=4, P 4 KiB-1 MiB, half 4-erasure decode, "
-                               "16 GiB budget, %d stream slots, batches up to 64; per_request_launches: the same "
-                               "arrivals one request per launch, 16 stream slots" % (rate / 1000, args.slots), "seconds": args.seconds},
-        "clocks": clk, "higher_is_better": False, "dtype": "u8", "data": "synthetic"})
-    print(json.dumps(out), flush=True)
+        "workload": "Poisson %gk req/s for %g s, GF(2^12) k=16 m=4, P 4 KiB-1 MiB, half 4-erasure decode, 16 GiB "
+                    "budget, %d stream slots, batches up to 64; per_request_launches: the same arrivals one request "
+                    "per launch, 16 stream slots" % (rate / 1000, seconds, slots),
+        "clocks": clk})
     pyrit.pyrit_plan_destroy(plan)
+    del buf, arr, keep
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_served(args):
+    """The served workload as its own JSON line (served_measure)."""
+    torch, pyrit, dev = _setup_gpu()
+    r = served_measure(torch, pyrit, dev, args.rate, args.seconds, args.slots)
+    out = {"metric": "served p50/p99 latency", "workload": "served", "unit": "us", "value": r["p99_us"]}
+    out.update(r)
+    out.update({"config": {"workload": r.pop("workload"), "seconds": args.seconds},
+                "higher_is_better": False, "dtype": "u8", "data": "synthetic"})
+    out.pop("workload", None)
+    print(json.dumps(out), flush=True)
 
 
 if __name__ == "__main__":

@@ -49,3 +49,40 @@ def stripe_layout(k: int, m: int, w: int, P: int):
     a stripe is k+m blocks, a block is w packets of P bytes (packet q at q*P)."""
     block = w * P
     return block, (k + m) * block
+
+
+def mixed_batch_specs(seed: int, count: int = 4096):
+    """The mixed-batch workload: ``count`` stripes (w, k, m, P, op, erasures) drawn with numpy's
+    PCG64 generator from ``seed``. Per stripe: the ring n uniform in {5, 11, 13} (w = n - 1); k in
+    4..32 and m in 2..8, both drawn again until k + m <= 2^w (the Cauchy code needs distinct
+    points); P log-uniform over [512 B, 256 KiB], rounded down to a multiple of 16; encode or decode
+    with equal odds, a decode losing e blocks, e uniform in 1..m, chosen uniformly among the k + m.
+    Random draws only: no coding arithmetic."""
+    rng = np.random.default_rng(seed)
+    specs = []
+    for _ in range(count):
+        n = int(rng.choice([5, 11, 13]))
+        w = n - 1
+        while True:
+            k, m = int(rng.integers(4, 33)), int(rng.integers(2, 9))
+            if k + m <= (1 << w):
+                break
+        P = max(16, int(2 ** rng.uniform(9, 18)) // 16 * 16)
+        op = int(rng.integers(0, 2))
+        er = 0
+        if op:
+            e = int(rng.integers(1, m + 1))
+            er = sum(1 << int(x) for x in rng.choice(k + m, e, replace=False))
+        specs.append((w, k, m, P, op, er))
+    return specs
+
+
+def stripe_offsets(specs, align: int = 256):
+    """Byte offsets of stripes (w, k, m, P, ...) laid out one after another in one buffer, each
+    starting on an ``align``-byte boundary; returns (offsets, total bytes)."""
+    offs, total = [], 0
+    for s in specs:
+        w, k, m, P = s[:4]
+        offs.append(total)
+        total += ((k + m) * w * P + align - 1) // align * align
+    return offs, total

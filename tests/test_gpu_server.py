@@ -49,12 +49,34 @@ def _layout(reqs):
     return offs, total
 
 
+def _codewords(reqs, offs, total, seed):
+    """Host image of the request stripes: every stripe a codeword of its code (random data, parity
+    from the oracle). Returns (image with the outputs of each request overwritten by junk, the
+    expected image)."""
+    want = np.zeros(total, np.uint8)
+    for i, (w, k, m, P, op, er) in enumerate(reqs):
+        data = synth_bytes(seed, offs[i], k * w * P).reshape(k, w, P)
+        par = oracle.encode(w, k, m, oracle.cauchy(w, k, m), data, nthreads=NCPU)
+        want[offs[i]:offs[i] + (k + m) * w * P] = np.concatenate([data, par]).reshape(-1)
+    start = want.copy()
+    for i, (w, k, m, P, op, er) in enumerate(reqs):
+        blk = w * P
+        lost = range(k, k + m) if op == 0 else [e for e in range(k + m) if (er >> e) & 1]
+        for e in lost:
+            start[offs[i] + e * blk:offs[i] + (e + 1) * blk] = 0xE7
+    return start, want
+
+
 def test_alone_equals_mix(pyrit):
+    """Every request of a mix of codes, packet sizes and operations is coded once alone (submitted
+    to a server, drained, then the next) and once in a mix (bursts submitted while earlier batches
+    run); the two must write the same bytes, and each must equal the oracle's codeword: encodes
+    write the oracle's parity, decodes rebuild the oracle's lost blocks."""
     reqs = _requests(3, 40)
     offs, total = _layout(reqs)
     plans = {c: pyrit.pyrit_plan_create(c[0], c[0] + 1, c[1], c[2]) for c in CODES}
-    init = torch.empty(total, dtype=torch.uint8, device="cuda")
-    pyrit.pyrit_synth_fill(init.data_ptr(), total, 77)
+    start, want = _codewords(reqs, offs, total, 77)
+    init = torch.from_numpy(start).cuda()
     torch.cuda.synchronize()
 
     def stripes(buf):
@@ -64,11 +86,19 @@ def test_alone_equals_mix(pyrit):
 
     try:
         alone = init.clone()
-        for st in stripes(alone):  # each request coded by itself, one after the other
-            b = pyrit.pyrit_batch_create([st])
-            pyrit.pyrit_batch_run(b)
-            torch.cuda.synchronize()
-            pyrit.pyrit_batch_destroy(b)
+        torch.cuda.synchronize()
+        srv = pyrit.pyrit_server_create(64 << 30, max_batch=16, slots=4)
+        try:
+            for i, s in enumerate(stripes(alone)):  # one request in the server at a time
+                pyrit.pyrit_server_submit(srv, [s + (i, 0)])
+                assert pyrit.pyrit_server_drain(srv, 20000) == 0
+            done_alone = pyrit.pyrit_server_poll(srv)
+            st_alone = pyrit.pyrit_server_stats(srv)
+        finally:
+            pyrit.pyrit_server_destroy(srv)
+        assert sorted(d[0] for d in done_alone) == list(range(len(reqs)))
+        assert all(d[1] == 0 for d in done_alone)
+        assert st_alone["batches"] == len(reqs)  # each alone in its batch
         mix = init.clone()
         torch.cuda.synchronize()
         srv = pyrit.pyrit_server_create(64 << 30, max_batch=16, slots=4)
@@ -86,18 +116,66 @@ def test_alone_equals_mix(pyrit):
         assert all(d[1] == 0 for d in done)
         assert all(d[2] <= d[4] and d[3] <= d[4] for d in done)
         assert st["batches"] >= 2, st  # the requests were spread over several overlapping batches
+        assert st["batches"] < len(reqs), st  # and some batches held more than one request
         assert torch.equal(alone, mix)
-        # and the encoded parity of a few stripes is the oracle's
         h = mix.cpu().numpy()
         for i, (w, k, m, P, op, er) in enumerate(reqs):
-            if op != 0 or i > 12:
-                continue
-            stripe = h[offs[i]:offs[i] + (k + m) * w * P].reshape(k + m, w, P)
-            G = oracle.cauchy(w, k, m)
-            assert np.array_equal(stripe[k:], oracle.encode(w, k, m, G, stripe[:k], nthreads=NCPU)), i
+            n = (k + m) * w * P
+            assert np.array_equal(h[offs[i]:offs[i] + n], want[offs[i]:offs[i] + n]), (i, reqs[i])
     finally:
         for p in plans.values():
             pyrit.pyrit_plan_destroy(p)
+
+
+def test_served_config5_shape_against_oracle(pyrit):
+    """Requests of the served workload's shape (GF(2^12) k=16 m=4, P one of 4 KiB..1 MiB, half
+    encodes and half 4-erasure decodes) arriving as a seeded Poisson stream at 20k requests/s, each
+    on its own codeword: every encode must write the oracle's parity and every decode rebuild the
+    oracle's lost blocks, with the plan's generated networks (encode table, syndrome decode)
+    compiled before serving, as the benchmark serves them."""
+    w, k, m = 12, 16, 4
+    rng = np.random.default_rng(0x5E4E)
+    count = 48
+    reqs = []
+    for _ in range(count):
+        P = 1 << int(rng.integers(12, 21))
+        op = int(rng.integers(0, 2))
+        er = sum(1 << int(x) for x in rng.choice(k + m, m, replace=False)) if op else 0
+        reqs.append((w, k, m, P, op, er))
+    gaps = rng.exponential(1e9 / 20000, count)
+    offs, total = _layout(reqs)
+    start, want = _codewords(reqs, offs, total, 91)
+    buf = torch.from_numpy(start).cuda()
+    plan = pyrit.pyrit_plan_create(w, w + 1, k, m)
+    try:
+        pyrit.pyrit_plan_specialise(plan, pyrit.PYRIT_OP_ENCODE)
+        pyrit.pyrit_plan_specialise(plan, pyrit.PYRIT_OP_DECODE_ANY)
+        torch.cuda.synchronize()
+        base = buf.data_ptr()
+        srv = pyrit.pyrit_server_create(16 << 30, max_batch=64, slots=16)
+        try:
+            t0 = pyrit.pyrit_server_now_ns(srv) + 2_000_000
+            arr = (t0 + np.cumsum(gaps)).astype(np.int64)
+            items = [(plan, op, er, P, [base + o + e * w * P for e in range(k + m)], i, int(arr[i]))
+                     for i, ((w_, k_, m_, P, op, er), o) in enumerate(zip(reqs, offs))]
+            i = 0
+            while i < count:  # submit each request at its arrival time
+                if pyrit.pyrit_server_now_ns(srv) >= arr[i]:
+                    pyrit.pyrit_server_submit(srv, [items[i]])
+                    i += 1
+            assert pyrit.pyrit_server_drain(srv, 60000) == 0
+            done = pyrit.pyrit_server_poll(srv)
+        finally:
+            pyrit.pyrit_server_destroy(srv)
+        assert sorted(d[0] for d in done) == list(range(count))
+        assert all(d[1] == 0 for d in done)
+        h = buf.cpu().numpy()
+        for i, (w_, k_, m_, P, op, er) in enumerate(reqs):
+            n = (k + m) * w * P
+            assert np.array_equal(h[offs[i]:offs[i] + n], want[offs[i]:offs[i] + n]), (i, reqs[i])
+        assert pyrit.pyrit_device_status() == (0, 0)
+    finally:
+        pyrit.pyrit_plan_destroy(plan)
 
 
 def test_admission_respects_budget(pyrit):
