@@ -248,8 +248,10 @@ typedef struct {
 /* Prepares a batch: validates every stripe (the same checks and codes as pyrit_encode /
  * pyrit_decode), resolves the decoding matrices through the plans' caches, builds one coding job
  * per stripe (stripes with nothing erased are dropped) and a work list of column tiles, and copies
- * both to library-owned device memory (synchronous). Stripes are grouped by ring size; each group is
- * one persistent launch of the staged kernel in which every CTA walks the tile list. Stripes whose
+ * both to library-owned device memory (synchronous). Stripes are grouped by ring size (stripes that
+ * the generic kernel codes also by output count: 1-2, 3-4 or 5-8 per job, so that a launch's shape
+ * fits its jobs); each group is one persistent launch of the staged kernel in which every CTA walks
+ * the tile list. Stripes whose
  * P or pointers do not allow 16-byte bulk copies run on the plain-load kernel, one launch each.
  *   stripes : host array of `count` stripes (copied; the block pointer arrays are read here only).
  *   tile    : NULL for the automatic shape, else overrides.
@@ -388,8 +390,11 @@ typedef struct {
   int64_t arrival_ns;
 } pyrit_request_t;
 
-/* A finished request: times on the server clock. start_ns / done_ns are device-timeline times of
- * the beginning and end of the batch that coded it. */
+/* A finished request: times on the server clock. start_ns is when the scheduler launched the batch
+ * that coded it; done_ns when the scheduler saw the request's own completion stamp (written by the
+ * kernel when the request's last tile was stored, before the rest of a shared launch ends). status
+ * is PYRIT_OK, or PYRIT_E_TIMEOUT when the launch ended without completing the request (a bounded
+ * device wait gave up), or PYRIT_E_CUDA when the launch failed. */
 typedef struct {
   uint64_t tag;
   int status;
@@ -404,9 +409,13 @@ typedef struct {
  * ring kernel per ring size. A launch of one request passes its job in the kernel parameters;
  * larger launches copy their jobs into the slot's device descriptor table first. Batches on
  * different slots overlap on the device; new arrivals join the next free slot (continuous
- * batching). Decoding matrices come from the plans' caches; launch shapes from the
- * autotuner's table when it has the key. queue_cap bounds the requests waiting for admission.
- * Allocates its slots' device tables and pinned staging. */
+ * batching). Each request completes on its own: the kernel stamps a request done when its last
+ * tile is stored, and the scheduler then retires it and releases its admission bytes, while the
+ * slot itself is reused once its launches have ended. The scheduler thread spins (yielding) while
+ * any work is in flight and sleeps when idle. Decoding matrices come from the plans' caches;
+ * launch shapes from the autotuner's table when it has the key. queue_cap bounds the requests
+ * waiting for admission. Allocates its slots' device tables, pinned staging and host-mapped
+ * completion stamps. */
 PYRIT_API int pyrit_server_create(size_t hbm_budget, int max_batch, int slots, int queue_cap, pyrit_server_t* out);
 
 /* Validates and enqueues requests (all or none). Errors before any device work: the codes of

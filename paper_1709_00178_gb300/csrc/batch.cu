@@ -1,6 +1,6 @@
 // Batched coding: many stripes (possibly of different codes, operations and packet sizes) coded by
-// one persistent launch of the staged ring kernel per ring size, optionally replayed from a CUDA
-// graph.
+// one persistent launch of the staged ring kernel per ring size (and, for stripes the generic
+// kernel codes, per class of output count), optionally replayed from a CUDA graph.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -184,6 +184,65 @@ int pyrit_batch_create(const pyrit_stripe_t* stripes, int count, const pyrit_til
         b->plain.emplace_back(n, jobs[q]);
       }
     }
+  }
+
+  // Groups that only the generic kernel will code -- run-time compilation off, or more distinct
+  // mask tables than a network holds (or different source counts) and not the decodes of one plan
+  // -- are split by their jobs' output counts (1-2, 3-4, 5-8): a launch is shaped for its largest
+  // job, and a job with fewer outputs would leave the other output groups' warps idle on its
+  // tiles. A stripe's jobs stay in one class (its wide stripes' jobs stay adjacent).
+  if (!(tile && hint.dispatch == PYRIT_DISPATCH_NETWORK)) {
+    const bool jit_on = jit_mode() != PYRIT_JIT_OFF;
+    std::vector<SlotKey> keys2;
+    std::vector<std::vector<JobDesc>> by_n2;
+    std::vector<std::vector<int>> src_of2;
+    for (size_t slot = 0; slot < keys.size(); ++slot) {
+      const std::vector<JobDesc>& jobs = by_n[slot];
+      const bool net_only = keys[slot].transform == PYRIT_TRANSFORM_PARITY || keys[slot].g != 0;
+      bool generic = !net_only;
+      if (generic && jit_on) {
+        std::vector<const JobDesc*> tabs;
+        bool same_in = true;
+        for (const JobDesc& j : jobs) {
+          same_in = same_in && j.nin == jobs[0].nin;
+          bool seen = false;
+          for (const JobDesc* t : tabs)
+            seen = seen || (t->nout == j.nout && std::memcmp(t->mask, j.mask, sizeof(j.mask)) == 0);
+          if (!seen && tabs.size() <= (size_t)kMaxJobs) tabs.push_back(&j);
+        }
+        const pyrit_plan_s* plan0 = stripes[src_of[slot][0]].plan;
+        bool syn = plan0->k + plan0->m <= kMaxIn && plan0->m <= kMaxOut && plan0->native;
+        for (int si : src_of[slot]) syn = syn && stripes[si].op == PYRIT_OP_DECODE && stripes[si].plan == plan0;
+        generic = !(same_in && tabs.size() <= (size_t)kMaxJobs) && !syn;
+      }
+      if (!generic) {
+        keys2.push_back(keys[slot]);
+        by_n2.push_back(jobs);
+        src_of2.push_back(src_of[slot]);
+        continue;
+      }
+      // outputs of each stripe in the group: the class of its jobs
+      std::vector<int> outs(count, 0);
+      for (size_t q = 0; q < jobs.size(); ++q) outs[src_of[slot][q]] += jobs[q].nout;
+      for (int cls = 0; cls < 3; ++cls) {
+        SlotKey k = keys[slot];
+        std::vector<JobDesc> part;
+        std::vector<int> part_src;
+        for (size_t q = 0; q < jobs.size(); ++q) {
+          const int o = outs[src_of[slot][q]];
+          if ((o <= 2 ? 0 : o <= 4 ? 1 : 2) != cls) continue;
+          part.push_back(jobs[q]);
+          part_src.push_back(src_of[slot][q]);
+        }
+        if (part.empty()) continue;
+        keys2.push_back(k);
+        by_n2.push_back(std::move(part));
+        src_of2.push_back(std::move(part_src));
+      }
+    }
+    keys.swap(keys2);
+    by_n.swap(by_n2);
+    src_of.swap(src_of2);
   }
 
   // Shapes, tile lists and the device image.

@@ -70,6 +70,19 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* e
   return mbar_wait_for(bar, parity, err, site, kWaitLimitNs);
 }
 
+// Memory-model fences (PTX fence.acq_rel) at device and system scope.
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+__device__ __forceinline__ void fence_acq_rel_sys() { asm volatile("fence.acq_rel.sys;" ::: "memory"); }
+
+// *p += 1 at device scope with release semantics (the calling thread's earlier writes, and those
+// it has synchronised with, e.g. its warp's at a __syncwarp, are ordered before it); returns the
+// old value.
+__device__ __forceinline__ uint32_t count_release_gpu(uint32_t* p) {
+  uint32_t old;
+  asm volatile("atom.add.release.gpu.u32 %0, [%1], 1;" : "=r"(old) : "l"(p) : "memory");
+  return old;
+}
+
 // Bulk asynchronous copy global -> shared of `bytes` (multiple of 16, both addresses 16-byte
 // aligned); completion is counted in transaction bytes on `bar`.
 __device__ __forceinline__ void bulk_load(void* dst_smem, const void* src, uint32_t bytes, uint64_t* bar,

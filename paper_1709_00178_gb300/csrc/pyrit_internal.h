@@ -208,9 +208,12 @@ int net_spill_bytes(const NetSpec& s);
 void resolve_grid(TileShape* shape);
 // Tiles of one job of packet size P under a shape.
 inline uint32_t tiles_for(uint64_t P, const TileShape& s) { return (uint32_t)((P + s.tw - 1) / s.tw); }
-// Launches the staged ring kernel. `jobs_dev` may be null for a single job passed by value.
+// Launches the staged ring kernel. `jobs_dev` may be null for a single job passed by value. With
+// done_cnt / done_ns (the served path) job j of the launch counts its finished warp-tiles in
+// done_cnt[j] (zero before, left zero) and stamps done_ns[j] (host-mapped) when its last one ends.
 int launch_staged(const TileShape& sh, const JobDesc* job0, const JobDesc* jobs_dev, const uint2* tiles_dev,
-                  uint32_t ntiles, uint32_t tiles_per_job, cudaStream_t stream);
+                  uint32_t ntiles, uint32_t tiles_per_job, cudaStream_t stream, uint32_t* done_cnt = nullptr,
+                  uint64_t* done_ns = nullptr);
 // Launches the plain-load kernel (any P and alignment) for one job.
 int launch_plain(int n, const JobDesc& job, cudaStream_t stream);
 // Device error word of the current device (allocated on first use), or nullptr on failure.

@@ -64,6 +64,11 @@ struct CodeArgs {
   uint32_t groups;      // consumer warps are split into this many output groups
   uint32_t stages;      // shared-memory pipeline depth
   int* err;             // device error word (code, site) or nullptr
+  // Per-job completion (the served path; nullptr elsewhere). done_cnt[j] counts the consumer warps
+  // that have stored job j's tiles (device memory, zero before the launch and left zero after it);
+  // the warp completing the count writes the global timer into done_ns[j] (host-mapped memory).
+  uint32_t* done_cnt;
+  uint64_t* done_ns;
   JobDesc job0;
 };
 

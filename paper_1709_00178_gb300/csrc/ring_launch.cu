@@ -163,7 +163,8 @@ void resolve_grid(TileShape* s) {
 }
 
 int launch_staged(const TileShape& sh, const JobDesc* job0, const JobDesc* jobs_dev, const uint2* tiles_dev,
-                  uint32_t ntiles, uint32_t tiles_per_job, cudaStream_t stream) {
+                  uint32_t ntiles, uint32_t tiles_per_job, cudaStream_t stream, uint32_t* done_cnt,
+                  uint64_t* done_ns) {
   if (ntiles == 0) return PYRIT_OK;
   if (!sh.v) return PYRIT_E_INVALID_ARG;
   CodeArgs a;
@@ -175,6 +176,8 @@ int launch_staged(const TileShape& sh, const JobDesc* job0, const JobDesc* jobs_
   a.groups = (uint32_t)sh.groups;
   a.stages = (uint32_t)sh.stages;
   a.err = device_error_word();
+  a.done_cnt = done_ns ? done_cnt : nullptr;
+  a.done_ns = done_cnt ? done_ns : nullptr;
   if (job0)
     a.job0 = *job0;
   else

@@ -45,8 +45,7 @@
 
 namespace pyrit {
 
-__device__ __forceinline__ const JobDesc* tile_job(const CodeArgs& a, uint32_t t, uint32_t& col0) {
-  uint32_t jid;
+__device__ __forceinline__ const JobDesc* tile_job(const CodeArgs& a, uint32_t t, uint32_t& col0, uint32_t& jid) {
   if (a.tiles) {
     const uint2 v = a.tiles[t];
     jid = v.x;
@@ -291,8 +290,8 @@ __device__ __forceinline__ void ring_staged_body(const CodeArgs& a) {
     uint64_t armed = 0;  // stages armed so far
     bool ok = true;
     for (uint32_t t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
-      uint32_t col0;
-      const JobDesc* J = tile_job(a, t, col0);
+      uint32_t col0, jid;
+      const JobDesc* J = tile_job(a, t, col0, jid);
       const uint64_t P = J->P;
       if (col0 >= P) continue;  // a tiling that does not match the tile width codes nothing past P
       const uint32_t width = (uint32_t)(P - col0 < (uint64_t)TW ? P - col0 : (uint64_t)TW);
@@ -334,8 +333,8 @@ __device__ __forceinline__ void ring_staged_body(const CodeArgs& a) {
   const uint32_t off = (uint32_t)((warp % wpg) * 32 + lane) * (4u * WORDS);
   uint32_t stage = 0, phase = 0;
   for (uint32_t t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
-    uint32_t col0;
-    const JobDesc* J = tile_job(a, t, col0);
+    uint32_t col0, jid;
+    const JobDesc* J = tile_job(a, t, col0, jid);
     const uint64_t P = J->P;
     if (col0 >= P) continue;  // same rule as the producer: such a tile has no stages
     const uint32_t width = (uint32_t)(P - col0 < (uint64_t)TW ? P - col0 : (uint64_t)TW);
@@ -383,6 +382,24 @@ __device__ __forceinline__ void ring_staged_body(const CodeArgs& a) {
     }
 
     mac.template store<N, WORDS, MG>(acc, J, g, col0, off, valid);
+
+    if (a.done_cnt) {
+      // Per-job completion: each consumer warp counts each tile of the job once, its stores
+      // ordered before the count at device scope (release); the warp that completes the count
+      // (tiles x consumer warps) acquires the others' stores, leaves the counter at zero for the
+      // next launch and stamps the job done in host memory after a system-scope fence.
+      __syncwarp();
+      if (lane == 0) {
+        const uint32_t target = (uint32_t)((P + TW - 1) / TW) * (uint32_t)NC;
+        if (count_release_gpu(&a.done_cnt[jid]) + 1u == target) {
+          fence_acq_rel_gpu();
+          a.done_cnt[jid] = 0u;
+          fence_acq_rel_sys();
+          const uint64_t now = global_timer_ns();
+          *reinterpret_cast<volatile uint64_t*>(&a.done_ns[jid]) = now ? now : 1ull;
+        }
+      }
+    }
   }
 }
 

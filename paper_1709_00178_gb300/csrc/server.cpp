@@ -9,9 +9,18 @@
 // that network per plan and operation; a missing network is queued for the background compiler and
 // the generic kernel serves meanwhile, so the scheduler never waits for a compilation. Batches on
 // different slots overlap on the device, so requests that arrive while others are running start as
-// soon as a slot and budget free up. Completion is timestamped on the device timeline (CUDA events
-// measured against an origin event), so a request's latency is its arrival to the end of the GPU
-// work that coded it.
+// soon as a slot and budget free up. Each request completes on its own, inside a shared launch:
+// the kernel counts the consumer warps that have stored each job's tiles and the warp completing
+// the count writes the job's completion stamp into host-mapped memory. The scheduler, which spins
+// while work is in flight, retires a request (and its admission bytes) as soon as it sees the
+// stamp, and frees the slot when its launches have ended. A request's latency is its arrival to
+// that moment, on the server clock.
+//
+// Threads. Submitters validate requests (and size their tiles, under the shape-cache lock) and
+// append them to an inbox under the queue lock, which the scheduler holds only to take the inbox
+// and to publish completions; the slots, the admission queue and the launches belong to the
+// scheduler thread alone, and the counters callers read are atomics. So a scheduler that polls
+// continuously never holds up a submission.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -48,25 +57,37 @@ struct Pending {
   uint64_t tiles;    // column tiles of the stripe at the narrowest tile width that could code it
   uint64_t tag;
   int64_t arrival;   // server clock, ns
+  int idx = -1;      // completion slot of the request in its slot's stamp table (-1: no launch)
+  bool finished = false;
 };
 
 struct Slot {
   cudaStream_t st = nullptr;
-  cudaEvent_t start = nullptr, done = nullptr;
+  cudaStream_t aux = nullptr;        // second stream: a batch's launch groups alternate between the two
+  cudaEvent_t staged = nullptr;      // on st after the job and tile copies (aux waits for it)
+  cudaEvent_t aux_done = nullptr;    // on aux after its launches (st waits for it)
+  cudaEvent_t done = nullptr;  // recorded after the slot's launches
   JobDesc* dev_jobs = nullptr;
   uint2* dev_tiles = nullptr;
   JobDesc* host_jobs = nullptr;  // pinned staging
   uint2* host_tiles = nullptr;
+  uint32_t* dev_cnt = nullptr;    // per-request count of finished warp-tiles (zero between launches)
+  uint64_t* host_done = nullptr;  // per-request completion stamps, host-mapped (0: not done)
+  uint64_t* dev_done = nullptr;   // the same memory as the kernels address it
   std::vector<Pending> reqs;
+  size_t open = 0;     // requests of the slot not yet retired
   uint64_t bytes = 0;
   uint64_t tiles = 0;  // sum of the admitted requests' tile bounds
   int64_t launch_ns = 0;
+  int64_t queried_ns = 0;  // last query of `done` while requests were still open
   bool busy = false;
 };
 
 }  // namespace
 
 struct pyrit_server_s {
+  // Shape caches (cache_mu): submitters size requests' tiles with them, the scheduler shapes launches.
+  std::mutex cache_mu;
   TileShape shapes[16][kMaxOut + 1];  // launch shape per (ring size, largest output count), lazily
   bool shape_set[16][kMaxOut + 1] = {};
   std::map<const Variant*, TileShape> net_shapes;  // launch shapes of the generated networks used
@@ -75,23 +96,29 @@ struct pyrit_server_s {
   std::map<uint64_t, const Variant*> nets;
   std::map<uint64_t, uint32_t> net_tw;
   uint32_t generic_tw[16] = {};  // narrowest generic tile width per ring size (0: not computed)
+
   size_t budget = 0;
   int max_batch = 0;
   uint32_t max_tiles = 0;
   int device = 0;
-  int64_t origin_host = 0;  // host time of the origin event
-  cudaEvent_t origin = nullptr;
-  std::vector<Slot> slots;
+  size_t queue_cap = 0;
+  int64_t origin_host = 0;  // host steady-clock time of the server clock's zero
 
+  // The scheduler thread's own state.
+  std::vector<Slot> slots;
+  std::deque<Pending> arrivals;  // taken from the inbox, waiting for admission
+
+  // Queue lock: the inbox, the completions and the stop flag.
   std::mutex mu;
   std::condition_variable cv;
-  std::deque<Pending> arrivals;
+  std::deque<Pending> inbox;
   std::vector<pyrit_completion_t> done;
-  size_t queue_cap = 0;
-  uint64_t inflight = 0, max_inflight = 0;
-  uint64_t batches = 0, completed = 0, submitted = 0, launches = 0;
-  std::atomic<bool> stop{false};
-  int fatal = PYRIT_OK;
+  bool stop = false;
+
+  std::atomic<int> fatal{PYRIT_OK};
+  std::atomic<uint64_t> queued{0};  // inbox + arrivals
+  std::atomic<uint64_t> inflight{0}, max_inflight{0};
+  std::atomic<uint64_t> batches{0}, completed{0}, submitted{0}, launches{0};
   std::thread worker;
 
   int64_t now() const { return host_now_ns() - origin_host; }
@@ -99,33 +126,46 @@ struct pyrit_server_s {
 
 namespace {
 
-// Device time of an event that has completed, on the server clock.
-int64_t event_ns(pyrit_server_s* s, cudaEvent_t e) {
-  float ms = 0.f;
-  cudaEventElapsedTime(&ms, s->origin, e);
-  return (int64_t)((double)ms * 1e6);
+// Retires request p of a slot at server time t with `status` into `fin`.
+void retire(pyrit_server_s* s, Slot& sl, Pending& p, int status, int64_t t, std::vector<pyrit_completion_t>& fin) {
+  pyrit_completion_t c;
+  c.tag = p.tag;
+  c.status = status;
+  c.arrival_ns = p.arrival;
+  c.start_ns = sl.launch_ns;
+  c.done_ns = t;
+  fin.push_back(c);
+  p.finished = true;
+  --sl.open;
+  s->inflight -= p.bytes;
 }
 
-// Retires every slot whose work has finished. Called with the lock held.
-void reap(pyrit_server_s* s) {
+// Retires every request whose completion stamp has arrived, and frees every slot whose launches
+// have ended (a request still unstamped then did not complete: a bounded device wait gave up, or
+// the launch failed). A slot's completion event is queried once all its requests are stamped, and
+// otherwise at most every 200 us, to notice a launch that ended without completing them.
+void reap(pyrit_server_s* s, std::vector<pyrit_completion_t>& fin) {
   for (Slot& sl : s->slots) {
     if (!sl.busy) continue;
+    const int64_t t = s->now();
+    if (sl.open)
+      for (Pending& p : sl.reqs)
+        if (!p.finished && p.idx >= 0 && reinterpret_cast<volatile uint64_t*>(sl.host_done)[p.idx] != 0)
+          retire(s, sl, p, PYRIT_OK, t, fin);
+    if (sl.open && t - sl.queried_ns < 200000) continue;
+    sl.queried_ns = t;
     const cudaError_t q = cudaEventQuery(sl.done);
     if (q == cudaErrorNotReady) continue;
-    const int status = q == cudaSuccess ? PYRIT_OK : PYRIT_E_CUDA;
-    const int64_t t_start = status == PYRIT_OK ? event_ns(s, sl.start) : sl.launch_ns;
-    const int64_t t_done = status == PYRIT_OK ? event_ns(s, sl.done) : s->now();
-    for (const Pending& p : sl.reqs) {
-      pyrit_completion_t c;
-      c.tag = p.tag;
-      c.status = status;
-      c.arrival_ns = p.arrival;
-      c.start_ns = t_start;
-      c.done_ns = t_done;
-      s->done.push_back(c);
+    if (sl.open) {
+      // the launches ended: stamps written before the end are visible now
+      for (Pending& p : sl.reqs) {
+        if (p.finished) continue;
+        const bool stamped = p.idx >= 0 && reinterpret_cast<volatile uint64_t*>(sl.host_done)[p.idx] != 0;
+        retire(s, sl, p, q != cudaSuccess ? PYRIT_E_CUDA : stamped ? PYRIT_OK : PYRIT_E_TIMEOUT, t, fin);
+      }
+      // an incomplete count would offset the next launch's: clear the table
+      cudaMemsetAsync(sl.dev_cnt, 0, sizeof(uint32_t) * (size_t)s->max_batch, sl.st);
     }
-    s->completed += sl.reqs.size();
-    s->inflight -= sl.bytes;
     sl.reqs.clear();
     sl.bytes = 0;
     sl.tiles = 0;
@@ -134,7 +174,8 @@ void reap(pyrit_server_s* s) {
 }
 
 // Launch shape for a batch whose ring-size-n jobs have at most max_nout outputs: the tuned shape of
-// that key for mixed packet sizes if the autotuner has one, else the default. Cached.
+// that key for mixed packet sizes if the autotuner has one, else the default. Cached; called
+// with cache_mu held.
 int slot_shape(pyrit_server_s* s, int n, int max_nout, TileShape* out) {
   if (n < 0 || n >= 16 || max_nout < 1 || max_nout > kMaxOut) return PYRIT_E_INVALID_ARG;
   if (!s->shape_set[n][max_nout]) {
@@ -162,7 +203,7 @@ uint64_t request_key(const Pending& p) { return p.plan->serial << 5 | (p.syn ? 1
 
 // The generated network that would code request p now (nullptr: the generic kernel), queued for
 // the background compiler if it is missing. A ready network is remembered per request key, so
-// later requests of the same plan and form skip building its spec. Called with the lock held.
+// later requests of the same plan and form skip building its spec. Called with cache_mu held.
 const Variant* request_network(pyrit_server_s* s, const Pending& p) {
   if (p.job.nout == 0 || jit_mode() == PYRIT_JIT_OFF) return nullptr;
   if (p.op != PYRIT_OP_ENCODE && !p.syn) return nullptr;
@@ -176,7 +217,7 @@ const Variant* request_network(pyrit_server_s* s, const Pending& p) {
   return v;
 }
 
-// Launch shape of a generated network (cached).
+// Launch shape of a generated network (cached; called with cache_mu held).
 const TileShape& network_shape(pyrit_server_s* s, const Variant* v) {
   auto it = s->net_shapes.find(v);
   if (it == s->net_shapes.end()) {
@@ -192,7 +233,7 @@ const TileShape& network_shape(pyrit_server_s* s, const Variant* v) {
 // narrowest tile width among its ring size's generic shapes (for any output count of the batch it
 // joins) and the default shape of the network that would code it, so that neither the batch's
 // composition nor a network finishing its compilation between admission and launch can overflow
-// a slot's tile table. Widths are cached. Called with the lock held.
+// a slot's tile table. Widths are cached. Called with cache_mu held.
 uint64_t request_tiles(pyrit_server_s* s, const Pending& p) {
   if (p.job.nout == 0) return 0;
   if (p.n < 0 || p.n >= 16) return ~0ull;
@@ -228,43 +269,55 @@ uint64_t request_tiles(pyrit_server_s* s, const Pending& p) {
 // kernel. A group of one request carries its job in the kernel parameters with implicit tiles
 // (nothing to copy first); larger groups get an explicit tile list, staged with their jobs in
 // pinned memory and copied on the slot's stream.
-int launch_slot(pyrit_server_s* s, Slot& sl) {
-  uint32_t nj = 0, nt = 0;
+int launch_slot(pyrit_server_s* s, Slot& sl, std::vector<pyrit_completion_t>& fin) {
+  std::unique_lock<std::mutex> cache_lk(s->cache_mu);
+  uint32_t nj = 0, nt = 0, nd = 0;  // jobs and tiles staged, completion stamps assigned
   struct G {
     TileShape shape;
-    uint32_t job0, njobs, tile0, ntiles;
+    uint32_t job0, njobs, tile0, ntiles, done0;
     bool single;     // one job, passed by value
     JobDesc job;     // that job
   };
   std::vector<G> groups;
   std::vector<const Variant*> net(sl.reqs.size());
   for (size_t i = 0; i < sl.reqs.size(); ++i) net[i] = request_network(s, sl.reqs[i]);
+  // A group's jobs take consecutive completion stamps in job order, so that job j of its launch
+  // (its position in the launch's job array) owns stamp done0 + j.
   auto add_group = [&](const TileShape& shape, auto member, bool syn_form) -> int {
     G g{};
     g.shape = shape;
     g.job0 = nj;
     g.tile0 = nt;
+    g.done0 = nd;
     size_t members = 0, first = 0;
     for (size_t i = 0; i < sl.reqs.size(); ++i)
       if (sl.reqs[i].job.nout != 0 && member(i) && members++ == 0) first = i;
     if (members == 1) {
-      const Pending& p = sl.reqs[first];
+      Pending& p = sl.reqs[first];
       g.single = true;
       g.job = syn_form ? p.syn_job : p.job;
       g.njobs = 1;
       g.ntiles = (uint32_t)((p.job.P + (uint64_t)g.shape.tw - 1) / (uint64_t)g.shape.tw);
+      p.idx = (int)nd++;
       groups.push_back(g);
       return PYRIT_OK;
     }
-    for (size_t i = 0; i < sl.reqs.size(); ++i) {
-      const Pending& p = sl.reqs[i];
-      if (p.job.nout == 0 || !member(i)) continue;
+    // members in increasing size: the persistent CTAs walk the tile list in order, so the small
+    // requests of a shared launch complete first
+    std::vector<size_t> order;
+    for (size_t i = 0; i < sl.reqs.size(); ++i)
+      if (sl.reqs[i].job.nout != 0 && member(i)) order.push_back(i);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](size_t a, size_t b) { return sl.reqs[a].bytes < sl.reqs[b].bytes; });
+    for (size_t i : order) {
+      Pending& p = sl.reqs[i];
       sl.host_jobs[nj] = syn_form ? p.syn_job : p.job;
       for (uint64_t c = 0; c < p.job.P; c += (uint64_t)g.shape.tw) {
         if (nt >= s->max_tiles) return PYRIT_E_INVALID_ARG;  // admission keeps batches within the table
         sl.host_tiles[nt++] = make_uint2(nj - g.job0, (uint32_t)c);
       }
       ++nj;
+      p.idx = (int)nd++;
     }
     g.njobs = nj - g.job0;
     g.ntiles = nt - g.tile0;
@@ -291,32 +344,70 @@ int launch_slot(pyrit_server_s* s, Slot& sl) {
     const int rc2 = add_group(sh, [&](size_t i) { return !net[i] && sl.reqs[i].n == n; }, false);
     if (rc2 != PYRIT_OK) return rc2;
   }
-  cudaEventRecord(sl.start, sl.st);
+  cache_lk.unlock();
+  // The slot's previous launches have ended (it was freed at their completion event): no kernel
+  // writes these stamps now.
+  for (uint32_t d = 0; d < nd; ++d) sl.host_done[d] = 0;
   if (nj && cudaMemcpyAsync(sl.dev_jobs, sl.host_jobs, nj * sizeof(JobDesc), cudaMemcpyHostToDevice, sl.st) != cudaSuccess)
     return PYRIT_E_CUDA;
   if (nt && cudaMemcpyAsync(sl.dev_tiles, sl.host_tiles, nt * sizeof(uint2), cudaMemcpyHostToDevice, sl.st) != cudaSuccess)
     return PYRIT_E_CUDA;
-  for (const G& g : groups) {
-    const int rc = g.single ? launch_staged(g.shape, &g.job, nullptr, nullptr, g.ntiles, g.ntiles, sl.st)
+  // Launch groups alternate between the slot's two streams so that, e.g., a batch's decodes do not
+  // wait for its encodes to finish: the second stream waits for the copies, and the first for the
+  // second's launches before the slot's completion event.
+  const bool two = groups.size() > 1;
+  if (two && (cudaEventRecord(sl.staged, sl.st) != cudaSuccess || cudaStreamWaitEvent(sl.aux, sl.staged, 0) != cudaSuccess))
+    return PYRIT_E_CUDA;
+  for (size_t gi = 0; gi < groups.size(); ++gi) {
+    const G& g = groups[gi];
+    const cudaStream_t st = two && (gi & 1) ? sl.aux : sl.st;
+    const int rc = g.single ? launch_staged(g.shape, &g.job, nullptr, nullptr, g.ntiles, g.ntiles, st,
+                                            sl.dev_cnt + g.done0, sl.dev_done + g.done0)
                             : launch_staged(g.shape, nullptr, sl.dev_jobs + g.job0, sl.dev_tiles + g.tile0, g.ntiles,
-                                            0, sl.st);
+                                            0, st, sl.dev_cnt + g.done0, sl.dev_done + g.done0);
     if (rc != PYRIT_OK) return rc;
-    ++s->launches;
+    s->launches += 1;
   }
+  if (two && (cudaEventRecord(sl.aux_done, sl.aux) != cudaSuccess || cudaStreamWaitEvent(sl.st, sl.aux_done, 0) != cudaSuccess))
+    return PYRIT_E_CUDA;
   if (cudaEventRecord(sl.done, sl.st) != cudaSuccess) return PYRIT_E_CUDA;
+  // requests with nothing to code (a decode with no block lost) are done at once
+  for (Pending& p : sl.reqs)
+    if (p.idx < 0) retire(s, sl, p, PYRIT_OK, s->now(), fin);
   return PYRIT_OK;
+}
+
+// Publishes retired requests to pyrit_server_poll before counting them complete (so a drain that
+// sees every request complete finds every completion).
+void publish(pyrit_server_s* s, std::vector<pyrit_completion_t>& fin) {
+  if (fin.empty()) return;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->done.insert(s->done.end(), fin.begin(), fin.end());
+  }
+  s->completed += fin.size();
+  fin.clear();
 }
 
 void run(pyrit_server_s* s) {
   cudaSetDevice(s->device);
-  std::unique_lock<std::mutex> lk(s->mu);
+  std::vector<pyrit_completion_t> fin;
   while (true) {
-    reap(s);
-    if (s->stop && s->arrivals.empty()) {
-      bool busy = false;
-      for (const Slot& sl : s->slots) busy = busy || sl.busy;
-      if (!busy) break;
+    bool busy = false;
+    for (const Slot& sl : s->slots) busy = busy || sl.busy;
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      if (!busy && s->arrivals.empty() && s->inbox.empty()) {
+        // idle: sleep until a submission or shutdown
+        s->cv.wait(lk, [&] { return s->stop || !s->inbox.empty(); });
+        if (s->inbox.empty()) break;  // stopped with nothing left to do
+      }
+      while (!s->inbox.empty()) {
+        s->arrivals.push_back(s->inbox.front());
+        s->inbox.pop_front();
+      }
     }
+    reap(s, fin);
     Slot* free_slot = nullptr;
     for (Slot& sl : s->slots)
       if (!sl.busy) {
@@ -334,23 +425,31 @@ void run(pyrit_server_s* s) {
         free_slot->bytes += p.bytes;
         free_slot->tiles += p.tiles;
         s->arrivals.pop_front();
+        s->queued -= 1;
       }
       if (!free_slot->reqs.empty()) {
         s->inflight += free_slot->bytes;
-        s->max_inflight = std::max(s->max_inflight, s->inflight);
+        const uint64_t cur = s->inflight;
+        if (cur > s->max_inflight) s->max_inflight = cur;
         free_slot->busy = true;
+        free_slot->open = free_slot->reqs.size();
         free_slot->launch_ns = s->now();
-        ++s->batches;
-        const int rc = launch_slot(s, *free_slot);
+        free_slot->queried_ns = free_slot->launch_ns;
+        s->batches += 1;
+        const int rc = launch_slot(s, *free_slot, fin);
         if (rc != PYRIT_OK) s->fatal = rc;
         launched = true;
       }
     }
+    publish(s, fin);
     if (!launched) {
-      // Nothing to start: wait briefly for an arrival or for a slot to finish.
-      s->cv.wait_for(lk, std::chrono::microseconds(20));
+      // Work in flight, or admission waiting for a slot or budget: poll again at once (a timed
+      // wait would sleep for the kernel's timer slack, tens of microseconds). This thread holds no
+      // lock here.
+      std::this_thread::yield();
     }
   }
+  publish(s, fin);
 }
 
 }  // namespace
@@ -373,17 +472,21 @@ int pyrit_server_create(size_t hbm_budget, int max_batch, int slots, int queue_c
   for (Slot& sl : s->slots) {
     if (rc != PYRIT_OK) break;
     if (cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreate(&sl.start) != cudaSuccess || cudaEventCreate(&sl.done) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&sl.aux, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&sl.staged, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&sl.aux_done, cudaEventDisableTiming) != cudaSuccess ||
         cudaMalloc(&sl.dev_jobs, sizeof(JobDesc) * max_batch) != cudaSuccess ||
         cudaMalloc(&sl.dev_tiles, sizeof(uint2) * s->max_tiles) != cudaSuccess ||
+        cudaMalloc(&sl.dev_cnt, sizeof(uint32_t) * max_batch) != cudaSuccess ||
+        cudaMemset(sl.dev_cnt, 0, sizeof(uint32_t) * max_batch) != cudaSuccess ||
         cudaMallocHost(&sl.host_jobs, sizeof(JobDesc) * max_batch) != cudaSuccess ||
-        cudaMallocHost(&sl.host_tiles, sizeof(uint2) * s->max_tiles) != cudaSuccess)
+        cudaMallocHost(&sl.host_tiles, sizeof(uint2) * s->max_tiles) != cudaSuccess ||
+        cudaHostAlloc(&sl.host_done, sizeof(uint64_t) * max_batch, cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer(&sl.dev_done, sl.host_done, 0) != cudaSuccess)
       rc = PYRIT_E_OOM;
   }
-  if (rc == PYRIT_OK && (cudaEventCreate(&s->origin) != cudaSuccess ||
-                         cudaEventRecord(s->origin, s->slots[0].st) != cudaSuccess ||
-                         cudaEventSynchronize(s->origin) != cudaSuccess))
-    rc = PYRIT_E_CUDA;
+  if (rc == PYRIT_OK && cudaDeviceSynchronize() != cudaSuccess) rc = PYRIT_E_CUDA;
   if (rc != PYRIT_OK) {
     pyrit_server_destroy(s);
     return rc;
@@ -430,7 +533,7 @@ int pyrit_server_submit(pyrit_server_t s, const pyrit_request_t* reqs, int count
     if (!job_is_staged(p.job) && p.job.nout > 0) return PYRIT_E_INVALID_ARG;  // served stripes must be 16-byte aligned
     {
       // one request must fit a slot's tile table even at the narrowest tiles of its ring size
-      std::lock_guard<std::mutex> lk(s->mu);
+      std::lock_guard<std::mutex> lk(s->cache_mu);
       p.tiles = request_tiles(s, p);
       if (p.tiles > s->max_tiles) return PYRIT_E_INVALID_ARG;
     }
@@ -439,12 +542,13 @@ int pyrit_server_submit(pyrit_server_t s, const pyrit_request_t* reqs, int count
   }
   std::lock_guard<std::mutex> lk(s->mu);
   if (s->fatal != PYRIT_OK) return s->fatal;
-  if (s->arrivals.size() + batch.size() > s->queue_cap) return PYRIT_E_BUSY;
+  if (s->queued + batch.size() > s->queue_cap) return PYRIT_E_BUSY;
   const int64_t now = s->now();
   for (size_t i = 0; i < batch.size(); ++i) {
     batch[i].arrival = reqs[i].arrival_ns > 0 ? reqs[i].arrival_ns : now;
-    s->arrivals.push_back(batch[i]);
+    s->inbox.push_back(batch[i]);
   }
+  s->queued += batch.size();
   s->submitted += batch.size();
   s->cv.notify_one();
   return PYRIT_OK;
@@ -463,13 +567,8 @@ int pyrit_server_drain(pyrit_server_t s, int timeout_ms) {
   if (!s) return PYRIT_E_INVALID_ARG;
   const int64_t limit = host_now_ns() + (int64_t)timeout_ms * 1000000;
   while (true) {
-    {
-      std::lock_guard<std::mutex> lk(s->mu);
-      if (s->fatal != PYRIT_OK) return s->fatal;
-      bool busy = !s->arrivals.empty();
-      for (const Slot& sl : s->slots) busy = busy || sl.busy;
-      if (!busy) return PYRIT_OK;
-    }
+    if (s->fatal != PYRIT_OK) return s->fatal;
+    if (s->completed >= s->submitted) return PYRIT_OK;
     if (host_now_ns() > limit) return PYRIT_E_TIMEOUT;
     std::this_thread::sleep_for(std::chrono::microseconds(50));
   }
@@ -477,7 +576,6 @@ int pyrit_server_drain(pyrit_server_t s, int timeout_ms) {
 
 int pyrit_server_stats(pyrit_server_t s, uint64_t* stats_out) {
   if (!s || !stats_out) return PYRIT_E_INVALID_ARG;
-  std::lock_guard<std::mutex> lk(s->mu);
   stats_out[0] = s->submitted;
   stats_out[1] = s->completed;
   stats_out[2] = s->batches;
@@ -504,11 +602,15 @@ void pyrit_server_destroy(pyrit_server_t s) {
     if (sl.dev_tiles) cudaFree(sl.dev_tiles);
     if (sl.host_jobs) cudaFreeHost(sl.host_jobs);
     if (sl.host_tiles) cudaFreeHost(sl.host_tiles);
-    if (sl.start) cudaEventDestroy(sl.start);
+    if (sl.dev_cnt) cudaFree(sl.dev_cnt);
+    if (sl.host_done) cudaFreeHost(sl.host_done);
+    if (sl.aux) cudaStreamSynchronize(sl.aux);
     if (sl.done) cudaEventDestroy(sl.done);
+    if (sl.staged) cudaEventDestroy(sl.staged);
+    if (sl.aux_done) cudaEventDestroy(sl.aux_done);
     if (sl.st) cudaStreamDestroy(sl.st);
+    if (sl.aux) cudaStreamDestroy(sl.aux);
   }
-  if (s->origin) cudaEventDestroy(s->origin);
   delete s;
 }
 
