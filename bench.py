@@ -1040,10 +1040,16 @@ def served_measure(torch, pyrit, dev, rate, seconds, slots, pool=512):
         st = pyrit.pyrit_server_stats(srv)
         pyrit.pyrit_server_destroy(srv)
         lat = np.array([d[4] - d[2] for d in done if d[0] < nreq], dtype=np.float64) / 1e3  # us
+        wait = np.array([d[3] - d[2] for d in done if d[0] < nreq], dtype=np.float64) / 1e3
+        run = np.array([d[4] - d[3] for d in done if d[0] < nreq], dtype=np.float64) / 1e3
         t_first = min(d[2] for d in done)
         t_last = max(d[4] for d in done)
         return {"p50_us": float(np.percentile(lat, 50)), "p99_us": float(np.percentile(lat, 99)),
                 "p999_us": float(np.percentile(lat, 99.9)), "max_us": float(lat.max()), "requests": len(lat),
+                "arrival_to_launch_p50_us": float(np.percentile(wait, 50)),
+                "arrival_to_launch_p99_us": float(np.percentile(wait, 99)),
+                "launch_to_done_p50_us": float(np.percentile(run, 50)),
+                "launch_to_done_p99_us": float(np.percentile(run, 99)),
                 "all_ok": all(d[1] == 0 for d in done),
                 "sustained_gbs": src_bytes / ((t_last - t_first) * 1e-9) / 1e9,
                 "batches": st["batches"], "launches": st["launches"], "max_inflight_bytes": st["max_inflight"],

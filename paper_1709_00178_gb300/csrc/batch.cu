@@ -456,17 +456,38 @@ int pyrit_batch_tune(pyrit_batch_t b, pyrit_stream_t stream, int iters) {
       const int ns = net_syndrome_shapes(g.syn_plan, specs, 8);
       add_networks(specs, ns, &cands);
     }
+    // Every candidate at its default pipeline depth; generated networks at every depth from 3
+    // stages to as many as shared memory holds: the best depth depends on the code and the
+    // network (measured on GB300: the syndrome decodes 4-5 stages, the config-2 encode 7, the
+    // GF(2^12) k=16 m=4 encode 6).
+    struct Try {
+      const Variant* v;
+      int stages;  // 0: the default
+    };
+    std::vector<Try> tries;
+    for (const Variant* v : cands) {
+      tries.push_back({v, 0});
+      if (v->dispatch == PYRIT_DISPATCH_NETWORK) {
+        TileShape def;
+        if (!shape_for_variant(v, g.max_nout, ShapeHint(), &def)) continue;
+        const int fit = (int)std::min<size_t>(8, (226 * 1024 / v->minb - 1024) / ((size_t)v->w * def.tw));
+        for (int st = 3; st <= fit; ++st)
+          if (st != def.stages) tries.push_back({v, st});
+      }
+    }
     float best = 1e30f;
     TileShape best_shape = g.shape;
-    for (size_t i = 0; i < cands.size() && rc == PYRIT_OK; ++i) {
+    for (size_t i = 0; i < tries.size() && rc == PYRIT_OK; ++i) {
       TileShape sh;
-      if (!shape_for_variant(cands[i], g.max_nout, ShapeHint(), &sh)) continue;
+      ShapeHint th;
+      th.stages = tries[i].stages;
+      if (!shape_for_variant(tries[i].v, g.max_nout, th, &sh)) continue;
       resolve_grid(&sh);
       uint2* tiles = nullptr;  // the tiling depends on the candidate's tile width
       uint32_t ntiles = 0, tpj = 0;
       rc = make_tiling(g, sh, &tiles, &ntiles, &tpj);
       if (rc != PYRIT_OK) break;
-      const JobDesc* jobs = group_jobs(b->dev, g, cands[i]);
+      const JobDesc* jobs = group_jobs(b->dev, g, tries[i].v);
       rc = launch_staged(sh, nullptr, jobs, tiles, ntiles, tpj, st);  // warm-up
       if (rc == PYRIT_OK) {
         cudaEventRecord(e0, st);

@@ -62,8 +62,8 @@ def emit_ring(N):
     return "\n".join(out)
 
 
-def main():
-    here = os.path.dirname(os.path.abspath(__file__))
+def source():
+    """The text of ring_network.inc."""
     body = ["// Generated by gen_ring_network.py -- do not edit by hand.",
             "// Paired ring multiply-accumulate automata (see the generator's docstring)."]
     for N in RINGS:
@@ -75,8 +75,13 @@ def main():
     for N in RINGS:
         body.append("  if constexpr (N == %d) ring_mac_pairs_n%d<WORDS>(acc, d, r);" % (N, N))
     body.append("}")
+    return "\n".join(body) + "\n"
+
+
+def main():
+    here = os.path.dirname(os.path.abspath(__file__))
     with open(os.path.join(here, "ring_network.inc"), "w") as f:
-        f.write("\n".join(body) + "\n")
+        f.write(source())
 
 
 if __name__ == "__main__":

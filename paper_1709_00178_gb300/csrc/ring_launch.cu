@@ -133,7 +133,11 @@ bool shape_for_variant(const Variant* v, int max_nout, const ShapeHint& h, TileS
   s.groups = groups;
   s.tw = (v->nc / groups) * 32 * 4 * v->words;
   const int w = v->w;
-  const int budget = (226 * 1024) / v->minb - 1024;  // shared memory per CTA at the target occupancy
+  // Shared memory per CTA for the stage ring at the target occupancy. Generated networks leave
+  // about 26 KB of the 228 KB to the L1 data cache, which holds the jobs' descriptors and
+  // coefficients: on GB300 the config-2 encode runs best at 7 stages (197 KB) rather than 8
+  // (225 KB), and the syndrome decode at 4-5 (143-179 KB) rather than 6 (215 KB).
+  const int budget = (v->dispatch == PYRIT_DISPATCH_NETWORK ? 200 * 1024 : 226 * 1024) / v->minb - 1024;
   s.stages = h.stages > 0 ? h.stages : std::max(2, std::min(8, budget / (w * s.tw)));
   s.grid = 0;
   if (h.ctas_per_sm > 0) s.grid = h.ctas_per_sm * sm_count();

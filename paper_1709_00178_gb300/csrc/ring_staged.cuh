@@ -57,6 +57,13 @@ __device__ __forceinline__ const JobDesc* tile_job(const CodeArgs& a, uint32_t t
   return a.jobs ? a.jobs + jid : &a.job0;
 }
 
+// A value every lane of a warp reads from the same job descriptor, broadcast from lane 0 (called
+// by all 32 lanes): the compiler then knows it warp-uniform and keeps tests and branches on it on
+// the uniform datapath. Used where a warp branches on descriptor values many times per tile (the
+// syndrome decode's second phase: on GB300 the decode 3.5% faster for GF(2^10) k=10 m=4 and 7%
+// for GF(2^12) k=16 m=4; broadcasting every descriptor read instead cost the encodes up to 2%).
+__device__ __forceinline__ uint32_t warp_uniform(uint32_t v) { return __shfl_sync(0xFFFFFFFFu, v, 0); }
+
 // a ^ b ^ c in one three-input logic instruction (truth table 0x96). Generated networks spell
 // their XORs this way so that each instruction absorbs two source terms.
 __device__ __forceinline__ uint32_t xor3(uint32_t a, uint32_t b, uint32_t c) {
@@ -159,7 +166,7 @@ struct SyndromeStoreT {
   static constexpr bool kSparse = true;  // erased columns and unused parity are absent sources
   uint32_t need;                         // rows the pattern uses (read once per tile)
 
-  __device__ __forceinline__ void load_rows(const JobDesc* J) { need = J->mask[kSyndromeNeedRow][0]; }
+  __device__ __forceinline__ void load_rows(const JobDesc* J) { need = warp_uniform(J->mask[kSyndromeNeedRow][0]); }
 
   template <int N, int WORDS, int MG>
   __device__ __forceinline__ void store(uint32_t (&acc)[MG][N][WORDS], const JobDesc* J, int, uint32_t col0,
@@ -176,7 +183,7 @@ struct SyndromeStoreT {
     const uint64_t P = J->P;
     const int nout = J->nout;
     for (int o = 0; o < nout; ++o) {
-      const uint32_t base = J->mask[kSyndromeBaseRow][o];
+      const uint32_t base = warp_uniform(J->mask[kSyndromeBaseRow][o]);
       uint32_t res[N][WORDS];
 #pragma unroll
       for (int t = 0; t < N; ++t)
@@ -193,7 +200,7 @@ struct SyndromeStoreT {
       }
 #pragma unroll
       for (int r = 0; r < MG; ++r) {
-        const uint32_t c = J->mask[r][o];
+        const uint32_t c = warp_uniform(J->mask[r][o]);
         if (c == 0u) continue;
         // res += c * acc_r: one rotation of the reduced row per set bit of c
 #pragma unroll

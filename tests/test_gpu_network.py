@@ -154,11 +154,34 @@ def test_jit_off_uses_the_generic_kernel(pyrit, jit_mode):
         pyrit.pyrit_plan_destroy(st.plan)
 
 
+def test_output_count_classes_split_a_generic_group(pyrit, jit_mode):
+    """Codes of one ring with different source and output counts share no network as one group; the
+    batch splits such a group by output count (1-2, 3-4, 5-8 per job), and each part, now of one
+    mask table, runs its own launch (a generated network when compilation is on). Every stripe must
+    equal the oracle's."""
+    a = Stripes(pyrit, 10, 10, 4, 4096 + 16, 2, 0x333)
+    c = Stripes(pyrit, 10, 12, 2, 4096, 2, 0x444)
+    try:
+        b = pyrit.pyrit_batch_create(a.stripes(pyrit.PYRIT_OP_ENCODE) + c.stripes(pyrit.PYRIT_OP_ENCODE))
+        try:
+            assert pyrit.pyrit_batch_stats(b)["launches"] == 2
+            pyrit.pyrit_batch_run(b)
+            for st in (a, c):
+                for s in range(st.count):
+                    np.testing.assert_array_equal(st.host(s), st.full(s))
+        finally:
+            pyrit.pyrit_batch_destroy(b)
+    finally:
+        pyrit.pyrit_plan_destroy(a.plan)
+        pyrit.pyrit_plan_destroy(c.plan)
+
+
 def test_network_request_without_a_network_is_refused(pyrit, jit_mode):
-    """Codes with different source counts share no network: an explicit network request is refused
-    before any device work; without it the group runs on a generic kernel."""
+    """Codes with different source counts (and the same output count, so one launch group) share no
+    network: an explicit network request is refused before any device work; without it the group
+    runs on a generic kernel."""
     a = Stripes(pyrit, 10, 10, 4, 4096, 1, 0x111)
-    c = Stripes(pyrit, 10, 12, 2, 4096, 1, 0x222)
+    c = Stripes(pyrit, 10, 12, 4, 4096, 1, 0x222)
     try:
         before = [a.host(0).copy(), c.host(0).copy()]
         mixed = a.stripes(pyrit.PYRIT_OP_ENCODE) + c.stripes(pyrit.PYRIT_OP_ENCODE)

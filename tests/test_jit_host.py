@@ -9,6 +9,7 @@ sparse representative r is (Sec. 2.2). The map is linear in the source, so check
 vector x^q (q < w) is exhaustive. They also run the run-time compiler (NVRTC) for sm_103a, which
 needs no device.
 """
+import os
 import re
 
 import numpy as np
@@ -552,3 +553,15 @@ def test_shared_terms_reduce_the_xor_count(w, k, m, enc_max, syn_max):
         pyrit.pyrit_plan_destroy(plan)
     assert enc <= enc_max and enc < 0.75 * unshared, (enc, unshared)
     assert syn <= syn_max, syn
+
+
+def test_committed_pairing_automata_match_their_generator():
+    # ring_network.inc is generated by csrc/gen_ring_network.py and committed (the build compiles the
+    # committed file); the two must not drift apart.
+    import importlib.util
+    here = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_1709_00178_gb300", "csrc")
+    spec = importlib.util.spec_from_file_location("gen_ring_network", os.path.join(here, "gen_ring_network.py"))
+    gen = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(gen)
+    with open(os.path.join(here, "ring_network.inc")) as f:
+        assert f.read() == gen.source()
