@@ -14,9 +14,10 @@ blocks (rebuilt in place), each as one persistent batched launch replayed from a
            ((k+m)wP per encoded stripe, (k+e)wP per decoded stripe with e erasures) per launch over
            its event-timed duration, against the measured HBM copy bandwidth; the headline object
            is the kernel with the larger share of the step.
-  served   (sub-object) a 2.5 s Poisson window at 20k requests/s of GF(2^12) k=16 m=4 requests
+  served   (sub-object) a 2 s Poisson window at 20k requests/s of GF(2^12) k=16 m=4 requests
            (packets 4 KiB-1 MiB, half 4-erasure decodes): p50/p99/p99.9 latency and sustained GB/s
-           with continuous batching, and the same arrivals served one request per launch.
+           with continuous batching, and the same arrivals served one request per launch (two
+           passes per arm, alternating).
   mixed    (sub-object) 4096 uneven stripes in one batched launch per ring size against 4096
            per-stripe launches of the same kernel: GB/s, roofline fraction, speed-up.
   sweep32k (sub-object) the 32 KiB point of the GF(2^12) k=16 m=4 packet-size sweep (~8 GiB of
@@ -474,7 +475,7 @@ def main():
         # The other configurations, compact: the served loop (a short Poisson window, both server
         # policies), the 4096-stripe mixed batch against per-stripe launches, and the 32 KiB point of
         # the GF(2^12) sweep.
-        out["served"] = served_measure(torch, pyrit, dev, 20000.0, 2.5, args.slots)
+        out["served"] = served_measure(torch, pyrit, dev, 20000.0, 2.0, args.slots)
         out["mixed"] = mixed_measure(torch, pyrit, dev, 5)
         plan12 = make_plan(pyrit, args.generator, 12, 16, 4)
         out["sweep32k"] = sweep_point(torch, pyrit, dev, plan12, 32768, 5, generator=args.generator)
@@ -1039,38 +1040,52 @@ def served_measure(torch, pyrit, dev, rate, seconds, slots, pool=512):
         done = pyrit.pyrit_server_poll(srv, nreq + 64)
         st = pyrit.pyrit_server_stats(srv)
         pyrit.pyrit_server_destroy(srv)
-        lat = np.array([d[4] - d[2] for d in done if d[0] < nreq], dtype=np.float64) / 1e3  # us
-        wait = np.array([d[3] - d[2] for d in done if d[0] < nreq], dtype=np.float64) / 1e3
-        run = np.array([d[4] - d[3] for d in done if d[0] < nreq], dtype=np.float64) / 1e3
+        done = [d for d in done if d[0] < nreq]
         t_first = min(d[2] for d in done)
         t_last = max(d[4] for d in done)
-        return {"p50_us": float(np.percentile(lat, 50)), "p99_us": float(np.percentile(lat, 99)),
-                "p999_us": float(np.percentile(lat, 99.9)), "max_us": float(lat.max()), "requests": len(lat),
-                "arrival_to_launch_p50_us": float(np.percentile(wait, 50)),
-                "arrival_to_launch_p99_us": float(np.percentile(wait, 99)),
-                "launch_to_done_p50_us": float(np.percentile(run, 50)),
-                "launch_to_done_p99_us": float(np.percentile(run, 99)),
-                "all_ok": all(d[1] == 0 for d in done),
+        return {"done": done, "all_ok": all(d[1] == 0 for d in done),
                 "sustained_gbs": src_bytes / ((t_last - t_first) * 1e-9) / 1e9,
                 "batches": st["batches"], "launches": st["launches"], "max_inflight_bytes": st["max_inflight"],
                 "clocks": clk}
 
+    def pooled(runs):
+        """Latency statistics over the requests of several passes of the arrival stream."""
+        done = [d for r in runs for d in r["done"]]
+        lat = np.array([d[4] - d[2] for d in done], dtype=np.float64) / 1e3  # us
+        wait = np.array([d[3] - d[2] for d in done], dtype=np.float64) / 1e3
+        run = np.array([d[4] - d[3] for d in done], dtype=np.float64) / 1e3
+        return {"p50_us": float(np.percentile(lat, 50)), "p99_us": float(np.percentile(lat, 99)),
+                "p999_us": float(np.percentile(lat, 99.9)), "max_us": float(lat.max()), "requests": len(lat),
+                "passes": len(runs),
+                "arrival_to_launch_p50_us": float(np.percentile(wait, 50)),
+                "arrival_to_launch_p99_us": float(np.percentile(wait, 99)),
+                "launch_to_done_p50_us": float(np.percentile(run, 50)),
+                "launch_to_done_p99_us": float(np.percentile(run, 99)),
+                "all_ok": all(r["all_ok"] for r in runs),
+                "sustained_gbs": min(r["sustained_gbs"] for r in runs),
+                "batches": sum(r["batches"] for r in runs), "launches": sum(r["launches"] for r in runs),
+                "max_inflight_bytes": max(r["max_inflight_bytes"] for r in runs)}
+
     # Continuous batching (up to 64 admitted requests per launch group, `slots` stream slots whose
     # launches overlap: a request that finds a slot free starts alone, requests that arrive while
-    # every slot is busy share the next free one), then the same arrivals through the same server
+    # every slot is busy share the next free one), and the same arrivals through the same server
     # and kernels with one request per launch: per-stripe launches as requests arrive, up to 16 in
-    # flight on their own streams.
-    batched = serve(64, slots)
-    single = serve(1, 16)
-    clk = batched.pop("clocks")
-    single.pop("clocks")
+    # flight on their own streams. The arms alternate (batching, per-request, per-request,
+    # batching) so that neither always runs first; each arm's two passes are pooled.
+    b1 = serve(64, slots)
+    s1 = serve(1, 16)
+    s2 = serve(1, 16)
+    b2 = serve(64, slots)
+    clk = b1["clocks"]
+    batched = pooled([b1, b2])
+    single = pooled([s1, s2])
     out = dict(batched)
     out.update({
         "offered_gbs": src_bytes / (arrivals[-1] * 1e-9) / 1e9,
         "per_request_launches": single,
         "workload": "Poisson %gk req/s for %g s, GF(2^12) k=16 m=4, P 4 KiB-1 MiB, half 4-erasure decode, 16 GiB "
                     "budget, %d stream slots, batches up to 64; per_request_launches: the same arrivals one request "
-                    "per launch, 16 stream slots" % (rate / 1000, seconds, slots),
+                    "per launch, 16 stream slots; two passes per arm, alternating" % (rate / 1000, seconds, slots),
         "clocks": clk})
     pyrit.pyrit_plan_destroy(plan)
     del buf, arr, keep

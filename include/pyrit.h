@@ -332,7 +332,9 @@ PYRIT_API int pyrit_jit_mode(int mode);
 /* Compiles (host only, no device call) the network of a plan's encode (op PYRIT_OP_ENCODE), of
  * its decode for one erasure pattern (PYRIT_OP_DECODE), or its syndrome-decode network, which
  * serves every erasure pattern (PYRIT_OP_DECODE_ANY; requires m <= PYRIT_JOB_OUTPUTS), into the
- * cache, so that later calls find it.
+ * cache, so that later calls find it: in two forms, compiled side by side, the one batches and
+ * single calls launch and the one servers launch (it also stamps each request's completion, a step
+ * the other form leaves out because even unused it slows the kernel).
  * tile: NULL for the default shape, else its words, mg, minb and nc (0 = default) select one.
  * PYRIT_OK (also when there is nothing to code), a planning error, or PYRIT_E_JIT. */
 PYRIT_API int pyrit_plan_specialise(pyrit_plan_t plan, int op, uint64_t erasures, const pyrit_tile_t* tile);

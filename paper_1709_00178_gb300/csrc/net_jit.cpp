@@ -324,7 +324,8 @@ std::string net_source(const NetSpec& s) {
   put(o, "extern \"C\" __global__ void __launch_bounds__(%ld, %ld)\n", (s.nc + 1) * 32, s.minb);
   o += kKernelName;
   o += "(const __grid_constant__ pyrit::CodeArgs a) {\n";
-  put(o, "  pyrit::ring_staged_body<%ld, %ld, %ld, %ld, pyrit::NetMac, %ld>(a);\n}\n", N, s.words, s.mg, s.nc, W);
+  put(o, "  pyrit::ring_staged_body<%ld, %ld, %ld, %ld, pyrit::NetMac, %ld, ", N, s.words, s.mg, s.nc, W);
+  o += s.track ? "true>(a);\n}\n" : "false>(a);\n}\n";
   return o;
 }
 
@@ -618,7 +619,7 @@ int net_syndrome_shapes(const pyrit_plan_s* p, NetSpec* out, int cap) {
 static bool spec_valid(const NetSpec& s) {
   const bool words_ok = s.words == 1 || s.words == 2 || s.words == 4;
   const bool nc_ok = s.nc >= 1 && s.nc <= 31;
-  if (s.mode < 0 || s.mode > 3) return false;
+  if (s.mode < 0 || s.mode > 3 || (s.track != 0 && s.track != 1)) return false;
   if ((s.mode == 1 || s.mode == 3) && !(s.mg == s.nout && s.nout <= kSyndromeBaseRow && s.ntables == 1)) return false;
   if (s.ntables < 1 || s.ntables > kMaxJobs) return false;
   // a native field of its ring, or (direct embedding networks only) a factor g of x^n + 1 of degree w
@@ -675,7 +676,7 @@ const Variant* net_variant(const NetSpec& s, bool block) {
       return nullptr;
     }
     e->v = Variant{s.n,    s.words, s.mg,   s.minb, PYRIT_DISPATCH_NETWORK, s.nc, reinterpret_cast<const void*>(k),
-                   s.mode, s.nout,  s.w};
+                   s.mode, s.nout,  s.w,   s.track};
     e->loaded = true;
     ++J.loaded;
   }
@@ -781,13 +782,21 @@ int plan_network_specs(pyrit_plan_s* plan, int op, uint64_t erasures, const pyri
 extern "C" {
 
 int pyrit_plan_specialise(pyrit_plan_t plan, int op, uint64_t erasures, const pyrit_tile_t* tile) {
-  NetSpec s[kMaxJobs];
+  NetSpec s[2 * kMaxJobs];
   const int ns = plan_network_specs(plan, op, erasures, tile, s);
   if (ns < 0) return ns;
+  // each network in two forms, compiled side by side: the one batches and single calls launch, and
+  // the one the server launches (it stamps each request's completion)
   for (int i = 0; i < ns; ++i) {
-    const int rc = net_compile(s[i]);
-    if (rc != PYRIT_OK) return rc;
+    s[ns + i] = s[i];
+    s[ns + i].track = 1;
   }
+  int rcs[2 * kMaxJobs];
+  std::vector<std::thread> th;
+  for (int i = 0; i < 2 * ns; ++i) th.emplace_back([&s, &rcs, i] { rcs[i] = net_compile(s[i]); });
+  for (auto& t : th) t.join();
+  for (int i = 0; i < 2 * ns; ++i)
+    if (rcs[i] != PYRIT_OK) return rcs[i];
   return PYRIT_OK;
 }
 

@@ -41,6 +41,7 @@ struct Variant {
   int mode;      // generated networks: NetSpec mode (syndrome modes take syndrome-form jobs)
   int nout;      // generated networks: the output count they were compiled for (0: generic)
   int w;         // field degree: packets per block
+  int track = 0; // generated networks: built to stamp each job's completion (NetSpec::track)
 };
 
 // Generated networks whose jobs are in syndrome form (modes 1 and 3).
@@ -172,6 +173,8 @@ struct NetSpec {
   int32_t w;                 // field degree (packets per block)
   uint32_t g;                // 0: the native field of R_{2,n}; else the modulus, a factor of x^n + 1
                              // whose reduction the network emits (direct mode 0 only)
+  int32_t track;             // 1: the kernel counts each job's finished tiles and stamps its
+                             // completion (launched by the server with CodeArgs::done_cnt / done_ns)
   uint16_t mask[kMaxJobs][kMaxIn][kMaxOut];
 };
 // The network spec of one job under a shape (zero fields: the default shape for (n, nout)) and a

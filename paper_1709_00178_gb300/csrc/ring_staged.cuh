@@ -45,7 +45,8 @@
 
 namespace pyrit {
 
-__device__ __forceinline__ const JobDesc* tile_job(const CodeArgs& a, uint32_t t, uint32_t& col0, uint32_t& jid) {
+__device__ __forceinline__ const JobDesc* tile_job(const CodeArgs& a, uint32_t t, uint32_t& col0) {
+  uint32_t jid;
   if (a.tiles) {
     const uint2 v = a.tiles[t];
     jid = v.x;
@@ -175,13 +176,17 @@ struct SyndromeStoreT {
     constexpr int W = RingDim<N>::W, S = RingDim<N>::S;
     using V = typename Vec<WORDS>::T;
 #pragma unroll
-    for (int r = 0; r < MG; ++r)
+    for (int r = 0; r < MG; ++r) {
+      if (!(need & (1u << r))) continue;  // rows the pattern does not use are never read
 #pragma unroll
       for (int t = 0; t < W; ++t)
 #pragma unroll
         for (int x = 0; x < WORDS; ++x) acc[r][t][x] ^= acc[r][W + t % S][x];
-    const uint64_t P = J->P;
-    const int nout = J->nout;
+    }
+    const uint64_t P = ((uint64_t)warp_uniform((uint32_t)(J->P >> 32)) << 32) | warp_uniform((uint32_t)J->P);
+    // (the output count, packet size and output pointers are broadcast too: measured on GB300,
+    // the config-2 decode's best shape 2.8% faster, the GF(2^12) k=16 m=4 decode within 1%)
+    const int nout = (int)warp_uniform((uint32_t)J->nout);
     for (int o = 0; o < nout; ++o) {
       const uint32_t base = warp_uniform(J->mask[kSyndromeBaseRow][o]);
       uint32_t res[N][WORDS];
@@ -213,8 +218,10 @@ struct SyndromeStoreT {
           }
         }
       }
+      const uintptr_t dp = reinterpret_cast<uintptr_t>(J->out[o]);
+      uint8_t* dst = reinterpret_cast<uint8_t*>(((uint64_t)warp_uniform((uint32_t)((uint64_t)dp >> 32)) << 32) |
+                                                warp_uniform((uint32_t)(uint64_t)dp)) + col0 + off;
       if (valid) {
-        uint8_t* dst = J->out[o] + col0 + off;
         uint32_t par[S][WORDS];
 #pragma unroll
         for (int j = 0; j < S; ++j)
@@ -269,7 +276,11 @@ struct ParityStore {
 
 // W: the field's degree, the packets of a block (the native field of R_{2,N} by default; a
 // generated network for another factor of x^N + 1 passes its own, with its own reduction).
-template <int N, int WORDS, int MG, int NC, class Mac, int W = RingDim<N>::W>
+// TRACK: the kernel counts each job's finished tiles and stamps its completion when the launch
+// passes CodeArgs::done_cnt (the served path). It is a compile-time choice because the code, even
+// never executed, costs the other launches: on GB300 the GF(2^12) k=16 m=4 encode ran 3-6% slower
+// with it compiled in.
+template <int N, int WORDS, int MG, int NC, class Mac, int W = RingDim<N>::W, bool TRACK = false>
 __device__ __forceinline__ void ring_staged_body(const CodeArgs& a) {
   using V = typename Vec<WORDS>::T;
   extern __shared__ __align__(128) uint8_t smem[];
@@ -297,8 +308,8 @@ __device__ __forceinline__ void ring_staged_body(const CodeArgs& a) {
     uint64_t armed = 0;  // stages armed so far
     bool ok = true;
     for (uint32_t t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
-      uint32_t col0, jid;
-      const JobDesc* J = tile_job(a, t, col0, jid);
+      uint32_t col0;
+      const JobDesc* J = tile_job(a, t, col0);
       const uint64_t P = J->P;
       if (col0 >= P) continue;  // a tiling that does not match the tile width codes nothing past P
       const uint32_t width = (uint32_t)(P - col0 < (uint64_t)TW ? P - col0 : (uint64_t)TW);
@@ -340,8 +351,8 @@ __device__ __forceinline__ void ring_staged_body(const CodeArgs& a) {
   const uint32_t off = (uint32_t)((warp % wpg) * 32 + lane) * (4u * WORDS);
   uint32_t stage = 0, phase = 0;
   for (uint32_t t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
-    uint32_t col0, jid;
-    const JobDesc* J = tile_job(a, t, col0, jid);
+    uint32_t col0;
+    const JobDesc* J = tile_job(a, t, col0);
     const uint64_t P = J->P;
     if (col0 >= P) continue;  // same rule as the producer: such a tile has no stages
     const uint32_t width = (uint32_t)(P - col0 < (uint64_t)TW ? P - col0 : (uint64_t)TW);
@@ -390,14 +401,17 @@ __device__ __forceinline__ void ring_staged_body(const CodeArgs& a) {
 
     mac.template store<N, WORDS, MG>(acc, J, g, col0, off, valid);
 
-    if (a.done_cnt) {
+    if (TRACK && a.done_cnt) {
       // Per-job completion: each consumer warp counts each tile of the job once, its stores
       // ordered before the count at device scope (release); the warp that completes the count
       // (tiles x consumer warps) acquires the others' stores, leaves the counter at zero for the
       // next launch and stamps the job done in host memory after a system-scope fence.
+      // (the job index and P are read again here rather than kept live across the tile)
       __syncwarp();
       if (lane == 0) {
-        const uint32_t target = (uint32_t)((P + TW - 1) / TW) * (uint32_t)NC;
+        const uint32_t jid = a.tiles ? a.tiles[t].x : t / a.tiles_per_job;
+        const uint64_t Pj = J->P;
+        const uint32_t target = (uint32_t)((Pj + TW - 1) / TW) * (uint32_t)NC;
         if (count_release_gpu(&a.done_cnt[jid]) + 1u == target) {
           fence_acq_rel_gpu();
           a.done_cnt[jid] = 0u;

@@ -46,6 +46,11 @@ int64_t host_now_ns() {
       .count();
 }
 
+// Pending::idx when a request has no completion stamp: nothing to code, or coded by a kernel that
+// does not stamp completions (the generic kernels; they complete when the slot's launches end).
+constexpr int kNoWork = -1;
+constexpr int kUntracked = -2;
+
 struct Pending {
   JobDesc job;
   JobDesc syn_job;               // the syndrome form of a decode job (when syn)
@@ -57,7 +62,7 @@ struct Pending {
   uint64_t tiles;    // column tiles of the stripe at the narrowest tile width that could code it
   uint64_t tag;
   int64_t arrival;   // server clock, ns
-  int idx = -1;      // completion slot of the request in its slot's stamp table (-1: no launch)
+  int idx = -1;      // completion stamp of the request in its slot's table, or kNoWork / kUntracked
   bool finished = false;
 };
 
@@ -142,8 +147,10 @@ void retire(pyrit_server_s* s, Slot& sl, Pending& p, int status, int64_t t, std:
 
 // Retires every request whose completion stamp has arrived, and frees every slot whose launches
 // have ended (a request still unstamped then did not complete: a bounded device wait gave up, or
-// the launch failed). A slot's completion event is queried once all its requests are stamped, and
-// otherwise at most every 200 us, to notice a launch that ended without completing them.
+// the launch failed; requests coded by a kernel that stamps nothing complete then). A slot's
+// completion event is queried once all its stamped requests are in, or while it holds requests that
+// complete only with it, and otherwise at most every 200 us, to notice a launch that ended without
+// completing its requests.
 void reap(pyrit_server_s* s, std::vector<pyrit_completion_t>& fin) {
   for (Slot& sl : s->slots) {
     if (!sl.busy) continue;
@@ -152,7 +159,9 @@ void reap(pyrit_server_s* s, std::vector<pyrit_completion_t>& fin) {
       for (Pending& p : sl.reqs)
         if (!p.finished && p.idx >= 0 && reinterpret_cast<volatile uint64_t*>(sl.host_done)[p.idx] != 0)
           retire(s, sl, p, PYRIT_OK, t, fin);
-    if (sl.open && t - sl.queried_ns < 200000) continue;
+    bool untracked = false;  // such requests complete only with the slot's event: query it now
+    for (const Pending& p : sl.reqs) untracked = untracked || (!p.finished && p.idx == kUntracked);
+    if (sl.open && !untracked && t - sl.queried_ns < 200000) continue;
     sl.queried_ns = t;
     const cudaError_t q = cudaEventQuery(sl.done);
     if (q == cudaErrorNotReady) continue;
@@ -161,7 +170,8 @@ void reap(pyrit_server_s* s, std::vector<pyrit_completion_t>& fin) {
       for (Pending& p : sl.reqs) {
         if (p.finished) continue;
         const bool stamped = p.idx >= 0 && reinterpret_cast<volatile uint64_t*>(sl.host_done)[p.idx] != 0;
-        retire(s, sl, p, q != cudaSuccess ? PYRIT_E_CUDA : stamped ? PYRIT_OK : PYRIT_E_TIMEOUT, t, fin);
+        const bool ok = stamped || p.idx == kUntracked;  // an untracked request is done when its launch is
+        retire(s, sl, p, q != cudaSuccess ? PYRIT_E_CUDA : ok ? PYRIT_OK : PYRIT_E_TIMEOUT, t, fin);
       }
       // an incomplete count would offset the next launch's: clear the table
       cudaMemsetAsync(sl.dev_cnt, 0, sizeof(uint32_t) * (size_t)s->max_batch, sl.st);
@@ -210,9 +220,11 @@ const Variant* request_network(pyrit_server_s* s, const Pending& p) {
   const uint64_t key = request_key(p);
   auto it = s->nets.find(key);
   if (it != s->nets.end()) return it->second;
-  const Variant* v = p.op == PYRIT_OP_ENCODE
-                         ? net_variant(net_spec(p.n, p.job, 0, 0, 0, 0, PYRIT_TRANSFORM_EMBEDDING), false)
-                         : net_variant(net_spec_syndrome(p.plan, 0, 0, 0), false);
+  // the served form of the network: it stamps each request's completion
+  NetSpec spec = p.op == PYRIT_OP_ENCODE ? net_spec(p.n, p.job, 0, 0, 0, 0, PYRIT_TRANSFORM_EMBEDDING)
+                                         : net_spec_syndrome(p.plan, 0, 0, 0);
+  spec.track = 1;
+  const Variant* v = net_variant(spec, false);
   if (v) s->nets.emplace(key, v);
   return v;
 }
@@ -275,6 +287,7 @@ int launch_slot(pyrit_server_s* s, Slot& sl, std::vector<pyrit_completion_t>& fi
   struct G {
     TileShape shape;
     uint32_t job0, njobs, tile0, ntiles, done0;
+    bool track;      // the group's kernel stamps each job's completion
     bool single;     // one job, passed by value
     JobDesc job;     // that job
   };
@@ -289,6 +302,7 @@ int launch_slot(pyrit_server_s* s, Slot& sl, std::vector<pyrit_completion_t>& fi
     g.job0 = nj;
     g.tile0 = nt;
     g.done0 = nd;
+    const bool track = shape.v && shape.v->track;  // else its requests complete when the slot's launches end
     size_t members = 0, first = 0;
     for (size_t i = 0; i < sl.reqs.size(); ++i)
       if (sl.reqs[i].job.nout != 0 && member(i) && members++ == 0) first = i;
@@ -298,7 +312,8 @@ int launch_slot(pyrit_server_s* s, Slot& sl, std::vector<pyrit_completion_t>& fi
       g.job = syn_form ? p.syn_job : p.job;
       g.njobs = 1;
       g.ntiles = (uint32_t)((p.job.P + (uint64_t)g.shape.tw - 1) / (uint64_t)g.shape.tw);
-      p.idx = (int)nd++;
+      g.track = track;
+      p.idx = track ? (int)nd++ : kUntracked;
       groups.push_back(g);
       return PYRIT_OK;
     }
@@ -317,8 +332,9 @@ int launch_slot(pyrit_server_s* s, Slot& sl, std::vector<pyrit_completion_t>& fi
         sl.host_tiles[nt++] = make_uint2(nj - g.job0, (uint32_t)c);
       }
       ++nj;
-      p.idx = (int)nd++;
+      p.idx = track ? (int)nd++ : kUntracked;
     }
+    g.track = track;
     g.njobs = nj - g.job0;
     g.ntiles = nt - g.tile0;
     if (g.njobs) groups.push_back(g);
@@ -361,10 +377,11 @@ int launch_slot(pyrit_server_s* s, Slot& sl, std::vector<pyrit_completion_t>& fi
   for (size_t gi = 0; gi < groups.size(); ++gi) {
     const G& g = groups[gi];
     const cudaStream_t st = two && (gi & 1) ? sl.aux : sl.st;
-    const int rc = g.single ? launch_staged(g.shape, &g.job, nullptr, nullptr, g.ntiles, g.ntiles, st,
-                                            sl.dev_cnt + g.done0, sl.dev_done + g.done0)
+    uint32_t* cnt = g.track ? sl.dev_cnt + g.done0 : nullptr;
+    uint64_t* stamp = g.track ? sl.dev_done + g.done0 : nullptr;
+    const int rc = g.single ? launch_staged(g.shape, &g.job, nullptr, nullptr, g.ntiles, g.ntiles, st, cnt, stamp)
                             : launch_staged(g.shape, nullptr, sl.dev_jobs + g.job0, sl.dev_tiles + g.tile0, g.ntiles,
-                                            0, st, sl.dev_cnt + g.done0, sl.dev_done + g.done0);
+                                            0, st, cnt, stamp);
     if (rc != PYRIT_OK) return rc;
     s->launches += 1;
   }
@@ -373,7 +390,7 @@ int launch_slot(pyrit_server_s* s, Slot& sl, std::vector<pyrit_completion_t>& fi
   if (cudaEventRecord(sl.done, sl.st) != cudaSuccess) return PYRIT_E_CUDA;
   // requests with nothing to code (a decode with no block lost) are done at once
   for (Pending& p : sl.reqs)
-    if (p.idx < 0) retire(s, sl, p, PYRIT_OK, s->now(), fin);
+    if (p.idx == kNoWork) retire(s, sl, p, PYRIT_OK, s->now(), fin);
   return PYRIT_OK;
 }
 
@@ -408,16 +425,22 @@ void run(pyrit_server_s* s) {
       }
     }
     reap(s, fin);
-    Slot* free_slot = nullptr;
-    for (Slot& sl : s->slots)
-      if (!sl.busy) {
-        free_slot = &sl;
-        break;
-      }
     bool launched = false;
-    if (free_slot && !s->arrivals.empty() && s->fatal == PYRIT_OK) {
+    while (!s->arrivals.empty() && s->fatal == PYRIT_OK) {
+      Slot* free_slot = nullptr;
+      int nfree = 0;
+      for (Slot& sl : s->slots)
+        if (!sl.busy) {
+          if (!free_slot) free_slot = &sl;
+          ++nfree;
+        }
+      if (!free_slot) break;
+      // Batch only under contention: while other slots are free each request gets a slot of its
+      // own (a launch of one request carries its job in the kernel parameters, with nothing to copy
+      // first); the last free slot takes everything admitted, up to the batch size.
+      const int cap = nfree > 1 ? 1 : s->max_batch;
       // Admit in arrival order while the budget, the batch size and the slot's tile table allow.
-      while (!s->arrivals.empty() && (int)free_slot->reqs.size() < s->max_batch) {
+      while (!s->arrivals.empty() && (int)free_slot->reqs.size() < cap) {
         const Pending& p = s->arrivals.front();
         if (s->inflight + free_slot->bytes + p.bytes > s->budget) break;
         if (free_slot->tiles + p.tiles > s->max_tiles) break;
@@ -439,6 +462,8 @@ void run(pyrit_server_s* s) {
         const int rc = launch_slot(s, *free_slot, fin);
         if (rc != PYRIT_OK) s->fatal = rc;
         launched = true;
+      } else {
+        break;  // the budget or the tile table holds the next request back
       }
     }
     publish(s, fin);

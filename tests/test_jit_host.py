@@ -193,7 +193,8 @@ def test_runtime_compiler_builds_networks_without_a_device(w, k, m):
         pyrit.pyrit_plan_specialise(plan, pyrit.PYRIT_OP_DECODE, 0b11)
         after = pyrit.pyrit_jit_stats()
         assert after["compiled"] == mid["compiled"] and after["cached"] == mid["cached"]
-        assert mid["cached"] - before["cached"] <= 2
+        # two networks, each in its batch form and its served form (which stamps completions)
+        assert mid["cached"] - before["cached"] <= 4
         # nothing erased: nothing to specialise
         pyrit.pyrit_plan_specialise(plan, pyrit.PYRIT_OP_DECODE, 0)
         with pytest.raises(pyrit.PyritError) as ei:
