@@ -80,9 +80,11 @@ int pyrit_decode(pyrit_plan_t plan, void* const* blocks, uint64_t erasures, size
   // where the decode is one job.
   if (e.syn_ok && nj == 1 && job_is_staged(jobs[0])) {
     const bool block = network_only(plan);
-    if (const Variant* net = net_variant(net_spec_syndrome(plan, 0, 0, 0), block)) {
-      JobDesc sj;
-      make_syndrome_job(plan, e, blocks, P, &sj);
+    JobDesc sj;
+    make_syndrome_job(plan, e, blocks, P, &sj);
+    // the network's all-rows body when this pattern needs every parity row
+    const int allrows = sj.mask[kSyndromeNeedRow][0] == (1u << plan->m) - 1u ? 1 : 0;
+    if (const Variant* net = net_variant(net_spec_syndrome(plan, 0, 0, 0, allrows), block)) {
       TileShape sh;
       shape_for_variant(net, plan->m, ShapeHint(), &sh);
       const uint32_t tpj = tiles_for(P, sh);

@@ -304,8 +304,22 @@ std::string net_source(const NetSpec& s) {
         emit_rows(o, rows, temps, W, N);
         o += "        }\n";
       } else {
-        // syndrome networks guard each parity row with one warp-uniform test of the tile's
-        // needed rows, so terms are shared within a row only
+        // Syndrome networks: when the tile's pattern needs every parity row (always when m blocks
+        // are lost) one body updates all rows, with terms shared across rows as in the encode;
+        // otherwise each parity row is guarded by one warp-uniform test of the needed rows, and
+        // terms are shared within a row only.
+        if (s.allrows) {
+          std::vector<XorRow> all;
+          for (auto& v : slot) all.insert(all.end(), v.begin(), v.end());
+          std::vector<XorTemp> all_temps;
+          share_terms(all, N, &all_temps);
+          put(o, "        if (need == %ldu) {\n#pragma unroll\n        for (int x = 0; x < WORDS; ++x) {\n",
+              (1L << s.mg) - 1);
+          emit_rows(o, all, all_temps, W, N);
+          o += "        }\n        } else {\n";
+        } else {
+          o += "        {\n";
+        }
         int next_id = N;  // temporaries are numbered across the case's blocks
         for (int ii = 0; ii < s.mg; ++ii) {
           if (slot[ii].empty()) continue;
@@ -316,6 +330,7 @@ std::string net_source(const NetSpec& s) {
           emit_rows(o, slot[ii], temps, W, N);
           o += "        }\n        }\n";
         }
+        o += "        }\n";
       }
       o += "      } break;\n";
     }
@@ -579,13 +594,14 @@ NetSpec net_spec(int n, const JobDesc& job, int words, int mg, int minb, int nc,
   return net_spec_tables(n, &t, 1, words, mg, minb, nc, transform, g);
 }
 
-NetSpec net_spec_syndrome(const pyrit_plan_s* p, int words, int minb, int nc) {
+NetSpec net_spec_syndrome(const pyrit_plan_s* p, int words, int minb, int nc, int allrows) {
   NetSpec s;
   std::memset(&s, 0, sizeof(s));
   NetSpec def[1];
   if (shapes_for(p->n, p->m, true, def, 1) == 1) s = def[0];
   s.n = p->n;
   s.mode = p->transform == PYRIT_TRANSFORM_PARITY ? 3 : 1;
+  s.allrows = allrows ? 1 : 0;
   s.nin = p->k + p->m;
   s.nout = p->m;
   s.mg = p->m;
@@ -609,17 +625,18 @@ NetSpec net_spec_syndrome(const pyrit_plan_s* p, int words, int minb, int nc) {
   return s;
 }
 
-int net_syndrome_shapes(const pyrit_plan_s* p, NetSpec* out, int cap) {
+int net_syndrome_shapes(const pyrit_plan_s* p, NetSpec* out, int cap, int allrows) {
   NetSpec shapes[8];
   const int c = shapes_for(p->n, p->m, true, shapes, cap < 8 ? cap : 8);
-  for (int i = 0; i < c; ++i) out[i] = net_spec_syndrome(p, shapes[i].words, shapes[i].minb, shapes[i].nc);
+  for (int i = 0; i < c; ++i) out[i] = net_spec_syndrome(p, shapes[i].words, shapes[i].minb, shapes[i].nc, allrows);
   return c;
 }
 
 static bool spec_valid(const NetSpec& s) {
   const bool words_ok = s.words == 1 || s.words == 2 || s.words == 4;
   const bool nc_ok = s.nc >= 1 && s.nc <= 31;
-  if (s.mode < 0 || s.mode > 3 || (s.track != 0 && s.track != 1)) return false;
+  if (s.mode < 0 || s.mode > 3 || (s.track != 0 && s.track != 1) || (s.allrows != 0 && s.allrows != 1)) return false;
+  if (s.allrows && !(s.mode == 1 || s.mode == 3)) return false;
   if ((s.mode == 1 || s.mode == 3) && !(s.mg == s.nout && s.nout <= kSyndromeBaseRow && s.ntables == 1)) return false;
   if (s.ntables < 1 || s.ntables > kMaxJobs) return false;
   // a native field of its ring, or (direct embedding networks only) a factor g of x^n + 1 of degree w
@@ -782,20 +799,28 @@ int plan_network_specs(pyrit_plan_s* plan, int op, uint64_t erasures, const pyri
 extern "C" {
 
 int pyrit_plan_specialise(pyrit_plan_t plan, int op, uint64_t erasures, const pyrit_tile_t* tile) {
-  NetSpec s[2 * kMaxJobs];
+  NetSpec s[3 * kMaxJobs];
   const int ns = plan_network_specs(plan, op, erasures, tile, s);
   if (ns < 0) return ns;
-  // each network in two forms, compiled side by side: the one batches and single calls launch, and
-  // the one the server launches (it stamps each request's completion)
+  // each network in the forms later calls look for, compiled side by side: the one batches and
+  // single calls launch, the one the server launches (it stamps each request's completion), and for
+  // a syndrome-decode network also the form without the all-rows body (batches whose stripes mostly
+  // need fewer rows)
+  int total = ns;
   for (int i = 0; i < ns; ++i) {
-    s[ns + i] = s[i];
-    s[ns + i].track = 1;
+    s[total] = s[i];
+    s[total++].track = 1;
   }
-  int rcs[2 * kMaxJobs];
+  for (int i = 0; i < ns && total < 3 * kMaxJobs; ++i)
+    if (s[i].allrows) {
+      s[total] = s[i];
+      s[total++].allrows = 0;
+    }
+  int rcs[3 * kMaxJobs];
   std::vector<std::thread> th;
-  for (int i = 0; i < 2 * ns; ++i) th.emplace_back([&s, &rcs, i] { rcs[i] = net_compile(s[i]); });
+  for (int i = 0; i < total; ++i) th.emplace_back([&s, &rcs, i] { rcs[i] = net_compile(s[i]); });
   for (auto& t : th) t.join();
-  for (int i = 0; i < 2 * ns; ++i)
+  for (int i = 0; i < total; ++i)
     if (rcs[i] != PYRIT_OK) return rcs[i];
   return PYRIT_OK;
 }

@@ -175,6 +175,8 @@ struct NetSpec {
                              // whose reduction the network emits (direct mode 0 only)
   int32_t track;             // 1: the kernel counts each job's finished tiles and stamps its
                              // completion (launched by the server with CodeArgs::done_cnt / done_ns)
+  int32_t allrows;           // syndrome modes: 1 adds a first-phase body for tiles that need every
+                             // parity row (terms shared across rows), 0 keeps only the guarded rows
   uint16_t mask[kMaxJobs][kMaxIn][kMaxOut];
 };
 // The network spec of one job under a shape (zero fields: the default shape for (n, nout)) and a
@@ -191,9 +193,9 @@ inline uint32_t plan_net_g(const pyrit_plan_s* p) { return p->native ? 0u : p->g
 inline bool network_only(const pyrit_plan_s* p) { return p->transform == PYRIT_TRANSFORM_PARITY || !p->native; }
 // The syndrome-decode network spec of a plan, under its transform (requires k + m <= kMaxIn and
 // m <= kMaxOut; zero fields: default).
-NetSpec net_spec_syndrome(const pyrit_plan_s* p, int words, int minb, int nc);
+NetSpec net_spec_syndrome(const pyrit_plan_s* p, int words, int minb, int nc, int allrows = 1);
 // Candidate shapes of a plan's syndrome network, the default first.
-int net_syndrome_shapes(const pyrit_plan_s* p, NetSpec* out, int cap);
+int net_syndrome_shapes(const pyrit_plan_s* p, NetSpec* out, int cap, int allrows = 1);
 // Candidate shapes for (n, nout), the default first; returns how many were written (<= cap).
 int net_candidate_shapes(int n, int nout, NetSpec* out, int cap);
 // Run-time compilation policy (PYRIT_JIT_*).

@@ -33,17 +33,29 @@ def _terms(text, temps):
 
 
 def _parse(src):
+    """Cases of a generated network: entries (slot, accumulator, source columns). A syndrome
+    network's case has two bodies: the one taken when every parity row is needed (its entries in
+    `cases_all`) and the per-row guarded one (in `cases`, with each entry's guard in `guards`)."""
     nin = int(re.search(r"switch \(g \* (\d+) \+ j\)", src).group(1))
     n, words, mg, nc = map(int, re.search(r"ring_staged_body<(\d+), (\d+), (\d+), (\d+),", src).groups())
-    cases, cur, temps, guard, guards = {}, None, {}, None, []
+    cases, cases_all, cur, temps, guard, guards, in_all, full = {}, {}, None, {}, None, [], False, None
     for line in src.splitlines():
         c = re.match(r"\s*case (\d+): \{", line)
         if c:
             cur = int(c.group(1))
             cases[cur] = []
-            temps, guard = {}, None
+            cases_all[cur] = []
+            temps, guard, in_all = {}, None, False
             continue
-        # syndrome networks: the accumulations of one parity row under a test of the needed rows
+        # syndrome networks: the body for a tile that needs every parity row, then the else branch
+        fa = re.match(r"\s*if \(need == (\d+)u\) \{", line)
+        if fa:
+            full, in_all = int(fa.group(1)), True
+            continue
+        if re.match(r"\s*\} else \{", line):
+            in_all, temps = False, {}  # the guarded body numbers its own temporaries
+            continue
+        # the accumulations of one parity row under a test of the needed rows
         gd = re.match(r"\s*if \(need & (\d+)u\) \{", line)
         if gd:
             guard = int(gd.group(1))
@@ -62,11 +74,15 @@ def _parse(src):
             a = b
         if a:
             assert cur is not None
-            cases[cur].append((int(a.group(1)), int(a.group(2)), _terms(a.groups()[-1], temps)))
-            guards.append((int(a.group(1)), guard))
+            entry = (int(a.group(1)), int(a.group(2)), _terms(a.groups()[-1], temps))
+            if in_all:
+                cases_all[cur].append(entry)
+            else:
+                cases[cur].append(entry)
+                guards.append((int(a.group(1)), guard))
         if "} break;" in line:
             cur = None
-    return dict(nin=nin, n=n, words=words, mg=mg, nc=nc, cases=cases, guards=guards)
+    return dict(nin=nin, n=n, words=words, mg=mg, nc=nc, cases=cases, guards=guards, cases_all=cases_all, full=full)
 
 
 def _w_of(n):
@@ -222,16 +238,19 @@ def test_syndrome_network_is_the_parity_check_product(w, k, m):
         pyrit.pyrit_plan_destroy(plan)
     assert net["nin"] == k + m and net["mg"] >= m
     assert net["guards"] and all(g == 1 << i for i, g in net["guards"])
-    for j in range(k + m):
-        entries = net["cases"][j]
-        for i in range(net["mg"]):
-            r = int(masks[i][j]) if (i < m and j < k) else int(j - k == i)
-            cols = _ring_columns(entries, i, n, w)
-            for q in range(w):
-                assert cols[q] == oracle.ring_mul(n, r, 1 << q), (j, i, q)
-                if i < m:
-                    u = int(C[i][j]) if j < k else r
-                    assert oracle.poly_mod(cols[q], oracle.field_poly(w)) == oracle.gf_mul_slow(w, u, 1 << q)
+    # the body taken when every row is needed: same products, terms shared across rows
+    assert net["full"] == (1 << net["mg"]) - 1
+    for body in (net["cases"], net["cases_all"]):
+        for j in range(k + m):
+            entries = body[j]
+            for i in range(net["mg"]):
+                r = int(masks[i][j]) if (i < m and j < k) else int(j - k == i)
+                cols = _ring_columns(entries, i, n, w)
+                for q in range(w):
+                    assert cols[q] == oracle.ring_mul(n, r, 1 << q), (j, i, q)
+                    if i < m:
+                        u = int(C[i][j]) if j < k else r
+                        assert oracle.poly_mod(cols[q], oracle.field_poly(w)) == oracle.gf_mul_slow(w, u, 1 << q)
 
 
 def _field_of_mask(w, mask):
@@ -531,13 +550,30 @@ def _xor_statements(src):
     return sum(1 for line in body.splitlines() if re.search(r"xor3\(| \^= | \^ ", line))
 
 
-@pytest.mark.parametrize("w,k,m,enc_max,syn_max", [(10, 10, 4, 620, 735), (12, 16, 4, 1500, 1680)])
-def test_shared_terms_reduce_the_xor_count(w, k, m, enc_max, syn_max):
+def _syndrome_xor_statements(src):
+    """XOR statements of a syndrome network's two first-phase bodies: (the one for tiles that need
+    every parity row, the per-row guarded one)."""
+    body = src[src.index("switch ("):]
+    counts, in_all = [0, 0], False
+    for line in body.splitlines():
+        if re.match(r"\s*if \(need == \d+u\) \{", line):
+            in_all = True
+        elif re.match(r"\s*\} else \{", line):
+            in_all = False
+        elif re.search(r"xor3\(| \^= | \^ ", line):
+            counts[0 if in_all else 1] += 1
+    return tuple(counts)
+
+
+@pytest.mark.parametrize("w,k,m,enc_max,syn_max,all_max", [(10, 10, 4, 620, 735, 660), (12, 16, 4, 1500, 1680, 1560)])
+def test_shared_terms_reduce_the_xor_count(w, k, m, enc_max, syn_max, all_max):
     """The generated networks form shared pairs and triples of source packets once: each XOR
     statement is one 32-bit three-input operation per column word, so their count per network is
     the coding work. Without sharing the plain Cauchy codes take sum(ceil(terms / 2)) statements:
     868 (encode) and 908 (syndrome first phase) for GF(2^10) k=10 m=4, 2200 and 2248 for GF(2^12)
-    k=16 m=4; with it at most the bounds here (614 / 728 and 1492 / 1672 when written)."""
+    k=16 m=4; with it at most the bounds here (614 / 728 and 1492 / 1672 when written). The syndrome
+    network's body for tiles that need every parity row shares terms across rows as the encode
+    does, and stays within all_max."""
     n = oracle.ring_size(w)
     C, masks = _oracle_parity_masks(w, k, m)
     unshared = 0
@@ -549,11 +585,12 @@ def test_shared_terms_reduce_the_xor_count(w, k, m, enc_max, syn_max):
     plan = pyrit.pyrit_plan_create(w, n, k, m)
     try:
         enc = _xor_statements(pyrit.pyrit_plan_network_source(plan, pyrit.PYRIT_OP_ENCODE))
-        syn = _xor_statements(pyrit.pyrit_plan_network_source(plan, pyrit.PYRIT_OP_DECODE_ANY))
+        syn_all, syn = _syndrome_xor_statements(pyrit.pyrit_plan_network_source(plan, pyrit.PYRIT_OP_DECODE_ANY))
     finally:
         pyrit.pyrit_plan_destroy(plan)
     assert enc <= enc_max and enc < 0.75 * unshared, (enc, unshared)
     assert syn <= syn_max, syn
+    assert syn_all <= all_max and syn_all < syn, (syn_all, syn)
 
 
 def test_committed_pairing_automata_match_their_generator():
