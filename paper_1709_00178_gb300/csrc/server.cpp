@@ -167,14 +167,16 @@ void reap(pyrit_server_s* s, std::vector<pyrit_completion_t>& fin) {
     if (q == cudaErrorNotReady) continue;
     if (sl.open) {
       // the launches ended: stamps written before the end are visible now
+      bool incomplete = false;
       for (Pending& p : sl.reqs) {
         if (p.finished) continue;
         const bool stamped = p.idx >= 0 && reinterpret_cast<volatile uint64_t*>(sl.host_done)[p.idx] != 0;
         const bool ok = stamped || p.idx == kUntracked;  // an untracked request is done when its launch is
+        incomplete = incomplete || !ok || q != cudaSuccess;
         retire(s, sl, p, q != cudaSuccess ? PYRIT_E_CUDA : ok ? PYRIT_OK : PYRIT_E_TIMEOUT, t, fin);
       }
       // an incomplete count would offset the next launch's: clear the table
-      cudaMemsetAsync(sl.dev_cnt, 0, sizeof(uint32_t) * (size_t)s->max_batch, sl.st);
+      if (incomplete) cudaMemsetAsync(sl.dev_cnt, 0, sizeof(uint32_t) * (size_t)s->max_batch, sl.st);
     }
     sl.reqs.clear();
     sl.bytes = 0;
