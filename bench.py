@@ -766,6 +766,7 @@ def run_fields(args):
     import oracle
     peak, _ = peak_hbm()
     stream = torch.cuda.Stream(device=dev)
+    nvtx = torch.cuda.nvtx
     P = 65536
     for (w, n, k, m, name) in [(4, 5, 8, 4, "GF(2^4) from the AOP on R_{2,5} (native)"),
                                (4, 15, 8, 4, "GF(2^4) from x^4+x+1 on R_{2,15}"),
