@@ -23,9 +23,9 @@ static_assert(sizeof(JobDesc) == 1632, "the job descriptor size is documented in
 inline int field_degree(int n) { return n == 9 ? 6 : n - 1; }
 static_assert(RingDim<9>::W == 6 && RingDim<11>::W == 10, "field_degree follows RingDim");
 
-// Dynamic shared memory of the staged kernel: S stages of W packets x tw bytes and 2 S mbarriers.
+// Dynamic shared memory of the staged kernel: S stages of W packets x tw bytes, 2 S + 1 mbarriers.
 inline size_t staged_smem_bytes(int stages, int w, int tw) {
-  return (size_t)stages * w * tw + 2 * sizeof(uint64_t) * stages;
+  return (size_t)stages * w * tw + sizeof(uint64_t) * (2 * stages + 1);
 }
 
 // A compiled instance of the staged ring kernel.

@@ -288,6 +288,7 @@ __device__ __forceinline__ void ring_staged_body(const CodeArgs& a) {
   uint8_t* buf = smem;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)S * W * TW);
   uint64_t* empty = full + S;
+  uint64_t* tdone = empty + S;  // consumer warps finished with the tile (served launches)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (threadIdx.x == 0) {
@@ -295,6 +296,7 @@ __device__ __forceinline__ void ring_staged_body(const CodeArgs& a) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], NC);
     }
+    mbar_init(tdone, NC);
     mbar_fence_init();
   }
   __syncthreads();
@@ -349,7 +351,7 @@ __device__ __forceinline__ void ring_staged_body(const CodeArgs& a) {
   const int wpg = NC / (int)a.groups;  // warps per output group
   const int g = warp / wpg;
   const uint32_t off = (uint32_t)((warp % wpg) * 32 + lane) * (4u * WORDS);
-  uint32_t stage = 0, phase = 0;
+  uint32_t stage = 0, phase = 0, tphase = 0;
   for (uint32_t t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
     uint32_t col0;
     const JobDesc* J = tile_job(a, t, col0);
@@ -402,16 +404,17 @@ __device__ __forceinline__ void ring_staged_body(const CodeArgs& a) {
     mac.template store<N, WORDS, MG>(acc, J, g, col0, off, valid);
 
     if (TRACK && a.done_cnt) {
-      // Per-job completion: each consumer warp counts each tile of the job once, its stores
-      // ordered before the count at device scope (release); the warp that completes the count
-      // (tiles x consumer warps) acquires the others' stores, leaves the counter at zero for the
-      // next launch and stamps the job done in host memory after a system-scope fence.
-      // (the job index and P are read again here rather than kept live across the tile)
+      // Per-job completion: each consumer warp releases its stores to the CTA on the tile barrier;
+      // consumer warp 0 acquires them all and counts the tile once at device scope (release); the
+      // count that completes the job (its tiles) acquires the other CTAs' stores, leaves the
+      // counter at zero for the next launch and stamps the job done in host memory after a
+      // system-scope fence.
       __syncwarp();
-      if (lane == 0) {
+      if (lane == 0) mbar_arrive(tdone);
+      if (warp == 0 && lane == 0 && mbar_wait(tdone, tphase, a.err, 4)) {
         const uint32_t jid = a.tiles ? a.tiles[t].x : t / a.tiles_per_job;
         const uint64_t Pj = J->P;
-        const uint32_t target = (uint32_t)((Pj + TW - 1) / TW) * (uint32_t)NC;
+        const uint32_t target = (uint32_t)((Pj + TW - 1) / TW);
         if (count_release_gpu(&a.done_cnt[jid]) + 1u == target) {
           fence_acq_rel_gpu();
           a.done_cnt[jid] = 0u;
@@ -420,6 +423,7 @@ __device__ __forceinline__ void ring_staged_body(const CodeArgs& a) {
           *reinterpret_cast<volatile uint64_t*>(&a.done_ns[jid]) = now ? now : 1ull;
         }
       }
+      tphase ^= 1u;
     }
   }
 }

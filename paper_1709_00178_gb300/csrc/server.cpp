@@ -50,6 +50,8 @@ int64_t host_now_ns() {
 // does not stamp completions (the generic kernels; they complete when the slot's launches end).
 constexpr int kNoWork = -1;
 constexpr int kUntracked = -2;
+// How long an idle scheduler polls for submissions before it sleeps on the condition variable.
+constexpr int64_t kIdleSpinNs = 500000;
 
 struct Pending {
   JobDesc job;
@@ -411,19 +413,27 @@ void publish(pyrit_server_s* s, std::vector<pyrit_completion_t>& fin) {
 void run(pyrit_server_s* s) {
   cudaSetDevice(s->device);
   std::vector<pyrit_completion_t> fin;
+  uint64_t taken = 0;  // requests moved out of the inbox
   while (true) {
     bool busy = false;
     for (const Slot& sl : s->slots) busy = busy || sl.busy;
     {
       std::unique_lock<std::mutex> lk(s->mu);
       if (!busy && s->arrivals.empty() && s->inbox.empty()) {
-        // idle: sleep until a submission or shutdown
+        // idle: poll for a while without the lock (a request that arrives soon is taken without a
+        // thread wake-up), then sleep until a submission or shutdown
+        lk.unlock();
+        const int64_t until = host_now_ns() + kIdleSpinNs;
+        while (s->submitted.load(std::memory_order_acquire) == taken && host_now_ns() < until)
+          std::this_thread::yield();
+        lk.lock();
         s->cv.wait(lk, [&] { return s->stop || !s->inbox.empty(); });
         if (s->inbox.empty()) break;  // stopped with nothing left to do
       }
       while (!s->inbox.empty()) {
         s->arrivals.push_back(s->inbox.front());
         s->inbox.pop_front();
+        ++taken;
       }
     }
     reap(s, fin);
