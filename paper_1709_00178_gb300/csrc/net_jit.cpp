@@ -498,10 +498,12 @@ int shapes_for(int n, int nout, bool syndrome, NetSpec* out, int cap) {
   // (words, consumer warps) pair on 2-3 GiB batches of GF(2^10) k=10 m=4 and k=4 m=8, GF(2^12)
   // k=16 m=4 and k=2 m=6, GF(16) k=8 m=4, GF(4) k=1 m=2): the first shape whose accumulators fit
   // the register budget is the default, the rest are the tuner's other candidates. Few outputs
-  // favour two words per thread; eight outputs fill the registers at one word. The GF(2^12)
-  // syndrome network defaults to one word and 19 warps (96 registers, 20 warps per SM): untuned,
-  // the k=16 m=4 4-erasure decode runs at 0.65 of HBM against 0.61 at 16 warps, and a served
-  // 1 MiB decode finishes in 73 us instead of 89 (two words and 11 warps, 0.68, needs a
+  // favour two words per thread; eight outputs fill the registers at one word. For GF(2^12)
+  // k=16 m=4 (re-measured with the current networks) the direct network runs best at two words
+  // and 11 warps (0.97 of HBM against 0.83 at one word and 16 warps; one 1 MiB stripe in 51 us
+  // instead of 57), and the syndrome network defaults to one word and 19 warps (96 registers, 20
+  // warps per SM): untuned, the 4-erasure decode runs at 0.65 against 0.61 at 16 warps, and a
+  // served 1 MiB decode finishes in 73 us instead of 89 (two words and 11 warps, 0.68, needs a
   // 4-stage ring, which the tuner finds).
   static const Shape4 n11_d[] = {{2, 0, 1, 11}, {2, 0, 1, 10}, {2, 0, 1, 12}, {2, 0, 1, 15},
                                  {1, 0, 1, 15}, {1, 0, 1, 16}, {1, 0, 1, 11}, {1, 1, 1, 16}};
@@ -511,8 +513,8 @@ int shapes_for(int n, int nout, bool syndrome, NetSpec* out, int cap) {
                                  {2, 0, 1, 10}, {1, 0, 1, 16}, {1, 0, 1, 15}, {1, 0, 1, 8}};
   static const Shape4 n11_sw[] = {{1, 0, 1, 15}, {1, 0, 1, 14}, {1, 0, 1, 12}, {1, 0, 1, 11},
                                   {1, 0, 1, 8}, {1, 0, 1, 16}, {2, 0, 1, 11}, {2, 0, 1, 8}};
-  static const Shape4 n13_d[] = {{1, 0, 1, 16}, {1, 0, 1, 15}, {1, 0, 1, 14}, {1, 0, 1, 11},
-                                 {2, 0, 1, 11}, {2, 0, 1, 8}, {1, 0, 1, 12}, {1, 1, 1, 16}};
+  static const Shape4 n13_d[] = {{2, 0, 1, 11}, {2, 0, 1, 10}, {1, 0, 1, 16}, {1, 0, 1, 19},
+                                 {1, 0, 1, 15}, {1, 0, 1, 14}, {2, 0, 1, 8}, {1, 1, 1, 16}};
   static const Shape4 n13_dw[] = {{1, 0, 1, 11}, {1, 0, 1, 12}, {1, 0, 1, 14}, {1, 0, 1, 15},
                                   {1, 0, 1, 8}, {1, 1, 1, 16}, {1, 0, 1, 16}, {2, 1, 1, 11}};
   static const Shape4 n13_s[] = {{1, 0, 1, 19}, {2, 0, 1, 11}, {1, 0, 1, 16}, {1, 0, 1, 15},
