@@ -76,3 +76,23 @@ def test_two_gloo_ranks_shard_time_and_aggregate():
     for r in range(world):
         for pat in res[r][5]:
             assert 1 <= bin(pat).count("1") <= 4 and pat < (1 << 14)
+
+
+def test_traffic_record_digest_tracks_the_kernel_sources(tmp_path, monkeypatch):
+    # The DRAM traffic record applies only while the sources that shape the batched coding kernels
+    # are the ones it was captured with: an edit to the device code changes the digest, an edit to
+    # the server (host code the bench's kernels never run) does not.
+    import shutil
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    csrc = tmp_path / "paper_1709_00178_gb300" / "csrc"
+    shutil.copytree(os.path.join(ROOT, "paper_1709_00178_gb300", "csrc"), csrc)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    d0 = bench.kernel_source_digest()
+    with open(csrc / "server.cpp", "a") as f:
+        f.write("\n// host-only edit\n")
+    assert bench.kernel_source_digest() == d0
+    with open(csrc / "ring_staged.cuh", "a") as f:
+        f.write("\n// device edit\n")
+    assert bench.kernel_source_digest() != d0
