@@ -460,7 +460,10 @@ PYRIT_API void pyrit_server_destroy(pyrit_server_t server);
  * allocating routine is called (on the host, a decoding matrix for an erasure pattern that a plan has
  * not seen is computed and kept in the plan's cache, as pyrit_decode does).
  * Set-up. The first call on each device, with that device current, looks up the array's device
- * address (cudaGetSymbolAddress); make that first call before any stream capture.
+ * address (cudaGetSymbolAddress).
+ * Capture. The call uploads its descriptors from static pageable host arrays that the next call
+ * rewrites, so it cannot be captured into a CUDA graph: on a stream that is capturing it returns
+ * PYRIT_E_INVALID_ARG before any device work (call it eagerly).
  * Sharing. Every call reuses the same array, which keeps the last call's contents; each call clears
  * the status words and rewrites the descriptors on `stream` before its launches. Calls whose work
  * overlaps on the GPU (for example on two streams at once) race on the array: order them on one

@@ -78,6 +78,14 @@ extern "C" int pyrit_code_stripes_noalloc(const pyrit_stripe_t* stripes, int cou
   if (count > kNaMaxStripes) return PYRIT_E_SCRATCH_LIMIT;
   if (count == 0) return PYRIT_OK;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  // The descriptors are uploaded from static pageable host arrays that the next call rewrites: a
+  // graph captured from this call could not replay it, so capture is refused.
+  cudaStreamCaptureStatus capture = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &capture) != cudaSuccess) {
+    cudaGetLastError();
+    return PYRIT_E_CUDA;
+  }
+  if (capture != cudaStreamCaptureStatusNone) return PYRIT_E_INVALID_ARG;
   std::lock_guard<std::mutex> lk(g_mu);
   uint8_t* scratch = nullptr;
   int rc = scratch_address(&scratch);

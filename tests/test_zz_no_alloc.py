@@ -151,3 +151,33 @@ def test_noalloc_status_reports_a_wait_that_ran_out(pyrit):
     finally:
         for p in plans.values():
             pyrit.pyrit_plan_destroy(p)
+
+
+def test_noalloc_refuses_stream_capture(pyrit):
+    # The call uploads its descriptors from host arrays the next call rewrites, so a captured graph
+    # could not replay it: on a capturing stream it must return PYRIT_E_INVALID_ARG before any
+    # device work (nothing captured, nothing written), and code normally again once capture ends.
+    plans = {(4, 4, 2): pyrit.pyrit_plan_create(4, 5, 4, 2)}
+    try:
+        specs = [(4, 4, 2, 4096, pyrit.PYRIT_OP_ENCODE, 0)]
+        offs, total = _layout(specs)
+        buf = torch.empty(total, dtype=torch.uint8, device="cuda")
+        pyrit.pyrit_synth_fill(buf.data_ptr(), total, 0xE55F)
+        stripes = _stripes(pyrit, plans, specs, buf.data_ptr(), offs)
+        s = torch.cuda.Stream()
+        torch.cuda.synchronize()
+        before = buf.clone()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            with pytest.raises(pyrit.PyritError) as err:
+                pyrit.pyrit_code_stripes_noalloc(stripes, s)
+        assert err.value.status == pyrit.PYRIT_E_INVALID_ARG
+        torch.cuda.synchronize()
+        assert torch.equal(buf, before)
+        pyrit.pyrit_code_stripes_noalloc(stripes, s)
+        torch.cuda.synchronize()
+        assert not torch.equal(buf, before)  # the parity blocks were written
+        assert pyrit.pyrit_noalloc_status() == (0, 0)
+    finally:
+        for p in plans.values():
+            pyrit.pyrit_plan_destroy(p)
