@@ -298,6 +298,17 @@ PYRIT_API int pyrit_batch_shape(pyrit_batch_t batch, int group, int* params_out)
 /* Frees the batch's device memory and graph (synchronises the device). */
 PYRIT_API void pyrit_batch_destroy(pyrit_batch_t batch);
 
+/* One-shot batched coding under the names of the hot path's boundary: pyrit_batch_create over the
+ * `count` stripes (automatic shapes), one pyrit_batch_run on `stream`, a wait for its launches, then
+ * pyrit_batch_destroy. Every stripe must carry PYRIT_OP_ENCODE (pyrit_encode_batch) or
+ * PYRIT_OP_DECODE (pyrit_decode_batch). Each call allocates and frees the batch's device tables and
+ * synchronises `stream`; a batch coded again and again belongs in pyrit_batch_create /
+ * pyrit_batch_run. Returns PYRIT_OK (also for count == 0), PYRIT_E_INVALID_ARG for a NULL array,
+ * a negative count or a stripe of the other operation (before any device work), the codes of
+ * pyrit_batch_create, or PYRIT_E_CUDA when the launches or the wait fail. */
+PYRIT_API int pyrit_encode_batch(const pyrit_stripe_t* stripes, int count, pyrit_stream_t stream);
+PYRIT_API int pyrit_decode_batch(const pyrit_stripe_t* stripes, int count, pyrit_stream_t stream);
+
 /* ---- plan-specialised networks (run-time compilation) ---------------------------------------
  *
  * The generic kernels test every bit of phi_S(u) at run time to decide which packet rotations to

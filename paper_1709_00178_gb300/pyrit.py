@@ -267,6 +267,8 @@ _BATCH_SIGS = {
     "pyrit_batch_run": (_i, [_vp, _vp, _i]),
     "pyrit_batch_stats": (_i, [_vp, _vp, _vp, _vp, _vp]),
     "pyrit_batch_destroy": (None, [_vp]),
+    "pyrit_encode_batch": (_i, [ctypes.POINTER(pyrit_stripe_t), _i, _vp]),
+    "pyrit_decode_batch": (_i, [ctypes.POINTER(pyrit_stripe_t), _i, _vp]),
     "pyrit_batch_tune": (_i, [_vp, _vp, _i]),
     "pyrit_tune_save": (_i, [ctypes.c_char_p]),
     "pyrit_tune_load": (_i, [ctypes.c_char_p]),
@@ -281,12 +283,7 @@ EXPORTS = EXPORTS + tuple(_BATCH_SIGS)
 def pyrit_batch_create(stripes, tile=None):
     """stripes: list of (plan, op, erasures, P, block_ptrs[k+m]); tile: None or dict of overrides
     (words, mg, minb, nc, dispatch, stages, ctas_per_sm). Returns an opaque batch handle."""
-    arr = (pyrit_stripe_t * max(1, len(stripes)))()
-    keep = []
-    for i, (plan, op, er, P, blocks) in enumerate(stripes):
-        ba = _ptr_array(blocks)
-        keep.append(ba)
-        arr[i] = pyrit_stripe_t(plan, op, er, P, ctypes.cast(ba, ctypes.POINTER(ctypes.c_void_p)))
+    arr, keep = _stripe_array(stripes)
     t = None
     if tile is not None:
         t = pyrit_tile_t(tile.get("words", 0), tile.get("mg", 0), tile.get("minb", 0), tile.get("nc", 0),
@@ -295,6 +292,28 @@ def pyrit_batch_create(stripes, tile=None):
     _check(_lib.pyrit_batch_create(arr, len(stripes), ctypes.byref(t) if t is not None else None, ctypes.byref(h)),
            "pyrit_batch_create")
     return h.value
+
+
+def _stripe_array(stripes):
+    arr = (pyrit_stripe_t * max(1, len(stripes)))()
+    keep = []
+    for i, (plan, op, er, P, blocks) in enumerate(stripes):
+        ba = _ptr_array(blocks)
+        keep.append(ba)
+        arr[i] = pyrit_stripe_t(plan, op, er, P, ctypes.cast(ba, ctypes.POINTER(ctypes.c_void_p)))
+    return arr, keep
+
+
+def pyrit_encode_batch(stripes, stream=None):
+    """One-shot batched encode of stripes (plan, PYRIT_OP_ENCODE, 0, P, block_ptrs[k+m]); waits."""
+    arr, keep = _stripe_array(stripes)
+    return _check(_lib.pyrit_encode_batch(arr, len(stripes), _stream(stream)), "pyrit_encode_batch")
+
+
+def pyrit_decode_batch(stripes, stream=None):
+    """One-shot batched decode of stripes (plan, PYRIT_OP_DECODE, erasures, P, block_ptrs[k+m]); waits."""
+    arr, keep = _stripe_array(stripes)
+    return _check(_lib.pyrit_decode_batch(arr, len(stripes), _stream(stream)), "pyrit_decode_batch")
 
 
 def pyrit_batch_run(batch, stream=None, graph=False):

@@ -221,6 +221,15 @@ def test_invalid_coding_calls_fail_before_device_work():
             pyrit.pyrit_encode(plan, fake[:3] + [0], fake[4:], 64)  # null block
         assert ei.value.status == pyrit.PYRIT_E_INVALID_ARG
         assert pyrit.pyrit_decode(plan, fake, 0, 64) == 0  # nothing erased: no work
+        # the one-shot batched calls take stripes of their own operation only
+        with pytest.raises(pyrit.PyritError) as ei:
+            pyrit.pyrit_encode_batch([(plan, pyrit.PYRIT_OP_DECODE, 0b1, 64, fake)])
+        assert ei.value.status == pyrit.PYRIT_E_INVALID_ARG
+        with pytest.raises(pyrit.PyritError) as ei:
+            pyrit.pyrit_decode_batch([(plan, pyrit.PYRIT_OP_DECODE, 0b1, 64, fake),
+                                      (plan, pyrit.PYRIT_OP_ENCODE, 0, 64, fake)])
+        assert ei.value.status == pyrit.PYRIT_E_INVALID_ARG
+        assert pyrit.pyrit_encode_batch([]) == 0 and pyrit.pyrit_decode_batch([]) == 0
     finally:
         pyrit.pyrit_plan_destroy(plan)
 

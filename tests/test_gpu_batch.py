@@ -108,6 +108,45 @@ def test_mixed_batch_encode_then_decode(pyrit):
             pyrit.pyrit_plan_destroy(p)
 
 
+def test_one_shot_batches_match_the_oracle(pyrit):
+    # pyrit_encode_batch / pyrit_decode_batch: the same stripes as one call each, waited for
+    pool = Pool(MIXED, 8)
+    plans = _plans(pyrit, MIXED)
+    try:
+        full = []
+        for i, (w, k, m, P) in enumerate(MIXED):
+            data = synth_bytes(200 + i, 0, k * w * P).reshape(k, w, P)
+            arr = np.zeros((k + m, w, P), np.uint8)
+            arr[:k] = data
+            pool.put(i, arr)
+            full.append(np.concatenate([data, oracle.encode(w, k, m, oracle.cauchy(w, k, m), data, nthreads=NCPU)]))
+        torch.cuda.synchronize()
+        s = torch.cuda.Stream()
+        pyrit.pyrit_encode_batch([(plans[(w, k, m)], pyrit.PYRIT_OP_ENCODE, 0, P, pool.blocks(i))
+                                  for i, (w, k, m, P) in enumerate(MIXED)], s)
+        for i in range(len(MIXED)):
+            assert np.array_equal(pool.host(i), full[i]), MIXED[i]
+        rng = np.random.default_rng(6)
+        dec = []
+        for i, (w, k, m, P) in enumerate(MIXED):
+            e = int(rng.integers(1, m + 1))
+            pat = sum(1 << int(x) for x in rng.choice(k + m, e, replace=False))
+            arr = full[i].copy()
+            for x in range(k + m):
+                if (pat >> x) & 1:
+                    arr[x] ^= 0x5A
+            pool.put(i, arr)
+            dec.append((plans[(w, k, m)], pyrit.PYRIT_OP_DECODE, pat, P, pool.blocks(i)))
+        torch.cuda.synchronize()
+        pyrit.pyrit_decode_batch(dec, s)
+        for i in range(len(MIXED)):
+            assert np.array_equal(pool.host(i), full[i]), MIXED[i]
+        assert pyrit.pyrit_device_status() == (0, 0)
+    finally:
+        for p in plans.values():
+            pyrit.pyrit_plan_destroy(p)
+
+
 def _all_tiles(pyrit, n):
     """Hints that select exactly each compiled variant of ring size n, plus stage overrides."""
     out = [None, dict(stages=2), dict(stages=7, ctas_per_sm=1)]
