@@ -153,6 +153,7 @@ def test_noalloc_status_reports_a_wait_that_ran_out(pyrit):
             pyrit.pyrit_plan_destroy(p)
 
 
+@pytest.mark.filterwarnings("ignore:The CUDA Graph is empty")  # nothing is captured, by design
 def test_noalloc_refuses_stream_capture(pyrit):
     # The call uploads its descriptors from host arrays the next call rewrites, so a captured graph
     # could not replay it: on a capturing stream it must return PYRIT_E_INVALID_ARG before any
