@@ -1,4 +1,5 @@
-// C ABI entry points of the single-stripe coding path and of the device status word.
+// C ABI entry points of the single-stripe coding path, the one-shot batched calls and the device
+// status word.
 #include <cuda_runtime.h>
 
 #include "pyrit_internal.h"
@@ -92,6 +93,38 @@ int pyrit_decode(pyrit_plan_t plan, void* const* blocks, uint64_t erasures, size
     }
   }
   return run_jobs(plan, jobs, nj, st);
+}
+
+}  // extern "C"
+
+namespace {
+
+// A batch of stripes that all carry `op`, made, run once on `stream`, waited for and freed.
+int one_shot_batch(const pyrit_stripe_t* stripes, int count, int op, pyrit_stream_t stream) {
+  if (count < 0 || (count > 0 && !stripes)) return PYRIT_E_INVALID_ARG;
+  for (int i = 0; i < count; ++i)
+    if (stripes[i].op != op) return PYRIT_E_INVALID_ARG;
+  if (count == 0) return PYRIT_OK;
+  pyrit_batch_t b = nullptr;
+  int rc = pyrit_batch_create(stripes, count, nullptr, &b);
+  if (rc != PYRIT_OK) return rc;
+  rc = pyrit_batch_run(b, stream, 0);
+  // the batch's tables must outlive its launches
+  if (cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess && rc == PYRIT_OK) rc = PYRIT_E_CUDA;
+  pyrit_batch_destroy(b);
+  return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pyrit_encode_batch(const pyrit_stripe_t* stripes, int count, pyrit_stream_t stream) {
+  return one_shot_batch(stripes, count, PYRIT_OP_ENCODE, stream);
+}
+
+int pyrit_decode_batch(const pyrit_stripe_t* stripes, int count, pyrit_stream_t stream) {
+  return one_shot_batch(stripes, count, PYRIT_OP_DECODE, stream);
 }
 
 int pyrit_device_status(int* code_out, int* where_out) {
