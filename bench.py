@@ -1073,9 +1073,11 @@ def served_measure(torch, pyrit, dev, rate, seconds, slots, pool=512):
         lat = np.array([d[4] - d[2] for d in done], dtype=np.float64) / 1e3  # us
         wait = np.array([d[3] - d[2] for d in done], dtype=np.float64) / 1e3
         run = np.array([d[4] - d[3] for d in done], dtype=np.float64) / 1e3
+        per_pass = [float(np.percentile(np.array([d[4] - d[2] for d in r["done"]], dtype=np.float64) / 1e3, 99))
+                    for r in runs]
         return {"p50_us": float(np.percentile(lat, 50)), "p99_us": float(np.percentile(lat, 99)),
                 "p999_us": float(np.percentile(lat, 99.9)), "max_us": float(lat.max()), "requests": len(lat),
-                "passes": len(runs),
+                "passes": len(runs), "p99_per_pass_us": per_pass,
                 "arrival_to_launch_p50_us": float(np.percentile(wait, 50)),
                 "arrival_to_launch_p99_us": float(np.percentile(wait, 99)),
                 "launch_to_done_p50_us": float(np.percentile(run, 50)),
