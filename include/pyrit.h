@@ -436,6 +436,16 @@ PYRIT_API int pyrit_server_create(size_t hbm_budget, int max_batch, int slots, i
  * for a misaligned stripe or one too large for a slot, PYRIT_E_BUSY when the queue is full. */
 PYRIT_API int pyrit_server_submit(pyrit_server_t server, const pyrit_request_t* reqs, int count);
 
+/* Replays a request trace against the server from the calling thread: submits each request (as
+ * pyrit_server_submit) once the server clock reaches its arrival_ns, all requests whose time has
+ * come in one call, spinning in between, and returns when the last has been submitted (it does
+ * not wait for completions). Requests must be in non-decreasing arrival order. A load generator
+ * for measuring served latency without a caller-side submission delay: each request is validated
+ * when it arrives, as a client's would be. Returns PYRIT_OK, PYRIT_E_INVALID_ARG (before any
+ * submission) for NULL arguments or an arrival out of order, or the first failing submission's
+ * code (the requests before it were submitted). */
+PYRIT_API int pyrit_server_replay(pyrit_server_t server, const pyrit_request_t* reqs, int count);
+
 /* Moves up to `cap` completions into out (host array); returns how many. */
 PYRIT_API int pyrit_server_poll(pyrit_server_t server, pyrit_completion_t* out, int cap);
 

@@ -591,6 +591,26 @@ int pyrit_server_submit(pyrit_server_t s, const pyrit_request_t* reqs, int count
   return PYRIT_OK;
 }
 
+int pyrit_server_replay(pyrit_server_t s, const pyrit_request_t* reqs, int count) {
+  if (!s || count < 0 || (count > 0 && !reqs)) return PYRIT_E_INVALID_ARG;
+  for (int i = 1; i < count; ++i)
+    if (reqs[i].arrival_ns < reqs[i - 1].arrival_ns) return PYRIT_E_INVALID_ARG;
+  // Each pass submits every request whose arrival time has come, in one call; the thread spins
+  // between arrivals (it is the load generator: it must not sleep past an arrival).
+  int i = 0;
+  while (i < count) {
+    const int64_t now = s->now();
+    int j = i;
+    while (j < count && reqs[j].arrival_ns <= now) ++j;
+    if (j > i) {
+      const int rc = pyrit_server_submit(s, reqs + i, j - i);
+      if (rc != PYRIT_OK) return rc;
+      i = j;
+    }
+  }
+  return PYRIT_OK;
+}
+
 int pyrit_server_poll(pyrit_server_t s, pyrit_completion_t* out, int cap) {
   if (!s || cap < 0 || (cap > 0 && !out)) return PYRIT_E_INVALID_ARG;
   std::lock_guard<std::mutex> lk(s->mu);

@@ -516,6 +516,7 @@ _SERVER_SIGS = {
     "pyrit_server_create": (_i, [_sz, _i, _i, _i, ctypes.POINTER(_vp)]),
     "pyrit_server_submit": (_i, [_vp, ctypes.POINTER(pyrit_request_t), _i]),
     "pyrit_server_poll": (_i, [_vp, ctypes.POINTER(pyrit_completion_t), _i]),
+    "pyrit_server_replay": (_i, [_vp, ctypes.POINTER(pyrit_request_t), _i]),
     "pyrit_server_drain": (_i, [_vp, _i]),
     "pyrit_server_now_ns": (ctypes.c_int64, [_vp]),
     "pyrit_server_stats": (_i, [_vp, _vp]),
@@ -580,6 +581,15 @@ def pyrit_requests_array(requests):
         arr[i] = pyrit_request_t(pyrit_stripe_t(plan, op, er, P, ctypes.cast(ba, ctypes.POINTER(ctypes.c_void_p))),
                                  tag, arrival)
     return arr, keep
+
+
+def pyrit_server_replay(server, arr, start=0, count=None):
+    """Submits arr[start:start + count] of a prebuilt request array (non-decreasing arrival times),
+    each when the server clock reaches its arrival; returns once all are submitted."""
+    if count is None:
+        count = len(arr) - start
+    ptr = ctypes.cast(ctypes.byref(arr, start * ctypes.sizeof(pyrit_request_t)), ctypes.POINTER(pyrit_request_t))
+    return _check(_lib.pyrit_server_replay(server, ptr, count), "pyrit_server_replay")
 
 
 def pyrit_server_submit_slice(server, arr, start, count):

@@ -230,6 +230,10 @@ def test_invalid_coding_calls_fail_before_device_work():
                                       (plan, pyrit.PYRIT_OP_ENCODE, 0, 64, fake)])
         assert ei.value.status == pyrit.PYRIT_E_INVALID_ARG
         assert pyrit.pyrit_encode_batch([]) == 0 and pyrit.pyrit_decode_batch([]) == 0
+        arr, keep = pyrit.pyrit_requests_array([])
+        with pytest.raises(pyrit.PyritError) as ei:
+            pyrit.pyrit_server_replay(None, arr, 0, 0)  # no server
+        assert ei.value.status == pyrit.PYRIT_E_INVALID_ARG
     finally:
         pyrit.pyrit_plan_destroy(plan)
 

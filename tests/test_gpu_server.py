@@ -178,6 +178,62 @@ def test_served_config5_shape_against_oracle(pyrit):
         pyrit.pyrit_plan_destroy(plan)
 
 
+def test_replay_submits_each_request_at_its_arrival(pyrit):
+    """The native load generator (pyrit_server_replay) hands each request to the server when the
+    server clock reaches its arrival time: no request starts before it arrives, every result equals
+    the oracle's codeword, and a trace out of arrival order is refused before any submission."""
+    w, k, m = 12, 16, 4
+    rng = np.random.default_rng(0x5E4F)
+    count = 48
+    reqs = []
+    for _ in range(count):
+        P = 1 << int(rng.integers(12, 19))
+        op = int(rng.integers(0, 2))
+        er = sum(1 << int(x) for x in rng.choice(k + m, m, replace=False)) if op else 0
+        reqs.append((w, k, m, P, op, er))
+    gaps = rng.exponential(1e9 / 20000, count)
+    offs, total = _layout(reqs)
+    start, want = _codewords(reqs, offs, total, 92)
+    buf = torch.from_numpy(start).cuda()
+    plan = pyrit.pyrit_plan_create(w, w + 1, k, m)
+    try:
+        pyrit.pyrit_plan_specialise(plan, pyrit.PYRIT_OP_ENCODE)
+        pyrit.pyrit_plan_specialise(plan, pyrit.PYRIT_OP_DECODE_ANY)
+        torch.cuda.synchronize()
+        base = buf.data_ptr()
+        srv = pyrit.pyrit_server_create(16 << 30, max_batch=64, slots=16)
+        try:
+            items = [(plan, op, er, P, [base + o + e * w * P for e in range(k + m)], i, 0)
+                     for i, ((w_, k_, m_, P, op, er), o) in enumerate(zip(reqs, offs))]
+            arr, keep = pyrit.pyrit_requests_array(items)
+            # out of order: refused, nothing submitted
+            arr[0].arrival_ns, arr[1].arrival_ns = 10_000_000_000, 5_000_000_000
+            with pytest.raises(pyrit.PyritError) as ei:
+                pyrit.pyrit_server_replay(srv, arr, 0, 2)
+            assert ei.value.status == pyrit.PYRIT_E_INVALID_ARG
+            assert pyrit.pyrit_server_stats(srv)["submitted"] == 0
+            t0 = pyrit.pyrit_server_now_ns(srv) + 2_000_000
+            sched = (t0 + np.cumsum(gaps)).astype(np.int64)
+            for i in range(count):
+                arr[i].arrival_ns = int(sched[i])
+            pyrit.pyrit_server_replay(srv, arr, 0, count)
+            assert pyrit.pyrit_server_now_ns(srv) >= sched[-1]
+            assert pyrit.pyrit_server_drain(srv, 60000) == 0
+            done = pyrit.pyrit_server_poll(srv)
+        finally:
+            pyrit.pyrit_server_destroy(srv)
+        assert sorted(d[0] for d in done) == list(range(count))
+        for tag, status, arrival, start_ns, done_ns in done:
+            assert status == 0 and arrival == sched[tag] and arrival <= start_ns <= done_ns
+        h = buf.cpu().numpy()
+        for i, (w_, k_, m_, P, op, er) in enumerate(reqs):
+            n = (k + m) * w * P
+            assert np.array_equal(h[offs[i]:offs[i] + n], want[offs[i]:offs[i] + n]), (i, reqs[i])
+        assert pyrit.pyrit_device_status() == (0, 0)
+    finally:
+        pyrit.pyrit_plan_destroy(plan)
+
+
 def test_admission_respects_budget(pyrit):
     w, k, m, P = 12, 16, 4, 64 * 1024
     one = (k + m) * w * P
