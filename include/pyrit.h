@@ -425,7 +425,8 @@ typedef struct {
  * batching). Each request completes on its own: the kernel stamps a request done when its last
  * tile is stored, and the scheduler then retires it and releases its admission bytes, while the
  * slot itself is reused once its launches have ended. The scheduler thread spins (yielding) while
- * any work is in flight and sleeps when idle. Decoding matrices come from the plans' caches;
+ * any work is in flight, keeps polling for 0.5 ms once idle (a request arriving then starts without
+ * a thread wake-up), and then sleeps. Decoding matrices come from the plans' caches;
  * launch shapes from the autotuner's table when it has the key. queue_cap bounds the requests
  * waiting for admission. Allocates its slots' device tables, pinned staging and host-mapped
  * completion stamps. */
