@@ -149,13 +149,21 @@ void share_terms(std::vector<XorRow>& rows, int first_id, std::vector<XorTemp>* 
 
 // Writes rows (after share_terms) as statements inside a `for (x ...)` loop: each temporary just
 // before the first row that needs it (recursively), then each row's accumulation.
-void emit_rows(std::string& o, const std::vector<XorRow>& rows, const std::vector<XorTemp>& temps, int W, int N) {
+// Under source pairs (pair), columns kPairCol.. are the second source's packets (d2, dp2) and the
+// temporaries start at kPairTemp.
+constexpr int kPairCol = 64, kPairTemp = 128;
+void emit_rows(std::string& o, const std::vector<XorRow>& rows, const std::vector<XorTemp>& temps, int W, int N,
+               bool pair = false) {
   auto name = [&](int c) {
     char buf[32];
     if (c < W)
       std::snprintf(buf, sizeof(buf), "d[%d][x]", c);
     else if (c < N)
       std::snprintf(buf, sizeof(buf), "dp[%d][x]", c - W);
+    else if (pair && c >= kPairCol && c < kPairCol + W)
+      std::snprintf(buf, sizeof(buf), "d2[%d][x]", c - kPairCol);
+    else if (pair && c >= kPairCol + W && c < kPairCol + N)
+      std::snprintf(buf, sizeof(buf), "dp2[%d][x]", c - kPairCol - W);
     else
       std::snprintf(buf, sizeof(buf), "e%d", c);
     return std::string(buf);
@@ -246,19 +254,22 @@ std::string net_source(const NetSpec& s) {
   put(o, "  template <int N, int WORDS, int MG>\n"
          "  __device__ __forceinline__ void apply(uint32_t (&acc)[MG][N][WORDS],\n"
          "                                        const uint32_t (&d)[%ld][WORDS], int j, int g, int) {\n", W);
-  if (parity) {
-    // phi_P: parity packet j (ring packet W + j) is the XOR of the source's packets j, j + S, ...
-    // (one packet, the XOR of all W, for an all-one polynomial; S = 3 interleaved words for the ESP)
-    put(o, "    uint32_t dp[%ld][WORDS];\n#pragma unroll\n    for (int x = 0; x < WORDS; ++x) {\n", S);
+  // phi_P: parity packet j (ring packet W + j) is the XOR of the source's packets j, j + S, ...
+  // (one packet, the XOR of all W, for an all-one polynomial; S = 3 interleaved words for the ESP)
+  auto emit_dp = [&](const char* dp, const char* d) {
+    std::string t = "    uint32_t " + std::string(dp) + "[%ld][WORDS];\n#pragma unroll\n    for (int x = 0; x < WORDS; ++x) {\n";
+    put(o, t.c_str(), S);
     for (int j = 0; j < S; ++j) {
-      put(o, "      dp[%ld][x] = d[%ld][x];\n", j, j);
+      put(o, ("      " + std::string(dp) + "[%ld][x] = " + d + "[%ld][x];\n").c_str(), j, j);
       int q = j + S;
       for (; q + S < W; q += 2 * S)
-        put(o, "      dp[%ld][x] = xor3(dp[%ld][x], d[%ld][x], d[%ld][x]);\n", j, j, q, q + S);
-      if (q < W) put(o, "      dp[%ld][x] ^= d[%ld][x];\n", j, q);
+        put(o, ("      " + std::string(dp) + "[%ld][x] = xor3(" + dp + "[%ld][x], " + d + "[%ld][x], " + d +
+                "[%ld][x]);\n").c_str(), j, j, q, q + S);
+      if (q < W) put(o, ("      " + std::string(dp) + "[%ld][x] ^= " + d + "[%ld][x];\n").c_str(), j, q);
     }
     o += "    }\n";
-  }
+  };
+  if (parity) emit_dp("dp", "d");
   // Syndrome networks guard each parity row with one warp-uniform test of the tile's needed rows
   // (a switch on the needed-row set with one block per set measured no faster and compiled
   // several times longer).
@@ -267,33 +278,40 @@ std::string net_source(const NetSpec& s) {
     put(o, "    switch ((tbl * %ld + g) * %ld + j) {\n", groups, s.nin);
   else
     put(o, "    switch (g * %ld + j) {\n", s.nin);
+  // The accumulators source j updates in each output slot of group g of table tb, its packet
+  // columns offset by `base` (kPairCol for the second source of a pair).
+  auto source_rows = [&](int tb, int g, int j, int base) {
+    std::vector<std::vector<XorRow>> slot(s.mg);
+    for (int ii = 0; ii < s.mg; ++ii) {
+      const int out = g * s.mg + ii;
+      if (out >= s.tnout[tb]) break;
+      const uint32_t r = s.mask[tb][j][out];
+      for (int t = 0; t < N; ++t) {
+        // under the parity transform a direct network never builds the top accumulators
+        // (phi_P^{-1} drops them)
+        if (parity && !syndrome && t >= W) continue;
+        // accumulator t receives packet t - s for every set bit s; packets W..N-1 are the zero
+        // packets of phi_E (dropped) or the parity packets of phi_P
+        XorRow row{ii, t, {}};
+        for (int sh = 0; sh < N; ++sh) {
+          if (!((r >> sh) & 1u)) continue;
+          const int q = (t - sh + N) % N;
+          if (q < W || parity) row.cols.push_back(base + q);
+        }
+        if (row.cols.empty()) continue;
+        std::sort(row.cols.begin(), row.cols.end());
+        slot[ii].push_back(std::move(row));
+      }
+    }
+    return slot;
+  };
   for (int cs = 0; cs < s.ntables * groups; ++cs) {
     const int tb = cs / groups, g = cs % groups;
     for (int j = 0; j < s.nin; ++j) {
+      // under source pairs this step codes only an odd job's last source
+      if (s.pair && !(s.nin % 2 == 1 && j == s.nin - 1)) continue;
       put(o, "      case %ld: {\n", ((long)tb * groups + g) * s.nin + j);
-      // the accumulators this source updates in each output slot of the group
-      std::vector<std::vector<XorRow>> slot(s.mg);
-      for (int ii = 0; ii < s.mg; ++ii) {
-        const int out = g * s.mg + ii;
-        if (out >= s.tnout[tb]) break;
-        const uint32_t r = s.mask[tb][j][out];
-        for (int t = 0; t < N; ++t) {
-          // under the parity transform a direct network never builds the top accumulators
-          // (phi_P^{-1} drops them)
-          if (parity && !syndrome && t >= W) continue;
-          // accumulator t receives packet t - s for every set bit s; packets W..N-1 are the zero
-          // packets of phi_E (dropped) or the parity packets of phi_P
-          XorRow row{ii, t, {}};
-          for (int sh = 0; sh < N; ++sh) {
-            if (!((r >> sh) & 1u)) continue;
-            const int q = (t - sh + N) % N;
-            if (q < W || parity) row.cols.push_back(q);
-          }
-          if (row.cols.empty()) continue;
-          std::sort(row.cols.begin(), row.cols.end());
-          slot[ii].push_back(std::move(row));
-        }
-      }
+      std::vector<std::vector<XorRow>> slot = source_rows(tb, g, j, 0);
       if (!guard) {
         // one body for every output of the group: terms shared across outputs are formed once
         std::vector<XorRow> rows;
@@ -335,12 +353,57 @@ std::string net_source(const NetSpec& s) {
       o += "      } break;\n";
     }
   }
-  o += "      default: break;\n    }\n  }\n};\n}  // namespace pyrit\n\n";
+  o += "      default: break;\n    }\n  }\n";
+  if (s.pair) {
+    // Two sources per step (sources j and j + 1, j even): every accumulator row holds the terms of
+    // both, so one three-input XOR can take one term of each, and shared terms may mix them.
+    put(o, "  template <int N, int WORDS, int MG>\n"
+           "  __device__ __forceinline__ void apply2(uint32_t (&acc)[MG][N][WORDS], const uint32_t (&d)[%ld][WORDS],\n"
+           "                                         const uint32_t (&d2)[%ld][WORDS], int j, int g, int) {\n", W, W);
+    if (parity) {
+      emit_dp("dp", "d");
+      emit_dp("dp2", "d2");
+    }
+    const int npairs = s.nin / 2;
+    if (multi)
+      put(o, "    switch ((tbl * %ld + g) * %ld + j / 2) {\n", groups, npairs);
+    else
+      put(o, "    switch (g * %ld + j / 2) {\n", npairs);
+    for (int cs = 0; cs < s.ntables * groups; ++cs) {
+      const int tb = cs / groups, g = cs % groups;
+      for (int pi = 0; pi < npairs; ++pi) {
+        put(o, "      case %ld: {\n", ((long)tb * groups + g) * npairs + pi);
+        std::vector<std::vector<XorRow>> a = source_rows(tb, g, 2 * pi, 0);
+        std::vector<std::vector<XorRow>> b = source_rows(tb, g, 2 * pi + 1, kPairCol);
+        std::map<std::pair<int, int>, std::vector<int>> merged;  // (slot, accumulator) -> columns
+        for (auto* side : {&a, &b})
+          for (auto& v : *side)
+            for (XorRow& r : v) {
+              std::vector<int>& c = merged[{r.out, r.t}];
+              c.insert(c.end(), r.cols.begin(), r.cols.end());
+            }
+        std::vector<XorRow> rows;
+        for (auto& kv : merged) {
+          XorRow r{kv.first.first, kv.first.second, kv.second};
+          std::sort(r.cols.begin(), r.cols.end());
+          rows.push_back(std::move(r));
+        }
+        std::vector<XorTemp> temps;
+        share_terms(rows, kPairTemp, &temps);
+        o += "#pragma unroll\n        for (int x = 0; x < WORDS; ++x) {\n";
+        emit_rows(o, rows, temps, W, N, true);
+        o += "        }\n      } break;\n";
+      }
+    }
+    o += "      default: break;\n    }\n  }\n";
+  }
+  o += "};\n}  // namespace pyrit\n\n";
   put(o, "extern \"C\" __global__ void __launch_bounds__(%ld, %ld)\n", (s.nc + 1) * 32, s.minb);
   o += kKernelName;
   o += "(const __grid_constant__ pyrit::CodeArgs a) {\n";
   put(o, "  pyrit::ring_staged_body<%ld, %ld, %ld, %ld, pyrit::NetMac, %ld, ", N, s.words, s.mg, s.nc, W);
-  o += s.track ? "true>(a);\n}\n" : "false>(a);\n}\n";
+  o += s.track ? "true, " : "false, ";
+  o += s.pair ? "true>(a);\n}\n" : "false>(a);\n}\n";
   return o;
 }
 
@@ -548,7 +611,10 @@ int shapes_for(int n, int nout, bool syndrome, NetSpec* out, int cap) {
     // accumulators (+ an output under construction for syndrome decoding), one staged source and
     // addressing and loop state against the register budget; the estimate runs about 20 above
     // what the compiler allocates without spilling (measured), hence the allowance
-    if ((mg + (syndrome ? 1 : 0)) * n * c.words + (n - 1) * c.words + 16 > reg_cap(c.nc, c.minb) + 20) continue;
+    // (direct networks of more than four outputs take two staged sources per step: one more)
+    const int staged = (syndrome || nout <= 4) ? 1 : 2;
+    if ((mg + (syndrome ? 1 : 0)) * n * c.words + staged * (n - 1) * c.words + 16 > reg_cap(c.nc, c.minb) + 20)
+      continue;
     NetSpec s;
     std::memset(&s, 0, sizeof(s));
     s.n = n;
@@ -592,6 +658,13 @@ NetSpec net_spec_tables(int n, const JobDesc* const* tables, int ntables, int wo
       for (int o = 0; o < job.nout && o < kMaxOut; ++o) s.mask[t][j][o] = job.mask[j][o];
   }
   if (ntables > kMaxJobs) s.ntables = 0;  // rejected by spec_valid
+  // Jobs of more than four outputs (the paper's wide GF(2^6) codes) are bound by their XOR work:
+  // two sources per step let one three-input XOR take a term of each (measured on GB300: the
+  // (60,40) embedding 0.252-0.265 -> 0.265-0.290 of HBM, the (60,20) parity transform 0.293-0.342
+  // -> 0.299-0.371, bit-exact). Jobs of up to four outputs keep one source per step: their
+  // encodes run at HBM speed already, and the second source's registers cost the GF(2^12) k=16
+  // m=4 encode its 8-byte shape (0.98 -> 0.84).
+  s.pair = s.nout > 4 ? 1 : 0;
   return s;
 }
 
@@ -643,6 +716,7 @@ static bool spec_valid(const NetSpec& s) {
   const bool nc_ok = s.nc >= 1 && s.nc <= 31;
   if (s.mode < 0 || s.mode > 3 || (s.track != 0 && s.track != 1) || (s.allrows != 0 && s.allrows != 1)) return false;
   if (s.allrows && !(s.mode == 1 || s.mode == 3)) return false;
+  if ((s.pair != 0 && s.pair != 1) || (s.pair && !(s.mode == 0 || s.mode == 2))) return false;
   if ((s.mode == 1 || s.mode == 3) && !(s.mg == s.nout && s.nout <= kSyndromeBaseRow && s.ntables == 1)) return false;
   if (s.ntables < 1 || s.ntables > kMaxJobs) return false;
   // a native field of its ring, or (direct embedding networks only) a factor g of x^n + 1 of degree w

@@ -177,6 +177,8 @@ struct NetSpec {
                              // completion (launched by the server with CodeArgs::done_cnt / done_ns)
   int32_t allrows;           // syndrome modes: 1 adds a first-phase body for tiles that need every
                              // parity row (terms shared across rows), 0 keeps only the guarded rows
+  int32_t pair;              // direct modes: 1 takes two staged sources per step, so that one
+                             // three-input XOR can combine terms of both
   uint16_t mask[kMaxJobs][kMaxIn][kMaxOut];
 };
 // The network spec of one job under a shape (zero fields: the default shape for (n, nout)) and a

@@ -280,8 +280,10 @@ struct ParityStore {
 // passes CodeArgs::done_cnt (the served path). It is a compile-time choice because the code, even
 // never executed, costs the other launches: on GB300 the GF(2^12) k=16 m=4 encode ran 3-6% slower
 // with it compiled in.
-template <int N, int WORDS, int MG, int NC, class Mac, int W = RingDim<N>::W, bool TRACK = false>
+template <int N, int WORDS, int MG, int NC, class Mac, int W = RingDim<N>::W, bool TRACK = false,
+          bool PAIR = false>
 __device__ __forceinline__ void ring_staged_body(const CodeArgs& a) {
+  static_assert(!(PAIR && Mac::kSparse), "source pairs need every source present");
   using V = typename Vec<WORDS>::T;
   extern __shared__ __align__(128) uint8_t smem[];
   const uint32_t S = a.stages, TW = a.tw;
@@ -397,6 +399,34 @@ __device__ __forceinline__ void ring_staged_body(const CodeArgs& a) {
       if (++stage == S) {
         stage = 0;
         phase ^= 1u;
+      }
+      if constexpr (PAIR) {
+        // the next source too (the producer streams every source of the job in order)
+        if (j + 1 < nin) {
+          if (!__all_sync(0xFFFFFFFFu, mbar_wait(&full[stage], phase, a.err, 2))) return;
+          uint32_t d2[W][WORDS];
+          const uint8_t* sb2 = buf + (size_t)stage * W * TW + off;
+#pragma unroll
+          for (int q = 0; q < W; ++q) {
+            V v;
+            if (valid) {
+              v = *reinterpret_cast<const V*>(sb2 + (size_t)q * TW);
+            } else {
+              v = V{};
+            }
+#pragma unroll
+            for (int x = 0; x < WORDS; ++x) d2[q][x] = vword<WORDS>(v, x);
+          }
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&empty[stage]);
+          if (++stage == S) {
+            stage = 0;
+            phase ^= 1u;
+          }
+          mac.template apply2<N, WORDS, MG>(acc, d, d2, j, g, lane);
+          ++j;
+          continue;
+        }
       }
       mac.template apply<N, WORDS, MG>(acc, d, j, g, lane);
     }

@@ -19,17 +19,34 @@ import oracle
 from paper_1709_00178_gb300 import pyrit
 
 
+SECOND = 1000  # column offset of the second source of a pair step (d2, dp2)
+
+
 def _terms(text, temps):
     """Source columns of an XOR expression: d[q][x] is packet q of the source; dp[j][x] (the parity
     transform's padding packet j, the parity of the source's interleaved word j) is recorded as
-    q = -1 - j; a temporary e<id> stands for the columns it was formed from."""
+    q = -1 - j; d2 / dp2 (the second source of a pair step) as the same plus SECOND (minus SECOND
+    for dp2); a temporary e<id> stands for the columns it was formed from."""
     qs = []
-    for q, p, e in re.findall(r"d(?:\[(\d+)\]|p\[(\d+)\])\[x\]|\be(\d+)\b", text):
+    for name, idx, e in re.findall(r"\b(d|dp|d2|dp2)\[(\d+)\]\[x\]|\be(\d+)\b", text):
         if e:
             qs += temps[int(e)]
+        elif name == "d":
+            qs.append(int(idx))
+        elif name == "dp":
+            qs.append(-1 - int(idx))
+        elif name == "d2":
+            qs.append(SECOND + int(idx))
         else:
-            qs.append(int(q) if q else -1 - int(p))
+            qs.append(-1 - int(idx) - SECOND)
     return qs
+
+
+def _split_pair(qs):
+    """Columns of a pair step's expression, split into (first source's, second source's)."""
+    a = [q for q in qs if -SECOND < q < SECOND]
+    b = [q - SECOND if q >= SECOND else q + SECOND for q in qs if q >= SECOND or q <= -SECOND]
+    return a, b
 
 
 def _parse(src):
@@ -39,12 +56,21 @@ def _parse(src):
     nin = int(re.search(r"switch \(g \* (\d+) \+ j\)", src).group(1))
     n, words, mg, nc = map(int, re.search(r"ring_staged_body<(\d+), (\d+), (\d+), (\d+),", src).groups())
     cases, cases_all, cur, temps, guard, guards, in_all, full = {}, {}, None, {}, None, [], False, None
+    # pair steps (sources 2p and 2p + 1 in one case of apply2): entries kept per case, split below
+    npairs, in_pair, pair_cases = None, False, {}
     for line in src.splitlines():
+        sw = re.match(r"\s*switch \(g \* (\d+) \+ j / 2\) \{", line)
+        if sw:
+            npairs, in_pair = int(sw.group(1)), True
+            continue
         c = re.match(r"\s*case (\d+): \{", line)
         if c:
             cur = int(c.group(1))
-            cases[cur] = []
-            cases_all[cur] = []
+            if in_pair:
+                pair_cases[cur] = []
+            else:
+                cases.setdefault(cur, [])
+                cases_all[cur] = []
             temps, guard, in_all = {}, None, False
             continue
         # syndrome networks: the body for a tile that needs every parity row, then the else branch
@@ -75,6 +101,9 @@ def _parse(src):
         if a:
             assert cur is not None
             entry = (int(a.group(1)), int(a.group(2)), _terms(a.groups()[-1], temps))
+            if in_pair:
+                pair_cases[cur].append(entry)
+                continue
             if in_all:
                 cases_all[cur].append(entry)
             else:
@@ -82,7 +111,15 @@ def _parse(src):
                 guards.append((int(a.group(1)), guard))
         if "} break;" in line:
             cur = None
-    return dict(nin=nin, n=n, words=words, mg=mg, nc=nc, cases=cases, guards=guards, cases_all=cases_all, full=full)
+    for pc, entries in pair_cases.items():
+        g, p = divmod(pc, npairs)
+        for (ii, t, qs) in entries:
+            a, b = _split_pair(qs)
+            cases.setdefault(g * nin + 2 * p, []).append((ii, t, a))
+            cases.setdefault(g * nin + 2 * p + 1, []).append((ii, t, b))
+            guards += [(ii, None), (ii, None)]
+    return dict(nin=nin, n=n, words=words, mg=mg, nc=nc, cases=cases, guards=guards, cases_all=cases_all, full=full,
+                npairs=npairs)
 
 
 def _w_of(n):
@@ -603,3 +640,28 @@ def test_committed_pairing_automata_match_their_generator():
     spec.loader.exec_module(gen)
     with open(os.path.join(here, "ring_network.inc")) as f:
         assert f.read() == gen.source()
+
+
+def test_wide_networks_take_two_sources_per_step():
+    """Jobs of more than four outputs code two staged sources per step (one three-input XOR can take
+    a term of each); jobs of up to four keep one. The (60,40) GF(2^6) code's first job (8 outputs)
+    then needs 1972 XOR statements against 2712 one source at a time, and still computes the field
+    products of its table."""
+    w, k, m = 6, 40, 20
+    plan = pyrit.pyrit_plan_create(w, oracle.ring_size(w), k, m)
+    try:
+        src = pyrit.pyrit_plan_network_source(plan, pyrit.PYRIT_OP_ENCODE)
+    finally:
+        pyrit.pyrit_plan_destroy(plan)
+    assert "apply2" in src and _parse(src)["npairs"] == k // 2
+    assert _xor_statements(src) <= 2000
+    C, masks = _oracle_parity_masks(w, k, m)
+    _check_network(src, masks[:8], oracle.ring_size(w))
+    # an odd source count: the last source goes alone
+    C7, masks7 = _oracle_parity_masks(10, 7, 6)
+    src7 = pyrit.pyrit_jit_source(11, masks7)
+    assert _parse(src7)["npairs"] == 3
+    _check_network(src7, masks7, 11)
+    # four outputs: one source per step
+    C4, masks4 = _oracle_parity_masks(10, 10, 4)
+    assert "apply2" not in pyrit.pyrit_jit_source(11, masks4)
