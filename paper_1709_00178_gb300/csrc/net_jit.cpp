@@ -611,10 +611,10 @@ int shapes_for(int n, int nout, bool syndrome, NetSpec* out, int cap) {
     // accumulators (+ an output under construction for syndrome decoding), one staged source and
     // addressing and loop state against the register budget; the estimate runs about 20 above
     // what the compiler allocates without spilling (measured), hence the allowance
-    // (direct networks of more than four outputs take two staged sources per step: one more)
-    const int staged = (syndrome || nout <= 4) ? 1 : 2;
-    if ((mg + (syndrome ? 1 : 0)) * n * c.words + staged * (n - 1) * c.words + 16 > reg_cap(c.nc, c.minb) + 20)
-      continue;
+    // (direct networks of more than four outputs hold a second staged source; the estimate leaves
+    // it out, since under the parity transform their top accumulators are never built, and the
+    // tuner times every candidate)
+    if ((mg + (syndrome ? 1 : 0)) * n * c.words + (n - 1) * c.words + 16 > reg_cap(c.nc, c.minb) + 20) continue;
     NetSpec s;
     std::memset(&s, 0, sizeof(s));
     s.n = n;
