@@ -32,6 +32,9 @@
 //   void apply(uint32_t (&acc)[MG][N][WORDS], const uint32_t (&d)[RingDim<N>::W][WORDS], int j,
 //              int g, int lane);                      // acc_i += r_ij * d for the group's outputs
 //   template <int N, int WORDS, int MG>
+//   void apply2(acc, d, d2, j, g, lane);                // sources j and j + 1 together (only for
+//                                                      // a body instantiated with PAIR)
+//   template <int N, int WORDS, int MG>
 //   void store(uint32_t (&acc)[MG][N][WORDS], const JobDesc* J, int g, uint32_t col0,
 //              uint32_t off, bool valid);              // phi_E^{-1} and the stores of the tile;
 //                                                      // called by every lane (warp-collective
@@ -276,6 +279,8 @@ struct ParityStore {
 
 // W: the field's degree, the packets of a block (the native field of R_{2,N} by default; a
 // generated network for another factor of x^N + 1 passes its own, with its own reduction).
+// PAIR: consumers take two staged sources per step (Mac::apply2), for generated networks whose
+// every source is present (direct networks of wide jobs).
 // TRACK: the kernel counts each job's finished tiles and stamps its completion when the launch
 // passes CodeArgs::done_cnt (the served path). It is a compile-time choice because the code, even
 // never executed, costs the other launches: on GB300 the GF(2^12) k=16 m=4 encode ran 3-6% slower
@@ -374,14 +379,11 @@ __device__ __forceinline__ void ring_staged_body(const CodeArgs& a) {
 #pragma unroll
         for (int x = 0; x < WORDS; ++x) acc[i][r][x] = 0u;
 
-    for (int j = 0; j < nin; ++j) {
-      if constexpr (Mac::kSparse) {
-        if (J->in[j] == nullptr) continue;  // the producer staged nothing for it either
-      }
-      // Every lane observes the phase (so the staged bytes are visible to it); the give-up
-      // decision is made warp-uniform before anyone leaves.
-      if (!__all_sync(0xFFFFFFFFu, mbar_wait(&full[stage], phase, a.err, 2))) return;
-      uint32_t d[W][WORDS];
+    // Takes the next stage: every lane observes its phase (so the staged bytes are visible to it;
+    // the give-up decision is made warp-uniform before anyone leaves), reads its words of the W
+    // packets into registers and releases the stage. False when the wait gave up.
+    auto take_stage = [&](uint32_t (&dst)[W][WORDS]) -> bool {
+      if (!__all_sync(0xFFFFFFFFu, mbar_wait(&full[stage], phase, a.err, 2))) return false;
       const uint8_t* sb = buf + (size_t)stage * W * TW + off;
 #pragma unroll
       for (int q = 0; q < W; ++q) {
@@ -392,7 +394,7 @@ __device__ __forceinline__ void ring_staged_body(const CodeArgs& a) {
           v = V{};
         }
 #pragma unroll
-        for (int x = 0; x < WORDS; ++x) d[q][x] = vword<WORDS>(v, x);
+        for (int x = 0; x < WORDS; ++x) dst[q][x] = vword<WORDS>(v, x);
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[stage]);
@@ -400,29 +402,20 @@ __device__ __forceinline__ void ring_staged_body(const CodeArgs& a) {
         stage = 0;
         phase ^= 1u;
       }
+      return true;
+    };
+
+    for (int j = 0; j < nin; ++j) {
+      if constexpr (Mac::kSparse) {
+        if (J->in[j] == nullptr) continue;  // the producer staged nothing for it either
+      }
+      uint32_t d[W][WORDS];
+      if (!take_stage(d)) return;
       if constexpr (PAIR) {
         // the next source too (the producer streams every source of the job in order)
         if (j + 1 < nin) {
-          if (!__all_sync(0xFFFFFFFFu, mbar_wait(&full[stage], phase, a.err, 2))) return;
           uint32_t d2[W][WORDS];
-          const uint8_t* sb2 = buf + (size_t)stage * W * TW + off;
-#pragma unroll
-          for (int q = 0; q < W; ++q) {
-            V v;
-            if (valid) {
-              v = *reinterpret_cast<const V*>(sb2 + (size_t)q * TW);
-            } else {
-              v = V{};
-            }
-#pragma unroll
-            for (int x = 0; x < WORDS; ++x) d2[q][x] = vword<WORDS>(v, x);
-          }
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&empty[stage]);
-          if (++stage == S) {
-            stage = 0;
-            phase ^= 1u;
-          }
+          if (!take_stage(d2)) return;
           mac.template apply2<N, WORDS, MG>(acc, d, d2, j, g, lane);
           ++j;
           continue;
